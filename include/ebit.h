@@ -1,0 +1,190 @@
+/*
+ * ebit.h -- C ABI of the GB300 EBIT kinematics library (libebit.so).
+ *
+ * The library advances an interface represented by the 3D Edge-Based Interface
+ * Tracking method (arxiv 2509.26361) on a uniform periodic N^3 grid:
+ *   - one marker per grid edge, stored as an FP64 offset along the edge;
+ *   - a colour-vertex field at the cell corners and face centres that encodes
+ *     the marker connectivity (Sec. 2.2, Fig. 7b);
+ *   - split advection: each sweep moves the markers along one axis and
+ *     rebuilds the unaligned markers by circle fits on the two face families
+ *     that contain that axis (Sec. 2.1 Eqs. 1-2, Fig. 1, Fig. 2; Sec. 2.3 Fig. 6);
+ *   - Front2VOF volume fractions (Sec. 2.6, Eq. 7) and height-function
+ *     curvature from them (Sec. 2.6).
+ *
+ * Conventions shared by every call.
+ *   Grid: nx, ny, nz cells, periodic on every axis, each >= 8.  Node (i,j,k) is
+ *     the lowest corner of cell (i,j,k); linear index idx = (k*ny + j)*nx + i.
+ *     The a-edge of node idx joins it to the next node along axis a (a = 0,1,2
+ *     for x,y,z).  The a-face of node idx is the face normal to a whose lowest
+ *     corner is node idx.  A velocity component u_a lives at the centres of the
+ *     a-faces (MAC layout).
+ *   State (owned by the context, on the device): one colour byte per node --
+ *     bit 0 the node colour (1 = reference phase), bit 1+a the colour of the
+ *     a-face (stored for saddle faces, i.e. faces with a marker on all four
+ *     edges; any other face stores its lowest corner's colour) -- and three
+ *     FP64 arrays s[a][idx], the marker offset in [0, 1) of the a-edge of node
+ *     idx, in units of that edge.  An edge carries a marker iff the colours of
+ *     its two end nodes differ; the offset of an edge without a marker is
+ *     unspecified inside the context and reads back as 0.
+ *   Pointers: unless stated otherwise every array argument is a DEVICE pointer
+ *     (cudaMalloc or torch) of the documented size, borrowed for the duration
+ *     of the call and used in stream order on the context's stream.  The
+ *     caller keeps ownership.  All arrays are dense, C-contiguous, idx-ordered;
+ *     arrays of three families are family-major ([a][idx]).
+ *   Errors: every call returns an int status; 0 = EBIT_OK, negative = error,
+ *     positive = warning.  No exception, abort or exit crosses the ABI.  A
+ *     failed call leaves a message readable with ebit_last_error().  Errors
+ *     found on the device (CFL >= 1 at a marker, a device wait that gave up)
+ *     are raised by the next call that synchronises (ebit_sync,
+ *     ebit_counters, ebit_get_state).
+ */
+#ifndef EBIT_H
+#define EBIT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum {
+    EBIT_OK = 0,
+    EBIT_EINVAL = -1,     /* bad argument: dir, sizes, null pointer, non-finite dt */
+    EBIT_ENONFINITE = -2, /* non-finite data where finite data is required */
+    EBIT_ECUDA = -3,      /* a CUDA runtime call failed */
+    EBIT_ETIMEOUT = -4,   /* a bounded device wait gave up */
+    EBIT_ENOMEM = -5,     /* device allocation failed */
+    EBIT_ECFL = -6,       /* a marker moved a full cell or more in one sweep */
+    EBIT_WINCONSISTENT = 1 /* consistency counters are non-zero (warning) */
+};
+
+/* flags for ebit_front2vof / ebit_curvature */
+enum {
+    EBIT_INCREMENTAL = 0, /* recompute only the cells the sweeps may have changed */
+    EBIT_FULL = 1         /* recompute every cell */
+};
+
+/* curvature modes */
+enum {
+    EBIT_CURV_HF = 0,     /* height functions only */
+    EBIT_CURV_MLP = 1,    /* learned curvature only (needs ebit_mlp_load) */
+    EBIT_CURV_MLP_HF = 2  /* learned curvature, height functions where it falls back */
+};
+
+/* height-function status codes written by ebit_curvature */
+enum {
+    EBIT_ST_NONE = 0,     /* not an interface cell (C is 0 or 1); kappa*h = 0 */
+    EBIT_ST_HF_X = 1,     /* heights along x */
+    EBIT_ST_HF_Y = 2,     /* heights along y */
+    EBIT_ST_HF_Z = 3,     /* heights along z */
+    EBIT_ST_NO_HF = 4,    /* no consistent 3x3 stencil of 9-cell columns; kappa*h = 0 */
+    EBIT_ST_MLP = 5       /* learned curvature */
+};
+
+typedef struct ebit_ctx ebit_ctx;
+
+typedef struct {
+    int nx, ny, nz;    /* cells per axis, periodic, each >= 8 */
+    double h;          /* cell size (> 0); dt/h is the sweep's CFL factor */
+    void *cuda_stream; /* cudaStream_t used for every launch; NULL = legacy default stream */
+    int flags;         /* EBIT_DESC_DENSE: process every tile on every call (no band) */
+} ebit_desc;
+
+enum { EBIT_DESC_DENSE = 1 };
+
+typedef struct {
+    int64_t markers;      /* markers present after the last sweep, summed over sweeps */
+    int64_t annihilate;   /* edges where an even number (>= 2) of markers met (Fig. 5) */
+    int64_t multi;        /* edges where three markers met; the median was kept */
+    int64_t inconsistent; /* colour/crossing parity disagreements (never expected) */
+    int64_t cfl;          /* marker displacements of a full cell or more (error) */
+} ebit_counters_t;
+
+/* Create a context for one grid: allocates the double-buffered state and the
+ * tile tables on the current CUDA device.  *out receives the handle.
+ * Errors: EBIT_EINVAL (null, sizes < 8, h <= 0), EBIT_ENOMEM, EBIT_ECUDA. */
+int ebit_create(const ebit_desc *desc, ebit_ctx **out);
+
+/* Release every device allocation of the context (synchronises its stream).
+ * Accepts NULL. */
+void ebit_destroy(ebit_ctx *ctx);
+
+/* Marker initialisation from a level set (Sec. 3.1: colour = (phi >= 0); a
+ * marker at the linear-interpolation root of phi on every edge whose end
+ * colours differ).
+ *   phi_nodes  [N]   phi at the nodes (device).
+ *   phi_faces  [3N]  phi at the face centres, family-major; decides the colour
+ *                    of saddle faces.  May be NULL: the mean of the four corner
+ *                    values is used instead.
+ *   s_exact    [3N]  optional offsets that replace the linear root on
+ *                    sign-change edges (NaN entries keep the linear root).
+ *                    May be NULL.
+ * Errors: EBIT_EINVAL (null ctx or phi_nodes), EBIT_ECUDA. */
+int ebit_init(ebit_ctx *ctx, const double *phi_nodes, const double *phi_faces, const double *s_exact);
+
+/* Replace the state.  cb [N] colour bytes, s [3N] offsets (offsets of edges
+ * without a marker are ignored).  Host or device pointers (copied with
+ * cudaMemcpyDefault).  Errors: EBIT_EINVAL, EBIT_ECUDA. */
+int ebit_set_state(ebit_ctx *ctx, const uint8_t *cb, const double *s);
+
+/* Read the state: cb [N] and s [3N] (0 on edges without a marker).  Host or
+ * device pointers.  Synchronises the stream and raises pending device errors. */
+int ebit_get_state(ebit_ctx *ctx, uint8_t *cb, double *s);
+
+/* One split advection sweep along axis dir (0,1,2) (Sec. 2.1 Eq. 2, Fig. 1;
+ * Sec. 2.3 Fig. 6): every marker moves by u_dir * dt along dir (explicit Euler
+ * with trilinearly interpolated velocity); aligned markers (on dir-edges)
+ * land on the edge that holds them, node colours flip where markers cross
+ * them (Fig. 4), edges whose end colours became equal lose their markers
+ * (topology change, Fig. 5), and the markers of the two unaligned families are
+ * rebuilt from the advected polylines of the two face families containing dir
+ * by the two-circle fit with the radius-ratio rule (Fig. 2).
+ *   u_face [N]  u_dir at the dir-faces (device).  A field of the form
+ *               g(t) * u0 may be passed as u0 with dt * g(t).
+ *   dt          signed time step (finite); |u| dt / h must stay below 1.
+ * Errors: EBIT_EINVAL (dir, null, non-finite dt), EBIT_ECUDA; EBIT_ECFL is
+ * raised later if a marker moved a full cell. */
+int ebit_advect_sweep(ebit_ctx *ctx, int dir, const double *u_face, double dt);
+
+/* Front2VOF volume fractions (Sec. 2.6, Eq. 7): per cell, the face segments
+ * given by the colours are chained into closed loops, each loop is fanned
+ * into triangles around the centroid of its markers, and the enclosed volume
+ * of the reference phase follows from Gauss's theorem.  C [N] (device).
+ * flags: EBIT_INCREMENTAL writes only cells that may have changed since the
+ * last call on this context with the same C pointer (anything else is taken
+ * as a full request); EBIT_FULL writes every cell. */
+int ebit_front2vof(ebit_ctx *ctx, double *C, int flags);
+
+/* Curvature kappa*h of every interface cell (0 < C < 1) from the volume
+ * fractions C [N]: height functions on a 3x3 stencil of 9-cell columns along
+ * the dominant normal axis, other axes as fallback (Sec. 2.6, standard
+ * height-function method); mode selects HF, learned, or learned with HF
+ * fallback.  kappa_h [N] FP64 and status [N] (EBIT_ST_*) are written (device).
+ * flags as for ebit_front2vof (incremental only when C is this context's last
+ * Front2VOF output and kappa_h/status are the previous call's buffers). */
+int ebit_curvature(ebit_ctx *ctx, const double *C, double *kappa_h, uint8_t *status, int mode,
+                   int flags);
+
+/* Copy the event counters accumulated since the last reset (synchronises). */
+int ebit_counters(ebit_ctx *ctx, ebit_counters_t *out);
+
+/* Zero the event counters (stream-ordered). */
+int ebit_reset_counters(ebit_ctx *ctx);
+
+/* Wait for the context's stream; returns pending device errors (EBIT_ECFL,
+ * EBIT_ETIMEOUT) or EBIT_OK. */
+int ebit_sync(ebit_ctx *ctx);
+
+/* Number of tiles (8x8x8 cells) the last sweep processed; -1 if unknown. */
+int ebit_band_tiles(ebit_ctx *ctx);
+
+/* Message of the last failed call on this context (never NULL). */
+const char *ebit_last_error(const ebit_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* EBIT_H */

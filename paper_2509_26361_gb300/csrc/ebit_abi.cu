@@ -1,0 +1,377 @@
+// ebit_abi.cu -- the C ABI of libebit.so (declared in include/ebit.h).
+//
+// The context owns a double-buffered EBIT state (colour bytes + three FP64
+// offset arrays) and per-tile tables that keep every call on the active band:
+// a sweep processes the tiles whose 3x3x3 tile neighbourhood held a marker
+// before or after the previous sweep, Front2VOF the tiles swept since its last
+// call, curvature the tiles around cells whose volume fraction was rewritten.
+// A tile outside the band provably holds no marker and is not changed by the
+// call, and both state buffers agree on it, so band processing gives the same
+// state as processing every tile (tests compare both against the oracle).
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+
+#include "../../include/ebit.h"
+#include "common.cuh"
+#include "f2v.cuh"
+#include "hf.cuh"
+#include "state.cuh"
+#include "sweep.cuh"
+
+using namespace ebit;
+
+struct ebit_ctx {
+    Grid g;
+    long long N;
+    double h;
+    cudaStream_t stream;
+    int dense;
+    int sms;
+    uint8_t *cb[2];
+    double *s[2][3];
+    int cur;
+    uint8_t *tile_marker, *tile_dirty, *tile_cchg;
+    int *band_list, *band_count;
+    int *work_list, *work_count;
+    int *all_list, *all_count;
+    unsigned long long *ctr;  // C_N event counters + Front2VOF inconsistencies
+    double *scratch;          // 3N doubles, allocated on first ebit_get_state
+    const double *last_C;
+    const double *last_kh;
+    const uint8_t *last_st;
+    int grid_sweep, grid_f2v, grid_hf;
+    std::string err;
+};
+
+namespace {
+
+int fail(ebit_ctx *c, int code, const std::string &msg) {
+    if (c) c->err = msg;
+    return code;
+}
+
+#define CU(call)                                                                                       \
+    do {                                                                                               \
+        cudaError_t e_ = (call);                                                                       \
+        if (e_ != cudaSuccess) return fail(ctx, EBIT_ECUDA, std::string(#call ": ") + cudaGetErrorString(e_)); \
+    } while (0)
+
+int launch_check(ebit_ctx *ctx, const char *what) {
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return fail(ctx, EBIT_ECUDA, std::string(what) + ": " + cudaGetErrorString(e));
+    return EBIT_OK;
+}
+
+int mark_all(ebit_ctx *ctx) {
+    CU(cudaMemsetAsync(ctx->tile_marker, 1, ctx->g.ntiles, ctx->stream));
+    CU(cudaMemsetAsync(ctx->tile_dirty, 1, ctx->g.ntiles, ctx->stream));
+    ctx->last_C = nullptr;
+    ctx->last_kh = nullptr;
+    ctx->last_st = nullptr;
+    return EBIT_OK;
+}
+
+int copy_other(ebit_ctx *ctx) {
+    int o = ctx->cur ^ 1;
+    CU(cudaMemcpyAsync(ctx->cb[o], ctx->cb[ctx->cur], ctx->N, cudaMemcpyDeviceToDevice, ctx->stream));
+    for (int a = 0; a < 3; a++)
+        CU(cudaMemcpyAsync(ctx->s[o][a], ctx->s[ctx->cur][a], ctx->N * sizeof(double), cudaMemcpyDeviceToDevice,
+                           ctx->stream));
+    return EBIT_OK;
+}
+
+int blocks_for(long long n, int threads, int sms) {
+    long long b = (n + threads - 1) / threads;
+    long long cap = (long long)sms * 16;
+    if (b > cap) b = cap;
+    if (b < 1) b = 1;
+    return (int)b;
+}
+
+template <int D>
+int sweep_launch(ebit_ctx *ctx, const SweepArgs &args) {
+    sweep_kernel<D><<<ctx->grid_sweep, 256, 0, ctx->stream>>>(args);
+    return launch_check(ctx, "sweep_kernel");
+}
+
+}  // namespace
+
+extern "C" {
+
+int ebit_create(const ebit_desc *desc, ebit_ctx **out) {
+    ebit_ctx *ctx = nullptr;
+    if (!desc || !out) return EBIT_EINVAL;
+    *out = nullptr;
+    if (desc->nx < 8 || desc->ny < 8 || desc->nz < 8) return EBIT_EINVAL;
+    if (!(desc->h > 0.0) || !std::isfinite(desc->h)) return EBIT_EINVAL;
+    if ((long long)desc->nx * desc->ny * desc->nz >= (1LL << 31)) return EBIT_EINVAL;
+    ctx = new ebit_ctx();
+    std::memset(&ctx->g, 0, sizeof(ctx->g));
+    ctx->g.n[0] = desc->nx;
+    ctx->g.n[1] = desc->ny;
+    ctx->g.n[2] = desc->nz;
+    for (int a = 0; a < 3; a++) ctx->g.td[a] = (ctx->g.n[a] + TILE - 1) / TILE;
+    ctx->g.ntiles = ctx->g.td[0] * ctx->g.td[1] * ctx->g.td[2];
+    ctx->N = (long long)desc->nx * desc->ny * desc->nz;
+    ctx->h = desc->h;
+    ctx->stream = (cudaStream_t)desc->cuda_stream;
+    ctx->dense = (desc->flags & EBIT_DESC_DENSE) ? 1 : 0;
+    ctx->cur = 0;
+    ctx->scratch = nullptr;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&ctx->sms, cudaDevAttrMultiProcessorCount, dev);
+    if (ctx->sms <= 0) ctx->sms = 1;
+    auto alloc = [&](void **p, size_t bytes) -> bool { return cudaMalloc(p, bytes) == cudaSuccess; };
+    bool ok = true;
+    for (int b = 0; b < 2 && ok; b++) {
+        ok = ok && alloc((void **)&ctx->cb[b], ctx->N);
+        for (int a = 0; a < 3 && ok; a++) ok = ok && alloc((void **)&ctx->s[b][a], ctx->N * sizeof(double));
+    }
+    int nt = ctx->g.ntiles;
+    ok = ok && alloc((void **)&ctx->tile_marker, nt) && alloc((void **)&ctx->tile_dirty, nt) &&
+         alloc((void **)&ctx->tile_cchg, nt) && alloc((void **)&ctx->band_list, nt * sizeof(int)) &&
+         alloc((void **)&ctx->band_count, sizeof(int)) && alloc((void **)&ctx->work_list, nt * sizeof(int)) &&
+         alloc((void **)&ctx->work_count, sizeof(int)) && alloc((void **)&ctx->all_list, nt * sizeof(int)) &&
+         alloc((void **)&ctx->all_count, sizeof(int)) &&
+         alloc((void **)&ctx->ctr, (C_N + 1) * sizeof(unsigned long long));
+    if (!ok) {
+        cudaGetLastError();
+        ebit_destroy(ctx);
+        return EBIT_ENOMEM;
+    }
+    int occ = 1;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, sweep_kernel<0>, 256, 0);
+    ctx->grid_sweep = std::max(1, std::min(nt, ctx->sms * std::max(occ, 1)));
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, f2v_kernel, 256, 0);
+    ctx->grid_f2v = std::max(1, std::min(nt, ctx->sms * std::max(occ, 1)));
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, hf_kernel, 256, 0);
+    ctx->grid_hf = std::max(1, std::min(nt, ctx->sms * std::max(occ, 1)));
+    iota_kernel<<<blocks_for(nt, 256, ctx->sms), 256, 0, ctx->stream>>>(ctx->all_list, nt, ctx->all_count);
+    if (cudaMemsetAsync(ctx->ctr, 0, (C_N + 1) * sizeof(unsigned long long), ctx->stream) != cudaSuccess ||
+        cudaGetLastError() != cudaSuccess) {
+        ebit_destroy(ctx);
+        return EBIT_ECUDA;
+    }
+    mark_all(ctx);
+    *out = ctx;
+    return EBIT_OK;
+}
+
+void ebit_destroy(ebit_ctx *ctx) {
+    if (!ctx) return;
+    cudaStreamSynchronize(ctx->stream);
+    for (int b = 0; b < 2; b++) {
+        cudaFree(ctx->cb[b]);
+        for (int a = 0; a < 3; a++) cudaFree(ctx->s[b][a]);
+    }
+    cudaFree(ctx->tile_marker);
+    cudaFree(ctx->tile_dirty);
+    cudaFree(ctx->tile_cchg);
+    cudaFree(ctx->band_list);
+    cudaFree(ctx->band_count);
+    cudaFree(ctx->work_list);
+    cudaFree(ctx->work_count);
+    cudaFree(ctx->all_list);
+    cudaFree(ctx->all_count);
+    cudaFree(ctx->ctr);
+    cudaFree(ctx->scratch);
+    delete ctx;
+}
+
+int ebit_init(ebit_ctx *ctx, const double *phi_nodes, const double *phi_faces, const double *s_exact) {
+    if (!ctx || !phi_nodes) return fail(ctx, EBIT_EINVAL, "ebit_init: null argument");
+    int c = ctx->cur;
+    init_kernel<<<blocks_for(ctx->N, 256, ctx->sms), 256, 0, ctx->stream>>>(
+        ctx->g, phi_nodes, phi_faces, s_exact, ctx->cb[c], ctx->s[c][0], ctx->s[c][1], ctx->s[c][2]);
+    int r = launch_check(ctx, "init_kernel");
+    if (r) return r;
+    if ((r = copy_other(ctx))) return r;
+    return mark_all(ctx);
+}
+
+int ebit_set_state(ebit_ctx *ctx, const uint8_t *cb, const double *s) {
+    if (!ctx || !cb || !s) return fail(ctx, EBIT_EINVAL, "ebit_set_state: null argument");
+    int c = ctx->cur;
+    CU(cudaMemcpyAsync(ctx->cb[c], cb, ctx->N, cudaMemcpyDefault, ctx->stream));
+    for (int a = 0; a < 3; a++)
+        CU(cudaMemcpyAsync(ctx->s[c][a], s + a * ctx->N, ctx->N * sizeof(double), cudaMemcpyDefault, ctx->stream));
+    int r = copy_other(ctx);
+    if (r) return r;
+    return mark_all(ctx);
+}
+
+int ebit_get_state(ebit_ctx *ctx, uint8_t *cb, double *s) {
+    if (!ctx || !cb || !s) return fail(ctx, EBIT_EINVAL, "ebit_get_state: null argument");
+    if (!ctx->scratch) CU(cudaMalloc((void **)&ctx->scratch, 3 * ctx->N * sizeof(double)));
+    int c = ctx->cur;
+    canonical_s_kernel<<<blocks_for(ctx->N, 256, ctx->sms), 256, 0, ctx->stream>>>(
+        ctx->g, ctx->cb[c], ctx->s[c][0], ctx->s[c][1], ctx->s[c][2], ctx->scratch);
+    int r = launch_check(ctx, "canonical_s_kernel");
+    if (r) return r;
+    CU(cudaMemcpyAsync(cb, ctx->cb[c], ctx->N, cudaMemcpyDefault, ctx->stream));
+    CU(cudaMemcpyAsync(s, ctx->scratch, 3 * ctx->N * sizeof(double), cudaMemcpyDefault, ctx->stream));
+    return ebit_sync(ctx);
+}
+
+int ebit_advect_sweep(ebit_ctx *ctx, int dir, const double *u_face, double dt) {
+    if (!ctx) return EBIT_EINVAL;
+    if (dir < 0 || dir > 2) return fail(ctx, EBIT_EINVAL, "ebit_advect_sweep: dir must be 0, 1 or 2");
+    if (!u_face) return fail(ctx, EBIT_EINVAL, "ebit_advect_sweep: null velocity");
+    if (!std::isfinite(dt)) return fail(ctx, EBIT_EINVAL, "ebit_advect_sweep: non-finite dt");
+    const int *list, *count;
+    if (ctx->dense) {
+        list = ctx->all_list;
+        count = ctx->all_count;
+    } else {
+        CU(cudaMemsetAsync(ctx->band_count, 0, sizeof(int), ctx->stream));
+        band_kernel<<<blocks_for(ctx->g.ntiles, 256, ctx->sms), 256, 0, ctx->stream>>>(
+            ctx->g, ctx->tile_marker, ctx->band_list, ctx->band_count);
+        int r = launch_check(ctx, "band_kernel");
+        if (r) return r;
+        list = ctx->band_list;
+        count = ctx->band_count;
+    }
+    SweepArgs a;
+    a.g = ctx->g;
+    int c = ctx->cur, o = c ^ 1;
+    a.cb = ctx->cb[c];
+    a.cbo = ctx->cb[o];
+    for (int k = 0; k < 3; k++) {
+        a.s[k] = ctx->s[c][k];
+        a.so[k] = ctx->s[o][k];
+    }
+    a.u = u_face;
+    a.lam = dt / ctx->h;
+    a.list = list;
+    a.count = count;
+    a.ctr = ctx->ctr;
+    a.tile_marker = ctx->tile_marker;
+    a.tile_dirty = ctx->tile_dirty;
+    int r;
+    switch (dir) {
+    case 0: r = sweep_launch<0>(ctx, a); break;
+    case 1: r = sweep_launch<1>(ctx, a); break;
+    default: r = sweep_launch<2>(ctx, a); break;
+    }
+    if (r) return r;
+    ctx->cur = o;
+    return EBIT_OK;
+}
+
+int ebit_front2vof(ebit_ctx *ctx, double *C, int flags) {
+    if (!ctx || !C) return fail(ctx, EBIT_EINVAL, "ebit_front2vof: null argument");
+    const int *list, *count;
+    bool full = (flags & EBIT_FULL) || ctx->dense || C != ctx->last_C;
+    if (full) {
+        CU(cudaMemsetAsync(ctx->tile_dirty, 0, ctx->g.ntiles, ctx->stream));
+        list = ctx->all_list;
+        count = ctx->all_count;
+    } else {
+        CU(cudaMemsetAsync(ctx->work_count, 0, sizeof(int), ctx->stream));
+        take_flagged_kernel<<<blocks_for(ctx->g.ntiles, 256, ctx->sms), 256, 0, ctx->stream>>>(
+            ctx->g, ctx->tile_dirty, ctx->work_list, ctx->work_count);
+        int r = launch_check(ctx, "take_flagged_kernel");
+        if (r) return r;
+        list = ctx->work_list;
+        count = ctx->work_count;
+    }
+    F2VArgs a;
+    a.g = ctx->g;
+    int c = ctx->cur;
+    a.cb = ctx->cb[c];
+    for (int k = 0; k < 3; k++) a.s[k] = ctx->s[c][k];
+    a.C = C;
+    a.list = list;
+    a.count = count;
+    a.tile_cchg = ctx->tile_cchg;
+    a.bad = ctx->ctr + C_N;
+    f2v_kernel<<<ctx->grid_f2v, 256, 0, ctx->stream>>>(a);
+    int r = launch_check(ctx, "f2v_kernel");
+    if (r) return r;
+    ctx->last_C = C;
+    return EBIT_OK;
+}
+
+int ebit_curvature(ebit_ctx *ctx, const double *C, double *kappa_h, uint8_t *status, int mode, int flags) {
+    if (!ctx || !C || !kappa_h || !status) return fail(ctx, EBIT_EINVAL, "ebit_curvature: null argument");
+    if (mode != EBIT_CURV_HF) return fail(ctx, EBIT_EINVAL, "ebit_curvature: mode not available");
+    const int *list, *count;
+    bool full = (flags & EBIT_FULL) || ctx->dense || C != ctx->last_C || kappa_h != ctx->last_kh ||
+                status != ctx->last_st;
+    if (full) {
+        list = ctx->all_list;
+        count = ctx->all_count;
+    } else {
+        CU(cudaMemsetAsync(ctx->work_count, 0, sizeof(int), ctx->stream));
+        band_kernel<<<blocks_for(ctx->g.ntiles, 256, ctx->sms), 256, 0, ctx->stream>>>(
+            ctx->g, ctx->tile_cchg, ctx->work_list, ctx->work_count);
+        int r = launch_check(ctx, "band_kernel");
+        if (r) return r;
+        list = ctx->work_list;
+        count = ctx->work_count;
+    }
+    CU(cudaMemsetAsync(ctx->tile_cchg, 0, ctx->g.ntiles, ctx->stream));
+    HFArgs a;
+    a.g = ctx->g;
+    a.C = C;
+    a.kh = kappa_h;
+    a.st = status;
+    a.list = list;
+    a.count = count;
+    a.iface = nullptr;
+    a.iface_count = nullptr;
+    hf_kernel<<<ctx->grid_hf, 256, 0, ctx->stream>>>(a);
+    int r = launch_check(ctx, "hf_kernel");
+    if (r) return r;
+    ctx->last_kh = kappa_h;
+    ctx->last_st = status;
+    return EBIT_OK;
+}
+
+int ebit_counters(ebit_ctx *ctx, ebit_counters_t *out) {
+    if (!ctx || !out) return fail(ctx, EBIT_EINVAL, "ebit_counters: null argument");
+    unsigned long long h[C_N + 1];
+    CU(cudaMemcpyAsync(h, ctx->ctr, sizeof(h), cudaMemcpyDeviceToHost, ctx->stream));
+    CU(cudaStreamSynchronize(ctx->stream));
+    out->markers = (int64_t)h[C_MARKERS];
+    out->annihilate = (int64_t)h[C_ANNIHILATE];
+    out->multi = (int64_t)h[C_MULTI];
+    out->inconsistent = (int64_t)h[C_INCONSISTENT] + (int64_t)h[C_N];
+    out->cfl = (int64_t)h[C_CFL];
+    if (out->cfl) return fail(ctx, EBIT_ECFL, "a marker moved a full cell or more in one sweep");
+    return out->inconsistent ? EBIT_WINCONSISTENT : EBIT_OK;
+}
+
+int ebit_reset_counters(ebit_ctx *ctx) {
+    if (!ctx) return EBIT_EINVAL;
+    CU(cudaMemsetAsync(ctx->ctr, 0, (C_N + 1) * sizeof(unsigned long long), ctx->stream));
+    return EBIT_OK;
+}
+
+int ebit_sync(ebit_ctx *ctx) {
+    if (!ctx) return EBIT_EINVAL;
+    unsigned long long cfl = 0;
+    CU(cudaMemcpyAsync(&cfl, ctx->ctr + C_CFL, sizeof(cfl), cudaMemcpyDeviceToHost, ctx->stream));
+    CU(cudaStreamSynchronize(ctx->stream));
+    if (cfl) return fail(ctx, EBIT_ECFL, "a marker moved a full cell or more in one sweep");
+    return EBIT_OK;
+}
+
+int ebit_band_tiles(ebit_ctx *ctx) {
+    if (!ctx) return -1;
+    if (ctx->dense) return ctx->g.ntiles;
+    int n = -1;
+    if (cudaMemcpyAsync(&n, ctx->band_count, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream) != cudaSuccess) return -1;
+    if (cudaStreamSynchronize(ctx->stream) != cudaSuccess) return -1;
+    return n;
+}
+
+const char *ebit_last_error(const ebit_ctx *ctx) {
+    if (!ctx) return "null context";
+    return ctx->err.c_str();
+}
+
+}  // extern "C"

@@ -1,0 +1,249 @@
+"""Thin Python binding of libebit.so (the C ABI in include/ebit.h).
+
+Functions carry the C names and only marshal arguments: torch tensors supply
+device memory (``data_ptr()``) and the CUDA stream; every step of the EBIT path
+runs in the library's CUDA kernels.  There is no CPU fallback: importing works
+without a GPU, but any call needs the compiled library and a CUDA device and
+raises ``EbitError`` otherwise.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import torch
+
+from . import build as _build
+
+EBIT_OK = 0
+EBIT_EINVAL = -1
+EBIT_ENONFINITE = -2
+EBIT_ECUDA = -3
+EBIT_ETIMEOUT = -4
+EBIT_ENOMEM = -5
+EBIT_ECFL = -6
+EBIT_WINCONSISTENT = 1
+
+EBIT_INCREMENTAL = 0
+EBIT_FULL = 1
+EBIT_CURV_HF = 0
+EBIT_CURV_MLP = 1
+EBIT_CURV_MLP_HF = 2
+EBIT_DESC_DENSE = 1
+
+ST_NONE, ST_HF_X, ST_HF_Y, ST_HF_Z, ST_NO_HF, ST_MLP = 0, 1, 2, 3, 4, 5
+
+COUNTER_NAMES = ("markers", "annihilate", "multi", "inconsistent", "cfl")
+
+
+class EbitError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"ebit error {code}: {msg}")
+        self.code = code
+
+
+class _Desc(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int), ("ny", ctypes.c_int), ("nz", ctypes.c_int), ("h", ctypes.c_double),
+                ("cuda_stream", ctypes.c_void_p), ("flags", ctypes.c_int)]
+
+
+class _Counters(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_int64) for n in COUNTER_NAMES]
+
+
+_lib = None
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = True):
+    """Load libebit.so (building it with nvcc first if it is missing or stale)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if build_if_missing and not _build.up_to_date():
+        _build.build()
+    if not os.path.exists(_build.LIB):
+        raise EbitError(EBIT_ECUDA, f"CUDA library missing: {_build.LIB}")
+    lib = ctypes.CDLL(_build.LIB)
+    P, I, D = ctypes.c_void_p, ctypes.c_int, ctypes.c_double
+    lib.ebit_create.argtypes = [ctypes.POINTER(_Desc), ctypes.POINTER(ctypes.c_void_p)]
+    lib.ebit_destroy.argtypes = [P]
+    lib.ebit_destroy.restype = None
+    lib.ebit_init.argtypes = [P, P, P, P]
+    lib.ebit_set_state.argtypes = [P, P, P]
+    lib.ebit_get_state.argtypes = [P, P, P]
+    lib.ebit_advect_sweep.argtypes = [P, I, P, D]
+    lib.ebit_front2vof.argtypes = [P, P, I]
+    lib.ebit_curvature.argtypes = [P, P, P, P, I, I]
+    lib.ebit_counters.argtypes = [P, ctypes.POINTER(_Counters)]
+    lib.ebit_reset_counters.argtypes = [P]
+    lib.ebit_sync.argtypes = [P]
+    lib.ebit_band_tiles.argtypes = [P]
+    lib.ebit_last_error.argtypes = [P]
+    lib.ebit_last_error.restype = ctypes.c_char_p
+    _lib = lib
+    return lib
+
+
+def _check(ctx, code):
+    if code < 0:
+        msg = load().ebit_last_error(ctx).decode() if ctx else ""
+        raise EbitError(code, msg)
+    return code
+
+
+def _dev(t: torch.Tensor, dtype, numel=None, name="tensor"):
+    if not isinstance(t, torch.Tensor):
+        raise TypeError(f"{name} must be a torch.Tensor")
+    if t.dtype != dtype:
+        raise TypeError(f"{name} must be {dtype}, got {t.dtype}")
+    if not t.is_cuda:
+        raise TypeError(f"{name} must be on a CUDA device")
+    if not t.is_contiguous():
+        raise TypeError(f"{name} must be contiguous")
+    if numel is not None and t.numel() != numel:
+        raise ValueError(f"{name} must have {numel} elements, got {t.numel()}")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _any(t: torch.Tensor, dtype, numel, name):
+    if t.dtype != dtype or not t.is_contiguous() or t.numel() != numel:
+        raise ValueError(f"{name}: need a contiguous {dtype} tensor of {numel} elements")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+# ----------------------------------------------------------------- C names
+def ebit_create(nx, ny, nz, h, stream=None, flags=0):
+    lib = load()
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    sp = stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream)
+    d = _Desc(int(nx), int(ny), int(nz), float(h), ctypes.c_void_p(sp), int(flags))
+    out = ctypes.c_void_p()
+    code = lib.ebit_create(ctypes.byref(d), ctypes.byref(out))
+    if code != EBIT_OK:
+        raise EbitError(code, "ebit_create failed")
+    return out
+
+
+def ebit_destroy(ctx):
+    load().ebit_destroy(ctx)
+
+
+def ebit_init(ctx, n, phi_nodes, phi_faces=None, s_exact=None):
+    pf = None if phi_faces is None else _dev(phi_faces, torch.float64, 3 * n, "phi_faces")
+    se = None if s_exact is None else _dev(s_exact, torch.float64, 3 * n, "s_exact")
+    return _check(ctx, load().ebit_init(ctx, _dev(phi_nodes, torch.float64, n, "phi_nodes"), pf, se))
+
+
+def ebit_set_state(ctx, n, cb, s):
+    return _check(ctx, load().ebit_set_state(ctx, _any(cb, torch.uint8, n, "cb"), _any(s, torch.float64, 3 * n, "s")))
+
+
+def ebit_get_state(ctx, n, cb, s):
+    return _check(ctx, load().ebit_get_state(ctx, _any(cb, torch.uint8, n, "cb"), _any(s, torch.float64, 3 * n, "s")))
+
+
+def ebit_advect_sweep(ctx, n, d, u_face, dt):
+    return _check(ctx, load().ebit_advect_sweep(ctx, int(d), _dev(u_face, torch.float64, n, "u_face"), float(dt)))
+
+
+def ebit_front2vof(ctx, n, C, flags=EBIT_INCREMENTAL):
+    return _check(ctx, load().ebit_front2vof(ctx, _dev(C, torch.float64, n, "C"), int(flags)))
+
+
+def ebit_curvature(ctx, n, C, kappa_h, status, mode=EBIT_CURV_HF, flags=EBIT_INCREMENTAL):
+    return _check(ctx, load().ebit_curvature(ctx, _dev(C, torch.float64, n, "C"),
+                                             _dev(kappa_h, torch.float64, n, "kappa_h"),
+                                             _dev(status, torch.uint8, n, "status"), int(mode), int(flags)))
+
+
+def ebit_counters(ctx):
+    c = _Counters()
+    code = load().ebit_counters(ctx, ctypes.byref(c))
+    _check(ctx, code)
+    return {k: int(getattr(c, k)) for k in COUNTER_NAMES}, code
+
+
+def ebit_reset_counters(ctx):
+    return _check(ctx, load().ebit_reset_counters(ctx))
+
+
+def ebit_sync(ctx):
+    return _check(ctx, load().ebit_sync(ctx))
+
+
+def ebit_band_tiles(ctx):
+    return int(load().ebit_band_tiles(ctx))
+
+
+def ebit_last_error(ctx):
+    return load().ebit_last_error(ctx).decode()
+
+
+# ------------------------------------------------------------ convenience
+class Grid:
+    """One EBIT context with its device buffers (torch tensors on ``device``).
+
+    ``shape`` is (nz, ny, nx); every array is idx-ordered like the C ABI.
+    """
+
+    def __init__(self, nx, ny, nz, h=None, device="cuda", stream=None, dense=False):
+        self.n3 = (int(nx), int(ny), int(nz))
+        self.N = self.n3[0] * self.n3[1] * self.n3[2]
+        self.h = float(h if h is not None else 1.0 / nx)
+        self.device = torch.device(device)
+        self.shape = (self.n3[2], self.n3[1], self.n3[0])
+        self.ctx = ebit_create(nx, ny, nz, self.h, stream, EBIT_DESC_DENSE if dense else 0)
+
+    def close(self):
+        if self.ctx is not None:
+            ebit_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):  # pragma: no cover
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def init(self, phi_nodes, phi_faces=None, s_exact=None):
+        return ebit_init(self.ctx, self.N, phi_nodes, phi_faces, s_exact)
+
+    def set_state(self, cb, s):
+        return ebit_set_state(self.ctx, self.N, cb, s)
+
+    def get_state(self):
+        cb = torch.empty(self.shape, dtype=torch.uint8, device=self.device)
+        s = torch.empty((3,) + self.shape, dtype=torch.float64, device=self.device)
+        ebit_get_state(self.ctx, self.N, cb, s)
+        return cb, s
+
+    def sweep(self, d, u_face, dt):
+        return ebit_advect_sweep(self.ctx, self.N, d, u_face, dt)
+
+    def step(self, n, u_fields, dt):
+        """Three split sweeps: x-y-z on even steps, z-y-x on odd steps."""
+        for d in ((0, 1, 2) if n % 2 == 0 else (2, 1, 0)):
+            self.sweep(d, u_fields[d], dt)
+
+    def front2vof(self, C, flags=EBIT_INCREMENTAL):
+        return ebit_front2vof(self.ctx, self.N, C, flags)
+
+    def curvature(self, C, kappa_h, status, mode=EBIT_CURV_HF, flags=EBIT_INCREMENTAL):
+        return ebit_curvature(self.ctx, self.N, C, kappa_h, status, mode, flags)
+
+    def counters(self):
+        return ebit_counters(self.ctx)[0]
+
+    def reset_counters(self):
+        return ebit_reset_counters(self.ctx)
+
+    def sync(self):
+        return ebit_sync(self.ctx)
+
+    def band_tiles(self):
+        return ebit_band_tiles(self.ctx)

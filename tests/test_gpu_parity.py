@@ -1,0 +1,159 @@
+"""Parity of the CUDA path (through the C ABI) with the CPU FP64 oracle.
+
+Bar (from the method's data): colour bytes, topology counters and statuses
+bit-exact; FP64 marker offsets, volume fractions and curvature within 1e-12
+absolute.  Offsets are compared on edges that carry a marker (the offset of an
+empty edge is unspecified and reads back as 0).
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2509_26361_gb300 import ebit
+from paper_2509_26361_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+TOL = 1e-12
+
+
+def to_dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def present_mask(cb):
+    c = cb & 1
+    return np.stack([c != np.roll(c, -1, axis=2), c != np.roll(c, -1, axis=1), c != np.roll(c, -1, axis=0)])
+
+
+def compare_state(g, ost, where=""):
+    cb, s = g.get_state()
+    cb = cb.cpu().numpy()
+    s = s.cpu().numpy()
+    assert np.array_equal(cb, ost.cb), f"colour bytes differ {where}: {np.argwhere(cb != ost.cb)[:5]}"
+    m = present_mask(cb)
+    d = np.abs(s[m] - ost.s[m])
+    assert d.size == 0 or d.max() <= TOL, f"offsets differ {where}: {d.max()}"
+    assert np.all(s[~m] == 0.0)
+    return cb, s
+
+
+def run_pair(n3, phi, faces, u, lams, steps, s_exact=None, dense=False, check_every=1, f2v=True, hf=True):
+    nx, ny, nz = n3
+    g = ebit.Grid(nx, ny, nz, h=1.0 / nx, dense=dense)
+    g.init(to_dev(phi), None if faces is None else to_dev(faces), None if s_exact is None else to_dev(s_exact))
+    ost = oracle.init(phi, faces, s_exact)
+    compare_state(g, ost, "after init")
+    ud = [to_dev(u[d]) for d in range(3)]
+    C = torch.zeros(g.shape, dtype=torch.float64, device="cuda")
+    kh = torch.zeros_like(C)
+    st = torch.zeros(g.shape, dtype=torch.uint8, device="cuda")
+    ocnt = np.zeros(5, np.int64)
+    for n in range(steps):
+        order = (0, 1, 2) if n % 2 == 0 else (2, 1, 0)
+        for d in order:
+            lam = lams(n)
+            dt = lam * g.h
+            g.sweep(d, ud[d], dt)
+            ost, c = oracle.sweep(ost, d, u[d], dt / g.h)
+            ocnt += c
+            if (n % check_every) == 0:
+                compare_state(g, ost, f"step {n} dir {d}")
+        if f2v:
+            g.front2vof(C)
+            oC, nbad = oracle.front2vof(ost)
+            assert nbad == 0
+            dC = np.abs(C.cpu().numpy() - oC).max()
+            assert dC <= TOL, f"C differs at step {n}: {dC}"
+            if hf:
+                g.curvature(C, kh, st)
+                okh, ost_ = oracle.hf_curvature(oC)
+                assert np.array_equal(st.cpu().numpy(), ost_), f"HF status differs at step {n}"
+                dk = np.abs(kh.cpu().numpy() - okh).max()
+                assert dk <= TOL, f"kappa differs at step {n}: {dk}"
+    compare_state(g, ost, "final")
+    cnt = g.counters()
+    assert [cnt[k] for k in ebit.COUNTER_NAMES] == list(ocnt), (cnt, ocnt)
+    g.close()
+    return ost
+
+
+def blobs(n3, seed, count, rmin, rmax):
+    rng = np.random.default_rng(seed)
+    sp = [W.Sphere(tuple(rng.uniform(0, 1, 3)), rng.uniform(rmin, rmax)) for _ in range(count)]
+    return W.sphere_phi_nodes_faces(n3, sp)
+
+
+@pytest.mark.parametrize("dense", [False, True])
+def test_translation_sphere_exact_roots(dense):
+    w = W.translation_sphere(32)
+    run_pair(w.n3, w.phi, w.phi_faces, w.u, lambda n: 0.25, 8, s_exact=w.s_exact, dense=dense)
+
+
+@pytest.mark.parametrize("seed", [1, 2])
+def test_fourier_spheres_small(seed):
+    w = W.fourier_spheres(n=32, seed=seed, count=4, rmin=0.06, rmax=0.14, steps=6)
+    run_pair(w.n3, w.phi, w.phi_faces, w.u, w.lam, w.steps)
+
+
+@pytest.mark.parametrize("n3", [(20, 24, 28), (9, 17, 8)])
+def test_ragged_grid_random_blobs(n3):
+    """Grids that are not multiples of the 8-cell tile, lumpy shapes with thin
+    features (topology changes, saddle faces) in a seeded divergence-free field."""
+    rng = np.random.default_rng(7)
+    phi, faces = blobs(n3, 3, 9, 0.04, 0.12)
+    u = W.fourier_velocity(n3, rng)
+    run_pair(n3, phi, faces, u, lambda n: 0.9 if n % 3 else -0.7, 6)
+
+
+def test_empty_and_full_domains():
+    for val in (-1.0, 1.0):
+        n3 = (16, 16, 16)
+        phi = np.full((16, 16, 16), val)
+        u = W.fourier_velocity(n3, np.random.default_rng(1))
+        run_pair(n3, phi, None, u, lambda n: 0.5, 2)
+
+
+def test_band_matches_dense_over_many_steps():
+    w = W.fourier_spheres(n=48, seed=5, count=5, rmin=0.05, rmax=0.11)
+    res = []
+    for dense in (False, True):
+        g = ebit.Grid(48, 48, 48, dense=dense)
+        g.init(to_dev(w.phi), to_dev(w.phi_faces))
+        ud = [to_dev(w.u[d]) for d in range(3)]
+        C = torch.zeros(g.shape, dtype=torch.float64, device="cuda")
+        kh = torch.zeros_like(C)
+        st = torch.zeros(g.shape, dtype=torch.uint8, device="cuda")
+        for n in range(40):
+            g.step(n, ud, w.lam(n) * g.h)
+            g.front2vof(C)
+            g.curvature(C, kh, st)
+        cb, s = g.get_state()
+        res.append((cb.cpu().numpy(), s.cpu().numpy(), C.cpu().numpy(), kh.cpu().numpy(), st.cpu().numpy()))
+        g.close()
+    for a, b in zip(res[0], res[1]):
+        assert np.array_equal(a, b)
+
+
+def test_full_size_config_sampled_steps():
+    """128^3, 8 spheres, 12-mode field: the benchmark's launch configuration (band
+    mode); a few steps compared whole-array with the oracle."""
+    w = W.fourier_spheres(n=128, seed=2)
+    run_pair(w.n3, w.phi, w.phi_faces, w.u, w.lam, 2, check_every=1)
+
+
+def test_errors_are_reported():
+    g = ebit.Grid(16, 16, 16)
+    u = torch.ones(g.shape, dtype=torch.float64, device="cuda")
+    with pytest.raises(ebit.EbitError) as e:
+        g.sweep(3, u, 0.01)
+    assert e.value.code == ebit.EBIT_EINVAL
+    with pytest.raises(ebit.EbitError):
+        g.sweep(0, u, float("nan"))
+    phi, faces = blobs((16, 16, 16), 1, 3, 0.15, 0.3)
+    g.init(to_dev(phi), to_dev(faces))
+    g.sweep(0, u, 1.5 * g.h)  # markers move 1.5 cells: clamped on the device, raised at sync
+    with pytest.raises(ebit.EbitError) as e:
+        g.sync()
+    assert e.value.code == ebit.EBIT_ECFL
+    g.close()
