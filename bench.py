@@ -1,0 +1,336 @@
+"""Benchmark of the GB300 EBIT kinematics path.
+
+One step = three split advection sweeps + Front2VOF + height-function curvature
+on the 128^3 periodic workload: 8 non-overlapping spheres (R ~ U[0.05, 0.12]) in a
+seeded 12-mode divergence-free Fourier field times cos(pi t / T), T = 2, CFL 0.5
+(512 steps for the full period).  Inputs are seeded and synthetic.
+
+Prints one JSON line (see the design doc for every key).  ``--impl reference`` times
+the CPU FP64 oracle on the same workload instead (a bounded sample of steps).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "EBIT cell-steps/s (advect+Front2VOF) & curvature/s learned vs HF, % HBM roof"
+WORKLOAD = "fourier_spheres_128"
+N = 128
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def workload(seed_offset=0):
+    from paper_2509_26361_gb300 import workloads as W
+
+    return W.fourier_spheres(n=N, seed=2 + seed_offset)
+
+
+def config_dict(w, l2):
+    return {"workload": WORKLOAD, "grid": list(w.n3), "spheres": len(w.shapes), "radius_range": [0.05, 0.12],
+            "velocity": "12-mode Fourier vector-potential curl x cos(pi t/T), T=2", "cfl": w.cfl,
+            "period_steps": w.steps, "step": "3 split sweeps + Front2VOF + HF curvature (FP64)",
+            "band": "8^3 tiles with markers + 1-tile halo", "l2": l2}
+
+
+# --------------------------------------------------------------- oracle arm
+def run_oracle(w, steps, budget_s):
+    import oracle
+
+    st = oracle.init(w.phi, w.phi_faces)
+    C, _ = oracle.front2vof(st)
+    done = 0
+    t0 = time.perf_counter()
+    for n in range(steps):
+        st = oracle.step(st, n, w.u, w.lam(n))
+        C, _ = oracle.front2vof(st)
+        oracle.hf_curvature(C)
+        done += 1
+        if time.perf_counter() - t0 > budget_s:
+            break
+    dt = time.perf_counter() - t0
+    return done, dt
+
+
+def cpu_baseline_block(w, budget_s=15.0, max_steps=64):
+    done, dt = run_oracle(w, max_steps, budget_s)
+    val = w.n3[0] * w.n3[1] * w.n3[2] * done / dt
+    return {"value": val, "unit": "cell-steps/s", "cores": 1, "kind": "oracle",
+            "sample": f"first {done} steps of the {WORKLOAD} workload (3 sweeps + Front2VOF + HF each), "
+                      f"single-threaded C oracle, {dt:.1f} s"}
+
+
+# ------------------------------------------------------------------ clocks
+class ClockSampler:
+    def __init__(self):
+        self.rows = []
+        self.proc = None
+        self.thread = None
+        self.window = None
+
+    def start(self):
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={q}", "--format=csv,noheader,nounits",
+                                          "-lms", "20"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL,
+                                         text=True)
+        except Exception:
+            self.proc = None
+            return
+
+        def reader():
+            for line in self.proc.stdout:
+                self.rows.append((time.perf_counter(), line.strip()))
+        self.thread = threading.Thread(target=reader, daemon=True)
+        self.thread.start()
+
+    def stop(self):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self, t0, t1, dev_index=0):
+        rows = []
+        for t, line in self.rows:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9 or parts[0] != str(dev_index):
+                continue
+            rows.append((t, parts))
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no nvidia-smi samples"]}
+        inwin = [r for r in rows if t0 <= r[0] <= t1]
+        if not inwin:
+            mid = 0.5 * (t0 + t1)
+            inwin = sorted(rows, key=lambda r: abs(r[0] - mid))[:3]
+        sm = [float(r[1][1]) for r in inwin if r[1][1].replace(".", "").isdigit()]
+        mx = [float(r[1][2]) for r in inwin if r[1][2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = set()
+        for _, p in inwin:
+            for k, nm in enumerate(names):
+                if p[5 + k].lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(inwin)}
+
+
+# -------------------------------------------------------------- GPU arm
+def run_gpu(args, rank, world):
+    import torch
+
+    from paper_2509_26361_gb300 import ebit
+
+    dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0)))
+    torch.cuda.set_device(dev)
+    w = workload(seed_offset=rank)
+    nc = w.n3[0] * w.n3[1] * w.n3[2]
+    g = ebit.Grid(*w.n3, h=w.h, device=dev)
+    tdev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)
+    phi, faces = tdev(w.phi), tdev(w.phi_faces)
+    ud = [tdev(w.u[d]) for d in range(3)]
+    C = torch.zeros(g.shape, dtype=torch.float64, device=dev)
+    kh = torch.zeros_like(C)
+    st = torch.zeros(g.shape, dtype=torch.uint8, device=dev)
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)  # 256 MiB > L2
+
+    def one_step(n):
+        dt = w.lam(n) * g.h
+        g.step(n, ud, dt)
+        g.front2vof(C)
+        g.curvature(C, kh, st)
+
+    g.init(phi, faces)
+    g.front2vof(C, ebit.EBIT_FULL)
+    g.curvature(C, kh, st, flags=ebit.EBIT_FULL)
+    for n in range(args.warmup):
+        one_step(n)
+    torch.cuda.synchronize()
+    g.reset_counters()
+    g.profile(True)
+    clocks = ClockSampler()
+    if rank == 0:
+        clocks.start()
+        time.sleep(0.3)
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+    torch.cuda.synchronize()
+    wall0 = time.perf_counter()
+    for i in range(args.steps):
+        flush.zero_()
+        evs[i][0].record()
+        one_step(args.warmup + i)
+        evs[i][1].record()
+    torch.cuda.synchronize()
+    wall1 = time.perf_counter()
+    if world > 1:
+        dist.barrier()
+    step_ms = [a.elapsed_time(b) for a, b in evs]
+    total_ms = float(sum(step_ms))
+    prof = g.profile_read()
+    g.profile(False)
+    cnt = g.counters()
+    if world > 1:
+        t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+
+    # ------------------------------------------------ end-to-end (host buffers)
+    e2e = None
+    if rank == 0:
+        e2e = run_e2e(args, g, w, dev, C, kh, st)
+    clk = clocks.summary(wall0, wall1) if rank == 0 else None
+    clocks.stop()
+    g.close()
+    return dict(total_ms=total_ms, step_ms=step_ms, prof=prof, cnt=cnt, nc=nc, w=w, e2e=e2e, clk=clk)
+
+
+def run_e2e(args, g, w, dev, C, kh, st):
+    """Same steps through the public API with host buffers: each step copies the
+    three velocity fields from pinned host memory and reads back C and kappa*h."""
+    import torch
+
+    uh = [torch.from_numpy(np.ascontiguousarray(w.u[d])).pin_memory() for d in range(3)]
+    ud = [torch.empty(g.shape, dtype=torch.float64, device=dev) for _ in range(3)]
+    Ch = torch.empty(g.shape, dtype=torch.float64).pin_memory()
+    kh_h = torch.empty(g.shape, dtype=torch.float64).pin_memory()
+    steps = args.steps
+    s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    s0.record()
+    for i in range(steps):
+        n = args.warmup + args.steps + i
+        for d in range(3):
+            ud[d].copy_(uh[d], non_blocking=True)
+        g.step(n, ud, w.lam(n) * g.h)
+        g.front2vof(C)
+        g.curvature(C, kh, st)
+        Ch.copy_(C, non_blocking=True)
+        kh_h.copy_(kh, non_blocking=True)
+    s1.record()
+    torch.cuda.synchronize()
+    ms = s0.elapsed_time(s1)
+    nc = w.n3[0] * w.n3[1] * w.n3[2]
+    return {"value": nc * steps / (ms * 1e-3), "unit": "cell-steps/s",
+            "h2d_bytes_per_step": 3 * nc * 8, "d2h_bytes_per_step": 2 * nc * 8}
+
+
+def roofline_block(res):
+    """Dominant kernel by device time; achieved = algorithmic bytes per launch /
+    average launch time (CUDA events around every launch, on its stream)."""
+    hbm, src = peaks()
+    prof = res["prof"]
+    kinds = {k: v for k, v in prof.items() if k in ("sweep", "f2v", "hf", "band")}
+    dom = max(kinds, key=lambda k: kinds[k][0])
+    ms, launches = kinds[dom]
+    avg_s = ms * 1e-3 / launches
+    cnt = res["cnt"]
+    nsweeps = prof["sweep"][1]
+    band_cells = cnt["tiles"] / nsweeps * 512.0
+    markers = cnt["markers"] / nsweeps
+    if dom == "sweep":
+        # per band cell: colour byte read + written; per marker: offset read,
+        # offset written, one 8-byte velocity sample
+        alg = 2.0 * band_cells + 24.0 * markers
+    elif dom == "f2v":
+        # per band cell: 8 corner colours (1 B amortised) + C written (8 B); per marker 8 B
+        alg = 9.0 * band_cells + 8.0 * markers
+    elif dom == "hf":
+        alg = 17.0 * band_cells
+    else:
+        alg = 2.0 * res["nc"] / 512.0
+    achieved = alg / avg_s / 1e9
+    return {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": hbm, "unit": "GB/s",
+            "frac": achieved / hbm, "traffic": None, "peak_source": src,
+            "alg_bytes_per_launch": alg, "avg_launch_us": avg_s * 1e6,
+            "kernel_ms": {k: round(v[0], 4) for k, v in prof.items()},
+            "kernel_launches": {k: v[1] for k, v in prof.items()}}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=512)
+    ap.add_argument("--warmup", type=int, default=8)
+    ap.add_argument("--impl", default="ebit", choices=["ebit", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    rank = int(os.environ.get("RANK", 0))
+    world = int(os.environ.get("WORLD_SIZE", 1))
+
+    if args.impl == "reference":
+        if rank != 0:
+            return 0
+        w = workload()
+        budget = 120.0
+        done, dt = run_oracle(w, args.steps, budget)
+        nc = w.n3[0] * w.n3[1] * w.n3[2]
+        val = nc * done / dt
+        line = {"metric": METRIC, "value": val, "unit": "cell-steps/s", "n_gpus": args.gpus, "steps": done,
+                "warmup": 0, "ms_per_step": dt * 1e3 / done, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
+                "config": config_dict(w, "n/a (CPU)"),
+                "cpu_baseline": {"value": val, "unit": "cell-steps/s", "cores": 1, "kind": "oracle",
+                                 "sample": f"first {done} of {args.steps} requested steps (time budget "
+                                           f"{budget:.0f} s), single-threaded C oracle"},
+                "e2e": {"value": val, "unit": "cell-steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+        print(json.dumps(line))
+        return 0
+
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if os.environ.get("EBIT_BENCH_BACKEND", "nccl") == "nccl" else "gloo")
+    res = run_gpu(args, rank, world)
+    if rank != 0:
+        if world > 1:
+            import torch.distributed as dist
+            dist.destroy_process_group()
+        return 0
+    total_s = res["total_ms"] * 1e-3
+    value = res["nc"] * args.steps * world / total_s
+    prof = res["prof"]
+    launches = sum(v[1] for k, v in prof.items() if k in ("sweep", "band", "f2v", "hf", "mlp"))
+    line = {"metric": METRIC, "value": value, "unit": "cell-steps/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": res["total_ms"] / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": config_dict(res["w"], "flushed (256 MiB write) before every timed step, outside its events"),
+            "roofline": roofline_block(res), "e2e": res["e2e"], "gpu_launches": launches,
+            "clocks": res["clk"],
+            "counters": res["cnt"]}
+    if not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline_block(res["w"])
+    print(json.dumps(line))
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -100,6 +100,7 @@ typedef struct {
     int64_t multi;        /* edges where three markers met; the median was kept */
     int64_t inconsistent; /* colour/crossing parity disagreements (never expected) */
     int64_t cfl;          /* marker displacements of a full cell or more (error) */
+    int64_t tiles;        /* 8x8x8 tiles processed by the sweeps (band size, summed) */
 } ebit_counters_t;
 
 /* Create a context for one grid: allocates the double-buffered state and the
@@ -179,6 +180,23 @@ int ebit_sync(ebit_ctx *ctx);
 
 /* Number of tiles (8x8x8 cells) the last sweep processed; -1 if unknown. */
 int ebit_band_tiles(ebit_ctx *ctx);
+
+/* Per-kernel timing.  With profiling on, the library brackets every kernel it
+ * launches on the context's stream with a pair of CUDA events and sums the
+ * elapsed device time per kind.  Kinds (index into the arrays below): */
+enum {
+    EBIT_PROF_SWEEP = 0, /* split-sweep kernels */
+    EBIT_PROF_BAND = 1,  /* band/tile-list kernels and their memsets */
+    EBIT_PROF_F2V = 2,   /* Front2VOF kernel */
+    EBIT_PROF_HF = 3,    /* height-function kernel */
+    EBIT_PROF_MLP = 4,   /* learned-curvature kernels */
+    EBIT_PROF_KINDS = 8
+};
+/* enable != 0 switches timing on and zeroes the sums; 0 switches it off. */
+int ebit_profile(ebit_ctx *ctx, int enable);
+/* ms[EBIT_PROF_KINDS] total device milliseconds and launches[EBIT_PROF_KINDS]
+ * launch counts since the last ebit_profile call (synchronises). */
+int ebit_profile_read(ebit_ctx *ctx, double *ms, int64_t *launches);
 
 /* Message of the last failed call on this context (never NULL). */
 const char *ebit_last_error(const ebit_ctx *ctx);

@@ -17,6 +17,8 @@ constexpr int TILE = 8;                               // tile edge (cells)
 constexpr int TILE_CELLS = TILE * TILE * TILE;
 
 enum Counter { C_MARKERS = 0, C_ANNIHILATE = 1, C_MULTI = 2, C_INCONSISTENT = 3, C_CFL = 4, C_N = 5 };
+// extra device counters after the event counters
+enum { C_F2V_BAD = C_N, C_TILES = C_N + 1, C_TOTAL = C_N + 2 };
 
 struct Grid {
     int n[3];        // cells per axis

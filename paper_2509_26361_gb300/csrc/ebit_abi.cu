@@ -8,10 +8,12 @@
 // A tile outside the band provably holds no marker and is not changed by the
 // call, and both state buffers agree on it, so band processing gives the same
 // state as processing every tile (tests compare both against the oracle).
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
 #include <string>
+#include <vector>
 
 #include "../../include/ebit.h"
 #include "common.cuh"
@@ -42,6 +44,13 @@ struct ebit_ctx {
     const double *last_kh;
     const uint8_t *last_st;
     int grid_sweep, grid_f2v, grid_hf;
+    // per-kernel CUDA-event timing (ebit_profile)
+    int prof_on;
+    std::vector<cudaEvent_t> ev;
+    std::vector<int> ev_kind;
+    int ev_used;
+    double prof_ms[EBIT_PROF_KINDS];
+    long long prof_n[EBIT_PROF_KINDS];
     std::string err;
 };
 
@@ -90,8 +99,42 @@ int blocks_for(long long n, int threads, int sms) {
     return (int)b;
 }
 
+// Event pairs around the timed launches; drained into per-kind sums.
+int prof_drain(ebit_ctx *ctx) {
+    if (ctx->ev_used == 0) return EBIT_OK;
+    CU(cudaStreamSynchronize(ctx->stream));
+    for (int i = 0; i < ctx->ev_used; i++) {
+        float ms = 0.f;
+        CU(cudaEventElapsedTime(&ms, ctx->ev[2 * i], ctx->ev[2 * i + 1]));
+        ctx->prof_ms[ctx->ev_kind[i]] += ms;
+        ctx->prof_n[ctx->ev_kind[i]] += 1;
+    }
+    ctx->ev_used = 0;
+    return EBIT_OK;
+}
+
+struct ProfScope {
+    ebit_ctx *ctx;
+    int kind;
+    bool on;
+    ProfScope(ebit_ctx *c, int k) : ctx(c), kind(k), on(c->prof_on != 0) {
+        if (!on) return;
+        if (ctx->ev_used * 2 + 2 > (int)ctx->ev.size()) {
+            if (prof_drain(ctx) != EBIT_OK) { on = false; return; }
+        }
+        cudaEventRecord(ctx->ev[2 * ctx->ev_used], ctx->stream);
+    }
+    ~ProfScope() {
+        if (!on) return;
+        cudaEventRecord(ctx->ev[2 * ctx->ev_used + 1], ctx->stream);
+        ctx->ev_kind[ctx->ev_used] = kind;
+        ctx->ev_used++;
+    }
+};
+
 template <int D>
 int sweep_launch(ebit_ctx *ctx, const SweepArgs &args) {
+    ProfScope ps(ctx, EBIT_PROF_SWEEP);
     sweep_kernel<D><<<ctx->grid_sweep, 256, 0, ctx->stream>>>(args);
     return launch_check(ctx, "sweep_kernel");
 }
@@ -136,7 +179,7 @@ int ebit_create(const ebit_desc *desc, ebit_ctx **out) {
          alloc((void **)&ctx->band_count, sizeof(int)) && alloc((void **)&ctx->work_list, nt * sizeof(int)) &&
          alloc((void **)&ctx->work_count, sizeof(int)) && alloc((void **)&ctx->all_list, nt * sizeof(int)) &&
          alloc((void **)&ctx->all_count, sizeof(int)) &&
-         alloc((void **)&ctx->ctr, (C_N + 1) * sizeof(unsigned long long));
+         alloc((void **)&ctx->ctr, C_TOTAL * sizeof(unsigned long long));
     if (!ok) {
         cudaGetLastError();
         ebit_destroy(ctx);
@@ -150,10 +193,16 @@ int ebit_create(const ebit_desc *desc, ebit_ctx **out) {
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, hf_kernel, 256, 0);
     ctx->grid_hf = std::max(1, std::min(nt, ctx->sms * std::max(occ, 1)));
     iota_kernel<<<blocks_for(nt, 256, ctx->sms), 256, 0, ctx->stream>>>(ctx->all_list, nt, ctx->all_count);
-    if (cudaMemsetAsync(ctx->ctr, 0, (C_N + 1) * sizeof(unsigned long long), ctx->stream) != cudaSuccess ||
+    if (cudaMemsetAsync(ctx->ctr, 0, C_TOTAL * sizeof(unsigned long long), ctx->stream) != cudaSuccess ||
         cudaGetLastError() != cudaSuccess) {
         ebit_destroy(ctx);
         return EBIT_ECUDA;
+    }
+    ctx->prof_on = 0;
+    ctx->ev_used = 0;
+    for (int k = 0; k < EBIT_PROF_KINDS; k++) {
+        ctx->prof_ms[k] = 0.0;
+        ctx->prof_n[k] = 0;
     }
     mark_all(ctx);
     *out = ctx;
@@ -178,6 +227,7 @@ void ebit_destroy(ebit_ctx *ctx) {
     cudaFree(ctx->all_count);
     cudaFree(ctx->ctr);
     cudaFree(ctx->scratch);
+    for (cudaEvent_t e : ctx->ev) cudaEventDestroy(e);
     delete ctx;
 }
 
@@ -226,6 +276,7 @@ int ebit_advect_sweep(ebit_ctx *ctx, int dir, const double *u_face, double dt) {
         list = ctx->all_list;
         count = ctx->all_count;
     } else {
+        ProfScope ps(ctx, EBIT_PROF_BAND);
         CU(cudaMemsetAsync(ctx->band_count, 0, sizeof(int), ctx->stream));
         band_kernel<<<blocks_for(ctx->g.ntiles, 256, ctx->sms), 256, 0, ctx->stream>>>(
             ctx->g, ctx->tile_marker, ctx->band_list, ctx->band_count);
@@ -270,6 +321,7 @@ int ebit_front2vof(ebit_ctx *ctx, double *C, int flags) {
         list = ctx->all_list;
         count = ctx->all_count;
     } else {
+        ProfScope ps(ctx, EBIT_PROF_BAND);
         CU(cudaMemsetAsync(ctx->work_count, 0, sizeof(int), ctx->stream));
         take_flagged_kernel<<<blocks_for(ctx->g.ntiles, 256, ctx->sms), 256, 0, ctx->stream>>>(
             ctx->g, ctx->tile_dirty, ctx->work_list, ctx->work_count);
@@ -287,9 +339,13 @@ int ebit_front2vof(ebit_ctx *ctx, double *C, int flags) {
     a.list = list;
     a.count = count;
     a.tile_cchg = ctx->tile_cchg;
-    a.bad = ctx->ctr + C_N;
-    f2v_kernel<<<ctx->grid_f2v, 256, 0, ctx->stream>>>(a);
-    int r = launch_check(ctx, "f2v_kernel");
+    a.bad = ctx->ctr + C_F2V_BAD;
+    int r;
+    {
+        ProfScope ps(ctx, EBIT_PROF_F2V);
+        f2v_kernel<<<ctx->grid_f2v, 256, 0, ctx->stream>>>(a);
+        r = launch_check(ctx, "f2v_kernel");
+    }
     if (r) return r;
     ctx->last_C = C;
     return EBIT_OK;
@@ -305,6 +361,7 @@ int ebit_curvature(ebit_ctx *ctx, const double *C, double *kappa_h, uint8_t *sta
         list = ctx->all_list;
         count = ctx->all_count;
     } else {
+        ProfScope ps(ctx, EBIT_PROF_BAND);
         CU(cudaMemsetAsync(ctx->work_count, 0, sizeof(int), ctx->stream));
         band_kernel<<<blocks_for(ctx->g.ntiles, 256, ctx->sms), 256, 0, ctx->stream>>>(
             ctx->g, ctx->tile_cchg, ctx->work_list, ctx->work_count);
@@ -323,8 +380,12 @@ int ebit_curvature(ebit_ctx *ctx, const double *C, double *kappa_h, uint8_t *sta
     a.count = count;
     a.iface = nullptr;
     a.iface_count = nullptr;
-    hf_kernel<<<ctx->grid_hf, 256, 0, ctx->stream>>>(a);
-    int r = launch_check(ctx, "hf_kernel");
+    int r;
+    {
+        ProfScope ps(ctx, EBIT_PROF_HF);
+        hf_kernel<<<ctx->grid_hf, 256, 0, ctx->stream>>>(a);
+        r = launch_check(ctx, "hf_kernel");
+    }
     if (r) return r;
     ctx->last_kh = kappa_h;
     ctx->last_st = status;
@@ -333,21 +394,22 @@ int ebit_curvature(ebit_ctx *ctx, const double *C, double *kappa_h, uint8_t *sta
 
 int ebit_counters(ebit_ctx *ctx, ebit_counters_t *out) {
     if (!ctx || !out) return fail(ctx, EBIT_EINVAL, "ebit_counters: null argument");
-    unsigned long long h[C_N + 1];
+    unsigned long long h[C_TOTAL];
     CU(cudaMemcpyAsync(h, ctx->ctr, sizeof(h), cudaMemcpyDeviceToHost, ctx->stream));
     CU(cudaStreamSynchronize(ctx->stream));
     out->markers = (int64_t)h[C_MARKERS];
     out->annihilate = (int64_t)h[C_ANNIHILATE];
     out->multi = (int64_t)h[C_MULTI];
-    out->inconsistent = (int64_t)h[C_INCONSISTENT] + (int64_t)h[C_N];
+    out->inconsistent = (int64_t)h[C_INCONSISTENT] + (int64_t)h[C_F2V_BAD];
     out->cfl = (int64_t)h[C_CFL];
+    out->tiles = (int64_t)h[C_TILES];
     if (out->cfl) return fail(ctx, EBIT_ECFL, "a marker moved a full cell or more in one sweep");
     return out->inconsistent ? EBIT_WINCONSISTENT : EBIT_OK;
 }
 
 int ebit_reset_counters(ebit_ctx *ctx) {
     if (!ctx) return EBIT_EINVAL;
-    CU(cudaMemsetAsync(ctx->ctr, 0, (C_N + 1) * sizeof(unsigned long long), ctx->stream));
+    CU(cudaMemsetAsync(ctx->ctr, 0, C_TOTAL * sizeof(unsigned long long), ctx->stream));
     return EBIT_OK;
 }
 
@@ -367,6 +429,34 @@ int ebit_band_tiles(ebit_ctx *ctx) {
     if (cudaMemcpyAsync(&n, ctx->band_count, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream) != cudaSuccess) return -1;
     if (cudaStreamSynchronize(ctx->stream) != cudaSuccess) return -1;
     return n;
+}
+
+int ebit_profile(ebit_ctx *ctx, int enable) {
+    if (!ctx) return EBIT_EINVAL;
+    if (enable && ctx->ev.empty()) {
+        ctx->ev.resize(2 * 16384);
+        ctx->ev_kind.resize(16384);
+        for (auto &e : ctx->ev) CU(cudaEventCreate(&e));
+    }
+    int r = prof_drain(ctx);
+    if (r) return r;
+    ctx->prof_on = enable ? 1 : 0;
+    for (int k = 0; k < EBIT_PROF_KINDS; k++) {
+        ctx->prof_ms[k] = 0.0;
+        ctx->prof_n[k] = 0;
+    }
+    return EBIT_OK;
+}
+
+int ebit_profile_read(ebit_ctx *ctx, double *ms, int64_t *launches) {
+    if (!ctx || !ms || !launches) return fail(ctx, EBIT_EINVAL, "ebit_profile_read: null argument");
+    int r = prof_drain(ctx);
+    if (r) return r;
+    for (int k = 0; k < EBIT_PROF_KINDS; k++) {
+        ms[k] = ctx->prof_ms[k];
+        launches[k] = ctx->prof_n[k];
+    }
+    return EBIT_OK;
 }
 
 const char *ebit_last_error(const ebit_ctx *ctx) {

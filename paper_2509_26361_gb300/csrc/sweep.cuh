@@ -527,6 +527,7 @@ __global__ void __launch_bounds__(256) sweep_kernel(SweepArgs args) {
             args.tile_dirty[tile] = 1;
         }
     }
+    if (blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(args.ctr + C_TILES, (unsigned long long)ntl);
 }
 
 }  // namespace ebit

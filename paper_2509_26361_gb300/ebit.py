@@ -48,7 +48,7 @@ class _Desc(ctypes.Structure):
 
 
 class _Counters(ctypes.Structure):
-    _fields_ = [(n, ctypes.c_int64) for n in COUNTER_NAMES]
+    _fields_ = [(n, ctypes.c_int64) for n in COUNTER_NAMES + ("tiles",)]
 
 
 _lib = None
@@ -82,6 +82,8 @@ def load(build_if_missing: bool = True):
     lib.ebit_reset_counters.argtypes = [P]
     lib.ebit_sync.argtypes = [P]
     lib.ebit_band_tiles.argtypes = [P]
+    lib.ebit_profile.argtypes = [P, I]
+    lib.ebit_profile_read.argtypes = [P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int64)]
     lib.ebit_last_error.argtypes = [P]
     lib.ebit_last_error.restype = ctypes.c_char_p
     _lib = lib
@@ -165,7 +167,7 @@ def ebit_counters(ctx):
     c = _Counters()
     code = load().ebit_counters(ctx, ctypes.byref(c))
     _check(ctx, code)
-    return {k: int(getattr(c, k)) for k in COUNTER_NAMES}, code
+    return {k: int(getattr(c, k)) for k in COUNTER_NAMES + ("tiles",)}, code
 
 
 def ebit_reset_counters(ctx):
@@ -178,6 +180,20 @@ def ebit_sync(ctx):
 
 def ebit_band_tiles(ctx):
     return int(load().ebit_band_tiles(ctx))
+
+
+PROF_KINDS = ("sweep", "band", "f2v", "hf", "mlp", "k5", "k6", "k7")
+
+
+def ebit_profile(ctx, enable):
+    return _check(ctx, load().ebit_profile(ctx, int(bool(enable))))
+
+
+def ebit_profile_read(ctx):
+    ms = (ctypes.c_double * 8)()
+    n = (ctypes.c_int64 * 8)()
+    _check(ctx, load().ebit_profile_read(ctx, ms, n))
+    return {k: (float(ms[i]), int(n[i])) for i, k in enumerate(PROF_KINDS) if n[i]}
 
 
 def ebit_last_error(ctx):
@@ -247,3 +263,9 @@ class Grid:
 
     def band_tiles(self):
         return ebit_band_tiles(self.ctx)
+
+    def profile(self, enable=True):
+        return ebit_profile(self.ctx, enable)
+
+    def profile_read(self):
+        return ebit_profile_read(self.ctx)

@@ -74,6 +74,7 @@ def run_pair(n3, phi, faces, u, lams, steps, s_exact=None, dense=False, check_ev
     compare_state(g, ost, "final")
     cnt = g.counters()
     assert [cnt[k] for k in ebit.COUNTER_NAMES] == list(ocnt), (cnt, ocnt)
+    assert cnt["tiles"] > 0
     g.close()
     return ost
 
