@@ -185,11 +185,13 @@ int ebit_band_tiles(ebit_ctx *ctx);
  * launches on the context's stream with a pair of CUDA events and sums the
  * elapsed device time per kind.  Kinds (index into the arrays below): */
 enum {
-    EBIT_PROF_SWEEP = 0, /* split-sweep kernels */
+    EBIT_PROF_SWEEP = 0, /* split-sweep reconstruction kernels */
     EBIT_PROF_BAND = 1,  /* band/tile-list kernels and their memsets */
     EBIT_PROF_F2V = 2,   /* Front2VOF kernel */
     EBIT_PROF_HF = 3,    /* height-function kernel */
     EBIT_PROF_MLP = 4,   /* learned-curvature kernels */
+    EBIT_PROF_ADVECT = 5, /* marker advection (velocity interpolation) kernels */
+    EBIT_PROF_FP64 = 6,   /* sweep work lists: circle fits and face-centre colours */
     EBIT_PROF_KINDS = 8
 };
 /* enable != 0 switches timing on and zeroes the sums; 0 switches it off. */

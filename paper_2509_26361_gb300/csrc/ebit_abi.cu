@@ -40,10 +40,23 @@ struct ebit_ctx {
     int *all_list, *all_count;
     unsigned long long *ctr;  // C_N event counters + Front2VOF inconsistencies
     double *scratch;          // 3N doubles, allocated on first ebit_get_state
+    double *adv[3];           // advected marker coordinates of the current sweep (scratch)
+    int8_t *bin[3];           // floor(2 adv) (scratch)
+    unsigned *work[4];        // FP64 work lists of a sweep (scratch)
+    int *wcount;              // [4]
+    unsigned *cut;            // cells cut by the interface at the last Front2VOF
+    int *ncut;
+    unsigned *iface[2];       // interface cells of the last two curvature calls
+    int *niface;              // [2]
+    int cur_if;
+    unsigned *scan;           // interface cells found by a full curvature scan
+    int *nscan;
+    int *zero;                // a device int that stays 0
+    int sweeps_since_f2v;
     const double *last_C;
     const double *last_kh;
     const uint8_t *last_st;
-    int grid_sweep, grid_f2v, grid_hf;
+    int grid_sweep, grid_adv, grid_fp64, grid_f2v, grid_f2vl, grid_hf, grid_hfl;
     // per-kernel CUDA-event timing (ebit_profile)
     int prof_on;
     std::vector<cudaEvent_t> ev;
@@ -74,6 +87,7 @@ int launch_check(ebit_ctx *ctx, const char *what) {
 }
 
 int mark_all(ebit_ctx *ctx) {
+    ctx->sweeps_since_f2v = 1;
     CU(cudaMemsetAsync(ctx->tile_marker, 1, ctx->g.ntiles, ctx->stream));
     CU(cudaMemsetAsync(ctx->tile_dirty, 1, ctx->g.ntiles, ctx->stream));
     ctx->last_C = nullptr;
@@ -134,9 +148,21 @@ struct ProfScope {
 
 template <int D>
 int sweep_launch(ebit_ctx *ctx, const SweepArgs &args) {
-    ProfScope ps(ctx, EBIT_PROF_SWEEP);
-    sweep_kernel<D><<<ctx->grid_sweep, 256, 0, ctx->stream>>>(args);
-    return launch_check(ctx, "sweep_kernel");
+    {
+        ProfScope ps(ctx, EBIT_PROF_ADVECT);
+        advect_kernel<D><<<ctx->grid_adv, 256, 0, ctx->stream>>>(args);
+        int r = launch_check(ctx, "advect_kernel");
+        if (r) return r;
+    }
+    {
+        ProfScope ps(ctx, EBIT_PROF_SWEEP);
+        sweep_kernel<D><<<ctx->grid_sweep, 256, 0, ctx->stream>>>(args);
+        int r = launch_check(ctx, "sweep_kernel");
+        if (r) return r;
+    }
+    ProfScope ps(ctx, EBIT_PROF_FP64);
+    fp64_kernel<D><<<ctx->grid_fp64, 128, 0, ctx->stream>>>(args);
+    return launch_check(ctx, "fp64_kernel");
 }
 
 }  // namespace
@@ -152,6 +178,23 @@ int ebit_create(const ebit_desc *desc, ebit_ctx **out) {
     if ((long long)desc->nx * desc->ny * desc->nz >= (1LL << 31)) return EBIT_EINVAL;
     ctx = new ebit_ctx();
     std::memset(&ctx->g, 0, sizeof(ctx->g));
+    for (int b = 0; b < 2; b++) {
+        ctx->cb[b] = nullptr;
+        for (int a = 0; a < 3; a++) ctx->s[b][a] = nullptr;
+    }
+    for (int a = 0; a < 3; a++) {
+        ctx->adv[a] = nullptr;
+        ctx->bin[a] = nullptr;
+    }
+    for (int k = 0; k < 4; k++) ctx->work[k] = nullptr;
+    ctx->iface[0] = ctx->iface[1] = nullptr;
+    ctx->wcount = ctx->ncut = ctx->niface = ctx->nscan = ctx->zero = nullptr;
+    ctx->cut = ctx->scan = nullptr;
+    ctx->cur_if = 0;
+    ctx->sweeps_since_f2v = 0;
+    ctx->tile_marker = ctx->tile_dirty = ctx->tile_cchg = nullptr;
+    ctx->band_list = ctx->band_count = ctx->work_list = ctx->work_count = ctx->all_list = ctx->all_count = nullptr;
+    ctx->ctr = nullptr;
     ctx->g.n[0] = desc->nx;
     ctx->g.n[1] = desc->ny;
     ctx->g.n[2] = desc->nz;
@@ -170,9 +213,17 @@ int ebit_create(const ebit_desc *desc, ebit_ctx **out) {
     auto alloc = [&](void **p, size_t bytes) -> bool { return cudaMalloc(p, bytes) == cudaSuccess; };
     bool ok = true;
     for (int b = 0; b < 2 && ok; b++) {
-        ok = ok && alloc((void **)&ctx->cb[b], ctx->N);
+        ok = ok && alloc((void **)&ctx->cb[b], (ctx->N + 7) & ~7LL);  // whole 32-bit words
         for (int a = 0; a < 3 && ok; a++) ok = ok && alloc((void **)&ctx->s[b][a], ctx->N * sizeof(double));
     }
+    for (int a = 0; a < 3 && ok; a++)
+        ok = ok && alloc((void **)&ctx->adv[a], ctx->N * sizeof(double)) && alloc((void **)&ctx->bin[a], ctx->N);
+    for (int k = 0; k < 4 && ok; k++) ok = ok && alloc((void **)&ctx->work[k], ctx->N * sizeof(unsigned));
+    ok = ok && alloc((void **)&ctx->cut, ctx->N * sizeof(unsigned)) && alloc((void **)&ctx->scan, ctx->N * sizeof(unsigned)) &&
+         alloc((void **)&ctx->iface[0], ctx->N * sizeof(unsigned)) &&
+         alloc((void **)&ctx->iface[1], ctx->N * sizeof(unsigned)) && alloc((void **)&ctx->wcount, 4 * sizeof(int)) &&
+         alloc((void **)&ctx->ncut, sizeof(int)) && alloc((void **)&ctx->niface, 2 * sizeof(int)) &&
+         alloc((void **)&ctx->nscan, sizeof(int)) && alloc((void **)&ctx->zero, sizeof(int));
     int nt = ctx->g.ntiles;
     ok = ok && alloc((void **)&ctx->tile_marker, nt) && alloc((void **)&ctx->tile_dirty, nt) &&
          alloc((void **)&ctx->tile_cchg, nt) && alloc((void **)&ctx->band_list, nt * sizeof(int)) &&
@@ -188,10 +239,23 @@ int ebit_create(const ebit_desc *desc, ebit_ctx **out) {
     int occ = 1;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, sweep_kernel<0>, 256, 0);
     ctx->grid_sweep = std::max(1, std::min(nt, ctx->sms * std::max(occ, 1)));
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, f2v_kernel, 256, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, advect_kernel<0>, 256, 0);
+    ctx->grid_adv = std::max(1, std::min(nt, ctx->sms * std::max(occ, 1)));
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fp64_kernel<0>, 128, 0);
+    ctx->grid_fp64 = ctx->sms * std::max(occ, 1);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, f2v_band_kernel, 256, 0);
     ctx->grid_f2v = std::max(1, std::min(nt, ctx->sms * std::max(occ, 1)));
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, hf_kernel, 256, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, f2v_list_kernel, 128, 0);
+    ctx->grid_f2vl = ctx->sms * std::max(occ, 1);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, hf_scan_kernel, 256, 0);
     ctx->grid_hf = std::max(1, std::min(nt, ctx->sms * std::max(occ, 1)));
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, hf_list_kernel, 128, 0);
+    ctx->grid_hfl = ctx->sms * std::max(occ, 1);
+    cudaMemsetAsync(ctx->wcount, 0, 4 * sizeof(int), ctx->stream);
+    cudaMemsetAsync(ctx->ncut, 0, sizeof(int), ctx->stream);
+    cudaMemsetAsync(ctx->niface, 0, 2 * sizeof(int), ctx->stream);
+    cudaMemsetAsync(ctx->nscan, 0, sizeof(int), ctx->stream);
+    cudaMemsetAsync(ctx->zero, 0, sizeof(int), ctx->stream);
     iota_kernel<<<blocks_for(nt, 256, ctx->sms), 256, 0, ctx->stream>>>(ctx->all_list, nt, ctx->all_count);
     if (cudaMemsetAsync(ctx->ctr, 0, C_TOTAL * sizeof(unsigned long long), ctx->stream) != cudaSuccess ||
         cudaGetLastError() != cudaSuccess) {
@@ -227,6 +291,20 @@ void ebit_destroy(ebit_ctx *ctx) {
     cudaFree(ctx->all_count);
     cudaFree(ctx->ctr);
     cudaFree(ctx->scratch);
+    for (int a = 0; a < 3; a++) {
+        cudaFree(ctx->adv[a]);
+        cudaFree(ctx->bin[a]);
+    }
+    for (int k = 0; k < 4; k++) cudaFree(ctx->work[k]);
+    cudaFree(ctx->cut);
+    cudaFree(ctx->scan);
+    cudaFree(ctx->iface[0]);
+    cudaFree(ctx->iface[1]);
+    cudaFree(ctx->wcount);
+    cudaFree(ctx->ncut);
+    cudaFree(ctx->niface);
+    cudaFree(ctx->nscan);
+    cudaFree(ctx->zero);
     for (cudaEvent_t e : ctx->ev) cudaEventDestroy(e);
     delete ctx;
 }
@@ -293,7 +371,11 @@ int ebit_advect_sweep(ebit_ctx *ctx, int dir, const double *u_face, double dt) {
     for (int k = 0; k < 3; k++) {
         a.s[k] = ctx->s[c][k];
         a.so[k] = ctx->s[o][k];
+        a.adv[k] = ctx->adv[k];
+        a.bin[k] = ctx->bin[k];
     }
+    for (int k = 0; k < 4; k++) a.work[k] = ctx->work[k];
+    a.wcount = ctx->wcount;
     a.u = u_face;
     a.lam = dt / ctx->h;
     a.list = list;
@@ -309,6 +391,7 @@ int ebit_advect_sweep(ebit_ctx *ctx, int dir, const double *u_face, double dt) {
     }
     if (r) return r;
     ctx->cur = o;
+    ctx->sweeps_since_f2v++;
     return EBIT_OK;
 }
 
@@ -316,6 +399,9 @@ int ebit_front2vof(ebit_ctx *ctx, double *C, int flags) {
     if (!ctx || !C) return fail(ctx, EBIT_EINVAL, "ebit_front2vof: null argument");
     const int *list, *count;
     bool full = (flags & EBIT_FULL) || ctx->dense || C != ctx->last_C;
+    // nothing was swept since the last call on this buffer: C is current
+    if (!full && ctx->sweeps_since_f2v == 0) return EBIT_OK;
+    CU(cudaMemsetAsync(ctx->ncut, 0, sizeof(int), ctx->stream));
     if (full) {
         CU(cudaMemsetAsync(ctx->tile_dirty, 0, ctx->g.ntiles, ctx->stream));
         list = ctx->all_list;
@@ -338,55 +424,62 @@ int ebit_front2vof(ebit_ctx *ctx, double *C, int flags) {
     a.C = C;
     a.list = list;
     a.count = count;
-    a.tile_cchg = ctx->tile_cchg;
+    a.cut = ctx->cut;
+    a.ncut = ctx->ncut;
     a.bad = ctx->ctr + C_F2V_BAD;
     int r;
     {
         ProfScope ps(ctx, EBIT_PROF_F2V);
-        f2v_kernel<<<ctx->grid_f2v, 256, 0, ctx->stream>>>(a);
-        r = launch_check(ctx, "f2v_kernel");
+        f2v_band_kernel<<<ctx->grid_f2v, 256, 0, ctx->stream>>>(a);
+        r = launch_check(ctx, "f2v_band_kernel");
+        if (r) return r;
+        f2v_list_kernel<<<ctx->grid_f2vl, 128, 0, ctx->stream>>>(a);
+        r = launch_check(ctx, "f2v_list_kernel");
     }
     if (r) return r;
     ctx->last_C = C;
+    ctx->sweeps_since_f2v = 0;
     return EBIT_OK;
 }
 
 int ebit_curvature(ebit_ctx *ctx, const double *C, double *kappa_h, uint8_t *status, int mode, int flags) {
     if (!ctx || !C || !kappa_h || !status) return fail(ctx, EBIT_EINVAL, "ebit_curvature: null argument");
     if (mode != EBIT_CURV_HF) return fail(ctx, EBIT_EINVAL, "ebit_curvature: mode not available");
-    const int *list, *count;
     bool full = (flags & EBIT_FULL) || ctx->dense || C != ctx->last_C || kappa_h != ctx->last_kh ||
                 status != ctx->last_st;
-    if (full) {
-        list = ctx->all_list;
-        count = ctx->all_count;
-    } else {
-        ProfScope ps(ctx, EBIT_PROF_BAND);
-        CU(cudaMemsetAsync(ctx->work_count, 0, sizeof(int), ctx->stream));
-        band_kernel<<<blocks_for(ctx->g.ntiles, 256, ctx->sms), 256, 0, ctx->stream>>>(
-            ctx->g, ctx->tile_cchg, ctx->work_list, ctx->work_count);
-        int r = launch_check(ctx, "band_kernel");
-        if (r) return r;
-        list = ctx->work_list;
-        count = ctx->work_count;
-    }
-    CU(cudaMemsetAsync(ctx->tile_cchg, 0, ctx->g.ntiles, ctx->stream));
+    const int nw = ctx->cur_if ^ 1;
     HFArgs a;
     a.g = ctx->g;
     a.C = C;
     a.kh = kappa_h;
     a.st = status;
-    a.list = list;
-    a.count = count;
-    a.iface = nullptr;
-    a.iface_count = nullptr;
-    int r;
-    {
-        ProfScope ps(ctx, EBIT_PROF_HF);
-        hf_kernel<<<ctx->grid_hf, 256, 0, ctx->stream>>>(a);
-        r = launch_check(ctx, "hf_kernel");
+    a.iface = ctx->iface[nw];
+    a.niface = ctx->niface + nw;
+    a.list = ctx->all_list;
+    a.count = ctx->all_count;
+    CU(cudaMemsetAsync(ctx->niface + nw, 0, sizeof(int), ctx->stream));
+    ProfScope ps(ctx, EBIT_PROF_HF);
+    if (full) {
+        // any C: scan every tile, reset non-interface cells, list the interface cells
+        CU(cudaMemsetAsync(ctx->nscan, 0, sizeof(int), ctx->stream));
+        hf_scan_kernel<<<ctx->grid_hf, 256, 0, ctx->stream>>>(a, ctx->scan, ctx->nscan);
+        int r = launch_check(ctx, "hf_scan_kernel");
+        if (r) return r;
+        a.prev = ctx->iface[ctx->cur_if];
+        a.nprev = ctx->zero;
+        a.cand = ctx->scan;
+        a.ncand = ctx->nscan;
+    } else {
+        // C is this context's Front2VOF output: its cut cells hold every interface cell
+        a.prev = ctx->iface[ctx->cur_if];
+        a.nprev = ctx->niface + ctx->cur_if;
+        a.cand = ctx->cut;
+        a.ncand = ctx->ncut;
     }
+    hf_list_kernel<<<ctx->grid_hfl, 128, 0, ctx->stream>>>(a);
+    int r = launch_check(ctx, "hf_list_kernel");
     if (r) return r;
+    ctx->cur_if = nw;
     ctx->last_kh = kappa_h;
     ctx->last_st = status;
     return EBIT_OK;

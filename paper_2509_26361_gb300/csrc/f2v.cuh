@@ -29,9 +29,10 @@ struct F2VArgs {
     const uint8_t *__restrict__ cb;
     const double *__restrict__ s[3];
     double *__restrict__ C;
-    const int *__restrict__ list;
+    const int *__restrict__ list;    // tiles to recompute
     const int *__restrict__ count;
-    uint8_t *tile_cchg;   // per tile: C rewritten (for the curvature band)
+    unsigned *__restrict__ cut;      // cells cut by the interface (output list)
+    int *__restrict__ ncut;
     unsigned long long *bad;
 };
 
@@ -165,61 +166,241 @@ __device__ __noinline__ double cell_fraction(int K, const int F[6], const double
     return V;
 }
 
-__global__ void __launch_bounds__(256) f2v_kernel(F2VArgs a) {
+__device__ __forceinline__ void cell_ids(const Grid &g, int x, int y, int z, int ids[8]) {
+#pragma unroll
+    for (int cid = 0; cid < 8; cid++) ids[cid] = lin(g, x + (cid & 1), y + ((cid >> 1) & 1), z + ((cid >> 2) & 1));
+}
+
+// Band pass (integer only): a cell with eight equal corner colours holds no
+// marker and its fraction is that colour (written as a bit pattern); the other
+// cells go to the global cut list.
+__global__ void __launch_bounds__(256) f2v_band_kernel(F2VArgs a) {
     const int ntl = *a.count;
     for (int li = blockIdx.x; li < ntl; li += gridDim.x) {
         const int tile = a.list[li];
         int o[3];
         tile_origin(a.g, tile, o);
-        unsigned nbad = 0;
         for (int c = threadIdx.x; c < TILE_CELLS; c += blockDim.x) {
             int x = o[0] + (c & 7), y = o[1] + ((c >> 3) & 7), z = o[2] + (c >> 6);
-            if (x >= a.g.n[0] || y >= a.g.n[1] || z >= a.g.n[2]) continue;
-            int K = 0;
-            int ids[8];
-            for (int cid = 0; cid < 8; cid++) {
-                ids[cid] = lin(a.g, x + (cid & 1), y + ((cid >> 1) & 1), z + ((cid >> 2) & 1));
-                K |= (__ldg(a.cb + ids[cid]) & 1) << cid;
+            bool cutc = false;
+            int id0 = 0;
+            if (x < a.g.n[0] && y < a.g.n[1] && z < a.g.n[2]) {
+                int ids[8];
+                cell_ids(a.g, x, y, z, ids);
+                int K = 0;
+#pragma unroll
+                for (int cid = 0; cid < 8; cid++) K |= (__ldg(a.cb + ids[cid]) & 1) << cid;
+                id0 = ids[0];
+                if (K == 0 || K == 255)
+                    reinterpret_cast<unsigned long long *>(a.C)[id0] = (K & 1) ? 0x3FF0000000000000ull : 0ull;
+                else
+                    cutc = true;
             }
-            double val;
-            if (K == 0 || K == 255) {
-                val = (double)(K & 1);
-            } else {
-                const uint8_t b0 = __ldg(a.cb + ids[0]);
-                int F[6];
-                F[0] = (b0 >> 1) & 1;
-                F[1] = (__ldg(a.cb + ids[1]) >> 1) & 1;
-                F[2] = (b0 >> 2) & 1;
-                F[3] = (__ldg(a.cb + ids[2]) >> 2) & 1;
-                F[4] = (b0 >> 3) & 1;
-                F[5] = (__ldg(a.cb + ids[4]) >> 3) & 1;
-                double E[12];
-                // x-edges at corners (0,dy,dz); y-edges at (dx,0,dz); z-edges at (dx,dy,0)
-                const int xe[4] = {ids[0], ids[2], ids[4], ids[6]};
-                const int xo[4] = {ids[1], ids[3], ids[5], ids[7]};
-                const int ye[4] = {ids[0], ids[1], ids[4], ids[5]};
-                const int yo[4] = {ids[2], ids[3], ids[6], ids[7]};
-                const int ze[4] = {ids[0], ids[1], ids[2], ids[3]};
-                const int zo[4] = {ids[4], ids[5], ids[6], ids[7]};
-                const int cx[4] = {0, 2, 4, 6}, cxo[4] = {1, 3, 5, 7};
-                const int cy[4] = {0, 1, 4, 5}, cyo[4] = {2, 3, 6, 7};
-                const int cz[4] = {0, 1, 2, 3}, czo[4] = {4, 5, 6, 7};
-                for (int r = 0; r < 4; r++) {
-                    E[r] = (((K >> cx[r]) ^ (K >> cxo[r])) & 1) ? __ldg(a.s[0] + xe[r]) : 0.0;
-                    E[4 + r] = (((K >> cy[r]) ^ (K >> cyo[r])) & 1) ? __ldg(a.s[1] + ye[r]) : 0.0;
-                    E[8 + r] = (((K >> cz[r]) ^ (K >> czo[r])) & 1) ? __ldg(a.s[2] + ze[r]) : 0.0;
-                }
-                (void)xo; (void)yo; (void)zo;
-                int bad = 0;
-                val = cell_fraction(K, F, E, &bad);
-                nbad += bad;
+            const unsigned full = 0xffffffffu;
+            unsigned m = __ballot_sync(full, cutc);
+            if (m) {
+                const int lane = threadIdx.x & 31, leader = __ffs(m) - 1;
+                int base = 0;
+                if (lane == leader) base = atomicAdd(a.ncut, __popc(m));
+                base = __shfl_sync(full, base, leader);
+                if (cutc) a.cut[base + __popc(m & ((1u << lane) - 1u))] = (unsigned)id0;
             }
-            a.C[ids[0]] = val;
         }
-        unsigned v = __reduce_add_sync(0xffffffffu, nbad);
-        if ((threadIdx.x & 31) == 0 && v) atomicAdd(a.bad, (unsigned long long)v);
-        if (threadIdx.x == 0 && a.tile_cchg) a.tile_cchg[tile] = 1;
     }
+}
+
+// Per-cell reconstruction used by the list kernel.  Same geometry as
+// cell_fraction (the reference form above, kept for the exhaustive checks), in
+// a register-only formulation:
+//   * face areas from closed forms -- a corner cut is the triangle l1*l2/2, a
+//     cut across the face the trapezoid (l1 + l2)/2, three corners the
+//     complement of a corner cut (l = distances from the cut corner or side);
+//   * loops walked through successor codes packed 4 bits per edge;
+//   * sum_i det(c, p_i, p_i+1) = c . sum_i (p_i x p_i+1) with c the mean of
+//     the loop's markers (Eq. 7) -- the same sum reassociated, so C agrees
+//     with the fan-by-fan evaluation to rounding (about 1e-16).
+// face corner k -> k+1 runs along +axis when the edge goes from its lower to its
+// upper node: kFaceFwd[f][k] = 1 (then the marker sits at distance s from
+// corner k).
+__constant__ int8_t kFaceFwd[6][4] = {
+    {1, 1, 0, 0}, {1, 1, 0, 0}, {1, 1, 0, 0}, {1, 1, 0, 0}, {1, 1, 0, 0}, {1, 1, 0, 0}};
+
+__device__ __forceinline__ double sel01(int b) { return __longlong_as_double(b ? 0x3FF0000000000000ll : 0ll); }
+
+__device__ __forceinline__ void marker_xyz(int e, double s, double &x, double &y, double &z) {
+    const int ax = e >> 2, r = e & 3;
+    const double u = sel01(r & 1), v = sel01(r >> 1);
+    x = ax == 0 ? s : u;
+    y = ax == 1 ? s : (ax == 0 ? u : v);
+    z = ax == 2 ? s : v;
+}
+
+// distance from face corner k to the marker on face edge k (corner k -> k+1)
+// and from corner k+1 to it
+__device__ __forceinline__ double dist_from_k(int fwd, double s) { return fwd ? s : 1.0 - s; }
+__device__ __forceinline__ double dist_from_k1(int fwd, double s) { return fwd ? 1.0 - s : s; }
+
+template <int F>
+__device__ __forceinline__ double face_area_and_links(int K, int phif, const double *sE, int stride,
+                                                      unsigned long long &nxt) {
+    int col[4], ed[4], fw[4];
+#pragma unroll
+    for (int k = 0; k < 4; k++) {
+        col[k] = (K >> kFaceCorner[F][k]) & 1;
+        ed[k] = kFaceEdge[F][k];
+        fw[k] = kFaceFwd[F][k];
+    }
+    int mm = 0;
+#pragma unroll
+    for (int k = 0; k < 4; k++) mm |= (col[k] != col[(k + 1) & 3]) << k;
+    const int nm = __popc(mm);
+    double area = 0.0;
+    auto link = [&](int from, int to) {
+        nxt = (nxt & ~(0xFull << (4 * from))) | ((unsigned long long)to << (4 * from));
+    };
+    if (nm == 0) {
+        area = sel01(col[0]);
+    } else if (nm == 2) {
+        const int ea = __ffs(mm) - 1, eb = 31 - __clz(mm);
+        const int arc = col[(ea + 1) & 3];
+        if (arc) link(ed[eb], ed[ea]);
+        else link(ed[ea], ed[eb]);
+        if (F & 1) {
+            const double sa = sE[ed[ea] * stride], sb = sE[ed[eb] * stride];
+            double R;
+            if (eb == ea + 1) {
+                // triangle at corner ea+1: legs along E_ea (to corner ea+1) and E_eb (from it)
+                R = 0.5 * (dist_from_k1(fw[ea], sa) * dist_from_k(fw[eb], sb));
+            } else if (eb == ea + 2) {
+                // corners ea+1, ea+2 on the opposite parallel edges E_ea, E_eb
+                R = 0.5 * (dist_from_k1(fw[ea], sa) + dist_from_k(fw[eb], sb));
+            } else {
+                // three corners: complement of the triangle at corner ea (= eb + 1)
+                R = 1.0 - 0.5 * (dist_from_k(fw[ea], sa) * dist_from_k1(fw[eb], sb));
+            }
+            area = arc ? R : 1.0 - R;
+        }
+    } else if (nm == 4) {
+        double T = 0.0;
+#pragma unroll
+        for (int m = 0; m < 4; m++) {
+            if (col[m] == phif) continue;
+            const int ep = ed[(m + 3) & 3], en = ed[m];
+            if (col[m]) link(en, ep);
+            else link(ep, en);
+            if (F & 1) T += 0.5 * (dist_from_k1(fw[(m + 3) & 3], sE[ep * stride]) * dist_from_k(fw[m], sE[en * stride]));
+        }
+        area = (1 - phif) ? T : 1.0 - T;
+    }
+    return area;
+}
+
+__device__ double cell_fraction_fast(int K, const int Fc[6], const double *sE, int stride, int *bad) {
+    unsigned long long nxt = ~0ull;
+    double A1 = 0.0, A2 = 0.0, A3 = 0.0;
+    face_area_and_links<0>(K, Fc[0], sE, stride, nxt);
+    A1 = face_area_and_links<1>(K, Fc[1], sE, stride, nxt);
+    face_area_and_links<2>(K, Fc[2], sE, stride, nxt);
+    A2 = face_area_and_links<3>(K, Fc[3], sE, stride, nxt);
+    face_area_and_links<4>(K, Fc[4], sE, stride, nxt);
+    A3 = face_area_and_links<5>(K, Fc[5], sE, stride, nxt);
+    // markers: edges whose end colours differ
+    unsigned has = 0;
+    const int cx[4] = {0, 2, 4, 6}, cy[4] = {0, 1, 4, 5}, cz[4] = {0, 1, 2, 3};
+#pragma unroll
+    for (int r = 0; r < 4; r++) {
+        has |= (unsigned)(((K >> cx[r]) ^ (K >> (cx[r] + 1))) & 1) << r;
+        has |= (unsigned)(((K >> cy[r]) ^ (K >> (cy[r] + 2))) & 1) << (4 + r);
+        has |= (unsigned)(((K >> cz[r]) ^ (K >> (cz[r] + 4))) & 1) << (8 + r);
+    }
+    if (!has) return sel01(K & 1);
+    unsigned todo = has;
+    double acc = 0.0;
+    while (todo) {
+        const int e0 = __ffs(todo) - 1;
+        double x0, y0, z0;
+        marker_xyz(e0, sE[e0 * stride], x0, y0, z0);
+        double sx = x0, sy = y0, sz = z0;
+        double px = x0, py = y0, pz = z0;
+        double cxs = 0.0, cys = 0.0, czs = 0.0;
+        int len = 1, e = e0;
+        todo &= ~(1u << e0);
+        bool closed = false;
+        for (int guard = 0; guard < 12; guard++) {
+            int nx_ = (int)((nxt >> (4 * e)) & 0xF);
+            if (nx_ == 0xF) break;
+            double qx, qy, qz;
+            if (nx_ == e0) {
+                qx = x0; qy = y0; qz = z0;
+            } else {
+                if (!((todo >> nx_) & 1)) break;
+                marker_xyz(nx_, sE[nx_ * stride], qx, qy, qz);
+            }
+            cxs += py * qz - pz * qy;
+            cys += pz * qx - px * qz;
+            czs += px * qy - py * qx;
+            if (nx_ == e0) {
+                closed = true;
+                break;
+            }
+            sx += qx; sy += qy; sz += qz;
+            px = qx; py = qy; pz = qz;
+            todo &= ~(1u << nx_);
+            e = nx_;
+            len++;
+        }
+        if (!closed) {
+            *bad = 1;
+            continue;
+        }
+        acc += (sx * cxs + sy * cys + sz * czs) / (double)len;
+    }
+    double V = (2.0 * ((A1 + A2) + A3) - acc) / 6.0;
+    if (V < 0.0) V = 0.0;
+    if (V > 1.0) V = 1.0;
+    return V;
+}
+
+// FP64 pass: one thread per cut cell, full warps.
+__global__ void __launch_bounds__(128) f2v_list_kernel(F2VArgs a) {
+    __shared__ double sE[12 * 128];
+    const int n = *a.ncut;
+    unsigned nbad = 0;
+    const int stride = gridDim.x * blockDim.x;
+    const int iters = (n + stride - 1) / stride;
+    double *myE = sE + threadIdx.x;
+    for (int it = 0; it < iters; it++) {
+        int t = it * stride + blockIdx.x * blockDim.x + threadIdx.x;
+        if (t >= n) continue;
+        const int id = (int)a.cut[t];
+        const int x = id % a.g.n[0], y = (id / a.g.n[0]) % a.g.n[1], z = id / (a.g.n[0] * a.g.n[1]);
+        int ids[8];
+        cell_ids(a.g, x, y, z, ids);
+        int K = 0;
+#pragma unroll
+        for (int cid = 0; cid < 8; cid++) K |= (__ldg(a.cb + ids[cid]) & 1) << cid;
+        const uint8_t b0 = __ldg(a.cb + ids[0]);
+        int F[6];
+        F[0] = (b0 >> 1) & 1;
+        F[1] = (__ldg(a.cb + ids[1]) >> 1) & 1;
+        F[2] = (b0 >> 2) & 1;
+        F[3] = (__ldg(a.cb + ids[2]) >> 2) & 1;
+        F[4] = (b0 >> 3) & 1;
+        F[5] = (__ldg(a.cb + ids[4]) >> 3) & 1;
+        // x-edges at corners (0,dy,dz), y-edges at (dx,0,dz), z-edges at (dx,dy,0)
+        const int cx[4] = {0, 2, 4, 6}, cy[4] = {0, 1, 4, 5}, cz[4] = {0, 1, 2, 3};
+#pragma unroll
+        for (int r = 0; r < 4; r++) {
+            myE[r * 128] = (((K >> cx[r]) ^ (K >> (cx[r] + 1))) & 1) ? __ldg(a.s[0] + ids[cx[r]]) : 0.0;
+            myE[(4 + r) * 128] = (((K >> cy[r]) ^ (K >> (cy[r] + 2))) & 1) ? __ldg(a.s[1] + ids[cy[r]]) : 0.0;
+            myE[(8 + r) * 128] = (((K >> cz[r]) ^ (K >> (cz[r] + 4))) & 1) ? __ldg(a.s[2] + ids[cz[r]]) : 0.0;
+        }
+        int bad = 0;
+        a.C[id] = cell_fraction_fast(K, F, myE, 128, &bad);
+        nbad += bad;
+    }
+    unsigned v = __reduce_add_sync(0xffffffffu, nbad);
+    if ((threadIdx.x & 31) == 0 && v) atomicAdd(a.bad, (unsigned long long)v);
 }
 
 }  // namespace ebit

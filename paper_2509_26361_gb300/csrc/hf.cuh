@@ -23,83 +23,189 @@ struct HFArgs {
     const double *__restrict__ C;
     double *__restrict__ kh;
     uint8_t *__restrict__ st;
-    const int *__restrict__ list;
+    const unsigned *__restrict__ prev;  // interface cells of the previous call
+    const int *__restrict__ nprev;
+    const unsigned *__restrict__ cand;  // candidate cells (all interface cells are among them)
+    const int *__restrict__ ncand;
+    unsigned *__restrict__ iface;       // interface cells of this call (output list)
+    int *__restrict__ niface;
+    const int *__restrict__ list;       // tiles, for the full scan
     const int *__restrict__ count;
-    int *__restrict__ iface;        // optional: compacted interface-cell list
-    int *__restrict__ iface_count;
 };
 
-__device__ __forceinline__ double cval(const HFArgs &a, int x, int y, int z) {
-    return __ldg(a.C + lin(a.g, x, y, z));
+// 0 < C < 1 on the bit pattern (C is never negative; -0 and NaN fail as in IEEE)
+__device__ __forceinline__ bool is_interface(double c) {
+    long long b = __double_as_longlong(c);
+    return b > 0 && b < 0x3FF0000000000000ll;
 }
 
-__device__ __noinline__ int hf_cell(const HFArgs &a, int x, int y, int z, double *out) {
+// C at offset (dx, dy, dz) from the cell; WRAP = false uses direct strides (the
+// cell is at least HFH+1 cells from every periodic seam)
+template <bool WRAP>
+struct CAccess {
+    const double *__restrict__ C;
+    Grid g;
+    int x, y, z, id, sy, sz;
+    __device__ __forceinline__ double operator()(int dx, int dy, int dz) const {
+        if (WRAP) return __ldg(C + lin(g, x + dx, y + dy, z + dz));
+        return __ldg(C + id + dx + dy * sy + dz * sz);
+    }
+};
+
+// heights along axis D on the 3x3 stencil of 9-cell columns; returns false when
+// a column's ends are not pure with the reference phase on the expected side
+template <int D, bool WRAP>
+__device__ __forceinline__ bool hf_axis(const CAccess<WRAP> &c, bool below, double *out) {
+    constexpr int T1 = (D == 0) ? 1 : 0, T2 = (D == 2) ? 1 : 2;
+    double eta[3][3];
+    bool ok = true;
+#pragma unroll
+    for (int b2 = -1; b2 <= 1; b2++)
+#pragma unroll
+        for (int b1 = -1; b1 <= 1; b1++) {
+            double H = 0.0, lo = 0.0, hi = 0.0;
+#pragma unroll
+            for (int m = -HFH; m <= HFH; m++) {
+                int o[3] = {0, 0, 0};
+                o[D] += m;
+                o[T1] += b1;
+                o[T2] += b2;
+                double cv = c(o[0], o[1], o[2]);
+                H += cv;
+                if (m == -HFH) lo = cv;
+                if (m == HFH) hi = cv;
+            }
+            ok = ok && (below ? (lo == 1.0 && hi == 0.0) : (lo == 0.0 && hi == 1.0));
+            eta[b1 + 1][b2 + 1] = below ? H - (HFH + 0.5) : (HFH + 0.5) - H;
+        }
+    if (!ok) return false;
+    double hx = (eta[2][1] - eta[0][1]) * 0.5;
+    double hy = (eta[1][2] - eta[1][0]) * 0.5;
+    double hxx = (eta[2][1] + eta[0][1]) - 2.0 * eta[1][1];
+    double hyy = (eta[1][2] + eta[1][0]) - 2.0 * eta[1][1];
+    double hxy = ((eta[2][2] - eta[2][0]) - (eta[0][2] - eta[0][0])) * 0.25;
+    double num = (1.0 + hy * hy) * hxx + (1.0 + hx * hx) * hyy - 2.0 * hx * hy * hxy;
+    double q2 = 1.0 + hx * hx + hy * hy;
+    double den = q2 * sqrt(q2);
+    double kap = num / den;
+    *out = below ? -kap : kap;
+    return true;
+}
+
+template <bool WRAP>
+__device__ int hf_cell_impl(const CAccess<WRAP> &c, double *out) {
+    // the 3x3x3 block once; Youngs sums in the order (b2 outer, b1 inner)
+    double blk[3][3][3];
+#pragma unroll
+    for (int dz = -1; dz <= 1; dz++)
+#pragma unroll
+        for (int dy = -1; dy <= 1; dy++)
+#pragma unroll
+            for (int dx = -1; dx <= 1; dx++) blk[dz + 1][dy + 1][dx + 1] = c(dx, dy, dz);
     const double w[3] = {1.0, 2.0, 1.0};
     double n[3];
-    const int p[3] = {x, y, z};
+#pragma unroll
     for (int d = 0; d < 3; d++) {
-        int t1 = (d == 0) ? 1 : 0, t2 = (d == 2) ? 1 : 2;
+        const int t1 = (d == 0) ? 1 : 0, t2 = (d == 2) ? 1 : 2;
         double gsum = 0.0;
+#pragma unroll
         for (int b2 = -1; b2 <= 1; b2++)
+#pragma unroll
             for (int b1 = -1; b1 <= 1; b1++) {
-                int qp[3] = {p[0], p[1], p[2]}, qm[3] = {p[0], p[1], p[2]};
-                qp[d] += 1;
-                qm[d] -= 1;
-                qp[t1] += b1;
-                qm[t1] += b1;
-                qp[t2] += b2;
-                qm[t2] += b2;
-                gsum += (w[b1 + 1] * w[b2 + 1]) * (cval(a, qp[0], qp[1], qp[2]) - cval(a, qm[0], qm[1], qm[2]));
+                int op[3] = {0, 0, 0}, om[3] = {0, 0, 0};
+                op[d] = 1;
+                om[d] = -1;
+                op[t1] += b1;
+                om[t1] += b1;
+                op[t2] += b2;
+                om[t2] += b2;
+                gsum += (w[b1 + 1] * w[b2 + 1]) *
+                        (blk[op[2] + 1][op[1] + 1][op[0] + 1] - blk[om[2] + 1][om[1] + 1][om[0] + 1]);
             }
         n[d] = -gsum;
     }
-    int ord[3] = {0, 1, 2};
-    for (int i = 1; i < 3; i++)
-        for (int j = i; j > 0 && fabs(n[ord[j]]) > fabs(n[ord[j - 1]]); j--) {
-            int t = ord[j];
-            ord[j] = ord[j - 1];
-            ord[j - 1] = t;
-        }
+    int o0 = 0, o1 = 1, o2 = 2, tmp;
+    if (fabs(n[o1]) > fabs(n[o0])) { tmp = o0; o0 = o1; o1 = tmp; }
+    if (fabs(n[o2]) > fabs(n[o1])) {
+        tmp = o1; o1 = o2; o2 = tmp;
+        if (fabs(n[o1]) > fabs(n[o0])) { tmp = o0; o0 = o1; o1 = tmp; }
+    }
+    const int ord[3] = {o0, o1, o2};
+#pragma unroll
     for (int oi = 0; oi < 3; oi++) {
-        int d = ord[oi];
-        int t1 = (d == 0) ? 1 : 0, t2 = (d == 2) ? 1 : 2;
-        bool below = n[d] > 0.0;
-        double eta[3][3];
-        bool ok = true;
-        for (int b2 = -1; b2 <= 1 && ok; b2++)
-            for (int b1 = -1; b1 <= 1 && ok; b1++) {
-                double H = 0.0, lo = 0.0, hi = 0.0;
-                for (int m = -HFH; m <= HFH; m++) {
-                    int q[3] = {p[0], p[1], p[2]};
-                    q[d] += m;
-                    q[t1] += b1;
-                    q[t2] += b2;
-                    double cv = cval(a, q[0], q[1], q[2]);
-                    H += cv;
-                    if (m == -HFH) lo = cv;
-                    if (m == HFH) hi = cv;
-                }
-                if (below ? !(lo == 1.0 && hi == 0.0) : !(lo == 0.0 && hi == 1.0)) ok = false;
-                eta[b1 + 1][b2 + 1] = below ? H - (HFH + 0.5) : (HFH + 0.5) - H;
-            }
-        if (!ok) continue;
-        double hx = (eta[2][1] - eta[0][1]) * 0.5;
-        double hy = (eta[1][2] - eta[1][0]) * 0.5;
-        double hxx = (eta[2][1] + eta[0][1]) - 2.0 * eta[1][1];
-        double hyy = (eta[1][2] + eta[1][0]) - 2.0 * eta[1][1];
-        double hxy = ((eta[2][2] - eta[2][0]) - (eta[0][2] - eta[0][0])) * 0.25;
-        double num = (1.0 + hy * hy) * hxx + (1.0 + hx * hx) * hyy - 2.0 * hx * hy * hxy;
-        double q2 = 1.0 + hx * hx + hy * hy;
-        double den = q2 * sqrt(q2);
-        double kap = num / den;
-        *out = below ? -kap : kap;
-        return 1 + d;
+        const int d = ord[oi];
+        const bool below = n[d] > 0.0;
+        bool ok;
+        if (d == 0) ok = hf_axis<0, WRAP>(c, below, out);
+        else if (d == 1) ok = hf_axis<1, WRAP>(c, below, out);
+        else ok = hf_axis<2, WRAP>(c, below, out);
+        if (ok) return 1 + d;
     }
     *out = 0.0;
     return 4;
 }
 
-__global__ void __launch_bounds__(256) hf_kernel(HFArgs a) {
+__device__ __noinline__ int hf_cell(const HFArgs &a, int x, int y, int z, double *out) {
+    const int R = HFH + 1;
+    const int id = lin(a.g, x, y, z);
+    const int sy = a.g.n[0], sz = a.g.n[0] * a.g.n[1];
+    if (x >= R && x < a.g.n[0] - R && y >= R && y < a.g.n[1] - R && z >= R && z < a.g.n[2] - R) {
+        CAccess<false> c{a.C, a.g, x, y, z, id, sy, sz};
+        return hf_cell_impl<false>(c, out);
+    }
+    CAccess<true> c{a.C, a.g, x, y, z, id, sy, sz};
+    return hf_cell_impl<true>(c, out);
+}
+
+// Interface-cell pass: entries [0, nprev) reset the previous interface cells
+// that are no longer cut (their curvature becomes 0, status NONE); entries of
+// the candidate list are computed if 0 < C < 1 and reset otherwise.  Every
+// interface cell of the current C is a candidate, so the curvature field is
+// complete; one thread per entry, full warps for the FP64 work.
+__global__ void __launch_bounds__(128) hf_list_kernel(HFArgs a) {
+    const int np = *a.nprev, nc = *a.ncand;
+    const int total = np + nc;
+    const int stride = gridDim.x * blockDim.x;
+    const int iters = (total + stride - 1) / stride;
+    for (int it = 0; it < iters; it++) {
+        int t = it * stride + blockIdx.x * blockDim.x + threadIdx.x;
+        bool keep = false;
+        int id = 0;
+        if (t < total) {
+            id = (int)(t < np ? a.prev[t] : a.cand[t - np]);
+            bool iface = is_interface(__ldg(a.C + id));
+            if (t < np) {
+                if (!iface) {
+                    a.kh[id] = 0.0;
+                    a.st[id] = 0;
+                }
+            } else if (iface) {
+                const int x = id % a.g.n[0], y = (id / a.g.n[0]) % a.g.n[1], z = id / (a.g.n[0] * a.g.n[1]);
+                double kv = 0.0;
+                int st = hf_cell(a, x, y, z, &kv);
+                a.kh[id] = kv;
+                a.st[id] = (uint8_t)st;
+                keep = true;
+            } else {
+                a.kh[id] = 0.0;
+                a.st[id] = 0;
+            }
+        }
+        const unsigned full = 0xffffffffu;
+        unsigned m = __ballot_sync(full, keep);
+        if (m) {
+            const int lane = threadIdx.x & 31, leader = __ffs(m) - 1;
+            int base = 0;
+            if (lane == leader) base = atomicAdd(a.niface, __popc(m));
+            base = __shfl_sync(full, base, leader);
+            if (keep) a.iface[base + __popc(m & ((1u << lane) - 1u))] = (unsigned)id;
+        }
+    }
+}
+
+// Full scan of the listed tiles (any C): non-interface cells are reset, the
+// interface cells are appended to the candidate list for hf_list_kernel.
+__global__ void __launch_bounds__(256) hf_scan_kernel(HFArgs a, unsigned *cand, int *ncand) {
     const int ntl = *a.count;
     for (int li = blockIdx.x; li < ntl; li += gridDim.x) {
         const int tile = a.list[li];
@@ -107,20 +213,25 @@ __global__ void __launch_bounds__(256) hf_kernel(HFArgs a) {
         tile_origin(a.g, tile, o);
         for (int c = threadIdx.x; c < TILE_CELLS; c += blockDim.x) {
             int x = o[0] + (c & 7), y = o[1] + ((c >> 3) & 7), z = o[2] + (c >> 6);
-            if (x >= a.g.n[0] || y >= a.g.n[1] || z >= a.g.n[2]) continue;
-            int id = lin(a.g, x, y, z);
-            double c0 = __ldg(a.C + id);
-            double k = 0.0;
-            int st = 0;
-            if (c0 > 0.0 && c0 < 1.0) {
-                st = hf_cell(a, x, y, z, &k);
-                if (a.iface) {
-                    int slot = atomicAdd(a.iface_count, 1);
-                    a.iface[slot] = id;
+            bool iface = false;
+            int id = 0;
+            if (x < a.g.n[0] && y < a.g.n[1] && z < a.g.n[2]) {
+                id = lin(a.g, x, y, z);
+                iface = is_interface(__ldg(a.C + id));
+                if (!iface) {
+                    a.kh[id] = 0.0;
+                    a.st[id] = 0;
                 }
             }
-            a.kh[id] = k;
-            a.st[id] = (uint8_t)st;
+            const unsigned full = 0xffffffffu;
+            unsigned m = __ballot_sync(full, iface);
+            if (m) {
+                const int lane = threadIdx.x & 31, leader = __ffs(m) - 1;
+                int base = 0;
+                if (lane == leader) base = atomicAdd(ncand, __popc(m));
+                base = __shfl_sync(full, base, leader);
+                if (iface) cand[base + __popc(m & ((1u << lane) - 1u))] = (unsigned)id;
+            }
         }
     }
 }

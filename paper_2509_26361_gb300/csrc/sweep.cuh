@@ -12,12 +12,28 @@
 // crossing of that polyline with its grid line, refined by two circle fits with
 // the radius-ratio rule (Sec. 2.1, Fig. 2).
 //
-// GPU organisation: one CTA per 8x8x8 tile of the active band, one thread per
-// cell; each thread computes everything its cell owns (node colour, the three
-// edges leaving its node, the three faces whose lowest corner it is) directly
-// from the old state (gather form), so no two threads write the same word and
-// old and new state live in separate buffers.  Cells whose 4x2x2 colour
-// neighbourhood is uniform take a fast path (no marker can reach them).
+// GPU organisation.  GB300's FP64 pipe is narrow and a warp-level FP64
+// instruction costs its issue slots whatever the number of active lanes, so all
+// FP64 arithmetic runs from compacted lists with full warps, and the band pass
+// over the cells is integer work:
+//   advect_kernel -- per band tile, the markers owned by the tile are listed in
+//                    shared memory and each is moved once (trilinear velocity):
+//                    adv = its advected coordinate along D relative to its node
+//                    (s + u dt/h for an aligned marker, u dt/h for an unaligned
+//                    one) and bin = floor(2 adv), both in scratch arrays.
+//   sweep_kernel  -- per band tile, one thread per cell, integer only: new node
+//                    colours, aligned edges, canonical face colours; unaligned
+//                    edges that carry a marker and saddle faces are appended to
+//                    global work lists.
+//   fp64_kernel   -- one thread per list entry: crossings, circle fits, face
+//                    phases.
+// Every crossing decision compares an advected coordinate da + adv with 0 or
+// 1/2; for the integers da that occur the sum is exact near those thresholds,
+// so "da + adv < 0" equals "bin < -2 da" and "da + adv < 1/2" equals
+// "bin < 1 - 2 da" exactly, and the integer test gives the same answer as the
+// floating-point one.  Every output word has one owner thread (face bits of
+// saddle faces are OR-ed into the byte written by the band pass), and old and
+// new state live in separate buffers.
 #pragma once
 #include "common.cuh"
 
@@ -31,8 +47,12 @@ struct SweepArgs {
     double *__restrict__ so[3];      // new offsets (written only where a marker is)
     const double *__restrict__ u;    // u_D on D-faces
     double lam;                      // dt / h
+    double *__restrict__ adv[3];     // advected coordinate of each marker (scratch)
+    int8_t *__restrict__ bin[3];     // floor(2 adv) (scratch)
     const int *__restrict__ list;    // band tile ids
     const int *__restrict__ count;   // number of band tiles (device)
+    unsigned *__restrict__ work[4];  // FP64 work lists: unaligned fam.1, fam.2, saddle fam.1, fam.2
+    int *__restrict__ wcount;        // [4] list lengths (device)
     unsigned long long *ctr;         // event counters
     uint8_t *tile_marker;            // per tile: a marker in the input or the output
     uint8_t *tile_dirty;             // per tile: processed since the last Front2VOF
@@ -98,103 +118,137 @@ __device__ __noinline__ bool circle_root(P2 A, P2 B, P2 C, double ylin, double *
     return true;
 }
 
+// trilinear u_D at node q shifted by s along axis e; lerps in x, y, z order
+template <int D>
+__device__ double interp_u(const SweepArgs &a, const int q[3], int e, double s) {
+    int base[3];
+    double t[3];
+#pragma unroll
+    for (int b = 0; b < 3; b++) {
+        if (b == D) {
+            base[b] = q[b];
+            t[b] = (b == e) ? s : 0.0;
+        } else if (b != e) {
+            base[b] = q[b] - 1;
+            t[b] = 0.5;
+        } else if (s < 0.5) {
+            base[b] = q[b] - 1;
+            t[b] = s + 0.5;
+        } else {
+            base[b] = q[b];
+            t[b] = s - 0.5;
+        }
+    }
+    const Grid &g = a.g;
+    int x0 = wrapc(base[0], g.n[0]), x1 = wrapc(base[0] + 1, g.n[0]);
+    int y0 = wrapc(base[1], g.n[1]), y1 = wrapc(base[1] + 1, g.n[1]);
+    int z0 = wrapc(base[2], g.n[2]), z1 = wrapc(base[2] + 1, g.n[2]);
+    const double *u = a.u;
+    int r00 = (z0 * g.n[1] + y0) * g.n[0], r10 = (z0 * g.n[1] + y1) * g.n[0];
+    int r01 = (z1 * g.n[1] + y0) * g.n[0], r11 = (z1 * g.n[1] + y1) * g.n[0];
+    double c00 = (1.0 - t[0]) * __ldg(u + r00 + x0) + t[0] * __ldg(u + r00 + x1);
+    double c10 = (1.0 - t[0]) * __ldg(u + r10 + x0) + t[0] * __ldg(u + r10 + x1);
+    double c01 = (1.0 - t[0]) * __ldg(u + r01 + x0) + t[0] * __ldg(u + r01 + x1);
+    double c11 = (1.0 - t[0]) * __ldg(u + r11 + x0) + t[0] * __ldg(u + r11 + x1);
+    double c0 = (1.0 - t[1]) * c00 + t[1] * c10;
+    double c1 = (1.0 - t[1]) * c01 + t[1] * c11;
+    return (1.0 - t[2]) * c0 + t[2] * c1;
+}
+
+// warp-aggregated append: every lane of the warp must call it
+__device__ __forceinline__ int warp_append(int *counter, bool flag) {
+    const unsigned full = 0xffffffffu;
+    unsigned m = __ballot_sync(full, flag);
+    if (!m) return -1;
+    const int lane = threadIdx.x & 31;
+    const int leader = __ffs(m) - 1;
+    int base = 0;
+    if (lane == leader) base = atomicAdd(counter, __popc(m));
+    base = __shfl_sync(full, base, leader);
+    return flag ? base + __popc(m & ((1u << lane) - 1u)) : -1;
+}
+
+// ---------------------------------------------------------------- advection
+// Move every marker of the band once (Eq. 2).  CFL >= 1 is counted and clamped.
+template <int D>
+__global__ void __launch_bounds__(256) advect_kernel(SweepArgs a) {
+    __shared__ uint16_t s_mk[3 * TILE_CELLS];
+    __shared__ int s_n;
+    const int ntl = *a.count;
+    if (blockIdx.x == 0 && threadIdx.x < 4) a.wcount[threadIdx.x] = 0;
+    for (int li = blockIdx.x; li < ntl; li += gridDim.x) {
+        const int tile = a.list[li];
+        int o[3];
+        tile_origin(a.g, tile, o);
+        if (threadIdx.x == 0) s_n = 0;
+        __syncthreads();
+        for (int c = threadIdx.x; c < TILE_CELLS; c += blockDim.x) {
+            int q[3] = {o[0] + (c & 7), o[1] + ((c >> 3) & 7), o[2] + (c >> 6)};
+            bool valid = q[0] < a.g.n[0] && q[1] < a.g.n[1] && q[2] < a.g.n[2];
+            int mask = 0;
+            if (valid) {
+                const int c0 = __ldg(a.cb + lin3(a.g, q)) & 1;
+                mask = ((__ldg(a.cb + lin(a.g, q[0] + 1, q[1], q[2])) & 1) != c0) |
+                       (((__ldg(a.cb + lin(a.g, q[0], q[1] + 1, q[2])) & 1) != c0) << 1) |
+                       (((__ldg(a.cb + lin(a.g, q[0], q[1], q[2] + 1)) & 1) != c0) << 2);
+            }
+            for (int e = 0; e < 3; e++) {
+                int slot = warp_append(&s_n, (mask >> e) & 1);
+                if (slot >= 0) s_mk[slot] = (uint16_t)(c | (e << 9));
+            }
+        }
+        __syncthreads();
+        const int n = s_n;
+        unsigned hits = 0;
+        for (int k = threadIdx.x; k < n; k += blockDim.x) {
+            int it = s_mk[k], c = it & 511, e = it >> 9;
+            int q[3] = {o[0] + (c & 7), o[1] + ((c >> 3) & 7), o[2] + (c >> 6)};
+            const int id = lin3(a.g, q);
+            double sv = __ldg(a.s[e] + id);
+            double cf = interp_u<D>(a, q, e, sv) * a.lam;
+            if (!(fabs(cf) < 1.0)) {
+                hits++;
+                cf = cf > 0.0 ? ONE_MINUS : -ONE_MINUS;
+            }
+            double x = (e == D) ? sv + cf : cf;
+            a.adv[e][id] = x;
+            a.bin[e][id] = (int8_t)(int)floor(2.0 * x);
+        }
+        unsigned v = __reduce_add_sync(0xffffffffu, hits);
+        if ((threadIdx.x & 31) == 0 && v) atomicAdd(a.ctr + C_CFL, (unsigned long long)v);
+        __syncthreads();
+    }
+}
+
+// ----------------------------------------------------------- cell context
 template <int D>
 struct SweepCell {
     static constexpr int A = D, T1 = (D + 1) % 3, T2 = (D + 2) % 3;
     const SweepArgs &a;
     int p[3];
-    unsigned cfl_hits;
-    unsigned incons;
 
-    __device__ SweepCell(const SweepArgs &args, int x, int y, int z) : a(args), cfl_hits(0), incons(0) {
+    __device__ SweepCell(const SweepArgs &args, int x, int y, int z) : a(args) {
         p[0] = x;
         p[1] = y;
         p[2] = z;
     }
-
-    // global node for sweep-local offsets along (A, T1, T2)
-    __device__ __forceinline__ void node3(int da, int d1, int d2, int q[3]) const {
+    __device__ __forceinline__ int id3(int da, int d1, int d2) const {
+        int q[3];
         q[A] = p[A] + da;
         q[T1] = p[T1] + d1;
         q[T2] = p[T2] + d2;
-    }
-    __device__ __forceinline__ int id3(int da, int d1, int d2) const {
-        int q[3];
-        node3(da, d1, d2, q);
         return lin3(a.g, q);
     }
-
-    // trilinear u_D at node q shifted by s along axis e; lerps in x, y, z order
-    __device__ double interp(const int q[3], int e, double s) const {
-        int base[3];
-        double t[3];
-#pragma unroll
-        for (int b = 0; b < 3; b++) {
-            if (b == D) {
-                base[b] = q[b];
-                t[b] = (b == e) ? s : 0.0;
-            } else if (b != e) {
-                base[b] = q[b] - 1;
-                t[b] = 0.5;
-            } else if (s < 0.5) {
-                base[b] = q[b] - 1;
-                t[b] = s + 0.5;
-            } else {
-                base[b] = q[b];
-                t[b] = s - 0.5;
-            }
-        }
-        const Grid &g = a.g;
-        int x0 = wrapc(base[0], g.n[0]), x1 = wrapc(base[0] + 1, g.n[0]);
-        int y0 = wrapc(base[1], g.n[1]), y1 = wrapc(base[1] + 1, g.n[1]);
-        int z0 = wrapc(base[2], g.n[2]), z1 = wrapc(base[2] + 1, g.n[2]);
-        const double *u = a.u;
-        int r00 = (z0 * g.n[1] + y0) * g.n[0], r10 = (z0 * g.n[1] + y1) * g.n[0];
-        int r01 = (z1 * g.n[1] + y0) * g.n[0], r11 = (z1 * g.n[1] + y1) * g.n[0];
-        double c00 = (1.0 - t[0]) * __ldg(u + r00 + x0) + t[0] * __ldg(u + r00 + x1);
-        double c10 = (1.0 - t[0]) * __ldg(u + r10 + x0) + t[0] * __ldg(u + r10 + x1);
-        double c01 = (1.0 - t[0]) * __ldg(u + r01 + x0) + t[0] * __ldg(u + r01 + x1);
-        double c11 = (1.0 - t[0]) * __ldg(u + r11 + x0) + t[0] * __ldg(u + r11 + x1);
-        double c0 = (1.0 - t[1]) * c00 + t[1] * c10;
-        double c1 = (1.0 - t[1]) * c01 + t[1] * c11;
-        return (1.0 - t[2]) * c0 + t[2] * c1;
-    }
-
-    // displacement in cells of the marker at node q on its e-edge (CFL clamp)
-    __device__ double disp(const int q[3], int e, double s, bool own) {
-        double c = interp(q, e, s) * a.lam;
-        if (!(fabs(c) < 1.0)) {
-            if (own) cfl_hits++;
-            c = c > 0.0 ? ONE_MINUS : -ONE_MINUS;
-        }
-        return c;
-    }
-
     __device__ __forceinline__ int colid(int id) const { return __ldg(a.cb + id) & 1; }
 
-    // advected position (units of cells, relative to its node) of the aligned
-    // marker on the A-edge of node (da, d1, d2)
-    __device__ double Xa(int da, int d1, int d2, bool own) {
-        int q[3];
-        node3(da, d1, d2, q);
-        int id = lin3(a.g, q);
-        double sv = __ldg(a.s[A] + id);
-        return sv + disp(q, A, sv, own);
-    }
-
-    // ---------------------------------------------------------------- planes
-    // A plane of the face family with in-plane transverse axis TT and normal NN,
-    // through the thread's node; offsets (da, dt) along (A, TT).
-    template <int TT, int NN>
-    __device__ __forceinline__ void pnode(int da, int dt, int q[3]) const {
-        q[A] = p[A] + da;
-        q[TT] = p[TT] + dt;
-        q[NN] = p[NN];
-    }
+    // plane of the face family with in-plane transverse axis TT and normal NN
+    // through the cell's node; offsets (da, dt) along (A, TT)
     template <int TT, int NN>
     __device__ __forceinline__ int pid(int da, int dt) const {
         int q[3];
-        pnode<TT, NN>(da, dt, q);
+        q[A] = p[A] + da;
+        q[TT] = p[TT] + dt;
+        q[NN] = p[NN];
         return lin3(a.g, q);
     }
     template <int TT, int NN>
@@ -204,36 +258,57 @@ struct SweepCell {
         return cell_segs(b00 & 1, colid(pid<TT, NN>(da + 1, dt)), colid(pid<TT, NN>(da, dt + 1)),
                          colid(pid<TT, NN>(da + 1, dt + 1)), (b00 >> (1 + NN)) & 1, seg);
     }
-    // advected position of the marker on edge code e of the 2D cell (da, dt),
-    // relative to the thread's node
+    // bin of the advected a-coordinate of the marker on edge code e of cell
+    // (da, dt), and the integer da' with x = da' + adv
     template <int TT, int NN>
-    __device__ P2 ppos(int e, int da, int dt) {
+    __device__ __forceinline__ int pbin(int e, int da, int dt, int *off) const {
+        if (e == EB || e == ET) {
+            *off = da;
+            return __ldg(a.bin[A] + pid<TT, NN>(da, dt + (e == ET ? 1 : 0)));
+        }
+        int aa = da + (e == ER ? 1 : 0);
+        *off = aa;
+        return __ldg(a.bin[TT] + pid<TT, NN>(aa, dt));
+    }
+    // advected position (x along A, y along TT) relative to the cell's node
+    template <int TT, int NN>
+    __device__ __forceinline__ P2 ppos(int e, int da, int dt) const {
         P2 r;
-        int q[3];
         if (e == EB || e == ET) {
             int tt = dt + (e == ET ? 1 : 0);
-            pnode<TT, NN>(da, tt, q);
-            int id = lin3(a.g, q);
-            double sv = __ldg(a.s[A] + id);
-            double X = sv + disp(q, A, sv, false);
-            r.x = (double)da + X;
+            r.x = (double)da + __ldg(a.adv[A] + pid<TT, NN>(da, tt));
             r.y = (double)tt;
         } else {
             int aa = da + (e == ER ? 1 : 0);
-            pnode<TT, NN>(aa, dt, q);
-            int id = lin3(a.g, q);
-            double sv = __ldg(a.s[TT] + id);
-            double c = disp(q, TT, sv, false);
-            r.x = (double)aa + c;
-            r.y = (double)dt + sv;
+            int id = pid<TT, NN>(aa, dt);
+            r.x = (double)aa + __ldg(a.adv[TT] + id);
+            r.y = (double)dt + __ldg(a.s[TT] + id);
         }
         return r;
     }
-
-    // The neighbour along the polyline of the marker on edge code e of cell
-    // (da, dt), found in the cell across that edge.  Returns false if missing.
+    // is the endpoint left of x = 0 (thr = 0) or of x = 1/2 (thr = 1)?
     template <int TT, int NN>
-    __device__ bool neighbour(int e, int da, int dt, P2 *out) {
+    __device__ __forceinline__ bool pleft(int e, int da, int dt, int thr) const {
+        int off;
+        int b = pbin<TT, NN>(e, da, dt, &off);
+        return b < thr - 2 * off;
+    }
+    // number of segments of cells (-1, 0) and (0, 0) crossing x = 0
+    template <int TT, int NN>
+    __device__ int count_crossings() const {
+        int n = 0;
+        for (int da = -1; da <= 0; da++) {
+            int seg[2][2];
+            int ns = psegs<TT, NN>(da, 0, seg);
+            for (int k = 0; k < ns; k++)
+                n += pleft<TT, NN>(seg[k][0], da, 0, 0) != pleft<TT, NN>(seg[k][1], da, 0, 0);
+        }
+        return n;
+    }
+    // neighbour along the polyline of the marker on edge e of cell (da, dt),
+    // found in the cell across that edge
+    template <int TT, int NN>
+    __device__ bool neighbour(int e, int da, int dt, P2 *out) const {
         int oda = da, odt = dt, oe;
         switch (e) {
         case EB: odt = dt - 1; oe = ET; break;
@@ -255,51 +330,49 @@ struct SweepCell {
         return false;
     }
 
-    // Unaligned edge (family TT/NN) of the thread's node.  Returns the number of
-    // crossings; writes the reconstructed offset when present.
+    // Unaligned edge of family (TT, NN) at the cell's node (carries a marker):
+    // crossings of the advected polyline with the grid line x = 0 in strip 0
+    // (Fig. 1c), then the two circle fits with the ratio rule (Fig. 2).
     template <int TT, int NN>
-    __device__ void unaligned(bool present, unsigned *ev_ann, unsigned *ev_multi, double *sout) {
-        // crossings of the advected polyline with the grid line x = 0 in strip 0
+    __device__ void unaligned(unsigned ev[C_N]) const {
         P2 c2[4], c3[4];
         int e2[4], e3[4], cd[4];
-        double yl[4];
         int nc = 0;
         for (int da = -1; da <= 0; da++) {
             int seg[2][2];
             int ns = psegs<TT, NN>(da, 0, seg);
             for (int k = 0; k < ns; k++) {
-                P2 P = ppos<TT, NN>(seg[k][0], da, 0);
-                P2 Q = ppos<TT, NN>(seg[k][1], da, 0);
-                if ((P.x < 0.0) == (Q.x < 0.0)) continue;
-                bool pl = P.x < 0.0;
-                c2[nc] = pl ? P : Q;
-                c3[nc] = pl ? Q : P;
-                e2[nc] = pl ? seg[k][0] : seg[k][1];
-                e3[nc] = pl ? seg[k][1] : seg[k][0];
+                bool l0 = pleft<TT, NN>(seg[k][0], da, 0, 0), l1 = pleft<TT, NN>(seg[k][1], da, 0, 0);
+                if (l0 == l1) continue;
+                int el = l0 ? seg[k][0] : seg[k][1], er = l0 ? seg[k][1] : seg[k][0];
+                c2[nc] = ppos<TT, NN>(el, da, 0);
+                c3[nc] = ppos<TT, NN>(er, da, 0);
+                e2[nc] = el;
+                e3[nc] = er;
                 cd[nc] = da;
-                double tt = (0.0 - c2[nc].x) / (c3[nc].x - c2[nc].x);
-                yl[nc] = c2[nc].y + tt * (c3[nc].y - c2[nc].y);
                 nc++;
             }
         }
-        if (!present) {
-            if (nc >= 2) (*ev_ann)++;
+        const int myid = lin3(a.g, p);
+        ev[C_MARKERS]++;
+        if ((nc & 1) == 0) {
+            ev[C_INCONSISTENT]++;
+            a.so[TT][myid] = 0.5;
             return;
         }
-        if ((nc & 1) == 0) {
-            incons++;
-            *sout = 0.5;
-            return;
+        double yl[4];
+        for (int k = 0; k < nc; k++) {
+            double tt = (0.0 - c2[k].x) / (c3[k].x - c2[k].x);
+            yl[k] = c2[k].y + tt * (c3[k].y - c2[k].y);
         }
         int sel = 0;
         if (nc == 3) {
-            // median by ylin, equal values keep list order
             int o0 = 0, o1 = 1, o2 = 2, tmp;
             if (yl[o0] > yl[o1]) { tmp = o0; o0 = o1; o1 = tmp; }
             if (yl[o1] > yl[o2]) { tmp = o1; o1 = o2; o2 = tmp; }
             if (yl[o0] > yl[o1]) { tmp = o0; o0 = o1; o1 = tmp; }
             sel = o1;
-            (*ev_multi)++;
+            ev[C_MULTI]++;
         }
         P2 Pa = c2[sel], Pb = c3[sel];
         double ylin = yl[sel];
@@ -307,9 +380,9 @@ struct SweepCell {
         double ya = 0.0, ra = 0.0, yb = 0.0, rb = 0.0;
         bool va = false, vb = false;
         if (neighbour<TT, NN>(e2[sel], cd[sel], 0, &P1)) va = circle_root(P1, Pa, Pb, ylin, &ya, &ra);
-        else incons++;
+        else ev[C_INCONSISTENT]++;
         if (neighbour<TT, NN>(e3[sel], cd[sel], 0, &P4)) vb = circle_root(Pa, Pb, P4, ylin, &yb, &rb);
-        else incons++;
+        else ev[C_INCONSISTENT]++;
         double y;
         if (va && vb) {
             double rmax = ra > rb ? ra : rb, rmin = ra > rb ? rb : ra;
@@ -324,29 +397,28 @@ struct SweepCell {
         }
         if (y < 0.0) y = 0.0;
         if (y > ONE_MINUS) y = ONE_MINUS;
-        *sout = y;
+        a.so[TT][myid] = y;
     }
 
-    // Colour of the face-centre of the family's 2D cell at the thread's node:
-    // the phase of the advected polyline at the centre, reached from the node
-    // along the a-line to x = 1/2 and then up the line x = 1/2 to y = 1/2.
+    // Face-centre colour of the family's 2D cell at the node (saddle faces): the
+    // phase of the advected polyline at the centre, reached from the node along
+    // the a-line to x = 1/2 and then up the line x = 1/2 to y = 1/2.
     template <int TT, int NN>
-    __device__ int face_phase(int ncol0) {
+    __device__ int face_phase(int ncol0) const {
         int par = ncol0;
         for (int da = -1; da <= 1; da++) {
-            int i0 = pid<TT, NN>(da, 0), i1 = pid<TT, NN>(da + 1, 0);
-            if (colid(i0) == colid(i1)) continue;
-            P2 P = ppos<TT, NN>(EB, da, 0);
-            if (P.x >= 0.0 && P.x < 0.5) par ^= 1;
+            if (colid(pid<TT, NN>(da, 0)) == colid(pid<TT, NN>(da + 1, 0))) continue;
+            int b = __ldg(a.bin[A] + pid<TT, NN>(da, 0));
+            if (b >= -2 * da && b < 1 - 2 * da) par ^= 1;
         }
         for (int da = -1; da <= 1; da++) {
             int seg[2][2];
             int ns = psegs<TT, NN>(da, 0, seg);
             for (int k = 0; k < ns; k++) {
-                P2 P = ppos<TT, NN>(seg[k][0], da, 0);
-                P2 Q = ppos<TT, NN>(seg[k][1], da, 0);
-                if ((P.x < 0.5) == (Q.x < 0.5)) continue;
-                P2 L = (P.x < 0.5) ? P : Q, R = (P.x < 0.5) ? Q : P;
+                bool l0 = pleft<TT, NN>(seg[k][0], da, 0, 1), l1 = pleft<TT, NN>(seg[k][1], da, 0, 1);
+                if (l0 == l1) continue;
+                P2 L = ppos<TT, NN>(l0 ? seg[k][0] : seg[k][1], da, 0);
+                P2 R = ppos<TT, NN>(l0 ? seg[k][1] : seg[k][0], da, 0);
                 double tt = (0.5 - L.x) / (R.x - L.x);
                 double yl = L.y + tt * (R.y - L.y);
                 if (yl < 0.5) par ^= 1;
@@ -354,180 +426,212 @@ struct SweepCell {
         }
         return par;
     }
-
-    __device__ static bool saddle(int c00, int c10, int c01, int c11) {
-        return c00 == c11 && c10 == c01 && c00 != c10;
-    }
-
-    // Process the cell.  Returns whether any of its edges carries a marker in
-    // the input or in the output.
-    __device__ bool run(unsigned ev[C_N]) {
-        const int myid = lin(a.g, p[0], p[1], p[2]);
-        // old colours of the nodes (da, d1, d2), da in [-1, 2], d1, d2 in {0, 1}
-        int col[4][2][2];
-        int any = 0, c0 = colid(myid);
-#pragma unroll
-        for (int da = 0; da < 4; da++)
-#pragma unroll
-            for (int d1 = 0; d1 < 2; d1++)
-#pragma unroll
-                for (int d2 = 0; d2 < 2; d2++) {
-                    int c = (da == 1 && d1 == 0 && d2 == 0) ? c0 : colid(id3(da - 1, d1, d2));
-                    col[da][d1][d2] = c;
-                    any |= c ^ c0;
-                }
-        if (!any) {
-            a.cbo[myid] = (uint8_t)(c0 | (c0 << 1) | (c0 << 2) | (c0 << 3));
-            return false;
-        }
-        const uint8_t myb = __ldg(a.cb + myid);
-        bool in_marker = (col[1][0][0] != col[2][0][0]) || (col[1][0][0] != col[1][1][0]) ||
-                         (col[1][0][0] != col[1][0][1]);
-        // advected aligned markers on the A-edges (da in {-1,0,1}) of the 4 lines
-        double X[3][2][2];
-        bool has[3][2][2];
-#pragma unroll
-        for (int da = 0; da < 3; da++)
-#pragma unroll
-            for (int d1 = 0; d1 < 2; d1++)
-#pragma unroll
-                for (int d2 = 0; d2 < 2; d2++) {
-                    has[da][d1][d2] = col[da][d1][d2] != col[da + 1][d1][d2];
-                    X[da][d1][d2] = has[da][d1][d2] ? Xa(da - 1, d1, d2, da == 1 && d1 == 0 && d2 == 0) : 0.0;
-                }
-        // new colours of the nodes (dA, d1, d2), dA in {0, 1} (Fig. 4)
-        int nc[2][2][2];
-#pragma unroll
-        for (int dA = 0; dA < 2; dA++)
-#pragma unroll
-            for (int d1 = 0; d1 < 2; d1++)
-#pragma unroll
-                for (int d2 = 0; d2 < 2; d2++) {
-                    int c = col[dA + 1][d1][d2];
-                    if (has[dA][d1][d2] && X[dA][d1][d2] >= 1.0) c ^= 1;
-                    if (has[dA + 1][d1][d2] && X[dA + 1][d1][d2] < 0.0) c ^= 1;
-                    nc[dA][d1][d2] = c;
-                }
-        const int n0 = nc[0][0][0];
-        bool out_marker = false;
-        // aligned edge: presence from the new colours, markers landing on it (Fig. 5)
-        {
-            bool present = n0 != nc[1][0][0];
-            double land[3];
-            int nl = 0;
-#pragma unroll
-            for (int e = -1; e <= 1; e++) {
-                if (!has[e + 1][0][0]) continue;
-                double x = X[e + 1][0][0];
-                int dest = (x < 0.0) ? -1 : (x >= 1.0 ? 1 : 0);
-                if (e + dest != 0) continue;
-                double sn = x - (double)dest;
-                if (sn > ONE_MINUS) sn = ONE_MINUS;
-                land[nl++] = sn;
-            }
-            if (present) {
-                double v;
-                if (nl == 1) {
-                    v = land[0];
-                } else if (nl == 3) {
-                    double a0 = land[0], a1 = land[1], a2 = land[2], tmp;
-                    if (a0 > a1) { tmp = a0; a0 = a1; a1 = tmp; }
-                    if (a1 > a2) { tmp = a1; a1 = a2; a2 = tmp; }
-                    if (a0 > a1) { tmp = a0; a0 = a1; a1 = tmp; }
-                    v = a1;
-                    ev[C_MULTI]++;
-                } else {
-                    v = 0.5;
-                    incons++;
-                }
-                a.so[A][myid] = v;
-                ev[C_MARKERS]++;
-                out_marker = true;
-            } else if (nl >= 2) {
-                ev[C_ANNIHILATE]++;
-            }
-        }
-        // unaligned edges of the two families (Fig. 1c, Fig. 2)
-        {
-            int qo[3];
-            // own old unaligned markers: count a CFL violation once, by the owner
-            if (col[1][0][0] != col[1][1][0]) {
-                node3(0, 0, 0, qo);
-                disp(qo, T1, __ldg(a.s[T1] + myid), true);
-            }
-            if (col[1][0][0] != col[1][0][1]) {
-                node3(0, 0, 0, qo);
-                disp(qo, T2, __ldg(a.s[T2] + myid), true);
-            }
-            bool pres1 = n0 != nc[0][1][0];
-            bool cells1 = pres1 || col[0][0][0] != col[0][1][0] || col[0][0][0] != col[1][0][0] ||
-                          col[0][0][0] != col[2][0][0] || col[0][0][0] != col[0][1][0] ||
-                          col[0][0][0] != col[1][1][0] || col[0][0][0] != col[2][1][0];
-            if (cells1) {
-                double sv = 0.0;
-                unaligned<T1, T2>(pres1, &ev[C_ANNIHILATE], &ev[C_MULTI], &sv);
-                if (pres1) {
-                    a.so[T1][myid] = sv;
-                    ev[C_MARKERS]++;
-                    out_marker = true;
-                }
-            }
-            bool pres2 = n0 != nc[0][0][1];
-            bool cells2 = pres2 || col[0][0][0] != col[0][0][1] || col[0][0][0] != col[1][0][0] ||
-                          col[0][0][0] != col[2][0][0] || col[0][0][0] != col[1][0][1] ||
-                          col[0][0][0] != col[2][0][1];
-            if (cells2) {
-                double sv = 0.0;
-                unaligned<T2, T1>(pres2, &ev[C_ANNIHILATE], &ev[C_MULTI], &sv);
-                if (pres2) {
-                    a.so[T2][myid] = sv;
-                    ev[C_MARKERS]++;
-                    out_marker = true;
-                }
-            }
-        }
-        // face colours (Sec. 2.2): family 1 faces are normal to T2, family 2 to T1
-        int f1 = saddle(n0, nc[1][0][0], nc[0][1][0], nc[1][1][0]) ? face_phase<T1, T2>(n0) : n0;
-        int f2 = saddle(n0, nc[1][0][0], nc[0][0][1], nc[1][0][1]) ? face_phase<T2, T1>(n0) : n0;
-        int fa = saddle(n0, nc[0][1][0], nc[0][0][1], nc[0][1][1]) ? ((myb >> (1 + A)) & 1) : n0;
-        a.cbo[myid] = (uint8_t)(n0 | (fa << (1 + A)) | (f1 << (1 + T2)) | (f2 << (1 + T1)));
-        return in_marker || out_marker;
-    }
 };
 
+__device__ __forceinline__ bool saddle4(int c00, int c10, int c01, int c11) {
+    return c00 == c11 && c10 == c01 && c00 != c10;
+}
+
+// ------------------------------------------------------- band pass (integer)
 template <int D>
-__global__ void __launch_bounds__(256) sweep_kernel(SweepArgs args) {
+__global__ void __launch_bounds__(256) sweep_kernel(SweepArgs a) {
+    constexpr int A = D, T1 = (D + 1) % 3, T2 = (D + 2) % 3;
     __shared__ int s_flag;
-    const int ntl = *args.count;
+    const int ntl = *a.count;
     for (int li = blockIdx.x; li < ntl; li += gridDim.x) {
-        const int tile = args.list[li];
+        const int tile = a.list[li];
         int o[3];
-        tile_origin(args.g, tile, o);
+        tile_origin(a.g, tile, o);
         if (threadIdx.x == 0) s_flag = 0;
         __syncthreads();
         unsigned ev[C_N] = {0, 0, 0, 0, 0};
         bool mk = false;
         for (int c = threadIdx.x; c < TILE_CELLS; c += blockDim.x) {
             int x = o[0] + (c & 7), y = o[1] + ((c >> 3) & 7), z = o[2] + (c >> 6);
-            if (x >= args.g.n[0] || y >= args.g.n[1] || z >= args.g.n[2]) continue;
-            SweepCell<D> cell(args, x, y, z);
-            mk |= cell.run(ev);
-            ev[C_INCONSISTENT] += cell.incons;
-            ev[C_CFL] += cell.cfl_hits;
+            bool valid = x < a.g.n[0] && y < a.g.n[1] && z < a.g.n[2];
+            bool push[4] = {false, false, false, false};
+            int myid = 0;
+            if (valid) {
+                SweepCell<D> cell(a, x, y, z);
+                myid = lin(a.g, x, y, z);
+                int col[4][2][2];
+                const int c0 = cell.colid(myid);
+                int any = 0;
+#pragma unroll
+                for (int da = 0; da < 4; da++)
+#pragma unroll
+                    for (int d1 = 0; d1 < 2; d1++)
+#pragma unroll
+                        for (int d2 = 0; d2 < 2; d2++) {
+                            int v = (da == 1 && d1 == 0 && d2 == 0) ? c0 : cell.colid(cell.id3(da - 1, d1, d2));
+                            col[da][d1][d2] = v;
+                            any |= v ^ c0;
+                        }
+                if (!any) {
+                    a.cbo[myid] = (uint8_t)(c0 | (c0 << 1) | (c0 << 2) | (c0 << 3));
+                } else {
+                    const int myb = __ldg(a.cb + myid);
+                    bool in_marker = (c0 != col[2][0][0]) || (c0 != col[1][1][0]) || (c0 != col[1][0][1]);
+                    // bins of the aligned markers on the A-edges (da in {-1,0,1}) of 4 lines
+                    int bn[3][2][2];
+                    bool has[3][2][2];
+#pragma unroll
+                    for (int da = 0; da < 3; da++)
+#pragma unroll
+                        for (int d1 = 0; d1 < 2; d1++)
+#pragma unroll
+                            for (int d2 = 0; d2 < 2; d2++) {
+                                has[da][d1][d2] = col[da][d1][d2] != col[da + 1][d1][d2];
+                                bn[da][d1][d2] = has[da][d1][d2] ? __ldg(a.bin[A] + cell.id3(da - 1, d1, d2)) : 0;
+                            }
+                    // new colours: X >= 1 <=> bin >= 2 (crossed the right node),
+                    // X < 0 <=> bin < 0 (crossed the left node)  (Fig. 4)
+                    int nc[2][2][2];
+#pragma unroll
+                    for (int dA = 0; dA < 2; dA++)
+#pragma unroll
+                        for (int d1 = 0; d1 < 2; d1++)
+#pragma unroll
+                            for (int d2 = 0; d2 < 2; d2++) {
+                                int v = col[dA + 1][d1][d2];
+                                if (has[dA][d1][d2] && bn[dA][d1][d2] >= 2) v ^= 1;
+                                if (has[dA + 1][d1][d2] && bn[dA + 1][d1][d2] < 0) v ^= 1;
+                                nc[dA][d1][d2] = v;
+                            }
+                    const int n0 = nc[0][0][0];
+                    bool out_marker = false;
+                    // aligned edge (Fig. 5): presence from the new colours, landing markers
+                    {
+                        bool present = n0 != nc[1][0][0];
+                        int land[3], nl = 0;
+#pragma unroll
+                        for (int e = -1; e <= 1; e++) {
+                            if (!has[e + 1][0][0]) continue;
+                            int b = bn[e + 1][0][0];
+                            int dest = (b < 0) ? -1 : (b >= 2 ? 1 : 0);
+                            if (e + dest != 0) continue;
+                            land[nl++] = e;
+                        }
+                        if (present) {
+                            double v;
+                            if (nl == 1 || nl == 3) {
+                                double sv[3];
+                                for (int k = 0; k < nl; k++) {
+                                    double xv = __ldg(a.adv[A] + cell.id3(land[k], 0, 0));
+                                    double sn = xv - (double)(-land[k]);
+                                    if (sn > ONE_MINUS) sn = ONE_MINUS;
+                                    sv[k] = sn;
+                                }
+                                if (nl == 1) {
+                                    v = sv[0];
+                                } else {
+                                    double a0 = sv[0], a1 = sv[1], a2 = sv[2], tmp;
+                                    if (a0 > a1) { tmp = a0; a0 = a1; a1 = tmp; }
+                                    if (a1 > a2) { tmp = a1; a1 = a2; a2 = tmp; }
+                                    if (a0 > a1) { tmp = a0; a0 = a1; a1 = tmp; }
+                                    v = a1;
+                                    ev[C_MULTI]++;
+                                }
+                            } else {
+                                v = 0.5;
+                                ev[C_INCONSISTENT]++;
+                            }
+                            a.so[A][myid] = v;
+                            ev[C_MARKERS]++;
+                            out_marker = true;
+                        } else if (nl >= 2) {
+                            ev[C_ANNIHILATE]++;
+                        }
+                    }
+                    // unaligned edges: a marker -> FP64 list; none -> count the
+                    // crossings that met there (topology change, Fig. 5)
+                    const int m = col[0][0][0];
+                    const bool pres1 = n0 != nc[0][1][0];
+                    const bool pres2 = n0 != nc[0][0][1];
+                    push[0] = pres1;
+                    push[1] = pres2;
+                    if (!pres1 && ((col[1][0][0] ^ m) | (col[2][0][0] ^ m) | (col[0][1][0] ^ m) |
+                                   (col[1][1][0] ^ m) | (col[2][1][0] ^ m)))
+                        if (cell.template count_crossings<T1, T2>() >= 2) ev[C_ANNIHILATE]++;
+                    if (!pres2 && ((col[1][0][0] ^ m) | (col[2][0][0] ^ m) | (col[0][0][1] ^ m) |
+                                   (col[1][0][1] ^ m) | (col[2][0][1] ^ m)))
+                        if (cell.template count_crossings<T2, T1>() >= 2) ev[C_ANNIHILATE]++;
+                    out_marker |= pres1 || pres2;
+                    // face colours: family 1 faces are normal to T2, family 2 to T1
+                    int byte = n0;
+                    push[2] = saddle4(n0, nc[1][0][0], nc[0][1][0], nc[1][1][0]);
+                    if (!push[2]) byte |= n0 << (1 + T2);
+                    push[3] = saddle4(n0, nc[1][0][0], nc[0][0][1], nc[1][0][1]);
+                    if (!push[3]) byte |= n0 << (1 + T1);
+                    int fa = saddle4(n0, nc[0][1][0], nc[0][0][1], nc[0][1][1]) ? ((myb >> (1 + A)) & 1) : n0;
+                    byte |= fa << (1 + A);
+                    a.cbo[myid] = (uint8_t)byte;
+                    mk |= in_marker || out_marker;
+                }
+            }
+#pragma unroll
+            for (int k = 0; k < 4; k++) {
+                int slot = warp_append(a.wcount + k, push[k]);
+                if (slot >= 0) a.work[k][slot] = (unsigned)myid;
+            }
         }
         if (mk) s_flag = 1;
 #pragma unroll
         for (int k = 0; k < C_N; k++) {
             unsigned v = __reduce_add_sync(0xffffffffu, ev[k]);
-            if ((threadIdx.x & 31) == 0 && v) atomicAdd(args.ctr + k, (unsigned long long)v);
+            if ((threadIdx.x & 31) == 0 && v) atomicAdd(a.ctr + k, (unsigned long long)v);
         }
         __syncthreads();
         if (threadIdx.x == 0) {
-            args.tile_marker[tile] = (uint8_t)s_flag;
-            args.tile_dirty[tile] = 1;
+            a.tile_marker[tile] = (uint8_t)s_flag;
+            a.tile_dirty[tile] = 1;
+        }
+        __syncthreads();
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(a.ctr + C_TILES, (unsigned long long)ntl);
+}
+
+// ------------------------------------------------- FP64 work lists
+template <int D>
+__global__ void __launch_bounds__(128) fp64_kernel(SweepArgs a) {
+    constexpr int T1 = (D + 1) % 3, T2 = (D + 2) % 3;
+    const int n0 = a.wcount[0], n1 = a.wcount[1], n2 = a.wcount[2], n3 = a.wcount[3];
+    const int total = n0 + n1 + n2 + n3;
+    unsigned ev[C_N] = {0, 0, 0, 0, 0};
+    const int stride = gridDim.x * blockDim.x;
+    // uniform trip count so that every lane reaches the warp reductions
+    const int iters = (total + stride - 1) / stride;
+    for (int it = 0; it < iters; it++) {
+        int t = it * stride + blockIdx.x * blockDim.x + threadIdx.x;
+        if (t >= total) continue;
+        int k, kind;
+        if (t < n0) { kind = 0; k = t; }
+        else if (t < n0 + n1) { kind = 1; k = t - n0; }
+        else if (t < n0 + n1 + n2) { kind = 2; k = t - n0 - n1; }
+        else { kind = 3; k = t - n0 - n1 - n2; }
+        const int id = (int)a.work[kind][k];
+        const int x = id % a.g.n[0], y = (id / a.g.n[0]) % a.g.n[1], z = id / (a.g.n[0] * a.g.n[1]);
+        SweepCell<D> cell(a, x, y, z);
+        if (kind == 0) {
+            cell.template unaligned<T1, T2>(ev);
+        } else if (kind == 1) {
+            cell.template unaligned<T2, T1>(ev);
+        } else {
+            int ncol0 = a.cbo[id] & 1;
+            int bit = (kind == 2) ? (cell.template face_phase<T1, T2>(ncol0) << (1 + T2))
+                                  : (cell.template face_phase<T2, T1>(ncol0) << (1 + T1));
+            if (bit) {
+                uintptr_t addr = (uintptr_t)(a.cbo + id);
+                unsigned *w = (unsigned *)(addr & ~(uintptr_t)3);
+                atomicOr(w, (unsigned)bit << (8 * (addr & 3)));
+            }
         }
     }
-    if (blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(args.ctr + C_TILES, (unsigned long long)ntl);
+#pragma unroll
+    for (int k = 0; k < C_N; k++) {
+        unsigned v = __reduce_add_sync(0xffffffffu, ev[k]);
+        if ((threadIdx.x & 31) == 0 && v) atomicAdd(a.ctr + k, (unsigned long long)v);
+    }
 }
 
 }  // namespace ebit

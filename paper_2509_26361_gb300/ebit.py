@@ -182,7 +182,7 @@ def ebit_band_tiles(ctx):
     return int(load().ebit_band_tiles(ctx))
 
 
-PROF_KINDS = ("sweep", "band", "f2v", "hf", "mlp", "k5", "k6", "k7")
+PROF_KINDS = ("sweep", "band", "f2v", "hf", "mlp", "advect", "fp64", "k7")
 
 
 def ebit_profile(ctx, enable):

@@ -158,3 +158,73 @@ def test_errors_are_reported():
         g.sync()
     assert e.value.code == ebit.EBIT_ECFL
     g.close()
+
+
+def random_state(n3, seed):
+    """Any colour field is a valid EBIT state: markers where node colours differ,
+    face colours used on saddle faces.  Random fields reach every local corner
+    and face configuration, including saddles and several loops per cell."""
+    rng = np.random.default_rng(seed)
+    nx, ny, nz = n3
+    cb = rng.integers(0, 16, size=(nz, ny, nx), dtype=np.uint8)
+    s = rng.uniform(0.0, 1.0, size=(3, nz, ny, nx))
+    st = oracle.State(cb, s)
+    # canonical form: offsets 0 where no marker, face colour = lowest corner except saddles
+    c = cb & 1
+    pres = present_mask(cb)
+    s[~pres] = 0.0
+    for a in range(3):
+        ax1, ax2 = [b for b in range(3) if b != a]
+        sh = lambda arr, b: np.roll(arr, -1, axis=2 - b)
+        c10, c01 = sh(c, ax1), sh(c, ax2)
+        c11 = sh(c10, ax2)
+        sad = (c == c11) & (c10 == c01) & (c != c10)
+        bit = np.where(sad, (cb >> (1 + a)) & 1, c)
+        cb = (cb & ~np.uint8(1 << (1 + a))) | (bit.astype(np.uint8) << (1 + a))
+    st.cb = np.ascontiguousarray(cb)
+    st.s = np.ascontiguousarray(s)
+    return st
+
+
+@pytest.mark.parametrize("seed", [11, 12])
+def test_front2vof_hf_random_colour_fields(seed):
+    n3 = (16, 16, 16)
+    st = random_state(n3, seed)
+    g = ebit.Grid(*n3)
+    g.set_state(to_dev(st.cb), to_dev(st.s))
+    C = torch.zeros(g.shape, dtype=torch.float64, device="cuda")
+    kh = torch.zeros_like(C)
+    stt = torch.zeros(g.shape, dtype=torch.uint8, device="cuda")
+    g.front2vof(C, ebit.EBIT_FULL)
+    oC, nbad = oracle.front2vof(st)
+    assert nbad == 0
+    assert np.abs(C.cpu().numpy() - oC).max() <= TOL
+    g.curvature(C, kh, stt, flags=ebit.EBIT_FULL)
+    okh, ost = oracle.hf_curvature(oC)
+    assert np.array_equal(stt.cpu().numpy(), ost)
+    assert np.abs(kh.cpu().numpy() - okh).max() <= TOL
+    g.close()
+
+
+@pytest.mark.parametrize("seed", [21, 22, 23])
+def test_sweeps_on_random_colour_fields(seed):
+    """Sweeps from random states: saddles everywhere, many annihilations and
+    multi-crossings; every rule against the oracle."""
+    n3 = (12, 16, 20)
+    st = random_state(n3, seed)
+    rng = np.random.default_rng(seed)
+    u = W.fourier_velocity(n3, rng)
+    g = ebit.Grid(*n3)
+    g.set_state(to_dev(st.cb), to_dev(st.s))
+    ud = [to_dev(u[d]) for d in range(3)]
+    ocnt = np.zeros(5, np.int64)
+    ost = st
+    for k, d in enumerate((0, 1, 2, 2, 1, 0)):
+        dt = (0.93 if k % 2 == 0 else -0.61) * g.h
+        g.sweep(d, ud[d], dt)
+        ost, c = oracle.sweep(ost, d, u[d], dt / g.h)
+        ocnt += c
+        compare_state(g, ost, f"sweep {k} dir {d}")
+    cnt = g.counters()
+    assert [cnt[k] for k in ebit.COUNTER_NAMES] == list(ocnt), (cnt, ocnt)
+    g.close()
