@@ -52,25 +52,28 @@ struct CAccess {
     }
 };
 
-// heights along axis D on the 3x3 stencil of 9-cell columns; returns false when
-// a column's ends are not pure with the reference phase on the expected side
-template <int D, bool WRAP>
-__device__ __forceinline__ bool hf_axis(const CAccess<WRAP> &c, bool below, double *out) {
-    constexpr int T1 = (D == 0) ? 1 : 0, T2 = (D == 2) ? 1 : 2;
+// heights along axis d on the 3x3 stencil of 9-cell columns; returns false when
+// a column's ends are not pure with the reference phase on the expected side.
+// The axis is a run-time value so that lanes of a warp with different
+// dominant axes share one instruction stream.
+template <bool WRAP>
+__device__ __forceinline__ bool hf_axis(const CAccess<WRAP> &c, int d, bool below, double *out) {
+    const int t1 = (d == 0) ? 1 : 0, t2 = (d == 2) ? 1 : 2;
+    int ed[3] = {0, 0, 0}, e1[3] = {0, 0, 0}, e2[3] = {0, 0, 0};
+    ed[d] = 1;
+    e1[t1] = 1;
+    e2[t2] = 1;
     double eta[3][3];
     bool ok = true;
 #pragma unroll
     for (int b2 = -1; b2 <= 1; b2++)
 #pragma unroll
         for (int b1 = -1; b1 <= 1; b1++) {
+            const int ox = b1 * e1[0] + b2 * e2[0], oy = b1 * e1[1] + b2 * e2[1], oz = b1 * e1[2] + b2 * e2[2];
             double H = 0.0, lo = 0.0, hi = 0.0;
 #pragma unroll
             for (int m = -HFH; m <= HFH; m++) {
-                int o[3] = {0, 0, 0};
-                o[D] += m;
-                o[T1] += b1;
-                o[T2] += b2;
-                double cv = c(o[0], o[1], o[2]);
+                double cv = c(ox + m * ed[0], oy + m * ed[1], oz + m * ed[2]);
                 H += cv;
                 if (m == -HFH) lo = cv;
                 if (m == HFH) hi = cv;
@@ -131,15 +134,10 @@ __device__ int hf_cell_impl(const CAccess<WRAP> &c, double *out) {
         if (fabs(n[o1]) > fabs(n[o0])) { tmp = o0; o0 = o1; o1 = tmp; }
     }
     const int ord[3] = {o0, o1, o2};
-#pragma unroll
     for (int oi = 0; oi < 3; oi++) {
         const int d = ord[oi];
         const bool below = n[d] > 0.0;
-        bool ok;
-        if (d == 0) ok = hf_axis<0, WRAP>(c, below, out);
-        else if (d == 1) ok = hf_axis<1, WRAP>(c, below, out);
-        else ok = hf_axis<2, WRAP>(c, below, out);
-        if (ok) return 1 + d;
+        if (hf_axis<WRAP>(c, d, below, out)) return 1 + d;
     }
     *out = 0.0;
     return 4;

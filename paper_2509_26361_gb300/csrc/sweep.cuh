@@ -94,7 +94,7 @@ __device__ __forceinline__ int cell_segs(int c00, int c10, int c01, int c11, int
 
 // Circle through A, B, C meeting the grid line x = 0; only roots on the edge
 // (0 <= y <= 1) count, the one nearest ylin is kept (Fig. 2).
-__device__ __noinline__ bool circle_root(P2 A, P2 B, P2 C, double ylin, double *root, double *rad) {
+__device__ __forceinline__ bool circle_root(P2 A, P2 B, P2 C, double ylin, double *root, double *rad) {
     double bx = B.x - A.x, by = B.y - A.y;
     double cx = C.x - A.x, cy = C.y - A.y;
     double b2 = bx * bx + by * by;
@@ -173,6 +173,7 @@ __device__ __forceinline__ int warp_append(int *counter, bool flag) {
 template <int D>
 __global__ void __launch_bounds__(256) advect_kernel(SweepArgs a) {
     __shared__ uint16_t s_mk[3 * TILE_CELLS];
+    __shared__ uint8_t s_c[9 * 9 * 9];  // node colours of the tile and its +1 layer
     __shared__ int s_n;
     const int ntl = *a.count;
     if (blockIdx.x == 0 && threadIdx.x < 4) a.wcount[threadIdx.x] = 0;
@@ -181,16 +182,19 @@ __global__ void __launch_bounds__(256) advect_kernel(SweepArgs a) {
         int o[3];
         tile_origin(a.g, tile, o);
         if (threadIdx.x == 0) s_n = 0;
+        for (int r = threadIdx.x; r < 729; r += blockDim.x) {
+            int rx = r % 9, ry = (r / 9) % 9, rz = r / 81;
+            s_c[r] = __ldg(a.cb + lin(a.g, o[0] + rx, o[1] + ry, o[2] + rz)) & 1;
+        }
         __syncthreads();
         for (int c = threadIdx.x; c < TILE_CELLS; c += blockDim.x) {
             int q[3] = {o[0] + (c & 7), o[1] + ((c >> 3) & 7), o[2] + (c >> 6)};
             bool valid = q[0] < a.g.n[0] && q[1] < a.g.n[1] && q[2] < a.g.n[2];
             int mask = 0;
             if (valid) {
-                const int c0 = __ldg(a.cb + lin3(a.g, q)) & 1;
-                mask = ((__ldg(a.cb + lin(a.g, q[0] + 1, q[1], q[2])) & 1) != c0) |
-                       (((__ldg(a.cb + lin(a.g, q[0], q[1] + 1, q[2])) & 1) != c0) << 1) |
-                       (((__ldg(a.cb + lin(a.g, q[0], q[1], q[2] + 1)) & 1) != c0) << 2);
+                const int r = (c & 7) + 9 * ((c >> 3) & 7) + 81 * (c >> 6);
+                const int c0 = s_c[r];
+                mask = (s_c[r + 1] != c0) | ((s_c[r + 9] != c0) << 1) | ((s_c[r + 81] != c0) << 2);
             }
             for (int e = 0; e < 3; e++) {
                 int slot = warp_append(&s_n, (mask >> e) & 1);
@@ -226,6 +230,10 @@ struct SweepCell {
     static constexpr int A = D, T1 = (D + 1) % 3, T2 = (D + 2) % 3;
     const SweepArgs &a;
     int p[3];
+    // colour bytes of the plane window da in [-2, 2], dt in [-1, 2] of the
+    // family being processed, loaded in one batch (byte (da+2) + 5 (dt+1) of
+    // three 64-bit registers)
+    unsigned long long w0, w1, w2;
 
     __device__ SweepCell(const SweepArgs &args, int x, int y, int z) : a(args) {
         p[0] = x;
@@ -252,11 +260,29 @@ struct SweepCell {
         return lin3(a.g, q);
     }
     template <int TT, int NN>
+    __device__ __forceinline__ void loadw() {
+        unsigned long long v[3] = {0ull, 0ull, 0ull};
+#pragma unroll
+        for (int dt = -1; dt <= 2; dt++)
+#pragma unroll
+            for (int da = -2; da <= 2; da++) {
+                const int i = (da + 2) + 5 * (dt + 1);
+                v[i >> 3] |= (unsigned long long)__ldg(a.cb + pid<TT, NN>(da, dt)) << (8 * (i & 7));
+            }
+        w0 = v[0];
+        w1 = v[1];
+        w2 = v[2];
+    }
+    __device__ __forceinline__ int wb(int da, int dt) const {
+        const int i = (da + 2) + 5 * (dt + 1);
+        const unsigned long long v = i < 8 ? w0 : (i < 16 ? w1 : w2);
+        return (int)((v >> (8 * (i & 7))) & 0xFF);
+    }
+    template <int TT, int NN>
     __device__ int psegs(int da, int dt, int seg[2][2]) const {
-        int i00 = pid<TT, NN>(da, dt);
-        int b00 = __ldg(a.cb + i00);
-        return cell_segs(b00 & 1, colid(pid<TT, NN>(da + 1, dt)), colid(pid<TT, NN>(da, dt + 1)),
-                         colid(pid<TT, NN>(da + 1, dt + 1)), (b00 >> (1 + NN)) & 1, seg);
+        int b00 = wb(da, dt);
+        return cell_segs(b00 & 1, wb(da + 1, dt) & 1, wb(da, dt + 1) & 1, wb(da + 1, dt + 1) & 1,
+                         (b00 >> (1 + NN)) & 1, seg);
     }
     // bin of the advected a-coordinate of the marker on edge code e of cell
     // (da, dt), and the integer da' with x = da' + adv
@@ -376,13 +402,18 @@ struct SweepCell {
         }
         P2 Pa = c2[sel], Pb = c3[sel];
         double ylin = yl[sel];
-        P2 P1, P4;
+        // both neighbours first, then the two independent circle fits (the
+        // compiler interleaves the two FP64 chains)
+        P2 P1 = Pa, P4 = Pb;
         double ya = 0.0, ra = 0.0, yb = 0.0, rb = 0.0;
-        bool va = false, vb = false;
-        if (neighbour<TT, NN>(e2[sel], cd[sel], 0, &P1)) va = circle_root(P1, Pa, Pb, ylin, &ya, &ra);
-        else ev[C_INCONSISTENT]++;
-        if (neighbour<TT, NN>(e3[sel], cd[sel], 0, &P4)) vb = circle_root(Pa, Pb, P4, ylin, &yb, &rb);
-        else ev[C_INCONSISTENT]++;
+        const bool h1 = neighbour<TT, NN>(e2[sel], cd[sel], 0, &P1);
+        const bool h4 = neighbour<TT, NN>(e3[sel], cd[sel], 0, &P4);
+        if (!h1) ev[C_INCONSISTENT]++;
+        if (!h4) ev[C_INCONSISTENT]++;
+        bool va = circle_root(P1, Pa, Pb, ylin, &ya, &ra);
+        bool vb = circle_root(Pa, Pb, P4, ylin, &yb, &rb);
+        va = va && h1;
+        vb = vb && h4;
         double y;
         if (va && vb) {
             double rmax = ra > rb ? ra : rb, rmin = ra > rb ? rb : ra;
@@ -407,7 +438,7 @@ struct SweepCell {
     __device__ int face_phase(int ncol0) const {
         int par = ncol0;
         for (int da = -1; da <= 1; da++) {
-            if (colid(pid<TT, NN>(da, 0)) == colid(pid<TT, NN>(da + 1, 0))) continue;
+            if ((wb(da, 0) & 1) == (wb(da + 1, 0) & 1)) continue;
             int b = __ldg(a.bin[A] + pid<TT, NN>(da, 0));
             if (b >= -2 * da && b < 1 - 2 * da) par ^= 1;
         }
@@ -433,16 +464,29 @@ __device__ __forceinline__ bool saddle4(int c00, int c10, int c01, int c11) {
 }
 
 // ------------------------------------------------------- band pass (integer)
+// staged colour region of a tile, in sweep-local axes: A in [-1, 9], T1 and T2
+// in [0, 8] relative to the tile origin
+constexpr int RA = 11, R1 = 9, R2 = 9;
+
 template <int D>
 __global__ void __launch_bounds__(256) sweep_kernel(SweepArgs a) {
     constexpr int A = D, T1 = (D + 1) % 3, T2 = (D + 2) % 3;
     __shared__ int s_flag;
+    __shared__ uint8_t s_b[RA * R1 * R2];
     const int ntl = *a.count;
     for (int li = blockIdx.x; li < ntl; li += gridDim.x) {
         const int tile = a.list[li];
         int o[3];
         tile_origin(a.g, tile, o);
         if (threadIdx.x == 0) s_flag = 0;
+        for (int r = threadIdx.x; r < RA * R1 * R2; r += blockDim.x) {
+            int ka = r % RA, k1 = (r / RA) % R1, k2 = r / (RA * R1);
+            int q[3];
+            q[A] = o[A] + ka - 1;
+            q[T1] = o[T1] + k1;
+            q[T2] = o[T2] + k2;
+            s_b[r] = __ldg(a.cb + lin3(a.g, q));
+        }
         __syncthreads();
         unsigned ev[C_N] = {0, 0, 0, 0, 0};
         bool mk = false;
@@ -454,8 +498,13 @@ __global__ void __launch_bounds__(256) sweep_kernel(SweepArgs a) {
             if (valid) {
                 SweepCell<D> cell(a, x, y, z);
                 myid = lin(a.g, x, y, z);
+                const int l[3] = {c & 7, (c >> 3) & 7, c >> 6};
+                // staged index of node (da, d1, d2) relative to the cell
+                const int r0 = (l[A] + 1) + RA * (l[T1] + R1 * l[T2]);
+                auto sidx = [&](int da, int d1, int d2) { return r0 + da + RA * (d1 + R1 * d2); };
                 int col[4][2][2];
-                const int c0 = cell.colid(myid);
+                const int myb = s_b[r0];
+                const int c0 = myb & 1;
                 int any = 0;
 #pragma unroll
                 for (int da = 0; da < 4; da++)
@@ -463,14 +512,13 @@ __global__ void __launch_bounds__(256) sweep_kernel(SweepArgs a) {
                     for (int d1 = 0; d1 < 2; d1++)
 #pragma unroll
                         for (int d2 = 0; d2 < 2; d2++) {
-                            int v = (da == 1 && d1 == 0 && d2 == 0) ? c0 : cell.colid(cell.id3(da - 1, d1, d2));
+                            int v = s_b[sidx(da - 1, d1, d2)] & 1;
                             col[da][d1][d2] = v;
                             any |= v ^ c0;
                         }
                 if (!any) {
                     a.cbo[myid] = (uint8_t)(c0 | (c0 << 1) | (c0 << 2) | (c0 << 3));
                 } else {
-                    const int myb = __ldg(a.cb + myid);
                     bool in_marker = (c0 != col[2][0][0]) || (c0 != col[1][1][0]) || (c0 != col[1][0][1]);
                     // bins of the aligned markers on the A-edges (da in {-1,0,1}) of 4 lines
                     int bn[3][2][2];
@@ -552,10 +600,12 @@ __global__ void __launch_bounds__(256) sweep_kernel(SweepArgs a) {
                     push[1] = pres2;
                     if (!pres1 && ((col[1][0][0] ^ m) | (col[2][0][0] ^ m) | (col[0][1][0] ^ m) |
                                    (col[1][1][0] ^ m) | (col[2][1][0] ^ m)))
-                        if (cell.template count_crossings<T1, T2>() >= 2) ev[C_ANNIHILATE]++;
+                        if ((cell.template loadw<T1, T2>(), cell.template count_crossings<T1, T2>()) >= 2)
+                            ev[C_ANNIHILATE]++;
                     if (!pres2 && ((col[1][0][0] ^ m) | (col[2][0][0] ^ m) | (col[0][0][1] ^ m) |
                                    (col[1][0][1] ^ m) | (col[2][0][1] ^ m)))
-                        if (cell.template count_crossings<T2, T1>() >= 2) ev[C_ANNIHILATE]++;
+                        if ((cell.template loadw<T2, T1>(), cell.template count_crossings<T2, T1>()) >= 2)
+                            ev[C_ANNIHILATE]++;
                     out_marker |= pres1 || pres2;
                     // face colours: family 1 faces are normal to T2, family 2 to T1
                     int byte = n0;
@@ -612,6 +662,8 @@ __global__ void __launch_bounds__(128) fp64_kernel(SweepArgs a) {
         const int id = (int)a.work[kind][k];
         const int x = id % a.g.n[0], y = (id / a.g.n[0]) % a.g.n[1], z = id / (a.g.n[0] * a.g.n[1]);
         SweepCell<D> cell(a, x, y, z);
+        if ((kind & 1) == 0) cell.template loadw<T1, T2>();
+        else cell.template loadw<T2, T1>();
         if (kind == 0) {
             cell.template unaligned<T1, T2>(ev);
         } else if (kind == 1) {
