@@ -39,6 +39,10 @@
  *   of its lowest corner; velocity by trilinear interpolation of the MAC
  *   component; periodic grid, at least 8 cells per axis; CFL < 1.
  *
+ * Parity unpinned: the face-centre colour rule (phase of the advected polyline
+ * at the face centre) is checked only by self-consistency and by GPU = oracle;
+ * the paper fixes no value for it.
+ *
  * Layout (shared with the product only as a documented format): node/cell index
  * idx = (k*ny + j)*nx + i.  Colour byte cb[idx]: bit0 = node colour, bit(1+a) =
  * colour of the face normal to axis a whose lowest corner is node idx.
