@@ -200,6 +200,34 @@ int ebit_profile(ebit_ctx *ctx, int enable);
  * launch counts since the last ebit_profile call (synchronises). */
 int ebit_profile_read(ebit_ctx *ctx, double *ms, int64_t *launches);
 
+/* One split advection sweep that allocates no device memory.
+ * The paper has no counterpart: this entry point exists for callers that
+ * cannot allocate device memory -- a flow solver that reserves all of its
+ * device memory at start-up and forbids allocation afterwards, or a real-time
+ * loop in which a cudaMalloc (which may synchronise the device) is not
+ * allowed.  It needs no context: the caller passes the old state, the
+ * velocity and the output buffers (all DEVICE pointers), and the sweep's
+ * intermediate arrays live in one fixed file-scope device array.
+ *   nx, ny, nz, h   grid as in ebit_desc; nx*ny*nz must not exceed 64^3 =
+ *                   262144 cells (EBIT_EINVAL beyond), each axis >= 8.
+ *   dir, u_face, dt as for ebit_advect_sweep.
+ *   cb_in [N], s_in [3N]    state before the sweep (colour bytes, offsets).
+ *   cb_out [N], s_out [3N]  state after the sweep (offsets 0 on edges without
+ *                   a marker); must not overlap the inputs.
+ *   cuda_stream     cudaStream_t for every launch (NULL = default stream).
+ * Every tile is processed (no active band).  Marker displacements of a full
+ * cell or more are clamped and not reported (use ebit_advect_sweep for the
+ * event counters).  The scratch array is about 11.6 MB and is held by every
+ * GPU that loads the library until the process exits; its address is looked
+ * up on the first call made on each device, so make that first call before
+ * any stream capture.  All calls on a device share it: calls that overlap on
+ * the GPU race and must be ordered by the caller.
+ * Errors: EBIT_EINVAL (sizes, dir, null pointers, non-finite h or dt),
+ * EBIT_ECUDA (a launch or copy failed). */
+int ebit_advect_sweep_noalloc(int nx, int ny, int nz, double h, int dir, const uint8_t *cb_in,
+                              const double *s_in, const double *u_face, double dt, uint8_t *cb_out,
+                              double *s_out, void *cuda_stream);
+
 /* Message of the last failed call on this context (never NULL). */
 const char *ebit_last_error(const ebit_ctx *ctx);
 

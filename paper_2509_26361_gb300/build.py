@@ -1,8 +1,9 @@
 """Build libebit.so in-tree with nvcc for sm_103a (GB300).
 
-The library is one CUDA translation unit compiled with --fmad=false, so that
-every floating-point operation of the EBIT kernels rounds separately in the
-written order.  Output: ``paper_2509_26361_gb300/_build/libebit.so``.
+The library is built from two CUDA translation units (the context-based ABI
+and the allocation-free sweep), compiled with --fmad=false so that every
+floating-point operation of the EBIT kernels rounds separately in the written
+order.  Output: ``paper_2509_26361_gb300/_build/libebit.so``.
 """
 from __future__ import annotations
 
@@ -48,7 +49,8 @@ def build(force: bool = False, verbose: bool = False) -> str:
     os.makedirs(OUT_DIR, exist_ok=True)
     tmp = LIB + f".tmp{os.getpid()}"
     cmd = [_nvcc(), "-O3", "-std=c++17", *ARCH, "-lineinfo", "--fmad=false", "-Xcompiler", "-fPIC",
-           "-shared", "-o", tmp, os.path.join(CSRC, "ebit_abi.cu"), "-I", os.path.join(ROOT, "include")]
+           "-shared", "-o", tmp, os.path.join(CSRC, "ebit_abi.cu"), os.path.join(CSRC, "ebit_noalloc.cu"),
+           "-I", os.path.join(ROOT, "include")]
     if verbose:
         cmd.insert(1, "-Xptxas=-v")
     r = subprocess.run(cmd, capture_output=True, text=True)

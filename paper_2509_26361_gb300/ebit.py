@@ -84,6 +84,7 @@ def load(build_if_missing: bool = True):
     lib.ebit_band_tiles.argtypes = [P]
     lib.ebit_profile.argtypes = [P, I]
     lib.ebit_profile_read.argtypes = [P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int64)]
+    lib.ebit_advect_sweep_noalloc.argtypes = [I, I, I, D, I, P, P, P, D, P, P, P]
     lib.ebit_last_error.argtypes = [P]
     lib.ebit_last_error.restype = ctypes.c_char_p
     _lib = lib
@@ -194,6 +195,23 @@ def ebit_profile_read(ctx):
     n = (ctypes.c_int64 * 8)()
     _check(ctx, load().ebit_profile_read(ctx, ms, n))
     return {k: (float(ms[i]), int(n[i])) for i, k in enumerate(PROF_KINDS) if n[i]}
+
+
+def ebit_advect_sweep_noalloc(n3, h, d, cb_in, s_in, u_face, dt, cb_out, s_out, stream=None):
+    """One sweep with no device allocation (see include/ebit.h); all tensors on
+    the device, at most 64^3 cells."""
+    nx, ny, nz = (int(v) for v in n3)
+    n = nx * ny * nz
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    sp = stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream)
+    code = load().ebit_advect_sweep_noalloc(
+        nx, ny, nz, float(h), int(d), _dev(cb_in, torch.uint8, n, "cb_in"), _dev(s_in, torch.float64, 3 * n, "s_in"),
+        _dev(u_face, torch.float64, n, "u_face"), float(dt), _dev(cb_out, torch.uint8, n, "cb_out"),
+        _dev(s_out, torch.float64, 3 * n, "s_out"), ctypes.c_void_p(sp))
+    if code < 0:
+        raise EbitError(code, "ebit_advect_sweep_noalloc failed")
+    return code
 
 
 def ebit_last_error(ctx):
