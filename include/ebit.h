@@ -200,6 +200,50 @@ int ebit_profile(ebit_ctx *ctx, int enable);
  * launch counts since the last ebit_profile call (synchronises). */
 int ebit_profile_read(ebit_ctx *ctx, double *ms, int64_t *launches);
 
+/* ---------------------------------------------------------------------------
+ * Learned curvature.  Not in the paper: a 27 -> 128 -> 128 -> 1 ReLU network
+ * maps the canonically oriented 3x3x3 volume-fraction stencil of an interface
+ * cell to kappa*h, standing in for the height-function curvature of Sec. 2.6
+ * (which stays the fallback).  Canonical orientation: reflect the axes whose
+ * Youngs normal component is negative, then order the axes by increasing |n|.
+ * Inputs: 64 bf16 per stencil -- the 27 values rounded to float and split into
+ * a bf16 head (27 values, 5 zeros) and a bf16 tail (27, 5 zeros).  Tensor-core
+ * kernels (warp-level bf16 MMA, FP32 accumulation).  X buffers must start on a
+ * 16-byte boundary (EBIT_EINVAL otherwise); every call runs on the network's
+ * stream and returns EBIT_EINVAL on null or negative arguments.  Parameters are
+ * ebit_mlp_nparams() floats: W1[128][64], b1[128], W2[128][128], b2[128],
+ * w3[128], b3.  Loss of training: mean of ((y - t) / max(|t|, 0.05))^2; Adam
+ * (0.9, 0.999, 1e-8) on FP32 master weights.
+ * ------------------------------------------------------------------------- */
+typedef struct ebit_mlp ebit_mlp;
+
+int ebit_mlp_nparams(void);
+/* Create a network (parameters zero; set them with ebit_mlp_set_params). */
+int ebit_mlp_create(void *cuda_stream, ebit_mlp **out);
+void ebit_mlp_destroy(ebit_mlp *mlp);
+/* Parameters from / to host or device memory (set resets the Adam state). */
+int ebit_mlp_set_params(ebit_mlp *mlp, const float *params);
+int ebit_mlp_get_params(ebit_mlp *mlp, float *params);
+/* Encoded canonical stencils X [m][64] (bf16 bit patterns, device) of the
+ * cells cells[m] (linear ids, device) of the fractions C [nx*ny*nz] (device). */
+int ebit_mlp_gather(ebit_mlp *mlp, const double *C, int nx, int ny, int nz, const int *cells, int m, uint16_t *X);
+/* y [m] (device, FP32) = network(X [m][64]). */
+int ebit_mlp_forward(ebit_mlp *mlp, const uint16_t *X, int m, float *y);
+/* Gradient of the training loss over one batch X [batch][64], t [batch] into
+ * grad_out [nparams] (host or device); parameters unchanged. */
+int ebit_mlp_gradient(ebit_mlp *mlp, const uint16_t *X, const float *t, int batch, float *grad_out);
+/* One Adam step on a batch; *loss_out (host or device, may be NULL) receives
+ * the summed weighted squared error of the batch. */
+int ebit_mlp_train_step(ebit_mlp *mlp, const uint16_t *X, const float *t, int batch, float lr, float *loss_out);
+/* Wait for the network's stream; EBIT_ECUDA (message in ebit_mlp_last_error)
+ * if a launch or copy on it failed. */
+int ebit_mlp_sync(ebit_mlp *mlp);
+const char *ebit_mlp_last_error(const ebit_mlp *mlp);
+/* Network used by ebit_curvature in modes EBIT_CURV_MLP and EBIT_CURV_MLP_HF
+ * (NULL detaches).  In EBIT_CURV_MLP_HF the learned value is kept unless it
+ * leaves the trained range |kappa h| <= 1 where height functions gave a value. */
+int ebit_set_mlp(ebit_ctx *ctx, ebit_mlp *mlp);
+
 /* One split advection sweep that allocates no device memory.
  * The paper has no counterpart: this entry point exists for callers that
  * cannot allocate device memory -- a flow solver that reserves all of its

@@ -19,10 +19,21 @@
 #include "common.cuh"
 #include "f2v.cuh"
 #include "hf.cuh"
+#include "mlp.cuh"
 #include "state.cuh"
 #include "sweep.cuh"
 
 using namespace ebit;
+
+struct ebit_mlp {
+    cudaStream_t stream;
+    int sms;
+    float *p, *g, *m, *v;      // FP32 parameters, gradient, Adam moments
+    __nv_bfloat16 *w1b, *w2b;  // bf16 copies for the tensor cores
+    float *loss;               // summed weighted squared error of the last step
+    int step;
+    std::string errmsg;
+};
 
 struct ebit_ctx {
     Grid g;
@@ -53,6 +64,7 @@ struct ebit_ctx {
     int *nscan;
     int *zero;                // a device int that stays 0
     int sweeps_since_f2v;
+    ebit_mlp *mlp;            // learned curvature (ebit_set_mlp)
     const double *last_C;
     const double *last_kh;
     const uint8_t *last_st;
@@ -192,6 +204,7 @@ int ebit_create(const ebit_desc *desc, ebit_ctx **out) {
     ctx->cut = ctx->scan = nullptr;
     ctx->cur_if = 0;
     ctx->sweeps_since_f2v = 0;
+    ctx->mlp = nullptr;
     ctx->tile_marker = ctx->tile_dirty = ctx->tile_cchg = nullptr;
     ctx->band_list = ctx->band_count = ctx->work_list = ctx->work_count = ctx->all_list = ctx->all_count = nullptr;
     ctx->ctr = nullptr;
@@ -444,7 +457,9 @@ int ebit_front2vof(ebit_ctx *ctx, double *C, int flags) {
 
 int ebit_curvature(ebit_ctx *ctx, const double *C, double *kappa_h, uint8_t *status, int mode, int flags) {
     if (!ctx || !C || !kappa_h || !status) return fail(ctx, EBIT_EINVAL, "ebit_curvature: null argument");
-    if (mode != EBIT_CURV_HF) return fail(ctx, EBIT_EINVAL, "ebit_curvature: mode not available");
+    if (mode != EBIT_CURV_HF && mode != EBIT_CURV_MLP && mode != EBIT_CURV_MLP_HF)
+        return fail(ctx, EBIT_EINVAL, "ebit_curvature: unknown mode");
+    if (mode != EBIT_CURV_HF && !ctx->mlp) return fail(ctx, EBIT_EINVAL, "ebit_curvature: no network (ebit_set_mlp)");
     bool full = (flags & EBIT_FULL) || ctx->dense || C != ctx->last_C || kappa_h != ctx->last_kh ||
                 status != ctx->last_st;
     const int nw = ctx->cur_if ^ 1;
@@ -479,6 +494,25 @@ int ebit_curvature(ebit_ctx *ctx, const double *C, double *kappa_h, uint8_t *sta
     hf_list_kernel<<<ctx->grid_hfl, 128, 0, ctx->stream>>>(a);
     int r = launch_check(ctx, "hf_list_kernel");
     if (r) return r;
+    if (mode != EBIT_CURV_HF) {
+        // learned curvature on this call's interface cells (height functions
+        // already written: fallback in mode MLP_HF)
+        ProfScope pm(ctx, EBIT_PROF_MLP);
+        MlpArgs m{};
+        m.g = ctx->g;
+        m.C = C;
+        m.cells = reinterpret_cast<const int *>(ctx->iface[nw]);
+        m.ncells = ctx->niface + nw;
+        m.params = ctx->mlp->p;
+        m.w1b = ctx->mlp->w1b;
+        m.w2b = ctx->mlp->w2b;
+        m.kh = kappa_h;
+        m.st = status;
+        m.mode = mode;
+        mlp_fwd_kernel<true, true><<<2 * ctx->sms, 128, FWD_SMEM, ctx->stream>>>(m);
+        r = launch_check(ctx, "mlp_fwd_kernel");
+        if (r) return r;
+    }
     ctx->cur_if = nw;
     ctx->last_kh = kappa_h;
     ctx->last_st = status;
@@ -551,6 +585,181 @@ int ebit_profile_read(ebit_ctx *ctx, double *ms, int64_t *launches) {
     }
     return EBIT_OK;
 }
+
+int ebit_set_mlp(ebit_ctx *ctx, ebit_mlp *mlp) {
+    if (!ctx) return EBIT_EINVAL;
+    ctx->mlp = mlp;
+    return EBIT_OK;
+}
+
+// ------------------------------------------------------- learned curvature
+#define MCU(call)                                                                                          \
+    do {                                                                                                   \
+        cudaError_t e_ = (call);                                                                           \
+        if (e_ != cudaSuccess) {                                                                           \
+            mlp->errmsg = std::string(#call ": ") + cudaGetErrorString(e_);                               \
+            return EBIT_ECUDA;                                                                             \
+        }                                                                                                  \
+    } while (0)
+
+static bool aligned16(const void *p) { return ((uintptr_t)p & 15) == 0; }
+
+int ebit_mlp_nparams(void) { return MLP_NP; }
+
+int ebit_mlp_create(void *cuda_stream, ebit_mlp **out) {
+    if (!out) return EBIT_EINVAL;
+    *out = nullptr;
+    ebit_mlp *mlp = new ebit_mlp();
+    mlp->stream = (cudaStream_t)cuda_stream;
+    mlp->p = mlp->g = mlp->m = mlp->v = mlp->loss = nullptr;
+    mlp->w1b = mlp->w2b = nullptr;
+    mlp->step = 0;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&mlp->sms, cudaDevAttrMultiProcessorCount, dev);
+    bool ok = cudaMalloc((void **)&mlp->p, MLP_NP * 4) == cudaSuccess &&
+              cudaMalloc((void **)&mlp->g, MLP_NP * 4) == cudaSuccess &&
+              cudaMalloc((void **)&mlp->m, MLP_NP * 4) == cudaSuccess &&
+              cudaMalloc((void **)&mlp->v, MLP_NP * 4) == cudaSuccess &&
+              cudaMalloc((void **)&mlp->w1b, MLP_H * MLP_IN * 2) == cudaSuccess &&
+              cudaMalloc((void **)&mlp->w2b, MLP_H * MLP_H * 2) == cudaSuccess &&
+              cudaMalloc((void **)&mlp->loss, 4) == cudaSuccess;
+    if (!ok) {
+        cudaGetLastError();
+        ebit_mlp_destroy(mlp);
+        return EBIT_ENOMEM;
+    }
+    if (cudaFuncSetAttribute(mlp_fwd_kernel<false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, FWD_SMEM) !=
+            cudaSuccess ||
+        cudaFuncSetAttribute(mlp_fwd_kernel<true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, FWD_SMEM) !=
+            cudaSuccess ||
+        cudaFuncSetAttribute(mlp_train_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, TRAIN_SMEM) !=
+            cudaSuccess) {
+        cudaGetLastError();
+        ebit_mlp_destroy(mlp);
+        return EBIT_ECUDA;
+    }
+    cudaMemsetAsync(mlp->p, 0, MLP_NP * 4, mlp->stream);
+    cudaMemsetAsync(mlp->g, 0, MLP_NP * 4, mlp->stream);
+    cudaMemsetAsync(mlp->m, 0, MLP_NP * 4, mlp->stream);
+    cudaMemsetAsync(mlp->v, 0, MLP_NP * 4, mlp->stream);
+    if (cudaGetLastError() != cudaSuccess) {
+        ebit_mlp_destroy(mlp);
+        return EBIT_ECUDA;
+    }
+    *out = mlp;
+    return EBIT_OK;
+}
+
+void ebit_mlp_destroy(ebit_mlp *mlp) {
+    if (!mlp) return;
+    cudaStreamSynchronize(mlp->stream);
+    cudaFree(mlp->p);
+    cudaFree(mlp->g);
+    cudaFree(mlp->m);
+    cudaFree(mlp->v);
+    cudaFree(mlp->w1b);
+    cudaFree(mlp->w2b);
+    cudaFree(mlp->loss);
+    delete mlp;
+}
+
+int ebit_mlp_set_params(ebit_mlp *mlp, const float *params) {
+    if (!mlp || !params) return EBIT_EINVAL;
+    MCU(cudaMemcpyAsync(mlp->p, params, MLP_NP * 4, cudaMemcpyDefault, mlp->stream));
+    MCU(cudaMemsetAsync(mlp->g, 0, MLP_NP * 4, mlp->stream));
+    MCU(cudaMemsetAsync(mlp->m, 0, MLP_NP * 4, mlp->stream));
+    MCU(cudaMemsetAsync(mlp->v, 0, MLP_NP * 4, mlp->stream));
+    mlp->step = 0;
+    mlp_cast_kernel<<<(MLP_NP + 255) / 256, 256, 0, mlp->stream>>>(mlp->p, mlp->w1b, mlp->w2b);
+    MCU(cudaGetLastError());
+    return EBIT_OK;
+}
+
+int ebit_mlp_get_params(ebit_mlp *mlp, float *params) {
+    if (!mlp || !params) return EBIT_EINVAL;
+    MCU(cudaMemcpyAsync(params, mlp->p, MLP_NP * 4, cudaMemcpyDefault, mlp->stream));
+    MCU(cudaStreamSynchronize(mlp->stream));
+    return EBIT_OK;
+}
+
+int ebit_mlp_gather(ebit_mlp *mlp, const double *C, int nx, int ny, int nz, const int *cells, int m, uint16_t *X) {
+    if (!mlp || !C || !cells || !X || m < 0 || nx < 8 || ny < 8 || nz < 8 || !aligned16(X)) return EBIT_EINVAL;
+    if (m == 0) return EBIT_OK;
+    Grid g{};
+    g.n[0] = nx;
+    g.n[1] = ny;
+    g.n[2] = nz;
+    mlp_gather_kernel<<<std::min((m + 127) / 128, 8 * mlp->sms), 128, 0, mlp->stream>>>(
+        C, g, cells, m, reinterpret_cast<__nv_bfloat16 *>(X));
+    MCU(cudaGetLastError());
+    return EBIT_OK;
+}
+
+int ebit_mlp_forward(ebit_mlp *mlp, const uint16_t *X, int m, float *y) {
+    if (!mlp || !X || !y || m < 0 || !aligned16(X)) return EBIT_EINVAL;
+    if (m == 0) return EBIT_OK;
+    MlpArgs a{};
+    a.X = reinterpret_cast<const __nv_bfloat16 *>(X);
+    a.m = m;
+    a.ncells = nullptr;
+    a.params = mlp->p;
+    a.w1b = mlp->w1b;
+    a.w2b = mlp->w2b;
+    a.y = y;
+    const int ntile = (m + 127) / 128;
+    mlp_fwd_kernel<false, false><<<std::min(ntile, 2 * mlp->sms), 128, FWD_SMEM, mlp->stream>>>(a);
+    MCU(cudaGetLastError());
+    return EBIT_OK;
+}
+
+static int mlp_grad_launch(ebit_mlp *mlp, const uint16_t *X, const float *t, int batch) {
+    MCU(cudaMemsetAsync(mlp->loss, 0, 4, mlp->stream));
+    MlpArgs a{};
+    a.X = reinterpret_cast<const __nv_bfloat16 *>(X);
+    a.t = t;
+    a.batch = batch;
+    a.params = mlp->p;
+    a.w1b = mlp->w1b;
+    a.w2b = mlp->w2b;
+    a.grad = mlp->g;
+    a.loss = mlp->loss;
+    const int ntile = (batch + 127) / 128;
+    mlp_train_kernel<<<std::min(ntile, mlp->sms), 128, TRAIN_SMEM, mlp->stream>>>(a);
+    MCU(cudaGetLastError());
+    return EBIT_OK;
+}
+
+int ebit_mlp_gradient(ebit_mlp *mlp, const uint16_t *X, const float *t, int batch, float *grad_out) {
+    if (!mlp || !X || !t || !grad_out || batch <= 0 || !aligned16(X)) return EBIT_EINVAL;
+    MCU(cudaMemsetAsync(mlp->g, 0, MLP_NP * 4, mlp->stream));
+    int r = mlp_grad_launch(mlp, X, t, batch);
+    if (r) return r;
+    MCU(cudaMemcpyAsync(grad_out, mlp->g, MLP_NP * 4, cudaMemcpyDefault, mlp->stream));
+    MCU(cudaMemsetAsync(mlp->g, 0, MLP_NP * 4, mlp->stream));
+    return EBIT_OK;
+}
+
+int ebit_mlp_train_step(ebit_mlp *mlp, const uint16_t *X, const float *t, int batch, float lr, float *loss_out) {
+    if (!mlp || !X || !t || batch <= 0 || !(lr > 0.0f) || !aligned16(X)) return EBIT_EINVAL;
+    int r = mlp_grad_launch(mlp, X, t, batch);
+    if (r) return r;
+    mlp->step++;
+    const float bc1 = 1.0f - powf(0.9f, (float)mlp->step), bc2 = 1.0f - powf(0.999f, (float)mlp->step);
+    mlp_adam_kernel<<<(MLP_NP + 255) / 256, 256, 0, mlp->stream>>>(mlp->p, mlp->g, mlp->m, mlp->v, mlp->w1b, mlp->w2b,
+                                                                  lr, bc1, bc2);
+    MCU(cudaGetLastError());
+    if (loss_out) MCU(cudaMemcpyAsync(loss_out, mlp->loss, 4, cudaMemcpyDefault, mlp->stream));
+    return EBIT_OK;
+}
+
+int ebit_mlp_sync(ebit_mlp *mlp) {
+    if (!mlp) return EBIT_EINVAL;
+    MCU(cudaStreamSynchronize(mlp->stream));
+    return EBIT_OK;
+}
+
+const char *ebit_mlp_last_error(const ebit_mlp *mlp) { return mlp ? mlp->errmsg.c_str() : "null network"; }
 
 const char *ebit_last_error(const ebit_ctx *ctx) {
     if (!ctx) return "null context";

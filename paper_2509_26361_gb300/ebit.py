@@ -85,6 +85,20 @@ def load(build_if_missing: bool = True):
     lib.ebit_profile.argtypes = [P, I]
     lib.ebit_profile_read.argtypes = [P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int64)]
     lib.ebit_advect_sweep_noalloc.argtypes = [I, I, I, D, I, P, P, P, D, P, P, P]
+    lib.ebit_mlp_nparams.argtypes = []
+    lib.ebit_mlp_create.argtypes = [P, ctypes.POINTER(ctypes.c_void_p)]
+    lib.ebit_mlp_destroy.argtypes = [P]
+    lib.ebit_mlp_destroy.restype = None
+    lib.ebit_mlp_set_params.argtypes = [P, P]
+    lib.ebit_mlp_get_params.argtypes = [P, P]
+    lib.ebit_mlp_gather.argtypes = [P, P, I, I, I, P, I, P]
+    lib.ebit_mlp_forward.argtypes = [P, P, I, P]
+    lib.ebit_mlp_gradient.argtypes = [P, P, P, I, P]
+    lib.ebit_mlp_train_step.argtypes = [P, P, P, I, ctypes.c_float, P]
+    lib.ebit_mlp_sync.argtypes = [P]
+    lib.ebit_mlp_last_error.argtypes = [P]
+    lib.ebit_mlp_last_error.restype = ctypes.c_char_p
+    lib.ebit_set_mlp.argtypes = [P, P]
     lib.ebit_last_error.argtypes = [P]
     lib.ebit_last_error.restype = ctypes.c_char_p
     _lib = lib
@@ -218,6 +232,127 @@ def ebit_last_error(ctx):
     return load().ebit_last_error(ctx).decode()
 
 
+# ------------------------------------------------------- learned curvature
+def _mcheck(mlp, code):
+    if code < 0:
+        raise EbitError(code, load().ebit_mlp_last_error(mlp).decode())
+    return code
+
+
+def ebit_mlp_nparams():
+    return int(load().ebit_mlp_nparams())
+
+
+def ebit_mlp_create(stream=None):
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    sp = stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream)
+    out = ctypes.c_void_p()
+    code = load().ebit_mlp_create(ctypes.c_void_p(sp), ctypes.byref(out))
+    if code != EBIT_OK:
+        raise EbitError(code, "ebit_mlp_create failed")
+    return out
+
+
+def ebit_mlp_destroy(mlp):
+    load().ebit_mlp_destroy(mlp)
+
+
+def ebit_mlp_set_params(mlp, params):
+    return _mcheck(mlp, load().ebit_mlp_set_params(mlp, _any(params, torch.float32, ebit_mlp_nparams(), "params")))
+
+
+def ebit_mlp_get_params(mlp, params):
+    return _mcheck(mlp, load().ebit_mlp_get_params(mlp, _any(params, torch.float32, ebit_mlp_nparams(), "params")))
+
+
+def ebit_mlp_gather(mlp, C, n3, cells, X):
+    nx, ny, nz = (int(v) for v in n3)
+    m = cells.numel()
+    return _mcheck(mlp, load().ebit_mlp_gather(mlp, _dev(C, torch.float64, nx * ny * nz, "C"), nx, ny, nz,
+                                               _dev(cells, torch.int32, m, "cells"), m,
+                                               _dev(X, torch.bfloat16, 64 * m, "X")))
+
+
+def ebit_mlp_forward(mlp, X, y):
+    m = y.numel()
+    return _mcheck(mlp, load().ebit_mlp_forward(mlp, _dev(X, torch.bfloat16, 64 * m, "X"), m,
+                                                _dev(y, torch.float32, m, "y")))
+
+
+def ebit_mlp_gradient(mlp, X, t, grad):
+    b = t.numel()
+    return _mcheck(mlp, load().ebit_mlp_gradient(mlp, _dev(X, torch.bfloat16, 64 * b, "X"),
+                                                 _dev(t, torch.float32, b, "t"), b,
+                                                 _any(grad, torch.float32, ebit_mlp_nparams(), "grad")))
+
+
+def ebit_mlp_train_step(mlp, X, t, lr, loss=None):
+    b = t.numel()
+    lp = None if loss is None else _dev(loss, torch.float32, 1, "loss")
+    return _mcheck(mlp, load().ebit_mlp_train_step(mlp, _dev(X, torch.bfloat16, 64 * b, "X"),
+                                                   _dev(t, torch.float32, b, "t"), b, float(lr), lp))
+
+
+def ebit_mlp_sync(mlp):
+    return _mcheck(mlp, load().ebit_mlp_sync(mlp))
+
+
+def ebit_set_mlp(ctx, mlp):
+    return _check(ctx, load().ebit_set_mlp(ctx, mlp))
+
+
+class Mlp:
+    """The learned-curvature network on the device (parameters, Adam state)."""
+
+    def __init__(self, params=None, stream=None):
+        self.h = ebit_mlp_create(stream)
+        self.nparams = ebit_mlp_nparams()
+        if params is not None:
+            self.set_params(params)
+
+    def close(self):
+        if self.h is not None:
+            ebit_mlp_destroy(self.h)
+            self.h = None
+
+    def __del__(self):  # pragma: no cover
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_params(self, params):
+        p = torch.as_tensor(params, dtype=torch.float32).contiguous().cuda()
+        ebit_mlp_set_params(self.h, p)
+
+    def get_params(self):
+        p = torch.empty(self.nparams, dtype=torch.float32, device="cuda")
+        ebit_mlp_get_params(self.h, p)
+        return p
+
+    def gather(self, C, n3, cells):
+        X = torch.empty((cells.numel(), 64), dtype=torch.bfloat16, device="cuda")
+        ebit_mlp_gather(self.h, C, n3, cells, X)
+        return X
+
+    def forward(self, X):
+        y = torch.empty(X.shape[0], dtype=torch.float32, device="cuda")
+        ebit_mlp_forward(self.h, X, y)
+        return y
+
+    def gradient(self, X, t):
+        g = torch.empty(self.nparams, dtype=torch.float32, device="cuda")
+        ebit_mlp_gradient(self.h, X, t, g)
+        return g
+
+    def train_step(self, X, t, lr, loss=None):
+        return ebit_mlp_train_step(self.h, X, t, lr, loss)
+
+    def sync(self):
+        return ebit_mlp_sync(self.h)
+
+
 # ------------------------------------------------------------ convenience
 class Grid:
     """One EBIT context with its device buffers (torch tensors on ``device``).
@@ -281,6 +416,9 @@ class Grid:
 
     def band_tiles(self):
         return ebit_band_tiles(self.ctx)
+
+    def set_mlp(self, mlp):
+        return ebit_set_mlp(self.ctx, None if mlp is None else mlp.h)
 
     def profile(self, enable=True):
         return ebit_profile(self.ctx, enable)

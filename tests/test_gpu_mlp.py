@@ -1,0 +1,115 @@
+"""Learned curvature on the GPU (bf16 tensor-core kernels, through the C ABI) against the
+FP64 oracle of oracle/mlp.py: canonical stencils bit-exact, forward pass and
+gradients within the stated tolerances (bf16 operands, FP32 accumulation)."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from oracle import mlp as omlp
+from paper_2509_26361_gb300 import ebit
+from paper_2509_26361_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+def dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def sphere_fractions(n=48, seed=3, count=3):
+    w = W.fourier_spheres(n=n, seed=seed, count=count, rmin=0.08, rmax=0.2, steps=1)
+    st = oracle.init(w.phi, w.phi_faces)
+    C, _ = oracle.front2vof(st)
+    cells = np.nonzero(((C > 0) & (C < 1)).ravel())[0].astype(np.int32)
+    return w.n3, C, cells
+
+
+def bf16_bits_to_f64(X):
+    return X.float().cpu().numpy().astype(np.float64)
+
+
+def test_gather_matches_oracle_canonical_encoding():
+    n3, C, cells = sphere_fractions()
+    m = ebit.Mlp()
+    X = m.gather(dev(C), n3, dev(cells))
+    ref = omlp.encode(omlp.canonical_stencil(omlp.gather_stencils(C, cells)))
+    assert np.array_equal(bf16_bits_to_f64(X), ref)
+    m.close()
+
+
+def _random_inputs(n, rng):
+    blk = rng.uniform(0, 1, size=(n, 3, 3, 3))
+    return omlp.encode(omlp.canonical_stencil(blk))
+
+
+def test_forward_matches_oracle():
+    rng = np.random.default_rng(1)
+    p = omlp.init_params(2) + rng.normal(scale=0.02, size=omlp.N_PARAMS)
+    p = p.astype(np.float32).astype(np.float64)
+    X = _random_inputs(1000, rng)  # ragged tail: 1000 = 7 tiles of 128 + 104
+    m = ebit.Mlp(p)
+    y = m.forward(dev(X).to(torch.bfloat16)).cpu().numpy()
+    m.sync()
+    yr, _ = omlp.forward(p, X, emulate=True)
+    err = np.abs(y - yr)
+    assert np.max(err / (np.abs(yr) + 0.1)) <= 2e-3, np.max(err)
+    m.close()
+
+
+def test_gradient_matches_oracle_backprop():
+    rng = np.random.default_rng(5)
+    p = omlp.init_params(4) + rng.normal(scale=0.02, size=omlp.N_PARAMS)
+    p = p.astype(np.float32).astype(np.float64)
+    B = 640
+    X = _random_inputs(B, rng)
+    t = rng.uniform(0.05, 0.8, size=B).astype(np.float32).astype(np.float64)
+    m = ebit.Mlp(p)
+    g = m.gradient(dev(X).to(torch.bfloat16), dev(t.astype(np.float32))).cpu().numpy().astype(np.float64)
+    m.sync()
+    _, gr = omlp.loss_and_grad(p, X, t, emulate=True)
+    blocks = [("W1", 0, 128 * 64), ("b1", 8192, 8320), ("W2", 8320, 8320 + 16384), ("b2", 24704, 24832),
+              ("w3", 24832, 24960), ("b3", 24960, 24961)]
+    for name, a, b in blocks:
+        rel = np.linalg.norm(g[a:b] - gr[a:b]) / max(np.linalg.norm(gr[a:b]), 1e-12)
+        assert rel <= 2e-2, (name, rel)
+    m.close()
+
+
+def test_training_steps_reduce_the_loss():
+    rng = np.random.default_rng(9)
+    X = _random_inputs(4096, rng)
+    # a smooth target of the stencil: a fixed random linear map of the heads
+    wv = rng.normal(size=27)
+    t = (0.3 + 0.05 * np.tanh(X[:, :27] @ wv)).astype(np.float32)
+    m = ebit.Mlp(omlp.init_params(0))
+    Xd, td = dev(X).to(torch.bfloat16), dev(t)
+    loss = torch.zeros(1, dtype=torch.float32, device="cuda")
+    m.train_step(Xd, td, 1e-3, loss)
+    first = loss.item()
+    for _ in range(300):
+        m.train_step(Xd, td, 1e-3, loss)
+    m.sync()
+    assert loss.item() < 0.2 * first, (first, loss.item())
+    m.close()
+
+
+def test_curvature_mode_uses_the_network():
+    n3, C, cells = sphere_fractions()
+    rng = np.random.default_rng(2)
+    p = omlp.init_params(7) + rng.normal(scale=0.01, size=omlp.N_PARAMS)
+    m = ebit.Mlp(p)
+    g = ebit.Grid(*n3)
+    g.set_mlp(m)
+    Cd = dev(C)
+    kh = torch.zeros_like(Cd)
+    st = torch.zeros(Cd.shape, dtype=torch.uint8, device="cuda")
+    g.curvature(Cd, kh, st, mode=ebit.EBIT_CURV_MLP, flags=ebit.EBIT_FULL)
+    X = m.gather(Cd, n3, dev(cells))
+    y = m.forward(X).cpu().numpy()
+    st_h = st.cpu().numpy().ravel()
+    assert np.all(st_h[cells] == ebit.ST_MLP)
+    assert np.array_equal(np.nonzero(st_h)[0], np.sort(cells))
+    assert np.allclose(kh.cpu().numpy().ravel()[cells], y, rtol=0, atol=1e-6)
+    g.close()
+    m.close()
