@@ -188,10 +188,11 @@ enum {
     EBIT_PROF_SWEEP = 0, /* split-sweep reconstruction kernels */
     EBIT_PROF_BAND = 1,  /* band/tile-list kernels and their memsets */
     EBIT_PROF_F2V = 2,   /* Front2VOF kernel */
-    EBIT_PROF_HF = 3,    /* height-function kernel */
-    EBIT_PROF_MLP = 4,   /* learned-curvature kernels */
+    EBIT_PROF_HF = 3,    /* height-function kernel (interface-cell list pass) */
+    EBIT_PROF_MLP = 4,   /* learned-curvature kernels (with the height-function fallback pass) */
     EBIT_PROF_ADVECT = 5, /* marker advection (velocity interpolation) kernels */
     EBIT_PROF_FP64 = 6,   /* sweep work lists: circle fits and face-centre colours */
+    EBIT_PROF_SCAN = 7,   /* full interface-cell scan of ebit_curvature (EBIT_FULL or foreign C) */
     EBIT_PROF_KINDS = 8
 };
 /* enable != 0 switches timing on and zeroes the sums; 0 switches it off. */
@@ -225,23 +226,32 @@ void ebit_mlp_destroy(ebit_mlp *mlp);
 int ebit_mlp_set_params(ebit_mlp *mlp, const float *params);
 int ebit_mlp_get_params(ebit_mlp *mlp, float *params);
 /* Encoded canonical stencils X [m][64] (bf16 bit patterns, device) of the
- * cells cells[m] (linear ids, device) of the fractions C [nx*ny*nz] (device). */
-int ebit_mlp_gather(ebit_mlp *mlp, const double *C, int nx, int ny, int nz, const int *cells, int m, uint16_t *X);
+ * cells cells[m] (linear ids, device) of the fractions C [nx*ny*nz] (device).
+ * frag [m] (device, may be NULL) receives 1 where the 3x3x3 block holds a cell
+ * with C > 0 that is not 6-connected to the centre through cells with C > 0. */
+int ebit_mlp_gather(ebit_mlp *mlp, const double *C, int nx, int ny, int nz, const int *cells, int m, uint16_t *X,
+                    uint8_t *frag);
 /* y [m] (device, FP32) = network(X [m][64]). */
 int ebit_mlp_forward(ebit_mlp *mlp, const uint16_t *X, int m, float *y);
 /* Gradient of the training loss over one batch X [batch][64], t [batch] into
  * grad_out [nparams] (host or device); parameters unchanged. */
 int ebit_mlp_gradient(ebit_mlp *mlp, const uint16_t *X, const float *t, int batch, float *grad_out);
-/* One Adam step on a batch; *loss_out (host or device, may be NULL) receives
- * the summed weighted squared error of the batch. */
-int ebit_mlp_train_step(ebit_mlp *mlp, const uint16_t *X, const float *t, int batch, float lr, float *loss_out);
+/* One Adam step on a batch: rows X[idx[r]], t[idx[r]] for r < batch (idx
+ * device int32, or NULL for the first batch rows).  *loss_out (host or device,
+ * may be NULL) receives the summed weighted squared error of the batch. */
+int ebit_mlp_train_step(ebit_mlp *mlp, const uint16_t *X, const float *t, const int *idx, int batch, float lr,
+                        float *loss_out);
 /* Wait for the network's stream; EBIT_ECUDA (message in ebit_mlp_last_error)
  * if a launch or copy on it failed. */
 int ebit_mlp_sync(ebit_mlp *mlp);
 const char *ebit_mlp_last_error(const ebit_mlp *mlp);
 /* Network used by ebit_curvature in modes EBIT_CURV_MLP and EBIT_CURV_MLP_HF
- * (NULL detaches).  In EBIT_CURV_MLP_HF the learned value is kept unless it
- * leaves the trained range |kappa h| <= 1 where height functions gave a value. */
+ * (NULL detaches).  EBIT_CURV_MLP writes the learned value (status
+ * EBIT_ST_MLP) on every interface cell and computes no height functions.
+ * EBIT_CURV_MLP_HF computes height functions only where the learned value
+ * leaves the trained range |kappa h| <= 1 or the stencil holds a phase-1
+ * fragment (see ebit_mlp_gather); those cells get the height-function value
+ * and status. */
 int ebit_set_mlp(ebit_ctx *ctx, ebit_mlp *mlp);
 
 /* One split advection sweep that allocates no device memory.

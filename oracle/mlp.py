@@ -16,7 +16,10 @@ restates, in plain numpy FP64:
 * the forward pass as the tensor-core kernels compute it: layer 1 and 2 from
   bfloat16 operands (weights, inputs, and the layer-1 activation rounded to
   bfloat16), ReLU, the output layer from the layer-2 activation unrounded;
-* the backward pass (mean-squared relative error loss) and Adam.
+* the backward pass (mean-squared relative error loss) and Adam;
+* the fallback rules of the learned curvature: height functions where the
+  learned value leaves |kappa h| <= 1 or where the 3x3x3 stencil holds a cell
+  with C > 0 that is not face-connected to the centre through such cells.
 
 Parameters are one flat float vector in this order: W1[128][64], b1[128],
 W2[128][128], b2[128], w3[128], b3[1].
@@ -155,6 +158,47 @@ def gather_stencils(C, cells):
             for dx in (-1, 0, 1):
                 blk[:, dz + 1, dy + 1, dx + 1] = C[(z + dz) % nz, (y + dy) % ny, (x + dx) % nx]
     return blk
+
+
+def fragmented(blk):
+    """True if a cell of the 3x3x3 block (blk[dz, dy, dx]) with C > 0 cannot be
+    reached from the centre by face steps through cells with C > 0 (breadth-
+    first search from the centre)."""
+    blk = np.asarray(blk)
+    pos = {(z, y, x) for z in range(3) for y in range(3) for x in range(3) if blk[z, y, x] > 0.0}
+    seen = set()
+    if (1, 1, 1) in pos:
+        seen.add((1, 1, 1))
+        todo = [(1, 1, 1)]
+        while todo:
+            z, y, x = todo.pop()
+            for dz, dy, dx in ((1, 0, 0), (-1, 0, 0), (0, 1, 0), (0, -1, 0), (0, 0, 1), (0, 0, -1)):
+                q = (z + dz, y + dy, x + dx)
+                if q in pos and q not in seen:
+                    seen.add(q)
+                    todo.append(q)
+    return seen != pos
+
+
+def learned_curvature(C, p, mode, hf_kh, hf_st, cells=None):
+    """kappa*h and status on the interface cells (0 < C < 1) of C[nz, ny, nx]:
+    mode 1 the network's value (status 5) everywhere; mode 2 the height-function
+    value and status (hf_kh, hf_st, flat arrays) where the network's value has
+    |y| > 1 or the stencil is fragmented.  Returns (cells, kh, st, y, frag)."""
+    flat = np.asarray(C).reshape(-1)
+    if cells is None:
+        cells = np.nonzero((flat > 0.0) & (flat < 1.0))[0]
+    blk = gather_stencils(np.asarray(C), cells)
+    X = encode(canonical_stencil(blk))
+    y, _ = forward(p, X, emulate=True)
+    frag = np.array([fragmented(b) for b in blk], dtype=bool)
+    kh = y.copy()
+    st = np.full(len(cells), 5, dtype=np.uint8)
+    if mode == 2:
+        fb = (np.abs(y) > 1.0) | frag
+        kh[fb] = np.asarray(hf_kh).reshape(-1)[cells[fb]]
+        st[fb] = np.asarray(hf_st).reshape(-1)[cells[fb]]
+    return cells, kh, st, y, frag
 
 
 # ------------------------------------------------------------- network

@@ -262,7 +262,7 @@ int ebit_create(const ebit_desc *desc, ebit_ctx **out) {
     ctx->grid_f2vl = ctx->sms * std::max(occ, 1);
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, hf_scan_kernel, 256, 0);
     ctx->grid_hf = std::max(1, std::min(nt, ctx->sms * std::max(occ, 1)));
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, hf_list_kernel, 128, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, hf_list_kernel<true>, 128, 0);
     ctx->grid_hfl = ctx->sms * std::max(occ, 1);
     cudaMemsetAsync(ctx->wcount, 0, 4 * sizeof(int), ctx->stream);
     cudaMemsetAsync(ctx->ncut, 0, sizeof(int), ctx->stream);
@@ -473,9 +473,9 @@ int ebit_curvature(ebit_ctx *ctx, const double *C, double *kappa_h, uint8_t *sta
     a.list = ctx->all_list;
     a.count = ctx->all_count;
     CU(cudaMemsetAsync(ctx->niface + nw, 0, sizeof(int), ctx->stream));
-    ProfScope ps(ctx, EBIT_PROF_HF);
     if (full) {
         // any C: scan every tile, reset non-interface cells, list the interface cells
+        ProfScope ps(ctx, EBIT_PROF_SCAN);
         CU(cudaMemsetAsync(ctx->nscan, 0, sizeof(int), ctx->stream));
         hf_scan_kernel<<<ctx->grid_hf, 256, 0, ctx->stream>>>(a, ctx->scan, ctx->nscan);
         int r = launch_check(ctx, "hf_scan_kernel");
@@ -491,12 +491,19 @@ int ebit_curvature(ebit_ctx *ctx, const double *C, double *kappa_h, uint8_t *sta
         a.cand = ctx->cut;
         a.ncand = ctx->ncut;
     }
-    hf_list_kernel<<<ctx->grid_hfl, 128, 0, ctx->stream>>>(a);
-    int r = launch_check(ctx, "hf_list_kernel");
-    if (r) return r;
+    {
+        // height functions on every interface cell (mode HF), or only the list
+        ProfScope ps(ctx, EBIT_PROF_HF);
+        if (mode == EBIT_CURV_HF)
+            hf_list_kernel<true><<<ctx->grid_hfl, 128, 0, ctx->stream>>>(a);
+        else
+            hf_list_kernel<false><<<ctx->grid_hfl, 128, 0, ctx->stream>>>(a);
+        int r = launch_check(ctx, "hf_list_kernel");
+        if (r) return r;
+    }
     if (mode != EBIT_CURV_HF) {
         // learned curvature on this call's interface cells (height functions
-        // already written: fallback in mode MLP_HF)
+        // where it falls back, mode MLP_HF)
         ProfScope pm(ctx, EBIT_PROF_MLP);
         MlpArgs m{};
         m.g = ctx->g;
@@ -509,9 +516,25 @@ int ebit_curvature(ebit_ctx *ctx, const double *C, double *kappa_h, uint8_t *sta
         m.kh = kappa_h;
         m.st = status;
         m.mode = mode;
+        m.fb = ctx->scan;  // free again: the listing pass above has consumed it
+        m.nfb = ctx->nscan;
+        CU(cudaMemsetAsync(ctx->nscan, 0, sizeof(int), ctx->stream));
         mlp_fwd_kernel<true, true><<<2 * ctx->sms, 128, FWD_SMEM, ctx->stream>>>(m);
-        r = launch_check(ctx, "mlp_fwd_kernel");
+        int r = launch_check(ctx, "mlp_fwd_kernel");
         if (r) return r;
+        if (mode == EBIT_CURV_MLP_HF) {
+            // height functions on the cells the learned value left to them
+            HFArgs f = a;
+            f.prev = ctx->iface[ctx->cur_if];
+            f.nprev = ctx->zero;
+            f.cand = ctx->scan;
+            f.ncand = ctx->nscan;
+            f.iface = nullptr;
+            f.niface = nullptr;
+            hf_list_kernel<true><<<ctx->grid_hfl, 128, 0, ctx->stream>>>(f);
+            r = launch_check(ctx, "hf_list_kernel");
+            if (r) return r;
+        }
     }
     ctx->cur_if = nw;
     ctx->last_kh = kappa_h;
@@ -683,7 +706,8 @@ int ebit_mlp_get_params(ebit_mlp *mlp, float *params) {
     return EBIT_OK;
 }
 
-int ebit_mlp_gather(ebit_mlp *mlp, const double *C, int nx, int ny, int nz, const int *cells, int m, uint16_t *X) {
+int ebit_mlp_gather(ebit_mlp *mlp, const double *C, int nx, int ny, int nz, const int *cells, int m, uint16_t *X,
+                    uint8_t *frag) {
     if (!mlp || !C || !cells || !X || m < 0 || nx < 8 || ny < 8 || nz < 8 || !aligned16(X)) return EBIT_EINVAL;
     if (m == 0) return EBIT_OK;
     Grid g{};
@@ -691,7 +715,7 @@ int ebit_mlp_gather(ebit_mlp *mlp, const double *C, int nx, int ny, int nz, cons
     g.n[1] = ny;
     g.n[2] = nz;
     mlp_gather_kernel<<<std::min((m + 127) / 128, 8 * mlp->sms), 128, 0, mlp->stream>>>(
-        C, g, cells, m, reinterpret_cast<__nv_bfloat16 *>(X));
+        C, g, cells, m, reinterpret_cast<__nv_bfloat16 *>(X), frag);
     MCU(cudaGetLastError());
     return EBIT_OK;
 }
@@ -713,11 +737,12 @@ int ebit_mlp_forward(ebit_mlp *mlp, const uint16_t *X, int m, float *y) {
     return EBIT_OK;
 }
 
-static int mlp_grad_launch(ebit_mlp *mlp, const uint16_t *X, const float *t, int batch) {
+static int mlp_grad_launch(ebit_mlp *mlp, const uint16_t *X, const float *t, const int *idx, int batch) {
     MCU(cudaMemsetAsync(mlp->loss, 0, 4, mlp->stream));
     MlpArgs a{};
     a.X = reinterpret_cast<const __nv_bfloat16 *>(X);
     a.t = t;
+    a.idx = idx;
     a.batch = batch;
     a.params = mlp->p;
     a.w1b = mlp->w1b;
@@ -733,16 +758,17 @@ static int mlp_grad_launch(ebit_mlp *mlp, const uint16_t *X, const float *t, int
 int ebit_mlp_gradient(ebit_mlp *mlp, const uint16_t *X, const float *t, int batch, float *grad_out) {
     if (!mlp || !X || !t || !grad_out || batch <= 0 || !aligned16(X)) return EBIT_EINVAL;
     MCU(cudaMemsetAsync(mlp->g, 0, MLP_NP * 4, mlp->stream));
-    int r = mlp_grad_launch(mlp, X, t, batch);
+    int r = mlp_grad_launch(mlp, X, t, nullptr, batch);
     if (r) return r;
     MCU(cudaMemcpyAsync(grad_out, mlp->g, MLP_NP * 4, cudaMemcpyDefault, mlp->stream));
     MCU(cudaMemsetAsync(mlp->g, 0, MLP_NP * 4, mlp->stream));
     return EBIT_OK;
 }
 
-int ebit_mlp_train_step(ebit_mlp *mlp, const uint16_t *X, const float *t, int batch, float lr, float *loss_out) {
+int ebit_mlp_train_step(ebit_mlp *mlp, const uint16_t *X, const float *t, const int *idx, int batch, float lr,
+                        float *loss_out) {
     if (!mlp || !X || !t || batch <= 0 || !(lr > 0.0f) || !aligned16(X)) return EBIT_EINVAL;
-    int r = mlp_grad_launch(mlp, X, t, batch);
+    int r = mlp_grad_launch(mlp, X, t, idx, batch);
     if (r) return r;
     mlp->step++;
     const float bc1 = 1.0f - powf(0.9f, (float)mlp->step), bc2 = 1.0f - powf(0.999f, (float)mlp->step);

@@ -27,7 +27,7 @@ struct HFArgs {
     const int *__restrict__ nprev;
     const unsigned *__restrict__ cand;  // candidate cells (all interface cells are among them)
     const int *__restrict__ ncand;
-    unsigned *__restrict__ iface;       // interface cells of this call (output list)
+    unsigned *__restrict__ iface;       // interface cells of this call (output list, may be null)
     int *__restrict__ niface;
     const int *__restrict__ list;       // tiles, for the full scan
     const int *__restrict__ count;
@@ -159,7 +159,10 @@ __device__ __noinline__ int hf_cell(const HFArgs &a, int x, int y, int z, double
 // that are no longer cut (their curvature becomes 0, status NONE); entries of
 // the candidate list are computed if 0 < C < 1 and reset otherwise.  Every
 // interface cell of the current C is a candidate, so the curvature field is
-// complete; one thread per entry, full warps for the FP64 work.
+// complete; one thread per entry, full warps for the FP64 work.  Without
+// COMPUTE the interface cells are only listed (the learned curvature writes
+// them next).
+template <bool COMPUTE>
 __global__ void __launch_bounds__(128) hf_list_kernel(HFArgs a) {
     const int np = *a.nprev, nc = *a.ncand;
     const int total = np + nc;
@@ -178,11 +181,13 @@ __global__ void __launch_bounds__(128) hf_list_kernel(HFArgs a) {
                     a.st[id] = 0;
                 }
             } else if (iface) {
-                const int x = id % a.g.n[0], y = (id / a.g.n[0]) % a.g.n[1], z = id / (a.g.n[0] * a.g.n[1]);
-                double kv = 0.0;
-                int st = hf_cell(a, x, y, z, &kv);
-                a.kh[id] = kv;
-                a.st[id] = (uint8_t)st;
+                if (COMPUTE) {
+                    const int x = id % a.g.n[0], y = (id / a.g.n[0]) % a.g.n[1], z = id / (a.g.n[0] * a.g.n[1]);
+                    double kv = 0.0;
+                    int st = hf_cell(a, x, y, z, &kv);
+                    a.kh[id] = kv;
+                    a.st[id] = (uint8_t)st;
+                }
                 keep = true;
             } else {
                 a.kh[id] = 0.0;
@@ -191,7 +196,7 @@ __global__ void __launch_bounds__(128) hf_list_kernel(HFArgs a) {
         }
         const unsigned full = 0xffffffffu;
         unsigned m = __ballot_sync(full, keep);
-        if (m) {
+        if (m && a.iface) {
             const int lane = threadIdx.x & 31, leader = __ffs(m) - 1;
             int base = 0;
             if (lane == leader) base = atomicAdd(a.niface, __popc(m));

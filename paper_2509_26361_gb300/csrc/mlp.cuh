@@ -31,11 +31,36 @@ constexpr int P_B3 = P_W3 + MLP_H;
 constexpr int MLP_NP = P_B3 + 1;
 
 // ------------------------------------------------- stencil canonicalisation
+// True if some cell of the 3x3x3 block with C > 0 is not 6-connected to the
+// centre through cells with C > 0 (a phase-1 fragment: the learned value falls
+// back to height functions there).  Bit b = 9 dz + 3 dy + dx of `pos` (offsets
+// 0..2) marks C > 0; the reachable set grows by face neighbours until it stops.
+__device__ __forceinline__ bool fragmented27(unsigned pos) {
+    constexpr unsigned ALL = (1u << 27) - 1u;
+    unsigned x0 = 0, x2 = 0, y0 = 0, y2 = 0;
+    for (int b = 0; b < 27; b++) {
+        const int dx = b % 3, dy = (b / 3) % 3;
+        if (dx == 0) x0 |= 1u << b;
+        if (dx == 2) x2 |= 1u << b;
+        if (dy == 0) y0 |= 1u << b;
+        if (dy == 2) y2 |= 1u << b;
+    }
+    unsigned r = (1u << 13) & pos;
+    for (int it = 0; it < 27; it++) {
+        const unsigned nb = ((r & ~x2) << 1) | ((r & ~x0) >> 1) | ((r & ~y2) << 3) | ((r & ~y0) >> 3) | (r << 9) |
+                            (r >> 9);
+        const unsigned rn = (r | nb) & pos & ALL;
+        if (rn == r) break;
+        r = rn;
+    }
+    return r != pos;
+}
+
 // 3x3x3 block around cell (x, y, z); Youngs normal n = -grad C (1-2-1 weights,
 // b2 outer, b1 inner); reflect axes with n < 0; order axes by increasing |n|
 // (stable); write the 27 values in z-major order of the canonical axes, split
-// into bf16 head and tail.
-__device__ __forceinline__ void canon_encode(const double *__restrict__ C, const Grid &g, int x, int y, int z,
+// into bf16 head and tail.  Returns the fragment flag of the block.
+__device__ __forceinline__ bool canon_encode(const double *__restrict__ C, const Grid &g, int x, int y, int z,
                                              __nv_bfloat16 out[MLP_IN]) {
     double blk[3][3][3];
 #pragma unroll
@@ -93,15 +118,21 @@ __device__ __forceinline__ void canon_encode(const double *__restrict__ C, const
         out[q] = __float2bfloat16_rn(0.0f);
         out[32 + q] = __float2bfloat16_rn(0.0f);
     }
+    unsigned pos = 0;
+#pragma unroll
+    for (int b = 0; b < 27; b++)
+        if (blk[b / 9][(b / 3) % 3][b % 3] > 0.0) pos |= 1u << b;
+    return fragmented27(pos);
 }
 
 __global__ void mlp_gather_kernel(const double *__restrict__ C, Grid g, const int *__restrict__ cells, int m,
-                                  __nv_bfloat16 *__restrict__ X) {
+                                  __nv_bfloat16 *__restrict__ X, uint8_t *__restrict__ frag) {
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < m; i += gridDim.x * blockDim.x) {
         const int id = cells[i];
         const int x = id % g.n[0], y = (id / g.n[0]) % g.n[1], z = id / (g.n[0] * g.n[1]);
         __nv_bfloat16 v[MLP_IN];
-        canon_encode(C, g, x, y, z, v);
+        const bool fr = canon_encode(C, g, x, y, z, v);
+        if (frag) frag[i] = fr ? 1 : 0;
         uint4 *dst = reinterpret_cast<uint4 *>(X + (long long)i * MLP_IN);
         const uint4 *src = reinterpret_cast<const uint4 *>(v);
 #pragma unroll
@@ -232,11 +263,14 @@ struct MlpArgs {
     float *grad;                // FP32 gradient accumulator (training)
     float *loss;                // summed weighted squared error (training, optional)
     int batch;                  // training batch size (denominator of the mean)
+    const int *idx;             // training rows X[idx[r]], t[idx[r]] (null: rows 0..batch-1)
+    unsigned *fb;               // cells left to height functions (curvature mode 2)
+    int *nfb;                   // their number
 };
 
 // ------------------------------------------------------------ forward
-// smem: X [128][72] | W1 [128][72] | H1 [128][136] | W2 [128][136]
-constexpr int FWD_SMEM = (128 * LD64 * 2 + 128 * LD128 * 2) * 2;
+// smem: X [128][72] | W1 [128][72] | H1 [128][136] | W2 [128][136] | fragment flags [128]
+constexpr int FWD_SMEM = (128 * LD64 * 2 + 128 * LD128 * 2) * 2 + 128;
 
 template <bool GATHER, bool CURV>
 __global__ void __launch_bounds__(128) mlp_fwd_kernel(MlpArgs a) {
@@ -245,6 +279,7 @@ __global__ void __launch_bounds__(128) mlp_fwd_kernel(MlpArgs a) {
     __nv_bfloat16 *sW1 = sX + 128 * LD64;
     __nv_bfloat16 *sH1 = sW1 + 128 * LD64;
     __nv_bfloat16 *sW2 = sH1 + 128 * LD128;
+    uint8_t *sFrag = reinterpret_cast<uint8_t *>(sW2 + 128 * LD128);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31, g = lane >> 2, t4 = lane & 3;
     load_row(sW1, LD64, tid, a.w1b, tid, MLP_IN, MLP_H);
     load_row(sW2, LD128, tid, a.w2b, tid, MLP_H, MLP_H);
@@ -260,7 +295,7 @@ __global__ void __launch_bounds__(128) mlp_fwd_kernel(MlpArgs a) {
             if (live) {
                 const int cell = a.cells[row];
                 const int x = cell % a.g.n[0], y = (cell / a.g.n[0]) % a.g.n[1], z = cell / (a.g.n[0] * a.g.n[1]);
-                canon_encode(a.C, a.g, x, y, z, v);
+                sFrag[tid] = canon_encode(a.C, a.g, x, y, z, v) ? 1 : 0;
             } else {
                 for (int q = 0; q < MLP_IN; q++) v[q] = __float2bfloat16_rn(0.0f);
             }
@@ -326,12 +361,14 @@ __global__ void __launch_bounds__(128) mlp_fwd_kernel(MlpArgs a) {
                     if (orow >= m) continue;
                     const float yv = yp[mt][hh];
                     if (CURV) {
-                        // learned value unless it leaves the trained range
-                        // |kappa h| <= 1 where height functions gave one (mode 2)
+                        // mode 1: the learned value; mode 2: height functions where the
+                        // learned value leaves the trained range |kappa h| <= 1 or the
+                        // stencil holds a phase-1 fragment
                         const int cell = a.cells[orow];
-                        const int hs = a.st[cell];
-                        const bool hf_ok = hs >= 1 && hs <= 3;
-                        if (a.mode == 1 || !(fabsf(yv) > 1.0f && hf_ok)) {
+                        const int lr = m0 + mt * 16 + g + 8 * hh;
+                        if (a.mode == 2 && (fabsf(yv) > 1.0f || sFrag[lr])) {
+                            a.fb[atomicAdd(a.nfb, 1)] = (unsigned)cell;
+                        } else {
                             a.kh[cell] = (double)yv;
                             a.st[cell] = 5;
                         }
@@ -385,7 +422,8 @@ __global__ void __launch_bounds__(128) mlp_train_kernel(MlpArgs a) {
         load_row(sW2, LD128, tid, a.w2b, tid, MLP_H, MLP_H);
         __nv_bfloat16 xv[MLP_IN];
         if (live) {
-            const uint4 *s4 = reinterpret_cast<const uint4 *>(a.X + (long long)row * MLP_IN);
+            const long long src = a.idx ? a.idx[row] : row;
+            const uint4 *s4 = reinterpret_cast<const uint4 *>(a.X + src * MLP_IN);
             for (int q = 0; q < MLP_IN / 8; q++) reinterpret_cast<uint4 *>(xv)[q] = s4[q];
         } else {
             for (int q = 0; q < MLP_IN; q++) xv[q] = __float2bfloat16_rn(0.0f);
@@ -441,7 +479,7 @@ __global__ void __launch_bounds__(128) mlp_train_kernel(MlpArgs a) {
                 const int orow = tile * 128 + m0 + mt * 16 + g + 8 * hh;
                 float d = 0.0f;
                 if (orow < B) {
-                    const float tv = a.t[orow];
+                    const float tv = a.t[a.idx ? a.idx[orow] : orow];
                     const float den = fmaxf(fabsf(tv), 0.05f);
                     const float wgt = 1.0f / (den * den);
                     const float r = yv - tv;

@@ -91,10 +91,10 @@ def load(build_if_missing: bool = True):
     lib.ebit_mlp_destroy.restype = None
     lib.ebit_mlp_set_params.argtypes = [P, P]
     lib.ebit_mlp_get_params.argtypes = [P, P]
-    lib.ebit_mlp_gather.argtypes = [P, P, I, I, I, P, I, P]
+    lib.ebit_mlp_gather.argtypes = [P, P, I, I, I, P, I, P, P]
     lib.ebit_mlp_forward.argtypes = [P, P, I, P]
     lib.ebit_mlp_gradient.argtypes = [P, P, P, I, P]
-    lib.ebit_mlp_train_step.argtypes = [P, P, P, I, ctypes.c_float, P]
+    lib.ebit_mlp_train_step.argtypes = [P, P, P, P, I, ctypes.c_float, P]
     lib.ebit_mlp_sync.argtypes = [P]
     lib.ebit_mlp_last_error.argtypes = [P]
     lib.ebit_mlp_last_error.restype = ctypes.c_char_p
@@ -197,7 +197,7 @@ def ebit_band_tiles(ctx):
     return int(load().ebit_band_tiles(ctx))
 
 
-PROF_KINDS = ("sweep", "band", "f2v", "hf", "mlp", "advect", "fp64", "k7")
+PROF_KINDS = ("sweep", "band", "f2v", "hf", "mlp", "advect", "fp64", "scan")
 
 
 def ebit_profile(ctx, enable):
@@ -266,12 +266,13 @@ def ebit_mlp_get_params(mlp, params):
     return _mcheck(mlp, load().ebit_mlp_get_params(mlp, _any(params, torch.float32, ebit_mlp_nparams(), "params")))
 
 
-def ebit_mlp_gather(mlp, C, n3, cells, X):
+def ebit_mlp_gather(mlp, C, n3, cells, X, frag=None):
     nx, ny, nz = (int(v) for v in n3)
     m = cells.numel()
+    fp = None if frag is None else _dev(frag, torch.uint8, m, "frag")
     return _mcheck(mlp, load().ebit_mlp_gather(mlp, _dev(C, torch.float64, nx * ny * nz, "C"), nx, ny, nz,
                                                _dev(cells, torch.int32, m, "cells"), m,
-                                               _dev(X, torch.bfloat16, 64 * m, "X")))
+                                               _dev(X, torch.bfloat16, 64 * m, "X"), fp))
 
 
 def ebit_mlp_forward(mlp, X, y):
@@ -287,11 +288,21 @@ def ebit_mlp_gradient(mlp, X, t, grad):
                                                  _any(grad, torch.float32, ebit_mlp_nparams(), "grad")))
 
 
-def ebit_mlp_train_step(mlp, X, t, lr, loss=None):
-    b = t.numel()
+def ebit_mlp_train_step(mlp, X, t, lr, loss=None, idx=None, batch=None):
+    """One Adam step on rows idx[:batch] of (X, t), or on all of them without idx."""
+    if idx is None:
+        b = t.numel()
+        if X.numel() != 64 * b:
+            raise ValueError("X must have 64 values per label")
+        ip = None
+    else:
+        b = int(batch if batch is not None else idx.numel())
+        if b > idx.numel():
+            raise ValueError("batch larger than the index array")
+        ip = _dev(idx, torch.int32, idx.numel(), "idx")
     lp = None if loss is None else _dev(loss, torch.float32, 1, "loss")
-    return _mcheck(mlp, load().ebit_mlp_train_step(mlp, _dev(X, torch.bfloat16, 64 * b, "X"),
-                                                   _dev(t, torch.float32, b, "t"), b, float(lr), lp))
+    return _mcheck(mlp, load().ebit_mlp_train_step(mlp, _dev(X, torch.bfloat16, X.numel(), "X"),
+                                                   _dev(t, torch.float32, t.numel(), "t"), ip, b, float(lr), lp))
 
 
 def ebit_mlp_sync(mlp):
@@ -331,10 +342,11 @@ class Mlp:
         ebit_mlp_get_params(self.h, p)
         return p
 
-    def gather(self, C, n3, cells):
+    def gather(self, C, n3, cells, with_frag=False):
         X = torch.empty((cells.numel(), 64), dtype=torch.bfloat16, device="cuda")
-        ebit_mlp_gather(self.h, C, n3, cells, X)
-        return X
+        fr = torch.empty(cells.numel(), dtype=torch.uint8, device="cuda") if with_frag else None
+        ebit_mlp_gather(self.h, C, n3, cells, X, fr)
+        return (X, fr) if with_frag else X
 
     def forward(self, X):
         y = torch.empty(X.shape[0], dtype=torch.float32, device="cuda")
@@ -346,8 +358,8 @@ class Mlp:
         ebit_mlp_gradient(self.h, X, t, g)
         return g
 
-    def train_step(self, X, t, lr, loss=None):
-        return ebit_mlp_train_step(self.h, X, t, lr, loss)
+    def train_step(self, X, t, lr, loss=None, idx=None, batch=None):
+        return ebit_mlp_train_step(self.h, X, t, lr, loss, idx, batch)
 
     def sync(self):
         return ebit_mlp_sync(self.h)

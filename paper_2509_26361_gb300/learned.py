@@ -1,0 +1,268 @@
+"""Learned curvature: data, training and evaluation driven through the C ABI.
+
+The network (27 -> 128 -> 128 -> 1, ReLU, bf16 operands with FP32
+accumulation) maps the canonically oriented 3x3x3 volume-fraction stencil of an
+interface cell to kappa*h; height functions (Sec. 2.6) stay the fallback and
+the judge.  Every arithmetic step runs in the library's kernels: Front2VOF
+makes the fractions, the gather kernel encodes the stencils, the training
+kernel computes the loss gradient and the Adam kernel updates the weights.
+This module only orchestrates them and computes the analytic labels on the
+host (``curvature_data``).
+
+Command line (GPU):
+    python -m paper_2509_26361_gb300.learned train --out DIR [--stencils 2000000]
+    python -m paper_2509_26361_gb300.learned eval --params FILE [--out DIR]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import time
+
+import numpy as np
+import torch
+
+from . import curvature_data as D
+from . import ebit
+
+PARAMS_FILE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "data", "mlp_curvature_params.npy")
+RADIUS_BINS = (2.0, 4.0, 8.0, 16.0, 32.0, math.inf)
+
+
+def _dev(a, dtype=None):
+    t = torch.from_numpy(np.ascontiguousarray(a)).cuda()
+    return t if dtype is None else t.to(dtype)
+
+
+def finite_level(phi):
+    """Level sets evaluated only near each shape carry -inf (or +inf) far away;
+    the library needs finite values (only their signs matter there)."""
+    return np.where(np.isfinite(phi), phi, np.sign(phi))
+
+
+def stencil_set(n, ells, mlp, inside=1, with_hf=False):
+    """Interface stencils of one grid: fractions from the library's Front2VOF
+    on exact-crossing markers, encoded stencils and fragment flags from the
+    gather kernel, analytic labels from the markers' centroids.  Returns a
+    dict of device tensors X (bf16 [m, 64]), t (f32 [m]) and host arrays."""
+    n3 = (n, n, n)
+    f = D.ellipsoid_fields(n3, ells, inside)
+    g = ebit.Grid(n, n, n)
+    try:
+        g.init(_dev(finite_level(f.phi)), _dev(finite_level(f.phi_faces)), _dev(f.s_exact))
+        C = torch.empty(g.shape, dtype=torch.float64, device="cuda")
+        g.front2vof(C, flags=ebit.EBIT_FULL)
+        cb, s = g.get_state()
+        Ch = C.cpu().numpy().reshape(-1)
+        cells = np.nonzero((Ch > 0.0) & (Ch < 1.0))[0].astype(np.int32)
+        cent = D.interface_centroids(n3, cb.cpu().numpy(), s.cpu().numpy(), cells)
+        lab = D.curvature_labels(n3, ells, f, cent, cells, inside)
+        X, fr = mlp.gather(C, n3, _dev(cells), with_frag=True)
+        out = {"cells": cells, "label": lab, "frag": fr.cpu().numpy().astype(bool), "X": X, "C": C, "n3": n3}
+        if with_hf:
+            kh = torch.zeros_like(C)
+            st = torch.zeros(C.shape, dtype=torch.uint8, device="cuda")
+            g.curvature(C, kh, st, mode=ebit.EBIT_CURV_HF, flags=ebit.EBIT_FULL)
+            out["hf_kh"] = kh.reshape(-1)[_dev(cells).long()].cpu().numpy()
+            out["hf_st"] = st.reshape(-1)[_dev(cells).long()].cpu().numpy()
+        g.sync()
+        return out
+    finally:
+        g.close()
+
+
+def training_set(mlp, stencils=2_000_000, seed=3, n=256, bubble_every=4, log=print):
+    """About ``stencils`` labelled stencils from seeded grids of spheres and
+    ellipsoids with semi-axes between 2 and 32 cells (log-uniform, 30 %
+    spheres).  Grids alternate between 150 shapes over the whole range and
+    2000 small shapes (2 to 8 cells), so that small radii, whose shapes carry
+    few interface cells each, are not rare.  Every ``bubble_every``-th grid
+    swaps the phases (negative curvature).  Fragmented stencils (height-function
+    fallback) and stencils without a finite label are left out."""
+    rng = np.random.default_rng(seed)
+    Xs, ts = [], []
+    total = 0
+    grid = 0
+    while total < stencils:
+        if grid % 2 == 0:
+            ells = D.random_ellipsoids(rng, 150, 2.0, 32.0, n, log_uniform=True, sphere_fraction=0.3)
+        else:
+            ells = D.random_ellipsoids(rng, 2000, 2.0, 8.0, n, log_uniform=True, sphere_fraction=0.3)
+        inside = 0 if (bubble_every and grid % bubble_every == bubble_every - 1) else 1
+        st = stencil_set(n, ells, mlp, inside)
+        keep = np.isfinite(st["label"]) & ~st["frag"] & (np.abs(st["label"]) <= 1.0)
+        kidx = _dev(np.nonzero(keep)[0].astype(np.int64))
+        Xs.append(st["X"][kidx])
+        ts.append(_dev(st["label"][keep].astype(np.float32)))
+        total += int(keep.sum())
+        log(f"grid {grid}: {len(ells)} shapes, {int(keep.sum())} stencils (inside={inside}), total {total}")
+        grid += 1
+    X = torch.cat(Xs)
+    t = torch.cat(ts)
+    # a seeded subset of the requested size, mixed over the grids
+    pick = _dev(rng.permutation(t.numel())[:stencils].astype(np.int64))
+    return X[pick].contiguous(), t[pick].contiguous()
+
+
+def train(mlp, X, t, epochs=400, batch=16384, lr0=2e-3, lr1=2e-5, seed=0, log=print):
+    """Adam with a cosine learning-rate decay from lr0 to lr1; a fresh
+    permutation of the rows every epoch (the training kernel reads the rows
+    through the index array).  Returns the mean loss per epoch."""
+    m = t.numel()
+    rng = np.random.default_rng(seed)
+    steps_per_epoch = m // batch
+    total = epochs * steps_per_epoch
+    loss = torch.zeros(1, dtype=torch.float32, device="cuda")
+    hist = []
+    step = 0
+    for ep in range(epochs):
+        perm = _dev(rng.permutation(m).astype(np.int32))
+        acc = torch.zeros(1, dtype=torch.float64, device="cuda")
+        for b in range(steps_per_epoch):
+            lr = lr1 + 0.5 * (lr0 - lr1) * (1.0 + math.cos(math.pi * step / max(total - 1, 1)))
+            mlp.train_step(X, t, lr, loss, idx=perm[b * batch:(b + 1) * batch], batch=batch)
+            acc += loss
+            step += 1
+        mlp.sync()
+        hist.append(float(acc.item()) / (steps_per_epoch * batch))
+        log(f"epoch {ep}: loss {hist[-1]:.3e}")
+    return hist
+
+
+def _rms(e):
+    return float(np.sqrt(np.mean(e * e))) if len(e) else float("nan")
+
+
+def evaluate(mlp, seed=33, n=256, count=64, amin=4.0, amax=32.0, repeats=5):
+    """The learned-curvature benchmark grid: ``count`` seeded ellipsoids with
+    semi-axes U[amin, amax] cells and random rotations.  RMS kappa*h error
+    against the analytic labels for height functions (where they give a value),
+    the network alone, and the network with height-function fallback; binned
+    by the local radius 2/|kappa| in cells; and stencils per second of the
+    height-function pass and the learned pass on the same interface list."""
+    rng = np.random.default_rng(seed)
+    ells = D.random_ellipsoids(rng, count, amin, amax, n)
+    st = stencil_set(n, ells, mlp, 1, with_hf=True)
+    cells, lab = st["cells"], st["label"]
+    ok = np.isfinite(lab)
+    n3 = st["n3"]
+    g = ebit.Grid(*n3)
+    g.set_mlp(mlp)
+    C = st["C"]
+    kh = torch.zeros_like(C)
+    stt = torch.zeros(C.shape, dtype=torch.uint8, device="cuda")
+    res = {"grid": n, "ellipsoids": count, "semi_axes_cells": [amin, amax], "interface_cells": int(len(cells))}
+    idx = _dev(cells.astype(np.int64))
+    vals = {}
+    times = {}
+    for name, mode in (("hf", ebit.EBIT_CURV_HF), ("mlp", ebit.EBIT_CURV_MLP), ("mlp_hf", ebit.EBIT_CURV_MLP_HF)):
+        g.curvature(C, kh, stt, mode=mode, flags=ebit.EBIT_FULL)  # warm-up
+        g.profile(True)
+        for _ in range(repeats):
+            g.curvature(C, kh, stt, mode=mode, flags=ebit.EBIT_FULL)
+        prof = g.profile_read()
+        g.profile(False)
+        times[name] = {k: v[0] / repeats for k, v in prof.items()}
+        vals[name] = (kh.reshape(-1)[idx].cpu().numpy(), stt.reshape(-1)[idx].cpu().numpy())
+    g.close()
+    hf_k, hf_s = vals["hf"]
+    hf_ok = ok & (hf_s >= 1) & (hf_s <= 3)
+    res["hf_no_value"] = int(np.sum(ok & ~((hf_s >= 1) & (hf_s <= 3))))
+    res["fragmented"] = int(np.sum(st["frag"]))
+    mh_k, mh_s = vals["mlp_hf"]
+    res["mlp_hf_fallback"] = int(np.sum(mh_s != 5))
+    rad = 2.0 / np.maximum(np.abs(lab), 1e-30) / 1.0  # kappa*h -> 2/(kappa h) cells
+    rows = []
+    for lo, hi in zip(RADIUS_BINS[:-1], RADIUS_BINS[1:]):
+        b = ok & (rad >= lo) & (rad < hi)
+        bh = b & hf_ok
+        rows.append({"radius_cells": [lo, hi], "cells": int(b.sum()), "hf_cells": int(bh.sum()),
+                     "rms_hf": _rms(hf_k[bh] - lab[bh]), "rms_mlp": _rms(vals["mlp"][0][b] - lab[b]),
+                     "rms_mlp_hf": _rms(mh_k[b] - lab[b]),
+                     "rms_mlp_on_hf_cells": _rms(vals["mlp"][0][bh] - lab[bh])})
+    res["bins"] = rows
+    res["rms_hf"] = _rms(hf_k[hf_ok] - lab[hf_ok])
+    res["rms_mlp"] = _rms(vals["mlp"][0][ok] - lab[ok])
+    res["rms_mlp_hf"] = _rms(mh_k[ok] - lab[ok])
+    res["rms_mlp_on_hf_cells"] = _rms(vals["mlp"][0][hf_ok] - lab[hf_ok])
+    m = len(cells)
+    t_hf = times["hf"].get("hf", float("nan"))
+    t_list = times["mlp"].get("hf", 0.0)
+    t_mlp = times["mlp"].get("mlp", float("nan"))
+    t_mlp_hf = times["mlp_hf"].get("hf", 0.0) + times["mlp_hf"].get("mlp", float("nan"))
+    res["ms"] = times
+    res["hf_stencils_per_s"] = m / (t_hf * 1e-3)
+    res["mlp_stencils_per_s"] = m / ((t_list + t_mlp) * 1e-3)
+    res["mlp_hf_stencils_per_s"] = m / (t_mlp_hf * 1e-3)
+    return res
+
+
+def init_params(seed=0):
+    """He-uniform initial weights in the library's layout (W1[128][64], b1,
+    W2[128][128], b2, w3, b3); a tail input starts with its head's weights."""
+    rng = np.random.default_rng(seed)
+    W1 = np.zeros((128, 64))
+    W1[:, :27] = rng.uniform(-1.0, 1.0, (128, 27)) * math.sqrt(6.0 / 27.0)
+    W1[:, 32:59] = W1[:, :27]
+    W2 = rng.uniform(-1.0, 1.0, (128, 128)) * math.sqrt(6.0 / 128.0)
+    w3 = rng.uniform(-1.0, 1.0, 128) * math.sqrt(3.0 / 128.0)
+    return np.concatenate([W1.ravel(), np.zeros(128), W2.ravel(), np.zeros(128), w3, [0.1]])
+
+
+def save_params(mlp, path):
+    os.makedirs(os.path.dirname(os.path.abspath(path)), exist_ok=True)
+    np.save(path, mlp.get_params().cpu().numpy().astype(np.float32))
+
+
+def load_network(path=PARAMS_FILE):
+    """A network with the stored parameters (float32 vector, see include/ebit.h)."""
+    p = np.load(path)
+    return ebit.Mlp(p.astype(np.float64))
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser()
+    ap.add_argument("cmd", choices=("train", "eval"))
+    ap.add_argument("--out", default=".")
+    ap.add_argument("--params", default=PARAMS_FILE)
+    ap.add_argument("--stencils", type=int, default=2_000_000)
+    ap.add_argument("--epochs", type=int, default=400)
+    ap.add_argument("--batch", type=int, default=16384)
+    ap.add_argument("--seed", type=int, default=3)
+    a = ap.parse_args(argv)
+    os.makedirs(a.out, exist_ok=True)
+
+    def log(msg):
+        print(msg, flush=True)
+
+    if a.cmd == "train":
+        t0 = time.time()
+        mlp = ebit.Mlp(init_params(a.seed))
+        X, t = training_set(mlp, a.stencils, seed=a.seed, log=log)
+        t1 = time.time()
+        torch.cuda.synchronize()
+        t2 = time.time()
+        hist = train(mlp, X, t, epochs=a.epochs, batch=a.batch, seed=a.seed, log=log)
+        torch.cuda.synchronize()
+        t3 = time.time()
+        path = os.path.join(a.out, "mlp_curvature_params.npy")
+        save_params(mlp, path)
+        rep = {"stencils": int(t.numel()), "epochs": a.epochs, "batch": a.batch, "seed": a.seed,
+               "data_seconds": t1 - t0, "train_seconds": t3 - t2, "loss_per_epoch": hist}
+        rep["eval"] = evaluate(mlp)
+        with open(os.path.join(a.out, "train_report.json"), "w") as fh:
+            json.dump(rep, fh, indent=1)
+        log(json.dumps(rep["eval"], indent=1))
+    else:
+        mlp = load_network(a.params)
+        res = evaluate(mlp)
+        with open(os.path.join(a.out, "eval_report.json"), "w") as fh:
+            json.dump(res, fh, indent=1)
+        log(json.dumps(res, indent=1))
+    return 0
+
+
+if __name__ == "__main__":
+    raise SystemExit(main())

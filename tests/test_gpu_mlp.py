@@ -29,12 +29,29 @@ def bf16_bits_to_f64(X):
     return X.float().cpu().numpy().astype(np.float64)
 
 
+def with_satellites(C, rng, frac=0.004):
+    """C plus isolated small fractions in empty cells: stencils with phase-1
+    fragments (and lone interface cells)."""
+    C = C.copy()
+    flat = C.reshape(-1)
+    empty = np.nonzero(flat == 0.0)[0]
+    pick = rng.choice(empty, size=int(frac * flat.size), replace=False)
+    flat[pick] = rng.uniform(0.05, 0.6, size=len(pick))
+    return C
+
+
 def test_gather_matches_oracle_canonical_encoding():
     n3, C, cells = sphere_fractions()
+    C = with_satellites(C, np.random.default_rng(4))
+    cells = np.nonzero(((C > 0) & (C < 1)).ravel())[0].astype(np.int32)
     m = ebit.Mlp()
-    X = m.gather(dev(C), n3, dev(cells))
-    ref = omlp.encode(omlp.canonical_stencil(omlp.gather_stencils(C, cells)))
+    X, fr = m.gather(dev(C), n3, dev(cells), with_frag=True)
+    blk = omlp.gather_stencils(C, cells)
+    ref = omlp.encode(omlp.canonical_stencil(blk))
     assert np.array_equal(bf16_bits_to_f64(X), ref)
+    fref = np.array([omlp.fragmented(b) for b in blk])
+    assert fref.any() and not fref.all()
+    assert np.array_equal(fr.cpu().numpy().astype(bool), fref)
     m.close()
 
 
@@ -91,6 +108,62 @@ def test_training_steps_reduce_the_loss():
         m.train_step(Xd, td, 1e-3, loss)
     m.sync()
     assert loss.item() < 0.2 * first, (first, loss.item())
+    m.close()
+
+
+def test_indexed_training_step_equals_the_gathered_batch():
+    rng = np.random.default_rng(13)
+    X = _random_inputs(3000, rng)
+    t = rng.uniform(0.05, 0.6, size=3000).astype(np.float32)
+    idx = rng.permutation(3000)[:1000].astype(np.int32)
+    p0 = omlp.init_params(5)
+    a, b = ebit.Mlp(p0), ebit.Mlp(p0)
+    Xd, td = dev(X).to(torch.bfloat16), dev(t)
+    la = torch.zeros(1, dtype=torch.float32, device="cuda")
+    lb = torch.zeros(1, dtype=torch.float32, device="cuda")
+    a.train_step(Xd, td, 1e-3, la, idx=dev(idx), batch=1000)
+    b.train_step(Xd[dev(idx).long()].contiguous(), td[dev(idx).long()].contiguous(), 1e-3, lb)
+    a.sync()
+    b.sync()
+    pa, pb = a.get_params().cpu().numpy(), b.get_params().cpu().numpy()
+    # the same step up to the order of the FP32 gradient sums
+    assert np.max(np.abs(pa - pb)) <= 1e-6, np.max(np.abs(pa - pb))
+    assert abs(la.item() - lb.item()) <= 1e-4 * abs(lb.item())
+    a.close()
+    b.close()
+
+
+def test_curvature_mode_with_height_function_fallback_matches_oracle():
+    n3, C, _ = sphere_fractions()
+    C = with_satellites(C, np.random.default_rng(6))
+    rng = np.random.default_rng(8)
+    p = omlp.init_params(7) + rng.normal(scale=0.01, size=omlp.N_PARAMS)
+    p = p.astype(np.float32).astype(np.float64)
+    hf_kh, hf_st = oracle.hf_curvature(C)
+    # shift the output bias so that about half the cells leave |kappa h| <= 1
+    _, _, _, y0, _ = omlp.learned_curvature(C, p, 1, hf_kh, hf_st)
+    p[-1] += 1.0 - np.median(y0)
+    p = p.astype(np.float32).astype(np.float64)
+    cells, kh_ref, st_ref, y_ref, frag = omlp.learned_curvature(C, p, 2, hf_kh, hf_st)
+    assert frag.any() and (np.abs(y_ref) > 1.0).any() and (np.abs(y_ref) <= 1.0).any()
+    m = ebit.Mlp(p)
+    g = ebit.Grid(*n3)
+    g.set_mlp(m)
+    Cd = dev(C)
+    kh = torch.zeros_like(Cd)
+    st = torch.zeros(Cd.shape, dtype=torch.uint8, device="cuda")
+    g.curvature(Cd, kh, st, mode=ebit.EBIT_CURV_MLP_HF, flags=ebit.EBIT_FULL)
+    g.sync()
+    kh_h = kh.cpu().numpy().ravel()
+    st_h = st.cpu().numpy().ravel()
+    assert np.array_equal(np.nonzero(st_h)[0], np.sort(cells))
+    clear = np.abs(np.abs(y_ref) - 1.0) > 1e-2   # the FP32 and FP64 decisions agree away from 1
+    assert np.array_equal(st_h[cells][clear], st_ref[clear])
+    hf = clear & (st_ref != 5)
+    assert np.all(np.abs(kh_h[cells][hf] - kh_ref[hf]) <= 1e-12)
+    learned = clear & (st_ref == 5)
+    assert np.max(np.abs(kh_h[cells][learned] - y_ref[learned]) / (np.abs(y_ref[learned]) + 0.1)) <= 2e-3
+    g.close()
     m.close()
 
 

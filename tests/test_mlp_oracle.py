@@ -121,3 +121,51 @@ def test_bf16_split_reconstructs_float32():
     assert np.max(np.abs(hi + lo - f)) <= 2.0 ** -16 * 2 ** -1 * 1.0001
     # heads are bfloat16 values: low 16 bits of the float32 pattern are zero
     assert np.all((hi.astype(np.float32).view(np.uint32) & 0xFFFF) == 0)
+
+
+def test_fragment_rule_matches_connected_component_labelling():
+    from scipy import ndimage
+    rng = np.random.default_rng(11)
+    st6 = ndimage.generate_binary_structure(3, 1)
+    seen = {True: 0, False: 0}
+    for trial in range(3000):
+        dens = rng.uniform(0.15, 0.9)
+        blk = np.where(rng.uniform(size=(3, 3, 3)) < dens, rng.uniform(0.01, 1.0, size=(3, 3, 3)), 0.0)
+        if trial % 2 == 0:
+            blk[1, 1, 1] = 0.5
+        lab, _ = ndimage.label(blk > 0, structure=st6)
+        if blk[1, 1, 1] > 0:
+            expect = bool(np.any((blk > 0) & (lab != lab[1, 1, 1])))
+        else:
+            expect = bool(np.any(blk > 0))
+        assert mlp.fragmented(blk) == expect
+        seen[expect] += 1
+    assert seen[True] > 100 and seen[False] > 100
+    # a face-connected snake through the block is one piece; a diagonal neighbour is not
+    snake = np.zeros((3, 3, 3))
+    for z, y, x in [(1, 1, 1), (1, 1, 2), (1, 2, 2), (2, 2, 2), (2, 2, 1), (2, 2, 0), (2, 1, 0), (2, 0, 0)]:
+        snake[z, y, x] = 0.4
+    assert not mlp.fragmented(snake)
+    diag = np.zeros((3, 3, 3))
+    diag[1, 1, 1] = diag[2, 2, 2] = 0.5
+    assert mlp.fragmented(diag)
+
+
+def test_learned_curvature_fallback_selection():
+    rng = np.random.default_rng(12)
+    C = np.zeros((8, 8, 8))
+    C[3:5, 3:5, 3:5] = rng.uniform(0.2, 0.8, size=(2, 2, 2))
+    C[2, 2, 2] = 0.3                      # touches the cube only along a corner
+    p = mlp.init_params(1)
+    hf_kh = np.full(C.size, 7.0)
+    hf_st = np.full(C.size, 2, dtype=np.uint8)
+    cells, kh, st, y, frag = mlp.learned_curvature(C, p, 2, hf_kh, hf_st)
+    assert len(cells) == 9
+    for c, k, s_, yy, f in zip(cells, kh, st, y, frag):
+        if f or abs(yy) > 1.0:
+            assert k == 7.0 and s_ == 2
+        else:
+            assert k == yy and s_ == 5
+    assert frag.any() and not frag.all()
+    cells1, kh1, st1, y1, _ = mlp.learned_curvature(C, p, 1, hf_kh, hf_st)
+    assert np.array_equal(kh1, y1) and np.all(st1 == 5)
