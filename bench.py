@@ -273,6 +273,29 @@ def roofline_block(res):
             "kernel_launches": {k: v[1] for k, v in prof.items()}}
 
 
+def curvature_block():
+    """Learned vs height-function curvature on the 256^3 grid of 64 seeded
+    ellipsoids (semi-axes U[4, 32] cells, random rotations, seed 33): stencils
+    per second of each pass on the same interface-cell list (CUDA events around
+    each launch) and RMS kappa*h error against the analytic curvature."""
+    from paper_2509_26361_gb300 import learned
+
+    if not os.path.exists(learned.PARAMS_FILE):
+        return {"unavailable": "no trained parameters"}
+    mlp = learned.load_network()
+    r = learned.evaluate(mlp, repeats=10)
+    mlp.close()
+    return {"workload": "ellipsoids_256 (64 ellipsoids, semi-axes U[4,32] cells, random rotations, seed 33)",
+            "interface_cells": r["interface_cells"], "unit": "stencils/s",
+            "mlp": r["mlp_stencils_per_s"], "hf": r["hf_stencils_per_s"], "mlp_hf": r["mlp_hf_stencils_per_s"],
+            "mlp_over_hf": r["mlp_stencils_per_s"] / r["hf_stencils_per_s"],
+            "rms_kh": {"hf_on_hf_cells": r["rms_hf"], "mlp_on_hf_cells": r["rms_mlp_on_hf_cells"],
+                       "mlp_all_cells": r["rms_mlp"], "mlp_hf_all_cells": r["rms_mlp_hf"]},
+            "hf_no_value_cells": r["hf_no_value"], "mlp_hf_fallback_cells": r["mlp_hf_fallback"],
+            "dtype": "bf16 MMA, fp32 accumulate (HF: f64)",
+            "ms_per_pass": r["ms"]}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -280,6 +303,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=8)
     ap.add_argument("--impl", default="ebit", choices=["ebit", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-curvature", action="store_true")
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", 0))
     world = int(os.environ.get("WORLD_SIZE", 1))
@@ -323,6 +347,8 @@ def main():
             "roofline": roofline_block(res), "e2e": res["e2e"], "gpu_launches": launches,
             "clocks": res["clk"],
             "counters": res["cnt"]}
+    if not args.no_curvature:
+        line["curvature"] = curvature_block()
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline_block(res["w"])
     print(json.dumps(line))

@@ -254,6 +254,58 @@ const char *ebit_mlp_last_error(const ebit_mlp *mlp);
  * and status. */
 int ebit_set_mlp(ebit_ctx *ctx, ebit_mlp *mlp);
 
+/* ---------------------------------------------------------------------------
+ * Batches: many independent instances (each a periodic grid with its own size,
+ * velocity and time step; the method of ebit_advect_sweep, Sec. 2.1-2.3)
+ * advanced together.  One split sweep of every instance is ONE cooperative
+ * kernel launch whose phases (band listing, marker advection, integer band
+ * pass, FP64 work lists) are separated by a grid barrier; ebit_batch_run
+ * replays two whole steps (x-y-z then z-y-x sweeps) as a CUDA graph.
+ * Each instance's result equals that of a separate context given the same
+ * inputs.  The barrier waits a bounded time; if it gives up, the batch's
+ * state is undefined and ebit_batch_sync returns EBIT_ETIMEOUT.
+ * ------------------------------------------------------------------------- */
+typedef struct ebit_batch ebit_batch;
+
+/* descs[n]: one descriptor per instance (n <= 1024, every edge >= 8 cells, at
+ * most 2^20 tiles of 8^3 cells per instance and 2^31 cells in all, the same
+ * cuda_stream for all, no EBIT_DESC_DENSE).  EBIT_ECUDA if the device has no
+ * cooperative launch. */
+int ebit_batch_create(int n, const ebit_desc *descs, ebit_batch **out);
+void ebit_batch_destroy(ebit_batch *b);
+int ebit_batch_size(const ebit_batch *b);
+/* The context of instance i (owned by the batch; NULL if i is out of range):
+ * use it for ebit_init, ebit_set_state, ebit_get_state, ebit_front2vof,
+ * ebit_curvature and the counters.  ebit_advect_sweep on it returns
+ * EBIT_EINVAL: instances are swept through the batch. */
+ebit_ctx *ebit_batch_instance(ebit_batch *b, int i);
+/* Velocities and time steps for the following sweeps: u_faces[3 i + d] is
+ * instance i's u_d on its d-normal faces (device, N_i doubles, read at every
+ * sweep, so the caller keeps it alive and may rewrite it between sweeps);
+ * dt[i] (host) its time step.  Synchronises. */
+int ebit_batch_set_velocity(ebit_batch *b, const double *const *u_faces, const double *dt);
+/* One split sweep along dir (0, 1, 2) of every instance. */
+int ebit_batch_advect_sweep(ebit_batch *b, int dir);
+/* Steps first_step .. first_step + steps - 1 (even steps x-y-z, odd steps
+ * z-y-x).  use_graph != 0 replays pairs of steps from a CUDA graph captured on
+ * first use (and again after a launch-shape change); where capture is not
+ * available the sweeps are launched directly (ebit_batch_graph_active tells). */
+int ebit_batch_run(ebit_batch *b, int first_step, int steps, int use_graph);
+/* 0: no graph (sweeps launched directly), 1: graph from stream capture,
+ * 2: graph built node by node; ebit_batch_graph_note says how or why not. */
+int ebit_batch_graph_active(const ebit_batch *b);
+const char *ebit_batch_graph_note(const ebit_batch *b);
+/* Wait for the batch's stream; EBIT_ETIMEOUT if a grid barrier gave up. */
+int ebit_batch_sync(ebit_batch *b);
+/* Launch shape: blocks of 256 threads per SM (1 .. max co-resident). */
+int ebit_batch_launch_shape(const ebit_batch *b, int *ctas_per_sm, int *max_ctas_per_sm);
+int ebit_batch_set_launch_shape(ebit_batch *b, int ctas_per_sm);
+/* Times `sweeps` sweeps at every launch shape on a copy of the current state
+ * (put back afterwards), keeps the fastest; ms_out (host, may be NULL) gets
+ * the time of each shape, index ctas_per_sm - 1.  Allocates a state copy. */
+int ebit_batch_autotune(ebit_batch *b, int sweeps, double *ms_out);
+const char *ebit_batch_last_error(const ebit_batch *b);
+
 /* One split advection sweep that allocates no device memory.
  * The paper has no counterpart: this entry point exists for callers that
  * cannot allocate device memory -- a flow solver that reserves all of its

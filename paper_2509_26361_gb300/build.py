@@ -1,7 +1,7 @@
 """Build libebit.so in-tree with nvcc for sm_103a (GB300).
 
-The library is built from two CUDA translation units (the context-based ABI
-and the allocation-free sweep), compiled with --fmad=false so that every
+The library is built from three CUDA translation units (the context-based ABI,
+the allocation-free sweep and the batched persistent sweep), compiled with --fmad=false so that every
 floating-point operation of the EBIT kernels rounds separately in the written
 order.  Output: ``paper_2509_26361_gb300/_build/libebit.so``.
 """
@@ -50,6 +50,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
     tmp = LIB + f".tmp{os.getpid()}"
     cmd = [_nvcc(), "-O3", "-std=c++17", *ARCH, "-lineinfo", "--fmad=false", "-Xcompiler", "-fPIC",
            "-shared", "-o", tmp, os.path.join(CSRC, "ebit_abi.cu"), os.path.join(CSRC, "ebit_noalloc.cu"),
+           os.path.join(CSRC, "ebit_batch.cu"),
            "-I", os.path.join(ROOT, "include")]
     if verbose:
         cmd.insert(1, "-Xptxas=-v")

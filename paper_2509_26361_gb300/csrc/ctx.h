@@ -1,0 +1,84 @@
+// ctx.h -- the library's internal context types, shared by its translation units.
+#pragma once
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/ebit.h"
+#include "common.cuh"
+
+using ebit::Grid;
+
+struct ebit_mlp {
+    cudaStream_t stream;
+    int sms;
+    float *p, *g, *m, *v;      // FP32 parameters, gradient, Adam moments
+    __nv_bfloat16 *w1b, *w2b;  // bf16 copies for the tensor cores
+    float *loss;               // summed weighted squared error of the last step
+    int step;
+    std::string errmsg;
+};
+
+struct ebit_ctx {
+    Grid g;
+    int owns_state;           // 0: cb, s, scratch arrays, tile flags and counters belong to a batch
+    long long N;
+    double h;
+    cudaStream_t stream;
+    int dense;
+    int sms;
+    uint8_t *cb[2];
+    double *s[2][3];
+    int cur;
+    uint8_t *tile_marker, *tile_dirty, *tile_cchg;
+    int *band_list, *band_count;
+    int *work_list, *work_count;
+    int *all_list, *all_count;
+    unsigned long long *ctr;  // C_N event counters + Front2VOF inconsistencies
+    double *scratch;          // 3N doubles, allocated on first ebit_get_state
+    double *adv[3];           // advected marker coordinates of the current sweep (scratch)
+    int8_t *bin[3];           // floor(2 adv) (scratch)
+    unsigned *work[4];        // FP64 work lists of a sweep (scratch)
+    int *wcount;              // [4]
+    unsigned *cut;            // cells cut by the interface at the last Front2VOF
+    int *ncut;
+    unsigned *iface[2];       // interface cells of the last two curvature calls
+    int *niface;              // [2]
+    int cur_if;
+    unsigned *scan;           // interface cells found by a full curvature scan
+    int *nscan;
+    int *zero;                // a device int that stays 0
+    int sweeps_since_f2v;
+    ebit_mlp *mlp;            // learned curvature (ebit_set_mlp)
+    const double *last_C;
+    const double *last_kh;
+    const uint8_t *last_st;
+    int grid_sweep, grid_adv, grid_fp64, grid_f2v, grid_f2vl, grid_hf, grid_hfl;
+    // per-kernel CUDA-event timing (ebit_profile)
+    int prof_on;
+    std::vector<cudaEvent_t> ev;
+    std::vector<int> ev_kind;
+    int ev_used;
+    double prof_ms[EBIT_PROF_KINDS];
+    long long prof_n[EBIT_PROF_KINDS];
+    std::string err;
+};
+
+
+// Per-sweep state arrays that a batch provides for its instances (an
+// instance's context then owns only its Front2VOF and curvature scratch).
+struct ebit_state_arrays {
+    uint8_t *cb[2];
+    double *s[2][3];
+    double *adv[3];
+    int8_t *bin[3];
+    unsigned *work[4];
+    int *wcount;
+    uint8_t *tile_marker, *tile_dirty;
+    unsigned long long *ctr;
+};
+
+// A context over batch-owned state arrays (see ebit_create for the rest).
+int ebit_create_view(const ebit_desc *desc, const ebit_state_arrays *st, ebit_ctx **out);

@@ -17,6 +17,7 @@
 
 #include "../../include/ebit.h"
 #include "common.cuh"
+#include "ctx.h"
 #include "f2v.cuh"
 #include "hf.cuh"
 #include "mlp.cuh"
@@ -24,60 +25,6 @@
 #include "sweep.cuh"
 
 using namespace ebit;
-
-struct ebit_mlp {
-    cudaStream_t stream;
-    int sms;
-    float *p, *g, *m, *v;      // FP32 parameters, gradient, Adam moments
-    __nv_bfloat16 *w1b, *w2b;  // bf16 copies for the tensor cores
-    float *loss;               // summed weighted squared error of the last step
-    int step;
-    std::string errmsg;
-};
-
-struct ebit_ctx {
-    Grid g;
-    long long N;
-    double h;
-    cudaStream_t stream;
-    int dense;
-    int sms;
-    uint8_t *cb[2];
-    double *s[2][3];
-    int cur;
-    uint8_t *tile_marker, *tile_dirty, *tile_cchg;
-    int *band_list, *band_count;
-    int *work_list, *work_count;
-    int *all_list, *all_count;
-    unsigned long long *ctr;  // C_N event counters + Front2VOF inconsistencies
-    double *scratch;          // 3N doubles, allocated on first ebit_get_state
-    double *adv[3];           // advected marker coordinates of the current sweep (scratch)
-    int8_t *bin[3];           // floor(2 adv) (scratch)
-    unsigned *work[4];        // FP64 work lists of a sweep (scratch)
-    int *wcount;              // [4]
-    unsigned *cut;            // cells cut by the interface at the last Front2VOF
-    int *ncut;
-    unsigned *iface[2];       // interface cells of the last two curvature calls
-    int *niface;              // [2]
-    int cur_if;
-    unsigned *scan;           // interface cells found by a full curvature scan
-    int *nscan;
-    int *zero;                // a device int that stays 0
-    int sweeps_since_f2v;
-    ebit_mlp *mlp;            // learned curvature (ebit_set_mlp)
-    const double *last_C;
-    const double *last_kh;
-    const uint8_t *last_st;
-    int grid_sweep, grid_adv, grid_fp64, grid_f2v, grid_f2vl, grid_hf, grid_hfl;
-    // per-kernel CUDA-event timing (ebit_profile)
-    int prof_on;
-    std::vector<cudaEvent_t> ev;
-    std::vector<int> ev_kind;
-    int ev_used;
-    double prof_ms[EBIT_PROF_KINDS];
-    long long prof_n[EBIT_PROF_KINDS];
-    std::string err;
-};
 
 namespace {
 
@@ -179,9 +126,8 @@ int sweep_launch(ebit_ctx *ctx, const SweepArgs &args) {
 
 }  // namespace
 
-extern "C" {
 
-int ebit_create(const ebit_desc *desc, ebit_ctx **out) {
+static int create_ctx(const ebit_desc *desc, const ebit_state_arrays *st, ebit_ctx **out) {
     ebit_ctx *ctx = nullptr;
     if (!desc || !out) return EBIT_EINVAL;
     *out = nullptr;
@@ -189,6 +135,7 @@ int ebit_create(const ebit_desc *desc, ebit_ctx **out) {
     if (!(desc->h > 0.0) || !std::isfinite(desc->h)) return EBIT_EINVAL;
     if ((long long)desc->nx * desc->ny * desc->nz >= (1LL << 31)) return EBIT_EINVAL;
     ctx = new ebit_ctx();
+    ctx->owns_state = st ? 0 : 1;
     std::memset(&ctx->g, 0, sizeof(ctx->g));
     for (int b = 0; b < 2; b++) {
         ctx->cb[b] = nullptr;
@@ -225,25 +172,41 @@ int ebit_create(const ebit_desc *desc, ebit_ctx **out) {
     if (ctx->sms <= 0) ctx->sms = 1;
     auto alloc = [&](void **p, size_t bytes) -> bool { return cudaMalloc(p, bytes) == cudaSuccess; };
     bool ok = true;
-    for (int b = 0; b < 2 && ok; b++) {
-        ok = ok && alloc((void **)&ctx->cb[b], (ctx->N + 7) & ~7LL);  // whole 32-bit words
-        for (int a = 0; a < 3 && ok; a++) ok = ok && alloc((void **)&ctx->s[b][a], ctx->N * sizeof(double));
+    int nt = ctx->g.ntiles;
+    if (st) {
+        for (int b = 0; b < 2; b++) {
+            ctx->cb[b] = st->cb[b];
+            for (int a = 0; a < 3; a++) ctx->s[b][a] = st->s[b][a];
+        }
+        for (int a = 0; a < 3; a++) {
+            ctx->adv[a] = st->adv[a];
+            ctx->bin[a] = st->bin[a];
+        }
+        for (int k = 0; k < 4; k++) ctx->work[k] = st->work[k];
+        ctx->wcount = st->wcount;
+        ctx->tile_marker = st->tile_marker;
+        ctx->tile_dirty = st->tile_dirty;
+        ctx->ctr = st->ctr;
+    } else {
+        for (int b = 0; b < 2 && ok; b++) {
+            ok = ok && alloc((void **)&ctx->cb[b], (ctx->N + 7) & ~7LL);  // whole 32-bit words
+            for (int a = 0; a < 3 && ok; a++) ok = ok && alloc((void **)&ctx->s[b][a], ctx->N * sizeof(double));
+        }
+        for (int a = 0; a < 3 && ok; a++)
+            ok = ok && alloc((void **)&ctx->adv[a], ctx->N * sizeof(double)) && alloc((void **)&ctx->bin[a], ctx->N);
+        for (int k = 0; k < 4 && ok; k++) ok = ok && alloc((void **)&ctx->work[k], ctx->N * sizeof(unsigned));
+        ok = ok && alloc((void **)&ctx->wcount, 4 * sizeof(int)) && alloc((void **)&ctx->tile_marker, nt) &&
+             alloc((void **)&ctx->tile_dirty, nt) && alloc((void **)&ctx->ctr, C_TOTAL * sizeof(unsigned long long));
     }
-    for (int a = 0; a < 3 && ok; a++)
-        ok = ok && alloc((void **)&ctx->adv[a], ctx->N * sizeof(double)) && alloc((void **)&ctx->bin[a], ctx->N);
-    for (int k = 0; k < 4 && ok; k++) ok = ok && alloc((void **)&ctx->work[k], ctx->N * sizeof(unsigned));
     ok = ok && alloc((void **)&ctx->cut, ctx->N * sizeof(unsigned)) && alloc((void **)&ctx->scan, ctx->N * sizeof(unsigned)) &&
          alloc((void **)&ctx->iface[0], ctx->N * sizeof(unsigned)) &&
-         alloc((void **)&ctx->iface[1], ctx->N * sizeof(unsigned)) && alloc((void **)&ctx->wcount, 4 * sizeof(int)) &&
+         alloc((void **)&ctx->iface[1], ctx->N * sizeof(unsigned)) &&
          alloc((void **)&ctx->ncut, sizeof(int)) && alloc((void **)&ctx->niface, 2 * sizeof(int)) &&
          alloc((void **)&ctx->nscan, sizeof(int)) && alloc((void **)&ctx->zero, sizeof(int));
-    int nt = ctx->g.ntiles;
-    ok = ok && alloc((void **)&ctx->tile_marker, nt) && alloc((void **)&ctx->tile_dirty, nt) &&
-         alloc((void **)&ctx->tile_cchg, nt) && alloc((void **)&ctx->band_list, nt * sizeof(int)) &&
+    ok = ok && alloc((void **)&ctx->tile_cchg, nt) && alloc((void **)&ctx->band_list, nt * sizeof(int)) &&
          alloc((void **)&ctx->band_count, sizeof(int)) && alloc((void **)&ctx->work_list, nt * sizeof(int)) &&
          alloc((void **)&ctx->work_count, sizeof(int)) && alloc((void **)&ctx->all_list, nt * sizeof(int)) &&
-         alloc((void **)&ctx->all_count, sizeof(int)) &&
-         alloc((void **)&ctx->ctr, C_TOTAL * sizeof(unsigned long long));
+         alloc((void **)&ctx->all_count, sizeof(int));
     if (!ok) {
         cudaGetLastError();
         ebit_destroy(ctx);
@@ -286,15 +249,33 @@ int ebit_create(const ebit_desc *desc, ebit_ctx **out) {
     return EBIT_OK;
 }
 
+int ebit_create_view(const ebit_desc *desc, const ebit_state_arrays *st, ebit_ctx **out) {
+    if (!st) return EBIT_EINVAL;
+    return create_ctx(desc, st, out);
+}
+
+extern "C" {
+
+int ebit_create(const ebit_desc *desc, ebit_ctx **out) { return create_ctx(desc, nullptr, out); }
+
 void ebit_destroy(ebit_ctx *ctx) {
     if (!ctx) return;
     cudaStreamSynchronize(ctx->stream);
-    for (int b = 0; b < 2; b++) {
-        cudaFree(ctx->cb[b]);
-        for (int a = 0; a < 3; a++) cudaFree(ctx->s[b][a]);
+    if (ctx->owns_state) {
+        for (int b = 0; b < 2; b++) {
+            cudaFree(ctx->cb[b]);
+            for (int a = 0; a < 3; a++) cudaFree(ctx->s[b][a]);
+        }
+        cudaFree(ctx->tile_marker);
+        cudaFree(ctx->tile_dirty);
+        cudaFree(ctx->ctr);
+        for (int a = 0; a < 3; a++) {
+            cudaFree(ctx->adv[a]);
+            cudaFree(ctx->bin[a]);
+        }
+        for (int k = 0; k < 4; k++) cudaFree(ctx->work[k]);
+        cudaFree(ctx->wcount);
     }
-    cudaFree(ctx->tile_marker);
-    cudaFree(ctx->tile_dirty);
     cudaFree(ctx->tile_cchg);
     cudaFree(ctx->band_list);
     cudaFree(ctx->band_count);
@@ -302,18 +283,11 @@ void ebit_destroy(ebit_ctx *ctx) {
     cudaFree(ctx->work_count);
     cudaFree(ctx->all_list);
     cudaFree(ctx->all_count);
-    cudaFree(ctx->ctr);
     cudaFree(ctx->scratch);
-    for (int a = 0; a < 3; a++) {
-        cudaFree(ctx->adv[a]);
-        cudaFree(ctx->bin[a]);
-    }
-    for (int k = 0; k < 4; k++) cudaFree(ctx->work[k]);
     cudaFree(ctx->cut);
     cudaFree(ctx->scan);
     cudaFree(ctx->iface[0]);
     cudaFree(ctx->iface[1]);
-    cudaFree(ctx->wcount);
     cudaFree(ctx->ncut);
     cudaFree(ctx->niface);
     cudaFree(ctx->nscan);
@@ -361,6 +335,8 @@ int ebit_advect_sweep(ebit_ctx *ctx, int dir, const double *u_face, double dt) {
     if (!ctx) return EBIT_EINVAL;
     if (dir < 0 || dir > 2) return fail(ctx, EBIT_EINVAL, "ebit_advect_sweep: dir must be 0, 1 or 2");
     if (!u_face) return fail(ctx, EBIT_EINVAL, "ebit_advect_sweep: null velocity");
+    if (!ctx->owns_state)
+        return fail(ctx, EBIT_EINVAL, "ebit_advect_sweep: a batch instance is swept by ebit_batch_advect_sweep");
     if (!std::isfinite(dt)) return fail(ctx, EBIT_EINVAL, "ebit_advect_sweep: non-finite dt");
     const int *list, *count;
     if (ctx->dense) {

@@ -1,0 +1,809 @@
+// ebit_batch.cu -- many independent EBIT instances advanced by one launch per
+// split sweep (declared in include/ebit.h).
+//
+// Each instance is a periodic grid of its own size with its own velocity and
+// time step; the method is the same as for one context (Sec. 2.1-2.3: split
+// marker advection, colour-vertex update, unaligned reconstruction by circle
+// fits).  The batch owns one arena of per-sweep state for all instances (two
+// colour/offset buffers, advection scratch, FP64 work lists, tile flags,
+// counters); every instance also has a context that views its slice of the
+// arena, so Front2VOF, curvature, state access and counters work per instance
+// through the ordinary entry points' code.
+//
+// A sweep is one cooperative launch that runs four phases over all instances,
+// separated by a grid barrier:
+//   band    -- every (instance, tile) whose 3x3x3 tile neighbourhood held a
+//              marker is listed; the FP64 list lengths are cleared;
+//   advect  -- per listed tile: each marker moved once (velocity interpolated);
+//   sweep   -- per listed tile: integer colour/aligned-edge pass, FP64 lists;
+//   fp64    -- the FP64 lists of all instances as one index space.
+// Data written in one phase and read in a later one is loaded through L2 (not
+// the read-only path).  The barrier waits a bounded number of polls; on
+// timeout it sets an error flag, every block leaves, and ebit_batch_sync
+// reports EBIT_ETIMEOUT.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/ebit.h"
+#include "common.cuh"
+#include "ctx.h"
+#include "sweep.cuh"
+
+namespace ebit {
+
+constexpr int BATCH_MAX = 1024;      // instances per batch (tile ids keep 20 bits)
+constexpr int BATCH_THREADS = 256;
+constexpr long long BAR_POLLS = 1LL << 24;  // polls of 64 ns sleep: about a second
+
+struct BatchInst {
+    SweepArgs a;  // u, lam, list and count are unused (per-sweep arrays below)
+};
+
+struct BatchParams {
+    const BatchInst *inst;    // [n], for the current buffer parity
+    int n;
+    int total_tiles;
+    const int *toff;          // [n + 1] first global tile of each instance
+    const double *const *u;   // [n] velocity component of the sweep direction
+    const double *lam;        // [n] dt / h
+    int *band;                // (instance << 20) | tile
+    int *nband;
+    int *wcount;              // [4 n] FP64 list lengths (all instances)
+    unsigned *bar;            // [2] arrivals, generation
+    int *err;
+};
+
+// Grid-wide barrier of a cooperative launch (all blocks co-resident).
+__device__ bool grid_barrier(const BatchParams &p, int *s_ok) {
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int ok = 1;
+        volatile unsigned *gen = p.bar + 1;
+        const unsigned g0 = *gen;
+        __threadfence();
+        const unsigned arrived = atomicAdd(p.bar, 1u);
+        if (arrived == gridDim.x - 1) {
+            atomicExch(p.bar, 0u);
+            __threadfence();
+            atomicAdd(p.bar + 1, 1u);
+        } else {
+            long long it = 0;
+            while (*gen == g0) {
+                if (++it > BAR_POLLS) {
+                    atomicExch(p.err, 1);
+                    ok = 0;
+                    break;
+                }
+                __nanosleep(64);
+            }
+        }
+        __threadfence();
+        if (*(volatile int *)p.err) ok = 0;
+        *s_ok = ok;
+    }
+    __syncthreads();
+    return *s_ok != 0;
+}
+
+__device__ __forceinline__ int find_inst(const int *toff, int n, int gt) {
+    int lo = 0, hi = n;  // toff[lo] <= gt < toff[hi]
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (__ldg(toff + mid) <= gt) lo = mid;
+        else hi = mid;
+    }
+    return lo;
+}
+
+template <int D>
+__global__ void __launch_bounds__(BATCH_THREADS) batch_sweep_kernel(BatchParams p) {
+    __shared__ uint16_t s_mk[3 * TILE_CELLS];
+    __shared__ uint8_t s_c[9 * 9 * 9];
+    __shared__ uint8_t s_b[RA * R1 * R2];
+    __shared__ int s_n, s_flag, s_ok;
+    __shared__ int s_pre[4 * BATCH_MAX + 1];
+    __shared__ int s_wsum[BATCH_THREADS / 32];
+    if (*(volatile int *)p.err) return;
+    const int stride = gridDim.x * blockDim.x;
+    const int gtid = blockIdx.x * blockDim.x + threadIdx.x;
+
+    // ---- band: tiles near a marker, all instances
+    for (int k = gtid; k < 4 * p.n; k += stride) p.wcount[k] = 0;
+    {
+        const int iters = (p.total_tiles + stride - 1) / stride;
+        for (int it = 0; it < iters; it++) {
+            const int gt = it * stride + gtid;
+            bool on = false;
+            int i = 0, t = 0;
+            if (gt < p.total_tiles) {
+                i = find_inst(p.toff, p.n, gt);
+                t = gt - __ldg(p.toff + i);
+                const Grid &g = p.inst[i].a.g;
+                const uint8_t *flag = p.inst[i].a.tile_marker;
+                const int tx = t % g.td[0], ty = (t / g.td[0]) % g.td[1], tz = t / (g.td[0] * g.td[1]);
+                for (int dz = -1; dz <= 1 && !on; dz++)
+                    for (int dy = -1; dy <= 1 && !on; dy++)
+                        for (int dx = -1; dx <= 1 && !on; dx++) {
+                            const int nx = wrapc(tx + dx, g.td[0]), ny = wrapc(ty + dy, g.td[1]);
+                            const int nz = wrapc(tz + dz, g.td[2]);
+                            on = flag[(nz * g.td[1] + ny) * g.td[0] + nx] != 0;
+                        }
+            }
+            const int slot = warp_append(p.nband, on);
+            if (slot >= 0) p.band[slot] = (i << 20) | t;
+        }
+    }
+    if (!grid_barrier(p, &s_ok)) return;
+    const int nb = __ldcg(p.nband);
+
+    // ---- advect
+    for (int li = blockIdx.x; li < nb; li += gridDim.x) {
+        const int e = __ldcg(p.band + li);
+        const int i = e >> 20;
+        SweepArgs a = p.inst[i].a;
+        a.u = p.u[i];
+        a.lam = p.lam[i];
+        advect_tile<D>(a, e & 0xFFFFF, s_mk, s_c, &s_n);
+    }
+    if (!grid_barrier(p, &s_ok)) return;
+
+    // ---- integer band pass
+    for (int li = blockIdx.x; li < nb; li += gridDim.x) {
+        const int e = __ldcg(p.band + li);
+        const int i = e >> 20;
+        const SweepArgs a = p.inst[i].a;
+        sweep_tile<D, true>(a, e & 0xFFFFF, s_b, &s_flag);
+        if (threadIdx.x == 0) atomicAdd(a.ctr + C_TILES, 1ull);
+    }
+    if (!grid_barrier(p, &s_ok)) return;
+
+    // ---- FP64 lists of every instance as one index space: block-wide prefix
+    // sums of the 4 n list lengths
+    {
+        const int m = 4 * p.n;
+        const int per = (m + blockDim.x - 1) / blockDim.x;
+        int loc[4 * BATCH_MAX / BATCH_THREADS];
+        int sum = 0;
+        for (int q = 0; q < per; q++) {
+            const int j = threadIdx.x * per + q;
+            loc[q] = j < m ? __ldcg(p.wcount + j) : 0;
+            sum += loc[q];
+        }
+        const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+        int inc = sum;
+        for (int off = 1; off < 32; off <<= 1) {
+            const int v = __shfl_up_sync(0xffffffffu, inc, off);
+            if (lane >= off) inc += v;
+        }
+        if (lane == 31) s_wsum[wid] = inc;
+        __syncthreads();
+        int base = 0;
+        for (int w = 0; w < wid; w++) base += s_wsum[w];
+        int run = base + inc - sum;
+        for (int q = 0; q < per; q++) {
+            const int j = threadIdx.x * per + q;
+            if (j < m) s_pre[j] = run;
+            run += loc[q];
+        }
+        if (threadIdx.x == blockDim.x - 1) s_pre[m] = run;
+        __syncthreads();
+        // marker counts of the unaligned lists (one per entry)
+        if (blockIdx.x == 0)
+            for (int i = threadIdx.x; i < p.n; i += blockDim.x) {
+                const int nm = (s_pre[4 * i + 2] - s_pre[4 * i]);
+                if (nm) atomicAdd(p.inst[i].a.ctr + C_MARKERS, (unsigned long long)nm);
+            }
+        const int total = s_pre[m];
+        for (int t = gtid; t < total; t += stride) {
+            int lo = 0, hi = m;  // s_pre[lo] <= t < s_pre[hi]
+            while (hi - lo > 1) {
+                const int mid = (lo + hi) >> 1;
+                if (s_pre[mid] <= t) lo = mid;
+                else hi = mid;
+            }
+            const int i = lo >> 2, kind = lo & 3;
+            unsigned ev[C_N] = {0, 0, 0, 0, 0};
+            fp64_item<D, true>(p.inst[i].a, kind, t - s_pre[lo], ev);
+#pragma unroll
+            for (int k = 0; k < C_N; k++)
+                if (k != C_MARKERS && ev[k]) atomicAdd(p.inst[i].a.ctr + k, (unsigned long long)ev[k]);
+        }
+    }
+}
+
+}  // namespace ebit
+
+using namespace ebit;
+
+struct ebit_batch {
+    int n = 0;
+    cudaStream_t stream = nullptr;
+    int sms = 1;
+    std::vector<ebit_ctx *> inst;
+    std::vector<long long> coff;   // first cell of each instance in the arena
+    std::vector<int> toff;         // first tile
+    long long cells = 0;
+    int tiles = 0;
+    int parity = 0;                // buffer holding the current state
+    // arena
+    uint8_t *cb[2] = {nullptr, nullptr};
+    double *s[2][3] = {{nullptr, nullptr, nullptr}, {nullptr, nullptr, nullptr}};
+    double *adv[3] = {nullptr, nullptr, nullptr};
+    int8_t *bin[3] = {nullptr, nullptr, nullptr};
+    unsigned *work[4] = {nullptr, nullptr, nullptr, nullptr};
+    int *wcount = nullptr;
+    uint8_t *tile_marker = nullptr, *tile_dirty = nullptr;
+    unsigned long long *ctr = nullptr;
+    // launch data
+    BatchInst *table[2] = {nullptr, nullptr};
+    int *d_toff = nullptr;
+    double **u[3] = {nullptr, nullptr, nullptr};
+    double *lam = nullptr;
+    int *band = nullptr, *nband = nullptr;
+    unsigned *bar = nullptr;
+    int *err = nullptr;
+    int have_velocity = 0;
+    int occ[3] = {1, 1, 1};        // co-resident blocks per SM of each direction's kernel
+    int ctas_per_sm = 1;           // chosen launch shape (autotuned)
+    // CUDA graph of two steps (even: x y z, odd: z y x)
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t gexec = nullptr;
+    int graph_ok = 0;
+    int graph_parity = 0;          // buffer parity the graph was captured from
+    std::string graph_note;        // how the graph was made, or why not
+    std::string errmsg;
+};
+
+namespace {
+
+int bfail(ebit_batch *b, int code, const std::string &m) {
+    if (b) b->errmsg = m;
+    return code;
+}
+
+#define BCU(call)                                                                                        \
+    do {                                                                                                 \
+        cudaError_t e_ = (call);                                                                         \
+        if (e_ != cudaSuccess) return bfail(b, EBIT_ECUDA, std::string(#call ": ") + cudaGetErrorString(e_)); \
+    } while (0)
+
+const void *sweep_fn(int d) {
+    if (d == 0) return (const void *)batch_sweep_kernel<0>;
+    if (d == 1) return (const void *)batch_sweep_kernel<1>;
+    return (const void *)batch_sweep_kernel<2>;
+}
+
+BatchParams sweep_params(const ebit_batch *b, int d, int parity) {
+    BatchParams p;
+    p.inst = b->table[parity];
+    p.n = b->n;
+    p.total_tiles = b->tiles;
+    p.toff = b->d_toff;
+    p.u = b->u[d];
+    p.lam = b->lam;
+    p.band = b->band;
+    p.nband = b->nband;
+    p.wcount = b->wcount;
+    p.bar = b->bar;
+    p.err = b->err;
+    return p;
+}
+
+int sweep_grid(const ebit_batch *b, int d, int ctas_per_sm) {
+    return b->sms * std::max(1, std::min(ctas_per_sm, b->occ[d]));
+}
+
+// cooperative launch (all blocks co-resident: the grid barrier needs it)
+int launch_dir(ebit_batch *b, int d, int ctas_per_sm) {
+    BatchParams p = sweep_params(b, d, b->parity);
+    BCU(cudaMemsetAsync(b->nband, 0, sizeof(int), b->stream));
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(sweep_grid(b, d, ctas_per_sm));
+    cfg.blockDim = dim3(BATCH_THREADS);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = b->stream;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeCooperative;
+    at[0].val.cooperative = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    void *args[] = {&p};
+    BCU(cudaLaunchKernelExC(&cfg, sweep_fn(d), args));
+    return EBIT_OK;
+}
+
+// Two steps (x y z, then z y x) as an explicitly built graph: a memset of the
+// band count and a cooperative kernel node per sweep.
+cudaError_t build_graph(ebit_batch *b, cudaGraph_t *out) {
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaGraphCreate(&g, 0);
+    if (e != cudaSuccess) return e;
+    const int ord[6] = {0, 1, 2, 2, 1, 0};
+    int par = b->parity;
+    cudaGraphNode_t prev = nullptr;
+    for (int q = 0; q < 6 && e == cudaSuccess; q++) {
+        const int d = ord[q];
+        cudaMemsetParams mp = {};
+        mp.dst = b->nband;
+        mp.value = 0;
+        mp.elementSize = sizeof(int);
+        mp.width = 1;
+        mp.height = 1;
+        mp.pitch = 0;
+        cudaGraphNode_t mn = nullptr, kn = nullptr;
+        e = cudaGraphAddMemsetNode(&mn, g, prev ? &prev : nullptr, prev ? 1 : 0, &mp);
+        if (e != cudaSuccess) break;
+        BatchParams p = sweep_params(b, d, par);
+        void *args[] = {&p};
+        cudaKernelNodeParams kp = {};
+        kp.func = const_cast<void *>(sweep_fn(d));
+        kp.gridDim = dim3(sweep_grid(b, d, b->ctas_per_sm));
+        kp.blockDim = dim3(BATCH_THREADS);
+        kp.sharedMemBytes = 0;
+        kp.kernelParams = args;
+        kp.extra = nullptr;
+        e = cudaGraphAddKernelNode(&kn, g, &mn, 1, &kp);
+        if (e != cudaSuccess) break;
+        cudaLaunchAttributeValue v = {};
+        v.cooperative = 1;
+        e = cudaGraphKernelNodeSetAttribute(kn, cudaLaunchAttributeCooperative, &v);
+        prev = kn;
+        par ^= 1;
+    }
+    if (e != cudaSuccess) {
+        cudaGraphDestroy(g);
+        return e;
+    }
+    *out = g;
+    return cudaSuccess;
+}
+
+int sweep_once(ebit_batch *b, int dir, int ctas_per_sm) {
+    int r = launch_dir(b, dir, ctas_per_sm);
+    if (r) return r;
+    b->parity ^= 1;
+    for (ebit_ctx *c : b->inst) {
+        c->cur = b->parity;
+        c->sweeps_since_f2v++;
+    }
+    return EBIT_OK;
+}
+
+void drop_graph(ebit_batch *b) {
+    if (b->gexec) cudaGraphExecDestroy(b->gexec);
+    if (b->graph) cudaGraphDestroy(b->graph);
+    b->gexec = nullptr;
+    b->graph = nullptr;
+    b->graph_ok = 0;
+}
+
+}  // namespace
+
+extern "C" {
+
+int ebit_batch_create(int n, const ebit_desc *descs, ebit_batch **out) {
+    if (!out) return EBIT_EINVAL;
+    *out = nullptr;
+    if (n < 1 || n > BATCH_MAX || !descs) return EBIT_EINVAL;
+    ebit_batch *b = new ebit_batch();
+    b->n = n;
+    b->stream = (cudaStream_t)descs[0].cuda_stream;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&b->sms, cudaDevAttrMultiProcessorCount, dev);
+    int coop = 0;
+    cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev);
+    if (!coop) {
+        delete b;
+        return EBIT_ECUDA;
+    }
+    b->coff.resize(n + 1);
+    b->toff.resize(n + 1);
+    long long cells = 0;
+    long long tiles = 0;
+    for (int i = 0; i < n; i++) {
+        const ebit_desc &d = descs[i];
+        if (d.nx < 8 || d.ny < 8 || d.nz < 8 || !(d.h > 0.0) || d.cuda_stream != descs[0].cuda_stream ||
+            (d.flags & EBIT_DESC_DENSE)) {
+            delete b;
+            return EBIT_EINVAL;
+        }
+        const long long nc = (long long)d.nx * d.ny * d.nz;
+        const long long nt = (long long)((d.nx + 7) / 8) * ((d.ny + 7) / 8) * ((d.nz + 7) / 8);
+        if (nt >= (1 << 20)) {
+            delete b;
+            return EBIT_EINVAL;
+        }
+        b->coff[i] = cells;
+        b->toff[i] = (int)tiles;
+        cells += (nc + 7) & ~7LL;  // each slice starts on a 32-bit word of the colour bytes
+        tiles += nt;
+    }
+    if (cells >= (1LL << 31) || tiles >= (1LL << 31)) {
+        delete b;
+        return EBIT_EINVAL;
+    }
+    b->coff[n] = cells;
+    b->toff[n] = (int)tiles;
+    b->cells = cells;
+    b->tiles = (int)tiles;
+    auto alloc = [](void **p, size_t bytes) { return cudaMalloc(p, bytes) == cudaSuccess; };
+    bool ok = true;
+    for (int q = 0; q < 2 && ok; q++) {
+        ok = ok && alloc((void **)&b->cb[q], cells);
+        for (int a = 0; a < 3 && ok; a++) ok = ok && alloc((void **)&b->s[q][a], cells * sizeof(double));
+    }
+    for (int a = 0; a < 3 && ok; a++)
+        ok = ok && alloc((void **)&b->adv[a], cells * sizeof(double)) && alloc((void **)&b->bin[a], cells);
+    for (int k = 0; k < 4 && ok; k++) ok = ok && alloc((void **)&b->work[k], cells * sizeof(unsigned));
+    ok = ok && alloc((void **)&b->wcount, 4 * n * sizeof(int)) && alloc((void **)&b->tile_marker, tiles) &&
+         alloc((void **)&b->tile_dirty, tiles) && alloc((void **)&b->ctr, (size_t)n * C_TOTAL * 8) &&
+         alloc((void **)&b->table[0], n * sizeof(BatchInst)) && alloc((void **)&b->table[1], n * sizeof(BatchInst)) &&
+         alloc((void **)&b->d_toff, (n + 1) * sizeof(int)) && alloc((void **)&b->lam, n * sizeof(double)) &&
+         alloc((void **)&b->band, std::max<long long>(tiles, 1) * sizeof(int)) &&
+         alloc((void **)&b->nband, sizeof(int)) && alloc((void **)&b->bar, 2 * sizeof(unsigned)) &&
+         alloc((void **)&b->err, sizeof(int));
+    for (int d = 0; d < 3 && ok; d++) ok = ok && alloc((void **)&b->u[d], n * sizeof(double *));
+    if (!ok) {
+        cudaGetLastError();
+        ebit_batch_destroy(b);
+        return EBIT_ENOMEM;
+    }
+    // instance contexts over the arena slices
+    b->inst.assign(n, nullptr);
+    std::vector<BatchInst> tab[2];
+    tab[0].resize(n);
+    tab[1].resize(n);
+    for (int i = 0; i < n; i++) {
+        const long long c0 = b->coff[i];
+        const int t0 = b->toff[i];
+        ebit_state_arrays st;
+        for (int q = 0; q < 2; q++) {
+            st.cb[q] = b->cb[q] + c0;
+            for (int a = 0; a < 3; a++) st.s[q][a] = b->s[q][a] + c0;
+        }
+        for (int a = 0; a < 3; a++) {
+            st.adv[a] = b->adv[a] + c0;
+            st.bin[a] = b->bin[a] + c0;
+        }
+        for (int k = 0; k < 4; k++) st.work[k] = b->work[k] + c0;
+        st.wcount = b->wcount + 4 * i;
+        st.tile_marker = b->tile_marker + t0;
+        st.tile_dirty = b->tile_dirty + t0;
+        st.ctr = b->ctr + (size_t)i * C_TOTAL;
+        int r = ebit_create_view(&descs[i], &st, &b->inst[i]);
+        if (r) {
+            ebit_batch_destroy(b);
+            return r;
+        }
+        const ebit_ctx *c = b->inst[i];
+        for (int q = 0; q < 2; q++) {
+            SweepArgs &a = tab[q][i].a;
+            std::memset(&a, 0, sizeof(a));
+            a.g = c->g;
+            a.cb = st.cb[q];
+            a.cbo = st.cb[q ^ 1];
+            for (int k = 0; k < 3; k++) {
+                a.s[k] = st.s[q][k];
+                a.so[k] = st.s[q ^ 1][k];
+                a.adv[k] = st.adv[k];
+                a.bin[k] = st.bin[k];
+            }
+            for (int k = 0; k < 4; k++) a.work[k] = st.work[k];
+            a.wcount = st.wcount;
+            a.ctr = st.ctr;
+            a.tile_marker = st.tile_marker;
+            a.tile_dirty = st.tile_dirty;
+        }
+    }
+    if (cudaMemcpyAsync(b->table[0], tab[0].data(), n * sizeof(BatchInst), cudaMemcpyHostToDevice, b->stream) !=
+            cudaSuccess ||
+        cudaMemcpyAsync(b->table[1], tab[1].data(), n * sizeof(BatchInst), cudaMemcpyHostToDevice, b->stream) !=
+            cudaSuccess ||
+        cudaMemcpyAsync(b->d_toff, b->toff.data(), (n + 1) * sizeof(int), cudaMemcpyHostToDevice, b->stream) !=
+            cudaSuccess ||
+        cudaMemsetAsync(b->bar, 0, 2 * sizeof(unsigned), b->stream) != cudaSuccess ||
+        cudaMemsetAsync(b->err, 0, sizeof(int), b->stream) != cudaSuccess ||
+        cudaMemsetAsync(b->wcount, 0, 4 * n * sizeof(int), b->stream) != cudaSuccess ||
+        cudaStreamSynchronize(b->stream) != cudaSuccess) {
+        cudaGetLastError();
+        ebit_batch_destroy(b);
+        return EBIT_ECUDA;
+    }
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b->occ[0], batch_sweep_kernel<0>, BATCH_THREADS, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b->occ[1], batch_sweep_kernel<1>, BATCH_THREADS, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b->occ[2], batch_sweep_kernel<2>, BATCH_THREADS, 0);
+    for (int d = 0; d < 3; d++) b->occ[d] = std::max(1, b->occ[d]);
+    b->ctas_per_sm = std::min({b->occ[0], b->occ[1], b->occ[2]});
+    *out = b;
+    return EBIT_OK;
+}
+
+void ebit_batch_destroy(ebit_batch *b) {
+    if (!b) return;
+    cudaStreamSynchronize(b->stream);
+    drop_graph(b);
+    for (ebit_ctx *c : b->inst) ebit_destroy(c);
+    for (int q = 0; q < 2; q++) {
+        cudaFree(b->cb[q]);
+        for (int a = 0; a < 3; a++) cudaFree(b->s[q][a]);
+    }
+    for (int a = 0; a < 3; a++) {
+        cudaFree(b->adv[a]);
+        cudaFree(b->bin[a]);
+        cudaFree(b->u[a]);
+    }
+    for (int k = 0; k < 4; k++) cudaFree(b->work[k]);
+    cudaFree(b->wcount);
+    cudaFree(b->tile_marker);
+    cudaFree(b->tile_dirty);
+    cudaFree(b->ctr);
+    cudaFree(b->table[0]);
+    cudaFree(b->table[1]);
+    cudaFree(b->d_toff);
+    cudaFree(b->lam);
+    cudaFree(b->band);
+    cudaFree(b->nband);
+    cudaFree(b->bar);
+    cudaFree(b->err);
+    delete b;
+}
+
+int ebit_batch_size(const ebit_batch *b) { return b ? b->n : 0; }
+
+ebit_ctx *ebit_batch_instance(ebit_batch *b, int i) {
+    if (!b || i < 0 || i >= b->n) return nullptr;
+    return b->inst[i];
+}
+
+int ebit_batch_set_velocity(ebit_batch *b, const double *const *u_faces, const double *dt) {
+    if (!b || !u_faces || !dt) return EBIT_EINVAL;
+    std::vector<const double *> up[3];
+    std::vector<double> lam(b->n);
+    for (int i = 0; i < b->n; i++) {
+        for (int d = 0; d < 3; d++) {
+            if (!u_faces[3 * i + d]) return bfail(b, EBIT_EINVAL, "ebit_batch_set_velocity: null velocity");
+            up[d].push_back(u_faces[3 * i + d]);
+        }
+        if (!std::isfinite(dt[i])) return bfail(b, EBIT_EINVAL, "ebit_batch_set_velocity: non-finite dt");
+        lam[i] = dt[i] / b->inst[i]->h;
+    }
+    for (int d = 0; d < 3; d++)
+        BCU(cudaMemcpyAsync(b->u[d], up[d].data(), b->n * sizeof(double *), cudaMemcpyHostToDevice, b->stream));
+    BCU(cudaMemcpyAsync(b->lam, lam.data(), b->n * sizeof(double), cudaMemcpyHostToDevice, b->stream));
+    BCU(cudaStreamSynchronize(b->stream));
+    b->have_velocity = 1;
+    return EBIT_OK;
+}
+
+int ebit_batch_advect_sweep(ebit_batch *b, int dir) {
+    if (!b) return EBIT_EINVAL;
+    if (dir < 0 || dir > 2) return bfail(b, EBIT_EINVAL, "ebit_batch_advect_sweep: dir must be 0, 1 or 2");
+    if (!b->have_velocity) return bfail(b, EBIT_EINVAL, "ebit_batch_advect_sweep: no velocity set");
+    return sweep_once(b, dir, b->ctas_per_sm);
+}
+
+int ebit_batch_run(ebit_batch *b, int first_step, int steps, int use_graph) {
+    if (!b || steps < 0) return EBIT_EINVAL;
+    if (!b->have_velocity) return bfail(b, EBIT_EINVAL, "ebit_batch_run: no velocity set");
+    int n = first_step;
+    int left = steps;
+    auto one_step = [&](int k) -> int {
+        const int ord[2][3] = {{0, 1, 2}, {2, 1, 0}};
+        for (int q = 0; q < 3; q++) {
+            int r = sweep_once(b, ord[k & 1][q], b->ctas_per_sm);
+            if (r) return r;
+        }
+        return EBIT_OK;
+    };
+    // leading odd step, so that the graph always starts on an even step
+    if (left > 0 && (n & 1)) {
+        int r = one_step(n);
+        if (r) return r;
+        n++;
+        left--;
+    }
+    if (use_graph && left >= 2) {
+        if (b->graph_ok && b->graph_parity != b->parity) drop_graph(b);
+        if (!b->graph_ok) {
+            // two steps from the current parity (a replay restores it): stream
+            // capture first, else an explicitly built graph
+            drop_graph(b);
+            const int par0 = b->parity;
+            std::vector<int> since(b->n);
+            for (int i = 0; i < b->n; i++) since[i] = b->inst[i]->sweeps_since_f2v;
+            std::string why;
+            cudaGraph_t g = nullptr;
+            if (cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal) == cudaSuccess) {
+                int r = one_step(0);
+                if (r == EBIT_OK) r = one_step(1);
+                cudaError_t e = cudaStreamEndCapture(b->stream, &g);
+                if (r != EBIT_OK || e != cudaSuccess) {
+                    why = "capture: " + (r != EBIT_OK ? b->errmsg : std::string(cudaGetErrorString(e)));
+                    if (g) cudaGraphDestroy(g);
+                    g = nullptr;
+                }
+            }
+            cudaGetLastError();
+            b->parity = par0;
+            for (int i = 0; i < b->n; i++) {
+                b->inst[i]->cur = par0;
+                b->inst[i]->sweeps_since_f2v = since[i];
+            }
+            int how = 1;
+            if (g) {
+                cudaError_t e = cudaGraphInstantiate(&b->gexec, g, 0);
+                if (e != cudaSuccess) {
+                    why += std::string("; instantiate captured: ") + cudaGetErrorString(e);
+                    cudaGraphDestroy(g);
+                    g = nullptr;
+                    b->gexec = nullptr;
+                }
+            }
+            if (!g) {
+                how = 2;
+                cudaError_t e = build_graph(b, &g);
+                if (e == cudaSuccess) e = cudaGraphInstantiate(&b->gexec, g, 0);
+                if (e != cudaSuccess) {
+                    why += std::string("; built graph: ") + cudaGetErrorString(e);
+                    if (g) cudaGraphDestroy(g);
+                    g = nullptr;
+                    b->gexec = nullptr;
+                }
+            }
+            cudaGetLastError();
+            if (g) {
+                b->graph = g;
+                b->graph_ok = how;
+                b->graph_parity = par0;
+            }
+            b->graph_note = g ? (how == 1 ? "stream capture" : "explicit graph" + why) : "no graph" + why;
+        }
+        if (b->graph_ok) {
+            while (left >= 2) {
+                BCU(cudaGraphLaunch(b->gexec, b->stream));
+                for (ebit_ctx *c : b->inst) c->sweeps_since_f2v += 6;
+                n += 2;
+                left -= 2;
+            }
+        }
+    }
+    while (left > 0) {
+        int r = one_step(n);
+        if (r) return r;
+        n++;
+        left--;
+    }
+    return EBIT_OK;
+}
+
+int ebit_batch_graph_active(const ebit_batch *b) { return b ? b->graph_ok : 0; }
+
+const char *ebit_batch_graph_note(const ebit_batch *b) { return b ? b->graph_note.c_str() : "null batch"; }
+
+int ebit_batch_sync(ebit_batch *b) {
+    if (!b) return EBIT_EINVAL;
+    int e = 0;
+    BCU(cudaMemcpyAsync(&e, b->err, sizeof(int), cudaMemcpyDeviceToHost, b->stream));
+    BCU(cudaStreamSynchronize(b->stream));
+    if (e) return bfail(b, EBIT_ETIMEOUT, "a grid barrier of the batched sweep gave up");
+    return EBIT_OK;
+}
+
+int ebit_batch_launch_shape(const ebit_batch *b, int *ctas_per_sm, int *max_ctas_per_sm) {
+    if (!b) return EBIT_EINVAL;
+    if (ctas_per_sm) *ctas_per_sm = b->ctas_per_sm;
+    if (max_ctas_per_sm) *max_ctas_per_sm = std::min({b->occ[0], b->occ[1], b->occ[2]});
+    return EBIT_OK;
+}
+
+int ebit_batch_set_launch_shape(ebit_batch *b, int ctas_per_sm) {
+    if (!b || ctas_per_sm < 1 || ctas_per_sm > std::min({b->occ[0], b->occ[1], b->occ[2]})) return EBIT_EINVAL;
+    if (ctas_per_sm != b->ctas_per_sm) drop_graph(b);
+    b->ctas_per_sm = ctas_per_sm;
+    return EBIT_OK;
+}
+
+int ebit_batch_autotune(ebit_batch *b, int sweeps, double *ms_out) {
+    if (!b || sweeps < 1) return EBIT_EINVAL;
+    if (!b->have_velocity) return bfail(b, EBIT_EINVAL, "ebit_batch_autotune: no velocity set");
+    // trial sweeps run on a copy of the state, which is put back afterwards
+    const long long cells = b->cells;
+    const int par0 = b->parity;
+    uint8_t *cb_save = nullptr, *tm_save = nullptr, *td_save = nullptr;
+    double *s_save = nullptr;
+    unsigned long long *ctr_save = nullptr;
+    bool ok = cudaMalloc((void **)&cb_save, cells) == cudaSuccess &&
+              cudaMalloc((void **)&s_save, 3 * cells * sizeof(double)) == cudaSuccess &&
+              cudaMalloc((void **)&tm_save, b->tiles) == cudaSuccess &&
+              cudaMalloc((void **)&td_save, b->tiles) == cudaSuccess &&
+              cudaMalloc((void **)&ctr_save, (size_t)b->n * C_TOTAL * 8) == cudaSuccess;
+    auto release = [&]() {
+        cudaFree(cb_save);
+        cudaFree(s_save);
+        cudaFree(tm_save);
+        cudaFree(td_save);
+        cudaFree(ctr_save);
+    };
+    if (!ok) {
+        cudaGetLastError();
+        release();
+        return bfail(b, EBIT_ENOMEM, "ebit_batch_autotune: no room for the state copy");
+    }
+    auto copy = [&](bool save) -> cudaError_t {
+        cudaError_t e = cudaSuccess;
+        auto cp = [&](void *dst, const void *src, size_t bytes) {
+            if (e == cudaSuccess) e = cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToDevice, b->stream);
+        };
+        if (save) {
+            cp(cb_save, b->cb[par0], cells);
+            for (int a = 0; a < 3; a++) cp(s_save + a * cells, b->s[par0][a], cells * sizeof(double));
+            cp(tm_save, b->tile_marker, b->tiles);
+            cp(td_save, b->tile_dirty, b->tiles);
+            cp(ctr_save, b->ctr, (size_t)b->n * C_TOTAL * 8);
+        } else {
+            for (int q = 0; q < 2; q++) {
+                cp(b->cb[q], cb_save, cells);
+                for (int a = 0; a < 3; a++) cp(b->s[q][a], s_save + a * cells, cells * sizeof(double));
+            }
+            cp(b->tile_marker, tm_save, b->tiles);
+            cp(b->tile_dirty, td_save, b->tiles);
+            cp(b->ctr, ctr_save, (size_t)b->n * C_TOTAL * 8);
+        }
+        return e;
+    };
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    int best = b->ctas_per_sm;
+    double best_ms = 1e300;
+    const int maxc = std::min({b->occ[0], b->occ[1], b->occ[2]});
+    std::vector<int> since(b->n);
+    for (int i = 0; i < b->n; i++) since[i] = b->inst[i]->sweeps_since_f2v;
+    int r = EBIT_OK;
+    if (copy(true) != cudaSuccess) r = bfail(b, EBIT_ECUDA, "ebit_batch_autotune: state copy failed");
+    for (int c = 1; c <= maxc && r == EBIT_OK; c++) {
+        for (int rep = 0; rep < 2 && r == EBIT_OK; rep++) {  // first pass warms up
+            if (copy(false) != cudaSuccess) {
+                r = bfail(b, EBIT_ECUDA, "ebit_batch_autotune: state copy failed");
+                break;
+            }
+            b->parity = par0;
+            cudaEventRecord(e0, b->stream);
+            for (int k = 0; k < sweeps && r == EBIT_OK; k++) r = sweep_once(b, k % 3, c);
+            cudaEventRecord(e1, b->stream);
+            if (ebit_batch_sync(b) != EBIT_OK) r = EBIT_ETIMEOUT;
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            if (rep == 1 && r == EBIT_OK) {
+                if (ms_out) ms_out[c - 1] = ms;
+                if (ms < best_ms) {
+                    best_ms = ms;
+                    best = c;
+                }
+            }
+        }
+    }
+    if (r == EBIT_OK && copy(false) != cudaSuccess) r = bfail(b, EBIT_ECUDA, "ebit_batch_autotune: restore failed");
+    cudaStreamSynchronize(b->stream);
+    b->parity = par0;
+    for (int i = 0; i < b->n; i++) {
+        b->inst[i]->cur = par0;
+        b->inst[i]->sweeps_since_f2v = since[i];
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    release();
+    if (r == EBIT_OK) {
+        if (best != b->ctas_per_sm) drop_graph(b);
+        b->ctas_per_sm = best;
+    }
+    return r;
+}
+
+const char *ebit_batch_last_error(const ebit_batch *b) { return b ? b->errmsg.c_str() : "null batch"; }
+
+}  // extern "C"

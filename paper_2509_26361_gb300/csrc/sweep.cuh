@@ -62,6 +62,15 @@ struct P2 {
     double x, y;
 };
 
+// Loads of data produced earlier in the same launch (the persistent batched
+// sweep, F = true) bypass the non-coherent read-only path and L1; separate
+// launches (F = false) read them through the read-only cache.
+template <bool F, typename T>
+__device__ __forceinline__ T ld_in(const T *p) {
+    if (F) return __ldcg(p);
+    return __ldg(p);
+}
+
 // 2D cell edges in a plane spanned by (a, t): B a-edge at c00, R t-edge at c10,
 // T a-edge at c01, L t-edge at c00.
 enum { EB = 0, ER = 1, ET = 2, EL = 3 };
@@ -169,7 +178,55 @@ __device__ __forceinline__ int warp_append(int *counter, bool flag) {
 }
 
 // ---------------------------------------------------------------- advection
-// Move every marker of the band once (Eq. 2).  CFL >= 1 is counted and clamped.
+// Move every marker of one band tile once (Eq. 2).  CFL >= 1 is counted and
+// clamped.  Called by all threads of the block; s_mk/s_c/s_n are its shared
+// staging.
+template <int D>
+__device__ __forceinline__ void advect_tile(const SweepArgs &a, int tile, uint16_t *s_mk, uint8_t *s_c, int *s_n) {
+    int o[3];
+    tile_origin(a.g, tile, o);
+    if (threadIdx.x == 0) *s_n = 0;
+    for (int r = threadIdx.x; r < 729; r += blockDim.x) {
+        int rx = r % 9, ry = (r / 9) % 9, rz = r / 81;
+        s_c[r] = __ldg(a.cb + lin(a.g, o[0] + rx, o[1] + ry, o[2] + rz)) & 1;
+    }
+    __syncthreads();
+    for (int c = threadIdx.x; c < TILE_CELLS; c += blockDim.x) {
+        int q[3] = {o[0] + (c & 7), o[1] + ((c >> 3) & 7), o[2] + (c >> 6)};
+        bool valid = q[0] < a.g.n[0] && q[1] < a.g.n[1] && q[2] < a.g.n[2];
+        int mask = 0;
+        if (valid) {
+            const int r = (c & 7) + 9 * ((c >> 3) & 7) + 81 * (c >> 6);
+            const int c0 = s_c[r];
+            mask = (s_c[r + 1] != c0) | ((s_c[r + 9] != c0) << 1) | ((s_c[r + 81] != c0) << 2);
+        }
+        for (int e = 0; e < 3; e++) {
+            int slot = warp_append(s_n, (mask >> e) & 1);
+            if (slot >= 0) s_mk[slot] = (uint16_t)(c | (e << 9));
+        }
+    }
+    __syncthreads();
+    const int n = *s_n;
+    unsigned hits = 0;
+    for (int k = threadIdx.x; k < n; k += blockDim.x) {
+        int it = s_mk[k], c = it & 511, e = it >> 9;
+        int q[3] = {o[0] + (c & 7), o[1] + ((c >> 3) & 7), o[2] + (c >> 6)};
+        const int id = lin3(a.g, q);
+        double sv = __ldg(a.s[e] + id);
+        double cf = interp_u<D>(a, q, e, sv) * a.lam;
+        if (!(fabs(cf) < 1.0)) {
+            hits++;
+            cf = cf > 0.0 ? ONE_MINUS : -ONE_MINUS;
+        }
+        double x = (e == D) ? sv + cf : cf;
+        a.adv[e][id] = x;
+        a.bin[e][id] = (int8_t)(int)floor(2.0 * x);
+    }
+    unsigned v = __reduce_add_sync(0xffffffffu, hits);
+    if ((threadIdx.x & 31) == 0 && v) atomicAdd(a.ctr + C_CFL, (unsigned long long)v);
+    __syncthreads();
+}
+
 template <int D>
 __global__ void __launch_bounds__(256) advect_kernel(SweepArgs a) {
     __shared__ uint16_t s_mk[3 * TILE_CELLS];
@@ -177,55 +234,11 @@ __global__ void __launch_bounds__(256) advect_kernel(SweepArgs a) {
     __shared__ int s_n;
     const int ntl = *a.count;
     if (blockIdx.x == 0 && threadIdx.x < 4) a.wcount[threadIdx.x] = 0;
-    for (int li = blockIdx.x; li < ntl; li += gridDim.x) {
-        const int tile = a.list[li];
-        int o[3];
-        tile_origin(a.g, tile, o);
-        if (threadIdx.x == 0) s_n = 0;
-        for (int r = threadIdx.x; r < 729; r += blockDim.x) {
-            int rx = r % 9, ry = (r / 9) % 9, rz = r / 81;
-            s_c[r] = __ldg(a.cb + lin(a.g, o[0] + rx, o[1] + ry, o[2] + rz)) & 1;
-        }
-        __syncthreads();
-        for (int c = threadIdx.x; c < TILE_CELLS; c += blockDim.x) {
-            int q[3] = {o[0] + (c & 7), o[1] + ((c >> 3) & 7), o[2] + (c >> 6)};
-            bool valid = q[0] < a.g.n[0] && q[1] < a.g.n[1] && q[2] < a.g.n[2];
-            int mask = 0;
-            if (valid) {
-                const int r = (c & 7) + 9 * ((c >> 3) & 7) + 81 * (c >> 6);
-                const int c0 = s_c[r];
-                mask = (s_c[r + 1] != c0) | ((s_c[r + 9] != c0) << 1) | ((s_c[r + 81] != c0) << 2);
-            }
-            for (int e = 0; e < 3; e++) {
-                int slot = warp_append(&s_n, (mask >> e) & 1);
-                if (slot >= 0) s_mk[slot] = (uint16_t)(c | (e << 9));
-            }
-        }
-        __syncthreads();
-        const int n = s_n;
-        unsigned hits = 0;
-        for (int k = threadIdx.x; k < n; k += blockDim.x) {
-            int it = s_mk[k], c = it & 511, e = it >> 9;
-            int q[3] = {o[0] + (c & 7), o[1] + ((c >> 3) & 7), o[2] + (c >> 6)};
-            const int id = lin3(a.g, q);
-            double sv = __ldg(a.s[e] + id);
-            double cf = interp_u<D>(a, q, e, sv) * a.lam;
-            if (!(fabs(cf) < 1.0)) {
-                hits++;
-                cf = cf > 0.0 ? ONE_MINUS : -ONE_MINUS;
-            }
-            double x = (e == D) ? sv + cf : cf;
-            a.adv[e][id] = x;
-            a.bin[e][id] = (int8_t)(int)floor(2.0 * x);
-        }
-        unsigned v = __reduce_add_sync(0xffffffffu, hits);
-        if ((threadIdx.x & 31) == 0 && v) atomicAdd(a.ctr + C_CFL, (unsigned long long)v);
-        __syncthreads();
-    }
+    for (int li = blockIdx.x; li < ntl; li += gridDim.x) advect_tile<D>(a, a.list[li], s_mk, s_c, &s_n);
 }
 
 // ----------------------------------------------------------- cell context
-template <int D>
+template <int D, bool F = false>
 struct SweepCell {
     static constexpr int A = D, T1 = (D + 1) % 3, T2 = (D + 2) % 3;
     const SweepArgs &a;
@@ -290,11 +303,11 @@ struct SweepCell {
     __device__ __forceinline__ int pbin(int e, int da, int dt, int *off) const {
         if (e == EB || e == ET) {
             *off = da;
-            return __ldg(a.bin[A] + pid<TT, NN>(da, dt + (e == ET ? 1 : 0)));
+            return ld_in<F>(a.bin[A] + pid<TT, NN>(da, dt + (e == ET ? 1 : 0)));
         }
         int aa = da + (e == ER ? 1 : 0);
         *off = aa;
-        return __ldg(a.bin[TT] + pid<TT, NN>(aa, dt));
+        return ld_in<F>(a.bin[TT] + pid<TT, NN>(aa, dt));
     }
     // advected position (x along A, y along TT) relative to the cell's node
     template <int TT, int NN>
@@ -302,12 +315,12 @@ struct SweepCell {
         P2 r;
         if (e == EB || e == ET) {
             int tt = dt + (e == ET ? 1 : 0);
-            r.x = (double)da + __ldg(a.adv[A] + pid<TT, NN>(da, tt));
+            r.x = (double)da + ld_in<F>(a.adv[A] + pid<TT, NN>(da, tt));
             r.y = (double)tt;
         } else {
             int aa = da + (e == ER ? 1 : 0);
             int id = pid<TT, NN>(aa, dt);
-            r.x = (double)aa + __ldg(a.adv[TT] + id);
+            r.x = (double)aa + ld_in<F>(a.adv[TT] + id);
             r.y = (double)dt + __ldg(a.s[TT] + id);
         }
         return r;
@@ -439,7 +452,7 @@ struct SweepCell {
         int par = ncol0;
         for (int da = -1; da <= 1; da++) {
             if ((wb(da, 0) & 1) == (wb(da + 1, 0) & 1)) continue;
-            int b = __ldg(a.bin[A] + pid<TT, NN>(da, 0));
+            int b = ld_in<F>(a.bin[A] + pid<TT, NN>(da, 0));
             if (b >= -2 * da && b < 1 - 2 * da) par ^= 1;
         }
         for (int da = -1; da <= 1; da++) {
@@ -468,17 +481,14 @@ __device__ __forceinline__ bool saddle4(int c00, int c10, int c01, int c11) {
 // in [0, 8] relative to the tile origin
 constexpr int RA = 11, R1 = 9, R2 = 9;
 
-template <int D>
-__global__ void __launch_bounds__(256) sweep_kernel(SweepArgs a) {
+// One band tile, all threads of the block; s_b/s_flag are its shared staging.
+template <int D, bool F>
+__device__ __forceinline__ void sweep_tile(const SweepArgs &a, int tile, uint8_t *s_b, int *s_flag) {
     constexpr int A = D, T1 = (D + 1) % 3, T2 = (D + 2) % 3;
-    __shared__ int s_flag;
-    __shared__ uint8_t s_b[RA * R1 * R2];
-    const int ntl = *a.count;
-    for (int li = blockIdx.x; li < ntl; li += gridDim.x) {
-        const int tile = a.list[li];
+    {
         int o[3];
         tile_origin(a.g, tile, o);
-        if (threadIdx.x == 0) s_flag = 0;
+        if (threadIdx.x == 0) *s_flag = 0;
         for (int r = threadIdx.x; r < RA * R1 * R2; r += blockDim.x) {
             int ka = r % RA, k1 = (r / RA) % R1, k2 = r / (RA * R1);
             int q[3];
@@ -496,7 +506,7 @@ __global__ void __launch_bounds__(256) sweep_kernel(SweepArgs a) {
             bool push[4] = {false, false, false, false};
             int myid = 0;
             if (valid) {
-                SweepCell<D> cell(a, x, y, z);
+                SweepCell<D, F> cell(a, x, y, z);
                 myid = lin(a.g, x, y, z);
                 const int l[3] = {c & 7, (c >> 3) & 7, c >> 6};
                 // staged index of node (da, d1, d2) relative to the cell
@@ -530,7 +540,7 @@ __global__ void __launch_bounds__(256) sweep_kernel(SweepArgs a) {
 #pragma unroll
                             for (int d2 = 0; d2 < 2; d2++) {
                                 has[da][d1][d2] = col[da][d1][d2] != col[da + 1][d1][d2];
-                                bn[da][d1][d2] = has[da][d1][d2] ? __ldg(a.bin[A] + cell.id3(da - 1, d1, d2)) : 0;
+                                bn[da][d1][d2] = has[da][d1][d2] ? ld_in<F>(a.bin[A] + cell.id3(da - 1, d1, d2)) : 0;
                             }
                     // new colours: X >= 1 <=> bin >= 2 (crossed the right node),
                     // X < 0 <=> bin < 0 (crossed the left node)  (Fig. 4)
@@ -565,7 +575,7 @@ __global__ void __launch_bounds__(256) sweep_kernel(SweepArgs a) {
                             if (nl == 1 || nl == 3) {
                                 double sv[3];
                                 for (int k = 0; k < nl; k++) {
-                                    double xv = __ldg(a.adv[A] + cell.id3(land[k], 0, 0));
+                                    double xv = ld_in<F>(a.adv[A] + cell.id3(land[k], 0, 0));
                                     double sn = xv - (double)(-land[k]);
                                     if (sn > ONE_MINUS) sn = ONE_MINUS;
                                     sv[k] = sn;
@@ -625,7 +635,7 @@ __global__ void __launch_bounds__(256) sweep_kernel(SweepArgs a) {
                 if (slot >= 0) a.work[k][slot] = (unsigned)myid;
             }
         }
-        if (mk) s_flag = 1;
+        if (mk) *s_flag = 1;
 #pragma unroll
         for (int k = 0; k < C_N; k++) {
             unsigned v = __reduce_add_sync(0xffffffffu, ev[k]);
@@ -633,18 +643,52 @@ __global__ void __launch_bounds__(256) sweep_kernel(SweepArgs a) {
         }
         __syncthreads();
         if (threadIdx.x == 0) {
-            a.tile_marker[tile] = (uint8_t)s_flag;
+            a.tile_marker[tile] = (uint8_t)*s_flag;
             a.tile_dirty[tile] = 1;
         }
         __syncthreads();
     }
+}
+
+template <int D>
+__global__ void __launch_bounds__(256) sweep_kernel(SweepArgs a) {
+    __shared__ int s_flag;
+    __shared__ uint8_t s_b[RA * R1 * R2];
+    const int ntl = *a.count;
+    for (int li = blockIdx.x; li < ntl; li += gridDim.x) sweep_tile<D, false>(a, a.list[li], s_b, &s_flag);
     if (blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(a.ctr + C_TILES, (unsigned long long)ntl);
 }
 
+
 // ------------------------------------------------- FP64 work lists
+// Entry k of list `kind` (0, 1: unaligned edges of families 1, 2; 2, 3: saddle
+// faces of families 1, 2).
+template <int D, bool F>
+__device__ __forceinline__ void fp64_item(const SweepArgs &a, int kind, int k, unsigned ev[C_N]) {
+    constexpr int T1 = (D + 1) % 3, T2 = (D + 2) % 3;
+    const int id = (int)ld_in<F>(a.work[kind] + k);
+    const int x = id % a.g.n[0], y = (id / a.g.n[0]) % a.g.n[1], z = id / (a.g.n[0] * a.g.n[1]);
+    SweepCell<D, F> cell(a, x, y, z);
+    if ((kind & 1) == 0) cell.template loadw<T1, T2>();
+    else cell.template loadw<T2, T1>();
+    if (kind == 0) {
+        cell.template unaligned<T1, T2>(ev);
+    } else if (kind == 1) {
+        cell.template unaligned<T2, T1>(ev);
+    } else {
+        int ncol0 = ld_in<F>(a.cbo + id) & 1;
+        int bit = (kind == 2) ? (cell.template face_phase<T1, T2>(ncol0) << (1 + T2))
+                              : (cell.template face_phase<T2, T1>(ncol0) << (1 + T1));
+        if (bit) {
+            uintptr_t addr = (uintptr_t)(a.cbo + id);
+            unsigned *w = (unsigned *)(addr & ~(uintptr_t)3);
+            atomicOr(w, (unsigned)bit << (8 * (addr & 3)));
+        }
+    }
+}
+
 template <int D>
 __global__ void __launch_bounds__(128) fp64_kernel(SweepArgs a) {
-    constexpr int T1 = (D + 1) % 3, T2 = (D + 2) % 3;
     const int n0 = a.wcount[0], n1 = a.wcount[1], n2 = a.wcount[2], n3 = a.wcount[3];
     const int total = n0 + n1 + n2 + n3;
     unsigned ev[C_N] = {0, 0, 0, 0, 0};
@@ -659,25 +703,7 @@ __global__ void __launch_bounds__(128) fp64_kernel(SweepArgs a) {
         else if (t < n0 + n1) { kind = 1; k = t - n0; }
         else if (t < n0 + n1 + n2) { kind = 2; k = t - n0 - n1; }
         else { kind = 3; k = t - n0 - n1 - n2; }
-        const int id = (int)a.work[kind][k];
-        const int x = id % a.g.n[0], y = (id / a.g.n[0]) % a.g.n[1], z = id / (a.g.n[0] * a.g.n[1]);
-        SweepCell<D> cell(a, x, y, z);
-        if ((kind & 1) == 0) cell.template loadw<T1, T2>();
-        else cell.template loadw<T2, T1>();
-        if (kind == 0) {
-            cell.template unaligned<T1, T2>(ev);
-        } else if (kind == 1) {
-            cell.template unaligned<T2, T1>(ev);
-        } else {
-            int ncol0 = a.cbo[id] & 1;
-            int bit = (kind == 2) ? (cell.template face_phase<T1, T2>(ncol0) << (1 + T2))
-                                  : (cell.template face_phase<T2, T1>(ncol0) << (1 + T1));
-            if (bit) {
-                uintptr_t addr = (uintptr_t)(a.cbo + id);
-                unsigned *w = (unsigned *)(addr & ~(uintptr_t)3);
-                atomicOr(w, (unsigned)bit << (8 * (addr & 3)));
-            }
-        }
+        fp64_item<D, false>(a, kind, k, ev);
     }
 #pragma unroll
     for (int k = 0; k < C_N; k++) {

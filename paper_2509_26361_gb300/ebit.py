@@ -101,6 +101,24 @@ def load(build_if_missing: bool = True):
     lib.ebit_set_mlp.argtypes = [P, P]
     lib.ebit_last_error.argtypes = [P]
     lib.ebit_last_error.restype = ctypes.c_char_p
+    lib.ebit_batch_create.argtypes = [I, ctypes.POINTER(_Desc), ctypes.POINTER(ctypes.c_void_p)]
+    lib.ebit_batch_destroy.argtypes = [P]
+    lib.ebit_batch_destroy.restype = None
+    lib.ebit_batch_size.argtypes = [P]
+    lib.ebit_batch_instance.argtypes = [P, I]
+    lib.ebit_batch_instance.restype = P
+    lib.ebit_batch_set_velocity.argtypes = [P, ctypes.POINTER(ctypes.c_void_p), ctypes.POINTER(ctypes.c_double)]
+    lib.ebit_batch_advect_sweep.argtypes = [P, I]
+    lib.ebit_batch_run.argtypes = [P, I, I, I]
+    lib.ebit_batch_graph_active.argtypes = [P]
+    lib.ebit_batch_graph_note.argtypes = [P]
+    lib.ebit_batch_graph_note.restype = ctypes.c_char_p
+    lib.ebit_batch_sync.argtypes = [P]
+    lib.ebit_batch_launch_shape.argtypes = [P, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]
+    lib.ebit_batch_set_launch_shape.argtypes = [P, I]
+    lib.ebit_batch_autotune.argtypes = [P, I, ctypes.POINTER(ctypes.c_double)]
+    lib.ebit_batch_last_error.argtypes = [P]
+    lib.ebit_batch_last_error.restype = ctypes.c_char_p
     _lib = lib
     return lib
 
@@ -365,6 +383,110 @@ class Mlp:
         return ebit_mlp_sync(self.h)
 
 
+# ----------------------------------------------------------------- batches
+def _bcheck(b, code):
+    if code < 0:
+        raise EbitError(code, load().ebit_batch_last_error(b).decode())
+    return code
+
+
+def ebit_batch_create(n3s, hs=None, stream=None):
+    lib = load()
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    sp = stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream)
+    n = len(n3s)
+    descs = (_Desc * n)()
+    for i, n3 in enumerate(n3s):
+        h = float(hs[i]) if hs is not None else 1.0 / n3[0]
+        descs[i] = _Desc(int(n3[0]), int(n3[1]), int(n3[2]), h, ctypes.c_void_p(sp), 0)
+    out = ctypes.c_void_p()
+    code = lib.ebit_batch_create(n, descs, ctypes.byref(out))
+    if code != EBIT_OK:
+        raise EbitError(code, "ebit_batch_create failed")
+    return out
+
+
+def ebit_batch_set_velocity(b, n3s, u_fields, dts):
+    """u_fields[i] = (u_x, u_y, u_z) device float64 tensors of instance i."""
+    n = len(n3s)
+    ptrs = (ctypes.c_void_p * (3 * n))()
+    for i in range(n):
+        N = n3s[i][0] * n3s[i][1] * n3s[i][2]
+        for d in range(3):
+            ptrs[3 * i + d] = _dev(u_fields[i][d], torch.float64, N, "u_face").value
+    dt = (ctypes.c_double * n)(*[float(v) for v in dts])
+    return _bcheck(b, load().ebit_batch_set_velocity(b, ptrs, dt))
+
+
+class Batch:
+    """Independent instances advanced by one persistent launch per split sweep.
+    ``instance(i)`` is a :class:`Grid` view of instance i (state access,
+    Front2VOF, curvature, counters)."""
+
+    def __init__(self, n3s, hs=None, device="cuda", stream=None):
+        self.n3s = [tuple(int(v) for v in n3) for n3 in n3s]
+        self.hs = [float(hs[i]) if hs is not None else 1.0 / n3[0] for i, n3 in enumerate(self.n3s)]
+        self.device = torch.device(device)
+        self.b = ebit_batch_create(self.n3s, self.hs, stream)
+        self._views = [Grid._view(load().ebit_batch_instance(self.b, i), self.n3s[i], self.hs[i], self.device)
+                       for i in range(len(self.n3s))]
+        self._u = None
+
+    def __len__(self):
+        return len(self.n3s)
+
+    def instance(self, i):
+        return self._views[i]
+
+    def set_velocity(self, u_fields, dts):
+        self._u = [tuple(u) for u in u_fields]  # keep the device fields alive
+        return ebit_batch_set_velocity(self.b, self.n3s, self._u, dts)
+
+    def sweep(self, d):
+        return _bcheck(self.b, load().ebit_batch_advect_sweep(self.b, int(d)))
+
+    def run(self, first_step, steps, graph=True):
+        return _bcheck(self.b, load().ebit_batch_run(self.b, int(first_step), int(steps), int(bool(graph))))
+
+    def graph_active(self):
+        """0 none, 1 stream capture, 2 graph built node by node."""
+        return int(load().ebit_batch_graph_active(self.b))
+
+    def graph_note(self):
+        return load().ebit_batch_graph_note(self.b).decode()
+
+    def sync(self):
+        return _bcheck(self.b, load().ebit_batch_sync(self.b))
+
+    def launch_shape(self):
+        c, m = ctypes.c_int(), ctypes.c_int()
+        _bcheck(self.b, load().ebit_batch_launch_shape(self.b, ctypes.byref(c), ctypes.byref(m)))
+        return c.value, m.value
+
+    def set_launch_shape(self, ctas_per_sm):
+        return _bcheck(self.b, load().ebit_batch_set_launch_shape(self.b, int(ctas_per_sm)))
+
+    def autotune(self, sweeps=6):
+        _, m = self.launch_shape()
+        ms = (ctypes.c_double * m)()
+        _bcheck(self.b, load().ebit_batch_autotune(self.b, int(sweeps), ms))
+        return [float(v) for v in ms]
+
+    def close(self):
+        if self.b is not None:
+            for v in self._views:
+                v.ctx = None
+            load().ebit_batch_destroy(self.b)
+            self.b = None
+
+    def __del__(self):  # pragma: no cover
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
 # ------------------------------------------------------------ convenience
 class Grid:
     """One EBIT context with its device buffers (torch tensors on ``device``).
@@ -380,10 +502,23 @@ class Grid:
         self.shape = (self.n3[2], self.n3[1], self.n3[0])
         self.ctx = ebit_create(nx, ny, nz, self.h, stream, EBIT_DESC_DENSE if dense else 0)
 
+    @classmethod
+    def _view(cls, ctx, n3, h, device):
+        """A Grid over a context owned elsewhere (a batch instance)."""
+        g = cls.__new__(cls)
+        g.n3 = tuple(int(v) for v in n3)
+        g.N = g.n3[0] * g.n3[1] * g.n3[2]
+        g.h = float(h)
+        g.device = torch.device(device)
+        g.shape = (g.n3[2], g.n3[1], g.n3[0])
+        g.ctx = ctypes.c_void_p(ctx)
+        g._owned = False
+        return g
+
     def close(self):
-        if self.ctx is not None:
+        if self.ctx is not None and getattr(self, "_owned", True):
             ebit_destroy(self.ctx)
-            self.ctx = None
+        self.ctx = None
 
     def __del__(self):  # pragma: no cover
         try:

@@ -1,0 +1,129 @@
+"""Batched persistent sweeps (one cooperative launch per split sweep for all
+instances, CUDA-graph replay of whole steps): every instance must end in the
+state a separate context reaches from the same inputs (colour bytes and
+offsets bit for bit, the same event counters), and a small instance must
+match the CPU FP64 oracle."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2509_26361_gb300 import ebit
+from paper_2509_26361_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+def dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def instances(seed, sizes):
+    """Each instance: its own seeded 12-mode Fourier field and 1-3 spheres."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for n in sizes:
+        k = int(rng.integers(1, 4)) if n >= 16 else 1
+        rmin = 2.5 / n
+        sp = W.random_spheres(rng, k, rmin, max(0.16, rmin + 0.05), n)
+        phi, faces = W.sphere_phi_nodes_faces((n, n, n), sp)
+        u = W.fourier_velocity((n, n, n), rng)
+        out.append((n, phi, faces, u))
+    return out
+
+
+def make_batch(insts, cfl=0.5):
+    b = ebit.Batch([(n, n, n) for n, *_ in insts])
+    uf = []
+    for i, (n, phi, faces, u) in enumerate(insts):
+        b.instance(i).init(dev(phi), dev(faces))
+        uf.append(tuple(dev(u[d]) for d in range(3)))
+    b.set_velocity(uf, [cfl / n for n, *_ in insts])
+    return b
+
+
+def reference_states(insts, steps, cfl=0.5):
+    out = []
+    for n, phi, faces, u in insts:
+        g = ebit.Grid(n, n, n)
+        g.init(dev(phi), dev(faces))
+        ud = [dev(u[d]) for d in range(3)]
+        for k in range(steps):
+            g.step(k, ud, cfl / n)
+        cb, s = g.get_state()
+        C = torch.zeros(g.shape, dtype=torch.float64, device="cuda")
+        g.front2vof(C)
+        out.append((cb.cpu(), s.cpu(), C.cpu(), g.counters()))
+        g.close()
+    return out
+
+
+@pytest.mark.parametrize("graph", [True, False])
+def test_batch_equals_separate_contexts(graph):
+    insts = instances(4, [16, 24, 32, 16, 40, 24, 8])
+    steps = 7
+    ref = reference_states(insts, steps)
+    b = make_batch(insts)
+    b.run(0, steps, graph=graph)
+    b.sync()
+    for i, (cb_r, s_r, C_r, cnt_r) in enumerate(ref):
+        g = b.instance(i)
+        cb, s = g.get_state()
+        assert torch.equal(cb.cpu(), cb_r), f"instance {i}: colours differ"
+        assert torch.equal(s.cpu(), s_r), f"instance {i}: offsets differ"
+        C = torch.zeros(g.shape, dtype=torch.float64, device="cuda")
+        g.front2vof(C)
+        assert torch.equal(C.cpu(), C_r), f"instance {i}: volume fractions differ"
+        assert g.counters() == cnt_r, (i, g.counters(), cnt_r)
+    if graph:
+        assert b.graph_active() in (1, 2), b.graph_note()
+    b.close()
+
+
+def test_batch_instance_matches_oracle():
+    insts = instances(9, [16, 24])
+    b = make_batch(insts)
+    osts = [oracle.init(phi, faces) for _, phi, faces, _ in insts]
+    for k in range(3):
+        order = (0, 1, 2) if k % 2 == 0 else (2, 1, 0)
+        for d in order:
+            b.sweep(d)
+            osts = [oracle.sweep(o, d, u[d], 0.5)[0] for o, (_, _, _, u) in zip(osts, insts)]
+    b.sync()
+    for i, o in enumerate(osts):
+        cb, s = b.instance(i).get_state()
+        cb, s = cb.cpu().numpy(), s.cpu().numpy()
+        assert np.array_equal(cb, o.cb)
+        c = cb & 1
+        m = np.stack([c != np.roll(c, -1, axis=2), c != np.roll(c, -1, axis=1), c != np.roll(c, -1, axis=0)])
+        assert np.max(np.abs(s[m] - o.s[m])) <= 1e-12
+    b.close()
+
+
+def test_autotune_keeps_the_state_and_the_result():
+    insts = instances(5, [24, 32, 16])
+    ref = reference_states(insts, 4)
+    b = make_batch(insts)
+    before = [b.instance(i).get_state() for i in range(len(insts))]
+    ms = b.autotune(sweeps=3)
+    c, m = b.launch_shape()
+    assert 1 <= c <= m and len(ms) == m and all(v > 0 for v in ms)
+    for i in range(len(insts)):
+        cb, s = b.instance(i).get_state()
+        assert torch.equal(cb, before[i][0]) and torch.equal(s, before[i][1])
+    b.run(0, 4, graph=True)
+    b.sync()
+    for i, (cb_r, s_r, _, cnt_r) in enumerate(ref):
+        cb, s = b.instance(i).get_state()
+        assert torch.equal(cb.cpu(), cb_r) and torch.equal(s.cpu(), s_r)
+        assert b.instance(i).counters() == cnt_r
+    b.close()
+
+
+def test_instance_context_refuses_its_own_sweep():
+    insts = instances(6, [16])
+    b = make_batch(insts)
+    g = b.instance(0)
+    with pytest.raises(ebit.EbitError):
+        g.sweep(0, dev(insts[0][3][0]), 0.5 / 16)
+    b.close()
