@@ -202,19 +202,18 @@ def fourier_velocity(n3, rng, modes=12, kmax=3):
     amps = rng.normal(size=(modes, 3))
     phases = rng.uniform(0, 2 * np.pi, size=modes)
     x, y, z = _grid(n3)
-    X = x[None, None, :]
-    Y = y[None, :, None]
-    Z = z[:, None, None]
     hs = (1.0 / nx, 1.0 / ny, 1.0 / nz)
 
     def potential(comp, off):
-        # A_comp sampled at node + off (in cells)
-        v = np.zeros((nz, ny, nx))
+        # A_comp sampled at node + off (in cells): each mode's sine is the
+        # imaginary part of a product of three 1-D complex exponentials
+        v = np.zeros((nz, ny, nx), dtype=np.complex128)
         for m in range(modes):
-            arg = 2 * np.pi * (sel[m, 0] * (X + off[0] * hs[0]) + sel[m, 1] * (Y + off[1] * hs[1])
-                               + sel[m, 2] * (Z + off[2] * hs[2])) + phases[m]
-            v = v + amps[m, comp] * np.sin(arg)
-        return v
+            ex = np.exp(2j * np.pi * sel[m, 0] * (x + off[0] * hs[0]))
+            ey = np.exp(2j * np.pi * sel[m, 1] * (y + off[1] * hs[1]))
+            ez = np.exp(2j * np.pi * sel[m, 2] * (z + off[2] * hs[2])) * (amps[m, comp] * np.exp(1j * phases[m]))
+            v += (ez[:, None, None] * ey[None, :, None]) * ex[None, None, :]
+        return v.imag
 
     Ax = potential(0, (0.5, 0.0, 0.0))  # x-edge midpoints
     Ay = potential(1, (0.0, 0.5, 0.0))
@@ -349,3 +348,73 @@ def fourier_spheres(n=128, seed=2, count=8, rmin=0.05, rmax=0.12, cfl=0.5, perio
     if steps is None:
         steps = int(round(period / (cfl / n)))
     return Workload("fourier_spheres", n3, phi, faces, u, cfl, steps, period=period, shapes=sp)
+
+
+def batched_instances(seed=4, count=64, sizes=(32, 48, 64, 96, 128), cfl=0.5, rmin=0.07, rmax=0.15):
+    """Independent periodic instances for the batched sweeps: seeded grid sizes
+    from ``sizes``, each with its own seeded 12-mode Fourier field and 1-4
+    non-overlapping spheres (radii U[rmin, rmax]), dt = cfl * h of the instance.
+    Returns a list of (n, phi, phi_faces, u, dt)."""
+    rng = np.random.default_rng(seed)
+    ns = rng.choice(np.asarray(sizes), size=count)
+    out = []
+    for n in ns:
+        n = int(n)
+        k = int(rng.integers(1, 5))
+        sp = random_spheres(rng, k, rmin, rmax, n)
+        phi, faces = sphere_phi_nodes_faces((n, n, n), sp)
+        u = fourier_velocity((n, n, n), rng)
+        out.append((n, phi, faces, u, cfl / n))
+    return out
+
+
+def cellular_velocity(n3, centre, amp=0.5):
+    """Converging cellular mode about ``centre`` (x', y' = x - c_x, y - c_y):
+    u_x = -amp sin(2 pi x') cos(2 pi y'), u_y = amp cos(2 pi x') sin(2 pi y'),
+    u_z = 0, as the discrete curl of the stream function
+    psi = -(amp / 2 pi) sin(2 pi x') sin(2 pi y') sampled on the z-edges, so the
+    discrete divergence vanishes.  Shape (3, nz, ny, nx)."""
+    nx, ny, nz = n3
+    x, y, _ = _grid(n3)
+    psi = -(amp / (2 * np.pi)) * np.sin(2 * np.pi * (x[None, :] - centre[0])) * \
+        np.sin(2 * np.pi * (y[:, None] - centre[1]))
+    Az = np.broadcast_to(psi[None, :, :], (nz, ny, nx))
+    hx, hy = 1.0 / nx, 1.0 / ny
+    ux = (np.roll(Az, -1, axis=1) - Az) / hy
+    uy = -(np.roll(Az, -1, axis=2) - Az) / hx
+    return np.stack([ux, uy, np.zeros((nz, ny, nx))])
+
+
+def _extent(e, axis):
+    """Half-width of an ellipsoid along a coordinate axis (support function)."""
+    r = np.asarray(e.rot)[axis, :]
+    return float(np.sqrt(np.sum((np.asarray(e.axes) * r) ** 2)))
+
+
+def merging_drops(n=512, seed=5, amin_cells=40.0, amax_cells=80.0, gap_cells=8.0, fourier_scale=0.25, amp=0.5,
+                  cfl=0.5, steps=200):
+    """Two seeded ellipsoidal drops (semi-axes U[amin, amax] cells, random
+    rotations) on the x axis through the domain centre, their supporting planes
+    ``gap_cells`` apart, in a seeded 12-mode Fourier field (scaled to max
+    |u| = fourier_scale) plus a converging cellular mode of amplitude ``amp``
+    centred between them, dt = cfl * h.  Exact edge crossings of the quadratic
+    level sets are included.  The drops approach and merge."""
+    from .curvature_data import ellipsoid_fields  # local: that module builds on this one
+
+    rng = np.random.default_rng(seed)
+    h = 1.0 / n
+    e1 = Ellipsoid((0.0, 0.5, 0.5), tuple(rng.uniform(amin_cells, amax_cells, 3) * h), random_rotation(rng))
+    e2 = Ellipsoid((0.0, 0.5, 0.5), tuple(rng.uniform(amin_cells, amax_cells, 3) * h), random_rotation(rng))
+    w1, w2 = _extent(e1, 0), _extent(e2, 0)
+    d = w1 + w2 + gap_cells * h
+    mid = 0.5 + float(rng.uniform(-0.5, 0.5)) * h  # off the grid lines
+    e1 = Ellipsoid((mid - d / 2 - (w1 - w2) / 2, 0.5, 0.5), e1.axes, e1.rot)
+    e2 = Ellipsoid((mid + d / 2 - (w1 - w2) / 2, 0.5, 0.5), e2.axes, e2.rot)
+    n3 = (n, n, n)
+    f = ellipsoid_fields(n3, [e1, e2])
+    fin = lambda a: np.where(np.isfinite(a), a, np.sign(a))
+    # the gap centre: right end of drop 1
+    cx = e1.centre[0] + w1 + 0.5 * gap_cells * h
+    u = fourier_scale * fourier_velocity(n3, rng) + cellular_velocity(n3, (cx, 0.5), amp)
+    return Workload("merging_drops", n3, fin(f.phi), fin(f.phi_faces), u, cfl, steps, s_exact=f.s_exact,
+                    shapes=[e1, e2])
