@@ -59,7 +59,7 @@ def test_converging_drops_merge():
     g.front2vof(C, ebit.EBIT_FULL)
     v0 = float(C.sum())
     merged_at = None
-    for n in range(80):
+    for n in range(200):
         g.step(n, ud, w.lam(n) * g.h)
         g.front2vof(C)
         g.curvature(C, kh, st, mode=ebit.EBIT_CURV_MLP_HF)
