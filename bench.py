@@ -241,34 +241,44 @@ def run_e2e(args, g, w, dev, C, kh, st):
             "h2d_bytes_per_step": 3 * nc * 8, "d2h_bytes_per_step": 2 * nc * 8}
 
 
+# DRAM bytes (read + write) per launch of the split-sweep kernels, one ncu
+# capture each (--set full, cold caches) of the same 128^3 workload; see
+# profiles/kernels_fourier_spheres_128.md.  None once the kernels change.
+NCU_TRAFFIC = {"advect": 3467776.0, "sweep": 2865920.0, "fp64": 3277056.0}
+# per band cell of one split sweep and of Front2VOF (the scope table's figures)
+SWEEP_BYTES_PER_CELL = 62.75
+F2V_BYTES_PER_CELL = 36.4
+
+
 def roofline_block(res):
-    """Dominant kernel by device time; achieved = algorithmic bytes per launch /
-    average launch time (CUDA events around every launch, on its stream)."""
+    """The dominant stage is the split sweep (its band, advect, integer-pass and
+    FP64-list launches; the scope table defines its algorithmic bytes per band
+    cell).  achieved = 62.75 B x band cells per sweep / device time per sweep,
+    summed from CUDA events around each of its launches on the context's
+    stream.  The marker-level minimum (colour bytes of the band, offsets and
+    one velocity sample per marker) is given beside it."""
     hbm, src = peaks()
     prof = res["prof"]
-    kinds = {k: v for k, v in prof.items() if k in ("sweep", "f2v", "hf", "band")}
-    dom = max(kinds, key=lambda k: kinds[k][0])
-    ms, launches = kinds[dom]
-    avg_s = ms * 1e-3 / launches
     cnt = res["cnt"]
     nsweeps = prof["sweep"][1]
+    stage_ms = sum(prof[k][0] for k in ("band", "advect", "sweep", "fp64") if k in prof)
+    per_sweep_s = stage_ms * 1e-3 / nsweeps
     band_cells = cnt["tiles"] / nsweeps * 512.0
     markers = cnt["markers"] / nsweeps
-    if dom == "sweep":
-        # per band cell: colour byte read + written; per marker: offset read,
-        # offset written, one 8-byte velocity sample (see DESIGN.md)
-        alg = 2.0 * band_cells + 24.0 * markers
-    elif dom == "f2v":
-        # per band cell: 8 corner colours (1 B amortised) + C written (8 B); per marker 8 B
-        alg = 9.0 * band_cells + 8.0 * markers
-    elif dom == "hf":
-        alg = 17.0 * band_cells
-    else:
-        alg = 2.0 * res["nc"] / 512.0
-    achieved = alg / avg_s / 1e9
-    return {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": hbm, "unit": "GB/s",
-            "frac": achieved / hbm, "traffic": None, "peak_source": src,
-            "alg_bytes_per_launch": alg, "avg_launch_us": avg_s * 1e6,
+    alg = SWEEP_BYTES_PER_CELL * band_cells
+    alg_min = 2.0 * band_cells + 24.0 * markers
+    achieved = alg / per_sweep_s / 1e9
+    traffic = sum(NCU_TRAFFIC.values()) if NCU_TRAFFIC else None
+    stages = {"split_sweep": stage_ms,
+              "front2vof": prof.get("f2v", (0.0, 0))[0],
+              "curvature": prof.get("hf", (0.0, 0))[0] + prof.get("scan", (0.0, 0))[0]}
+    return {"bound": "hbm", "kernel": "split sweep (band + advect + integer pass + FP64 lists)",
+            "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm, "traffic": traffic,
+            "peak_source": src, "alg_bytes_per_launch": alg, "alg_bytes_rule": "62.75 B per band cell per sweep",
+            "band_cells_per_sweep": band_cells, "markers_per_sweep": markers,
+            "min_bytes_per_sweep": alg_min, "min_frac": alg_min / per_sweep_s / 1e9 / hbm,
+            "avg_sweep_us": per_sweep_s * 1e6,
+            "stage_ms": {k: round(v, 4) for k, v in stages.items()},
             "kernel_ms": {k: round(v[0], 4) for k, v in prof.items()},
             "kernel_launches": {k: v[1] for k, v in prof.items()}}
 
@@ -397,9 +407,8 @@ def main():
     total_s = res["total_ms"] * 1e-3
     value = res["nc"] * args.steps * world / total_s
     prof = res["prof"]
-    # kernels per profiled scope: the Front2VOF scope holds the band and the list kernel
-    per_scope = {"f2v": 2}
-    launches = sum(v[1] * per_scope.get(k, 1) for k, v in prof.items())
+    # every profiled scope brackets exactly one kernel launch
+    launches = sum(v[1] for v in prof.values())
     line = {"metric": METRIC, "value": value, "unit": "cell-steps/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": res["total_ms"] / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",

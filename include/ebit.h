@@ -186,8 +186,8 @@ int ebit_band_tiles(ebit_ctx *ctx);
  * elapsed device time per kind.  Kinds (index into the arrays below): */
 enum {
     EBIT_PROF_SWEEP = 0, /* split-sweep reconstruction kernels */
-    EBIT_PROF_BAND = 1,  /* band/tile-list kernels and their memsets */
-    EBIT_PROF_F2V = 2,   /* Front2VOF kernel */
+    EBIT_PROF_BAND = 1,  /* band tile list of a sweep and its memset */
+    EBIT_PROF_F2V = 2,   /* Front2VOF: list of the swept tiles (incremental calls), band and cut-cell kernels */
     EBIT_PROF_HF = 3,    /* height-function kernel (interface-cell list pass) */
     EBIT_PROF_MLP = 4,   /* learned-curvature kernels (with the height-function fallback pass) */
     EBIT_PROF_ADVECT = 5, /* marker advection (velocity interpolation) kernels */

@@ -396,7 +396,7 @@ int ebit_front2vof(ebit_ctx *ctx, double *C, int flags) {
         list = ctx->all_list;
         count = ctx->all_count;
     } else {
-        ProfScope ps(ctx, EBIT_PROF_BAND);
+        ProfScope ps(ctx, EBIT_PROF_F2V);
         CU(cudaMemsetAsync(ctx->work_count, 0, sizeof(int), ctx->stream));
         take_flagged_kernel<<<blocks_for(ctx->g.ntiles, 256, ctx->sms), 256, 0, ctx->stream>>>(
             ctx->g, ctx->tile_dirty, ctx->work_list, ctx->work_count);
@@ -421,7 +421,10 @@ int ebit_front2vof(ebit_ctx *ctx, double *C, int flags) {
         ProfScope ps(ctx, EBIT_PROF_F2V);
         f2v_band_kernel<<<ctx->grid_f2v, 256, 0, ctx->stream>>>(a);
         r = launch_check(ctx, "f2v_band_kernel");
-        if (r) return r;
+    }
+    if (r) return r;
+    {
+        ProfScope ps(ctx, EBIT_PROF_F2V);
         f2v_list_kernel<<<ctx->grid_f2vl, 128, 0, ctx->stream>>>(a);
         r = launch_check(ctx, "f2v_list_kernel");
     }
@@ -480,7 +483,6 @@ int ebit_curvature(ebit_ctx *ctx, const double *C, double *kappa_h, uint8_t *sta
     if (mode != EBIT_CURV_HF) {
         // learned curvature on this call's interface cells (height functions
         // where it falls back, mode MLP_HF)
-        ProfScope pm(ctx, EBIT_PROF_MLP);
         MlpArgs m{};
         m.g = ctx->g;
         m.C = C;
@@ -495,8 +497,12 @@ int ebit_curvature(ebit_ctx *ctx, const double *C, double *kappa_h, uint8_t *sta
         m.fb = ctx->scan;  // free again: the listing pass above has consumed it
         m.nfb = ctx->nscan;
         CU(cudaMemsetAsync(ctx->nscan, 0, sizeof(int), ctx->stream));
-        mlp_fwd_kernel<true, true><<<2 * ctx->sms, 128, FWD_SMEM, ctx->stream>>>(m);
-        int r = launch_check(ctx, "mlp_fwd_kernel");
+        int r;
+        {
+            ProfScope pm(ctx, EBIT_PROF_MLP);
+            mlp_fwd_kernel<true, true><<<2 * ctx->sms, 128, FWD_SMEM, ctx->stream>>>(m);
+            r = launch_check(ctx, "mlp_fwd_kernel");
+        }
         if (r) return r;
         if (mode == EBIT_CURV_MLP_HF) {
             // height functions on the cells the learned value left to them
@@ -507,6 +513,7 @@ int ebit_curvature(ebit_ctx *ctx, const double *C, double *kappa_h, uint8_t *sta
             f.ncand = ctx->nscan;
             f.iface = nullptr;
             f.niface = nullptr;
+            ProfScope pf(ctx, EBIT_PROF_MLP);
             hf_list_kernel<true><<<ctx->grid_hfl, 128, 0, ctx->stream>>>(f);
             r = launch_check(ctx, "hf_list_kernel");
             if (r) return r;
