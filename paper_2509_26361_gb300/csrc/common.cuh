@@ -16,6 +16,32 @@ constexpr double ONE_MINUS = 0.99999999999999988898;  // 1 - 2^-53, largest offs
 constexpr int TILE = 8;                               // tile edge (cells)
 constexpr int TILE_CELLS = TILE * TILE * TILE;
 
+// Tile proximity mask: bit near_bit(dx, dy, dz) is set when a marker owned by a
+// node of the tile lies within NEAR cells of the neighbour tile in direction
+// (dx, dy, dz) (the owner node in the NEAR layers next to that neighbour, along
+// every axis with a non-zero step); bit near_bit(0, 0, 0) whenever the tile
+// owns a marker.  A sweep changes a node's byte or edges only if a marker is
+// owned by a node within one cell behind or two cells ahead of it (the window of
+// the band pass), and Front2VOF reads a cell's corners one cell ahead, so a
+// tile next to a marker tile needs the sweep (and Front2VOF) only where that
+// neighbour owns a marker within three cells of it.
+constexpr int NEAR = 3;
+__host__ __device__ inline int near_bit(int dx, int dy, int dz) { return 9 * (dz + 1) + 3 * (dy + 1) + (dx + 1); }
+__host__ __device__ inline unsigned near_bits(int lx, int ly, int lz) {
+    unsigned m = 0;
+    for (int dz = -1; dz <= 1; dz++) {
+        if ((dz < 0 && lz >= NEAR) || (dz > 0 && lz < TILE - NEAR)) continue;
+        for (int dy = -1; dy <= 1; dy++) {
+            if ((dy < 0 && ly >= NEAR) || (dy > 0 && ly < TILE - NEAR)) continue;
+            for (int dx = -1; dx <= 1; dx++) {
+                if ((dx < 0 && lx >= NEAR) || (dx > 0 && lx < TILE - NEAR)) continue;
+                m |= 1u << near_bit(dx, dy, dz);
+            }
+        }
+    }
+    return m;
+}
+
 enum Counter { C_MARKERS = 0, C_ANNIHILATE = 1, C_MULTI = 2, C_INCONSISTENT = 3, C_CFL = 4, C_N = 5 };
 // extra device counters after the event counters
 enum { C_F2V_BAD = C_N, C_TILES = C_N + 1, C_TOTAL = C_N + 2 };
@@ -55,6 +81,19 @@ __device__ __forceinline__ void warp_count(unsigned long long *ctr, unsigned v) 
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(m, v, o);
     int leader = __ffs(m) - 1;
     if ((int)(threadIdx.x & 31) == leader && v) atomicAdd(ctr, (unsigned long long)v);
+}
+
+// Is tile (tx, ty, tz) in the band: does it own a marker, or does a neighbour
+// own one within NEAR cells of it (that neighbour's proximity bit toward it)?
+__device__ __forceinline__ bool in_band(const Grid &g, const uint32_t *__restrict__ mask, int tx, int ty, int tz) {
+    bool on = false;
+    for (int dz = -1; dz <= 1 && !on; dz++)
+        for (int dy = -1; dy <= 1 && !on; dy++)
+            for (int dx = -1; dx <= 1 && !on; dx++) {
+                const int nx = wrapc(tx + dx, g.td[0]), ny = wrapc(ty + dy, g.td[1]), nz = wrapc(tz + dz, g.td[2]);
+                on = (mask[(nz * g.td[1] + ny) * g.td[0] + nx] >> near_bit(-dx, -dy, -dz)) & 1u;
+            }
+    return on;
 }
 
 }  // namespace ebit

@@ -32,7 +32,8 @@ struct ebit_ctx {
     uint8_t *cb[2];
     double *s[2][3];
     int cur;
-    uint8_t *tile_marker, *tile_dirty, *tile_cchg;
+    uint32_t *tile_marker;    // per tile: proximity mask of its markers (see near_bits)
+    uint8_t *tile_dirty, *tile_cchg;
     int *band_list, *band_count;
     int *work_list, *work_count;
     int *all_list, *all_count;
@@ -76,7 +77,8 @@ struct ebit_state_arrays {
     int8_t *bin[3];
     unsigned *work[4];
     int *wcount;
-    uint8_t *tile_marker, *tile_dirty;
+    uint32_t *tile_marker;
+    uint8_t *tile_dirty;
     unsigned long long *ctr;
 };
 

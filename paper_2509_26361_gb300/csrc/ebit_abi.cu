@@ -47,7 +47,7 @@ int launch_check(ebit_ctx *ctx, const char *what) {
 
 int mark_all(ebit_ctx *ctx) {
     ctx->sweeps_since_f2v = 1;
-    CU(cudaMemsetAsync(ctx->tile_marker, 1, ctx->g.ntiles, ctx->stream));
+    CU(cudaMemsetAsync(ctx->tile_marker, 0xFF, ctx->g.ntiles * sizeof(uint32_t), ctx->stream));
     CU(cudaMemsetAsync(ctx->tile_dirty, 1, ctx->g.ntiles, ctx->stream));
     ctx->last_C = nullptr;
     ctx->last_kh = nullptr;
@@ -152,7 +152,8 @@ static int create_ctx(const ebit_desc *desc, const ebit_state_arrays *st, ebit_c
     ctx->cur_if = 0;
     ctx->sweeps_since_f2v = 0;
     ctx->mlp = nullptr;
-    ctx->tile_marker = ctx->tile_dirty = ctx->tile_cchg = nullptr;
+    ctx->tile_marker = nullptr;
+    ctx->tile_dirty = ctx->tile_cchg = nullptr;
     ctx->band_list = ctx->band_count = ctx->work_list = ctx->work_count = ctx->all_list = ctx->all_count = nullptr;
     ctx->ctr = nullptr;
     ctx->g.n[0] = desc->nx;
@@ -195,7 +196,7 @@ static int create_ctx(const ebit_desc *desc, const ebit_state_arrays *st, ebit_c
         for (int a = 0; a < 3 && ok; a++)
             ok = ok && alloc((void **)&ctx->adv[a], ctx->N * sizeof(double)) && alloc((void **)&ctx->bin[a], ctx->N);
         for (int k = 0; k < 4 && ok; k++) ok = ok && alloc((void **)&ctx->work[k], ctx->N * sizeof(unsigned));
-        ok = ok && alloc((void **)&ctx->wcount, 4 * sizeof(int)) && alloc((void **)&ctx->tile_marker, nt) &&
+        ok = ok && alloc((void **)&ctx->wcount, 4 * sizeof(int)) && alloc((void **)&ctx->tile_marker, nt * sizeof(uint32_t)) &&
              alloc((void **)&ctx->tile_dirty, nt) && alloc((void **)&ctx->ctr, C_TOTAL * sizeof(unsigned long long));
     }
     ok = ok && alloc((void **)&ctx->cut, ctx->N * sizeof(unsigned)) && alloc((void **)&ctx->scan, ctx->N * sizeof(unsigned)) &&

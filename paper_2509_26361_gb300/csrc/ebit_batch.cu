@@ -103,7 +103,8 @@ __global__ void __launch_bounds__(BATCH_THREADS) batch_sweep_kernel(BatchParams 
     __shared__ uint16_t s_mk[3 * TILE_CELLS];
     __shared__ uint8_t s_c[9 * 9 * 9];
     __shared__ uint8_t s_b[RA * R1 * R2];
-    __shared__ int s_n, s_flag, s_ok;
+    __shared__ int s_n, s_ok;
+    __shared__ unsigned s_flag;
     __shared__ int s_pre[4 * BATCH_MAX + 1];
     __shared__ int s_wsum[BATCH_THREADS / 32];
     if (*(volatile int *)p.err) return;
@@ -121,16 +122,9 @@ __global__ void __launch_bounds__(BATCH_THREADS) batch_sweep_kernel(BatchParams 
             if (gt < p.total_tiles) {
                 i = find_inst(p.toff, p.n, gt);
                 t = gt - __ldg(p.toff + i);
-                const Grid &g = p.inst[i].a.g;
-                const uint8_t *flag = p.inst[i].a.tile_marker;
+                const Grid g = p.inst[i].a.g;
                 const int tx = t % g.td[0], ty = (t / g.td[0]) % g.td[1], tz = t / (g.td[0] * g.td[1]);
-                for (int dz = -1; dz <= 1 && !on; dz++)
-                    for (int dy = -1; dy <= 1 && !on; dy++)
-                        for (int dx = -1; dx <= 1 && !on; dx++) {
-                            const int nx = wrapc(tx + dx, g.td[0]), ny = wrapc(ty + dy, g.td[1]);
-                            const int nz = wrapc(tz + dz, g.td[2]);
-                            on = flag[(nz * g.td[1] + ny) * g.td[0] + nx] != 0;
-                        }
+                on = in_band(g, p.inst[i].a.tile_marker, tx, ty, tz);
             }
             const int slot = warp_append(p.nband, on);
             if (slot >= 0) p.band[slot] = (i << 20) | t;
@@ -235,7 +229,8 @@ struct ebit_batch {
     int8_t *bin[3] = {nullptr, nullptr, nullptr};
     unsigned *work[4] = {nullptr, nullptr, nullptr, nullptr};
     int *wcount = nullptr;
-    uint8_t *tile_marker = nullptr, *tile_dirty = nullptr;
+    uint32_t *tile_marker = nullptr;
+    uint8_t *tile_dirty = nullptr;
     unsigned long long *ctr = nullptr;
     // launch data
     BatchInst *table[2] = {nullptr, nullptr};
@@ -439,7 +434,7 @@ int ebit_batch_create(int n, const ebit_desc *descs, ebit_batch **out) {
     for (int a = 0; a < 3 && ok; a++)
         ok = ok && alloc((void **)&b->adv[a], cells * sizeof(double)) && alloc((void **)&b->bin[a], cells);
     for (int k = 0; k < 4 && ok; k++) ok = ok && alloc((void **)&b->work[k], cells * sizeof(unsigned));
-    ok = ok && alloc((void **)&b->wcount, 4 * n * sizeof(int)) && alloc((void **)&b->tile_marker, tiles) &&
+    ok = ok && alloc((void **)&b->wcount, 4 * n * sizeof(int)) && alloc((void **)&b->tile_marker, tiles * sizeof(uint32_t)) &&
          alloc((void **)&b->tile_dirty, tiles) && alloc((void **)&b->ctr, (size_t)n * C_TOTAL * 8) &&
          alloc((void **)&b->table[0], n * sizeof(BatchInst)) && alloc((void **)&b->table[1], n * sizeof(BatchInst)) &&
          alloc((void **)&b->d_toff, (n + 1) * sizeof(int)) && alloc((void **)&b->lam, n * sizeof(double)) &&
@@ -713,12 +708,13 @@ int ebit_batch_autotune(ebit_batch *b, int sweeps, double *ms_out) {
     // trial sweeps run on a copy of the state, which is put back afterwards
     const long long cells = b->cells;
     const int par0 = b->parity;
-    uint8_t *cb_save = nullptr, *tm_save = nullptr, *td_save = nullptr;
+    uint8_t *cb_save = nullptr, *td_save = nullptr;
+    uint32_t *tm_save = nullptr;
     double *s_save = nullptr;
     unsigned long long *ctr_save = nullptr;
     bool ok = cudaMalloc((void **)&cb_save, cells) == cudaSuccess &&
               cudaMalloc((void **)&s_save, 3 * cells * sizeof(double)) == cudaSuccess &&
-              cudaMalloc((void **)&tm_save, b->tiles) == cudaSuccess &&
+              cudaMalloc((void **)&tm_save, b->tiles * sizeof(uint32_t)) == cudaSuccess &&
               cudaMalloc((void **)&td_save, b->tiles) == cudaSuccess &&
               cudaMalloc((void **)&ctr_save, (size_t)b->n * C_TOTAL * 8) == cudaSuccess;
     auto release = [&]() {
@@ -741,7 +737,7 @@ int ebit_batch_autotune(ebit_batch *b, int sweeps, double *ms_out) {
         if (save) {
             cp(cb_save, b->cb[par0], cells);
             for (int a = 0; a < 3; a++) cp(s_save + a * cells, b->s[par0][a], cells * sizeof(double));
-            cp(tm_save, b->tile_marker, b->tiles);
+            cp(tm_save, b->tile_marker, b->tiles * sizeof(uint32_t));
             cp(td_save, b->tile_dirty, b->tiles);
             cp(ctr_save, b->ctr, (size_t)b->n * C_TOTAL * 8);
         } else {
@@ -749,7 +745,7 @@ int ebit_batch_autotune(ebit_batch *b, int sweeps, double *ms_out) {
                 cp(b->cb[q], cb_save, cells);
                 for (int a = 0; a < 3; a++) cp(b->s[q][a], s_save + a * cells, cells * sizeof(double));
             }
-            cp(b->tile_marker, tm_save, b->tiles);
+            cp(b->tile_marker, tm_save, b->tiles * sizeof(uint32_t));
             cp(b->tile_dirty, td_save, b->tiles);
             cp(b->ctr, ctr_save, (size_t)b->n * C_TOTAL * 8);
         }

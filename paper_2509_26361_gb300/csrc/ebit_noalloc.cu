@@ -43,8 +43,8 @@ constexpr long long OFF_CBO = align256(OFF_WORK + 4 * NA_MAX_CELLS * 4);
 constexpr long long OFF_LIST = align256(OFF_CBO + NA_MAX_CELLS + 8);
 constexpr long long OFF_INTS = align256(OFF_LIST + NA_MAX_TILES * 4);  // all_count, wcount[4]
 constexpr long long OFF_CTR = align256(OFF_INTS + 8 * 4);
-constexpr long long OFF_TILES = align256(OFF_CTR + C_TOTAL * 8);       // tile_marker, tile_dirty
-constexpr long long NA_BYTES = align256(OFF_TILES + 2 * NA_MAX_TILES);
+constexpr long long OFF_TILES = align256(OFF_CTR + C_TOTAL * 8);       // tile_marker (u32), tile_dirty
+constexpr long long NA_BYTES = align256(OFF_TILES + 5 * NA_MAX_TILES);
 
 static __device__ __align__(256) unsigned char g_sweep_scratch[NA_BYTES];
 
@@ -142,8 +142,8 @@ extern "C" int ebit_advect_sweep_noalloc(int nx, int ny, int nz, double h, int d
     a.count = ints;
     a.wcount = ints + 1;
     a.ctr = ctr;
-    a.tile_marker = base + OFF_TILES;
-    a.tile_dirty = base + OFF_TILES + NA_MAX_TILES;
+    a.tile_marker = reinterpret_cast<uint32_t *>(base + OFF_TILES);
+    a.tile_dirty = base + OFF_TILES + 4 * NA_MAX_TILES;
 
     int dev = 0, sms = 1;
     cudaGetDevice(&dev);

@@ -75,18 +75,12 @@ __global__ void canonical_s_kernel(Grid g, const uint8_t *__restrict__ cb, const
     }
 }
 
-// Band: tiles whose 3x3x3 tile neighbourhood holds a flagged tile.  The list
-// order depends on scheduling; every consumer is order-independent.
-__global__ void band_kernel(Grid g, const uint8_t *__restrict__ flag, int *__restrict__ list, int *__restrict__ count) {
+// Band: the tiles in_band selects.  The list order depends on scheduling;
+// every consumer is order-independent.
+__global__ void band_kernel(Grid g, const uint32_t *__restrict__ flag, int *__restrict__ list, int *__restrict__ count) {
     for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < g.ntiles; t += gridDim.x * blockDim.x) {
         int tx = t % g.td[0], ty = (t / g.td[0]) % g.td[1], tz = t / (g.td[0] * g.td[1]);
-        bool on = false;
-        for (int dz = -1; dz <= 1 && !on; dz++)
-            for (int dy = -1; dy <= 1 && !on; dy++)
-                for (int dx = -1; dx <= 1 && !on; dx++) {
-                    int nx = wrapc(tx + dx, g.td[0]), ny = wrapc(ty + dy, g.td[1]), nz = wrapc(tz + dz, g.td[2]);
-                    on = flag[(nz * g.td[1] + ny) * g.td[0] + nx] != 0;
-                }
+        const bool on = in_band(g, flag, tx, ty, tz);
         if (on) {
             int slot = atomicAdd(count, 1);
             list[slot] = t;

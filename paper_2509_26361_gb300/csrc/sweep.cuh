@@ -54,7 +54,7 @@ struct SweepArgs {
     unsigned *__restrict__ work[4];  // FP64 work lists: unaligned fam.1, fam.2, saddle fam.1, fam.2
     int *__restrict__ wcount;        // [4] list lengths (device)
     unsigned long long *ctr;         // event counters
-    uint8_t *tile_marker;            // per tile: a marker in the input or the output
+    uint32_t *tile_marker;           // per tile: proximity mask of its markers in the input or the output
     uint8_t *tile_dirty;             // per tile: processed since the last Front2VOF
 };
 
@@ -483,7 +483,7 @@ constexpr int RA = 11, R1 = 9, R2 = 9;
 
 // One band tile, all threads of the block; s_b/s_flag are its shared staging.
 template <int D, bool F>
-__device__ __forceinline__ void sweep_tile(const SweepArgs &a, int tile, uint8_t *s_b, int *s_flag) {
+__device__ __forceinline__ void sweep_tile(const SweepArgs &a, int tile, uint8_t *s_b, unsigned *s_flag) {
     constexpr int A = D, T1 = (D + 1) % 3, T2 = (D + 2) % 3;
     {
         int o[3];
@@ -499,7 +499,7 @@ __device__ __forceinline__ void sweep_tile(const SweepArgs &a, int tile, uint8_t
         }
         __syncthreads();
         unsigned ev[C_N] = {0, 0, 0, 0, 0};
-        bool mk = false;
+        unsigned mk = 0;  // proximity mask of the markers of this thread's cells
         for (int c = threadIdx.x; c < TILE_CELLS; c += blockDim.x) {
             int x = o[0] + (c & 7), y = o[1] + ((c >> 3) & 7), z = o[2] + (c >> 6);
             bool valid = x < a.g.n[0] && y < a.g.n[1] && z < a.g.n[2];
@@ -626,7 +626,7 @@ __device__ __forceinline__ void sweep_tile(const SweepArgs &a, int tile, uint8_t
                     int fa = saddle4(n0, nc[0][1][0], nc[0][0][1], nc[0][1][1]) ? ((myb >> (1 + A)) & 1) : n0;
                     byte |= fa << (1 + A);
                     a.cbo[myid] = (uint8_t)byte;
-                    mk |= in_marker || out_marker;
+                    if (in_marker || out_marker) mk |= near_bits(l[0], l[1], l[2]);
                 }
             }
 #pragma unroll
@@ -635,7 +635,10 @@ __device__ __forceinline__ void sweep_tile(const SweepArgs &a, int tile, uint8_t
                 if (slot >= 0) a.work[k][slot] = (unsigned)myid;
             }
         }
-        if (mk) *s_flag = 1;
+        {
+            const unsigned v = __reduce_or_sync(0xffffffffu, mk);
+            if ((threadIdx.x & 31) == 0 && v) atomicOr(s_flag, v);
+        }
 #pragma unroll
         for (int k = 0; k < C_N; k++) {
             unsigned v = __reduce_add_sync(0xffffffffu, ev[k]);
@@ -643,7 +646,7 @@ __device__ __forceinline__ void sweep_tile(const SweepArgs &a, int tile, uint8_t
         }
         __syncthreads();
         if (threadIdx.x == 0) {
-            a.tile_marker[tile] = (uint8_t)*s_flag;
+            a.tile_marker[tile] = *s_flag;
             a.tile_dirty[tile] = 1;
         }
         __syncthreads();
@@ -652,7 +655,7 @@ __device__ __forceinline__ void sweep_tile(const SweepArgs &a, int tile, uint8_t
 
 template <int D>
 __global__ void __launch_bounds__(256) sweep_kernel(SweepArgs a) {
-    __shared__ int s_flag;
+    __shared__ unsigned s_flag;
     __shared__ uint8_t s_b[RA * R1 * R2];
     const int ntl = *a.count;
     for (int li = blockIdx.x; li < ntl; li += gridDim.x) sweep_tile<D, false>(a, a.list[li], s_b, &s_flag);
