@@ -85,15 +85,19 @@ __device__ __forceinline__ void warp_count(unsigned long long *ctr, unsigned v) 
 
 // Is tile (tx, ty, tz) in the band: does it own a marker, or does a neighbour
 // own one within NEAR cells of it (that neighbour's proximity bit toward it)?
+// (the 27 loads are independent: no early exit)
 __device__ __forceinline__ bool in_band(const Grid &g, const uint32_t *__restrict__ mask, int tx, int ty, int tz) {
-    bool on = false;
-    for (int dz = -1; dz <= 1 && !on; dz++)
-        for (int dy = -1; dy <= 1 && !on; dy++)
-            for (int dx = -1; dx <= 1 && !on; dx++) {
+    unsigned on = 0;
+#pragma unroll
+    for (int dz = -1; dz <= 1; dz++)
+#pragma unroll
+        for (int dy = -1; dy <= 1; dy++)
+#pragma unroll
+            for (int dx = -1; dx <= 1; dx++) {
                 const int nx = wrapc(tx + dx, g.td[0]), ny = wrapc(ty + dy, g.td[1]), nz = wrapc(tz + dz, g.td[2]);
-                on = (mask[(nz * g.td[1] + ny) * g.td[0] + nx] >> near_bit(-dx, -dy, -dz)) & 1u;
+                on |= mask[(nz * g.td[1] + ny) * g.td[0] + nx] >> near_bit(-dx, -dy, -dz);
             }
-    return on;
+    return on & 1u;
 }
 
 }  // namespace ebit

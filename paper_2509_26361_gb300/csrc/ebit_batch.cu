@@ -77,7 +77,7 @@ __device__ bool grid_barrier(const BatchParams &p, int *s_ok) {
                     ok = 0;
                     break;
                 }
-                __nanosleep(64);
+                if (it > 64) __nanosleep(64);
             }
         }
         __threadfence();
@@ -99,7 +99,7 @@ __device__ __forceinline__ int find_inst(const int *toff, int n, int gt) {
 }
 
 template <int D>
-__global__ void __launch_bounds__(BATCH_THREADS) batch_sweep_kernel(BatchParams p) {
+__global__ void __launch_bounds__(BATCH_THREADS, 4) batch_sweep_kernel(BatchParams p) {
     __shared__ uint16_t s_mk[3 * TILE_CELLS];
     __shared__ uint8_t s_c[9 * 9 * 9];
     __shared__ uint8_t s_b[RA * R1 * R2];
@@ -137,10 +137,7 @@ __global__ void __launch_bounds__(BATCH_THREADS) batch_sweep_kernel(BatchParams 
     for (int li = blockIdx.x; li < nb; li += gridDim.x) {
         const int e = __ldcg(p.band + li);
         const int i = e >> 20;
-        SweepArgs a = p.inst[i].a;
-        a.u = p.u[i];
-        a.lam = p.lam[i];
-        advect_tile<D>(a, e & 0xFFFFF, s_mk, s_c, &s_n);
+        advect_tile<D>(p.inst[i].a, p.u[i], p.lam[i], e & 0xFFFFF, s_mk, s_c, &s_n);
     }
     if (!grid_barrier(p, &s_ok)) return;
 
@@ -148,7 +145,7 @@ __global__ void __launch_bounds__(BATCH_THREADS) batch_sweep_kernel(BatchParams 
     for (int li = blockIdx.x; li < nb; li += gridDim.x) {
         const int e = __ldcg(p.band + li);
         const int i = e >> 20;
-        const SweepArgs a = p.inst[i].a;
+        const SweepArgs &a = p.inst[i].a;
         sweep_tile<D, true>(a, e & 0xFFFFF, s_b, &s_flag);
         if (threadIdx.x == 0) atomicAdd(a.ctr + C_TILES, 1ull);
     }

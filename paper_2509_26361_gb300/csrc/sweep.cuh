@@ -129,7 +129,7 @@ __device__ __forceinline__ bool circle_root(P2 A, P2 B, P2 C, double ylin, doubl
 
 // trilinear u_D at node q shifted by s along axis e; lerps in x, y, z order
 template <int D>
-__device__ double interp_u(const SweepArgs &a, const int q[3], int e, double s) {
+__device__ double interp_u(const Grid &g, const double *__restrict__ u, const int q[3], int e, double s) {
     int base[3];
     double t[3];
 #pragma unroll
@@ -148,11 +148,9 @@ __device__ double interp_u(const SweepArgs &a, const int q[3], int e, double s) 
             t[b] = s - 0.5;
         }
     }
-    const Grid &g = a.g;
     int x0 = wrapc(base[0], g.n[0]), x1 = wrapc(base[0] + 1, g.n[0]);
     int y0 = wrapc(base[1], g.n[1]), y1 = wrapc(base[1] + 1, g.n[1]);
     int z0 = wrapc(base[2], g.n[2]), z1 = wrapc(base[2] + 1, g.n[2]);
-    const double *u = a.u;
     int r00 = (z0 * g.n[1] + y0) * g.n[0], r10 = (z0 * g.n[1] + y1) * g.n[0];
     int r01 = (z1 * g.n[1] + y0) * g.n[0], r11 = (z1 * g.n[1] + y1) * g.n[0];
     double c00 = (1.0 - t[0]) * __ldg(u + r00 + x0) + t[0] * __ldg(u + r00 + x1);
@@ -180,9 +178,10 @@ __device__ __forceinline__ int warp_append(int *counter, bool flag) {
 // ---------------------------------------------------------------- advection
 // Move every marker of one band tile once (Eq. 2).  CFL >= 1 is counted and
 // clamped.  Called by all threads of the block; s_mk/s_c/s_n are its shared
-// staging.
+// staging; u is u_D on the D-faces and lam = dt / h.
 template <int D>
-__device__ __forceinline__ void advect_tile(const SweepArgs &a, int tile, uint16_t *s_mk, uint8_t *s_c, int *s_n) {
+__device__ __forceinline__ void advect_tile(const SweepArgs &a, const double *__restrict__ u, double lam, int tile,
+                                            uint16_t *s_mk, uint8_t *s_c, int *s_n) {
     int o[3];
     tile_origin(a.g, tile, o);
     if (threadIdx.x == 0) *s_n = 0;
@@ -213,7 +212,7 @@ __device__ __forceinline__ void advect_tile(const SweepArgs &a, int tile, uint16
         int q[3] = {o[0] + (c & 7), o[1] + ((c >> 3) & 7), o[2] + (c >> 6)};
         const int id = lin3(a.g, q);
         double sv = __ldg(a.s[e] + id);
-        double cf = interp_u<D>(a, q, e, sv) * a.lam;
+        double cf = interp_u<D>(a.g, u, q, e, sv) * lam;
         if (!(fabs(cf) < 1.0)) {
             hits++;
             cf = cf > 0.0 ? ONE_MINUS : -ONE_MINUS;
@@ -234,7 +233,7 @@ __global__ void __launch_bounds__(256) advect_kernel(SweepArgs a) {
     __shared__ int s_n;
     const int ntl = *a.count;
     if (blockIdx.x == 0 && threadIdx.x < 4) a.wcount[threadIdx.x] = 0;
-    for (int li = blockIdx.x; li < ntl; li += gridDim.x) advect_tile<D>(a, a.list[li], s_mk, s_c, &s_n);
+    for (int li = blockIdx.x; li < ntl; li += gridDim.x) advect_tile<D>(a, a.u, a.lam, a.list[li], s_mk, s_c, &s_n);
 }
 
 // ----------------------------------------------------------- cell context
