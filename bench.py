@@ -50,7 +50,8 @@ def config_dict(w, l2):
     return {"workload": WORKLOAD, "grid": list(w.n3), "spheres": len(w.shapes), "radius_range": [0.05, 0.12],
             "velocity": "12-mode Fourier vector-potential curl x cos(pi t/T), T=2", "cfl": w.cfl,
             "period_steps": w.steps, "step": "3 split sweeps + Front2VOF + HF curvature (FP64)",
-            "band": "8^3 tiles with markers + 1-tile halo", "l2": l2}
+            "band": "8^3 tiles owning a marker, and their neighbours where a marker lies within 3 cells",
+            "l2": l2}
 
 
 # --------------------------------------------------------------- oracle arm
