@@ -253,6 +253,11 @@ const char *ebit_mlp_last_error(const ebit_mlp *mlp);
  * fragment (see ebit_mlp_gather); those cells get the height-function value
  * and status. */
 int ebit_set_mlp(ebit_ctx *ctx, ebit_mlp *mlp);
+/* Parameters (host or device, ebit_mlp_nparams() floats in the order above,
+ * bytes = 4 * ebit_mlp_nparams()) into a network the context owns and uses
+ * for ebit_curvature (created on first use on the context's stream, freed by
+ * ebit_destroy).  EBIT_EINVAL on a size mismatch. */
+int ebit_mlp_load(ebit_ctx *ctx, const void *weights, size_t bytes);
 
 /* ---------------------------------------------------------------------------
  * Batches: many independent instances (each a periodic grid with its own size,
@@ -284,8 +289,12 @@ ebit_ctx *ebit_batch_instance(ebit_batch *b, int i);
  * sweep, so the caller keeps it alive and may rewrite it between sweeps);
  * dt[i] (host) its time step.  Synchronises. */
 int ebit_batch_set_velocity(ebit_batch *b, const double *const *u_faces, const double *dt);
-/* One split sweep along dir (0, 1, 2) of every instance. */
-int ebit_batch_advect_sweep(ebit_batch *b, int dir);
+/* One split sweep along dir (0, 1, 2) of every instance.  u_dev (host array
+ * of n device pointers: instance i's u_dir on its dir-normal faces) and dt
+ * (host array of n time steps) replace the stored velocity of that direction
+ * and the stored time steps; either may be NULL to keep what
+ * ebit_batch_set_velocity (or an earlier call) stored. */
+int ebit_batch_advect_sweep(ebit_batch *b, int dir, const double *const *u_dev, const double *dt);
 /* Steps first_step .. first_step + steps - 1 (even steps x-y-z, odd steps
  * z-y-x).  use_graph != 0 replays pairs of steps from a CUDA graph captured on
  * first use (and again after a launch-shape change); where capture is not

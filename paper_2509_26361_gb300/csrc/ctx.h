@@ -18,6 +18,7 @@ struct ebit_mlp {
     __nv_bfloat16 *w1b, *w2b;  // bf16 copies for the tensor cores
     float *loss;               // summed weighted squared error of the last step
     int step;
+    int fwd_blocks;            // co-resident forward blocks per SM
     std::string errmsg;
 };
 
@@ -52,7 +53,8 @@ struct ebit_ctx {
     int *nscan;
     int *zero;                // a device int that stays 0
     int sweeps_since_f2v;
-    ebit_mlp *mlp;            // learned curvature (ebit_set_mlp)
+    ebit_mlp *mlp;            // learned curvature (ebit_set_mlp or ebit_mlp_load)
+    ebit_mlp *own_mlp;        // the network ebit_mlp_load made (owned)
     const double *last_C;
     const double *last_kh;
     const uint8_t *last_st;

@@ -152,6 +152,7 @@ static int create_ctx(const ebit_desc *desc, const ebit_state_arrays *st, ebit_c
     ctx->cur_if = 0;
     ctx->sweeps_since_f2v = 0;
     ctx->mlp = nullptr;
+    ctx->own_mlp = nullptr;
     ctx->tile_marker = nullptr;
     ctx->tile_dirty = ctx->tile_cchg = nullptr;
     ctx->band_list = ctx->band_count = ctx->work_list = ctx->work_count = ctx->all_list = ctx->all_count = nullptr;
@@ -262,6 +263,7 @@ int ebit_create(const ebit_desc *desc, ebit_ctx **out) { return create_ctx(desc,
 void ebit_destroy(ebit_ctx *ctx) {
     if (!ctx) return;
     cudaStreamSynchronize(ctx->stream);
+    if (ctx->own_mlp) ebit_mlp_destroy(ctx->own_mlp);
     if (ctx->owns_state) {
         for (int b = 0; b < 2; b++) {
             cudaFree(ctx->cb[b]);
@@ -501,7 +503,7 @@ int ebit_curvature(ebit_ctx *ctx, const double *C, double *kappa_h, uint8_t *sta
         int r;
         {
             ProfScope pm(ctx, EBIT_PROF_MLP);
-            mlp_fwd_kernel<true, true><<<2 * ctx->sms, 128, FWD_SMEM, ctx->stream>>>(m);
+            mlp_fwd_kernel<true, true><<<ctx->mlp->fwd_blocks * ctx->sms, 128, FWD_SMEM, ctx->stream>>>(m);
             r = launch_check(ctx, "mlp_fwd_kernel");
         }
         if (r) return r;
@@ -599,6 +601,20 @@ int ebit_set_mlp(ebit_ctx *ctx, ebit_mlp *mlp) {
     return EBIT_OK;
 }
 
+int ebit_mlp_load(ebit_ctx *ctx, const void *weights, size_t bytes) {
+    if (!ctx || !weights) return fail(ctx, EBIT_EINVAL, "ebit_mlp_load: null argument");
+    if (bytes != (size_t)MLP_NP * sizeof(float))
+        return fail(ctx, EBIT_EINVAL, "ebit_mlp_load: expected ebit_mlp_nparams() floats");
+    if (!ctx->own_mlp) {
+        int r = ebit_mlp_create(ctx->stream, &ctx->own_mlp);
+        if (r) return fail(ctx, r, "ebit_mlp_load: could not create the network");
+    }
+    int r = ebit_mlp_set_params(ctx->own_mlp, static_cast<const float *>(weights));
+    if (r) return fail(ctx, r, std::string("ebit_mlp_load: ") + ebit_mlp_last_error(ctx->own_mlp));
+    ctx->mlp = ctx->own_mlp;
+    return EBIT_OK;
+}
+
 // ------------------------------------------------------- learned curvature
 #define MCU(call)                                                                                          \
     do {                                                                                                   \
@@ -646,6 +662,9 @@ int ebit_mlp_create(void *cuda_stream, ebit_mlp **out) {
         ebit_mlp_destroy(mlp);
         return EBIT_ECUDA;
     }
+    mlp->fwd_blocks = 1;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&mlp->fwd_blocks, mlp_fwd_kernel<true, true>, 128, FWD_SMEM);
+    mlp->fwd_blocks = std::max(1, mlp->fwd_blocks);
     cudaMemsetAsync(mlp->p, 0, MLP_NP * 4, mlp->stream);
     cudaMemsetAsync(mlp->g, 0, MLP_NP * 4, mlp->stream);
     cudaMemsetAsync(mlp->m, 0, MLP_NP * 4, mlp->stream);
@@ -716,7 +735,7 @@ int ebit_mlp_forward(ebit_mlp *mlp, const uint16_t *X, int m, float *y) {
     a.w2b = mlp->w2b;
     a.y = y;
     const int ntile = (m + 127) / 128;
-    mlp_fwd_kernel<false, false><<<std::min(ntile, 2 * mlp->sms), 128, FWD_SMEM, mlp->stream>>>(a);
+    mlp_fwd_kernel<false, false><<<std::min(ntile, mlp->fwd_blocks * mlp->sms), 128, FWD_SMEM, mlp->stream>>>(a);
     MCU(cudaGetLastError());
     return EBIT_OK;
 }

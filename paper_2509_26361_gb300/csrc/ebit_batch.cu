@@ -237,7 +237,8 @@ struct ebit_batch {
     int *band = nullptr, *nband = nullptr;
     unsigned *bar = nullptr;
     int *err = nullptr;
-    int have_velocity = 0;
+    int have_u[3] = {0, 0, 0};
+    int have_dt = 0;
     int occ[3] = {1, 1, 1};        // co-resident blocks per SM of each direction's kernel
     int ctas_per_sm = 1;           // chosen launch shape (autotuned)
     // CUDA graph of two steps (even: x y z, odd: z y x)
@@ -567,20 +568,39 @@ int ebit_batch_set_velocity(ebit_batch *b, const double *const *u_faces, const d
         BCU(cudaMemcpyAsync(b->u[d], up[d].data(), b->n * sizeof(double *), cudaMemcpyHostToDevice, b->stream));
     BCU(cudaMemcpyAsync(b->lam, lam.data(), b->n * sizeof(double), cudaMemcpyHostToDevice, b->stream));
     BCU(cudaStreamSynchronize(b->stream));
-    b->have_velocity = 1;
+    b->have_u[0] = b->have_u[1] = b->have_u[2] = 1;
+    b->have_dt = 1;
     return EBIT_OK;
 }
 
-int ebit_batch_advect_sweep(ebit_batch *b, int dir) {
+int ebit_batch_advect_sweep(ebit_batch *b, int dir, const double *const *u_dev, const double *dt) {
     if (!b) return EBIT_EINVAL;
     if (dir < 0 || dir > 2) return bfail(b, EBIT_EINVAL, "ebit_batch_advect_sweep: dir must be 0, 1 or 2");
-    if (!b->have_velocity) return bfail(b, EBIT_EINVAL, "ebit_batch_advect_sweep: no velocity set");
+    if (u_dev) {
+        for (int i = 0; i < b->n; i++)
+            if (!u_dev[i]) return bfail(b, EBIT_EINVAL, "ebit_batch_advect_sweep: null velocity");
+        BCU(cudaMemcpyAsync(b->u[dir], u_dev, b->n * sizeof(double *), cudaMemcpyHostToDevice, b->stream));
+        b->have_u[dir] = 1;
+    }
+    if (dt) {
+        std::vector<double> lam(b->n);
+        for (int i = 0; i < b->n; i++) {
+            if (!std::isfinite(dt[i])) return bfail(b, EBIT_EINVAL, "ebit_batch_advect_sweep: non-finite dt");
+            lam[i] = dt[i] / b->inst[i]->h;
+        }
+        BCU(cudaMemcpyAsync(b->lam, lam.data(), b->n * sizeof(double), cudaMemcpyHostToDevice, b->stream));
+        BCU(cudaStreamSynchronize(b->stream));  // the host copy of lam goes out of scope
+        b->have_dt = 1;
+    }
+    if (!b->have_u[dir] || !b->have_dt)
+        return bfail(b, EBIT_EINVAL, "ebit_batch_advect_sweep: no velocity or time step for this direction");
     return sweep_once(b, dir, b->ctas_per_sm);
 }
 
 int ebit_batch_run(ebit_batch *b, int first_step, int steps, int use_graph) {
     if (!b || steps < 0) return EBIT_EINVAL;
-    if (!b->have_velocity) return bfail(b, EBIT_EINVAL, "ebit_batch_run: no velocity set");
+    if (!(b->have_u[0] && b->have_u[1] && b->have_u[2] && b->have_dt))
+        return bfail(b, EBIT_EINVAL, "ebit_batch_run: no velocity set");
     int n = first_step;
     int left = steps;
     auto one_step = [&](int k) -> int {
@@ -701,7 +721,8 @@ int ebit_batch_set_launch_shape(ebit_batch *b, int ctas_per_sm) {
 
 int ebit_batch_autotune(ebit_batch *b, int sweeps, double *ms_out) {
     if (!b || sweeps < 1) return EBIT_EINVAL;
-    if (!b->have_velocity) return bfail(b, EBIT_EINVAL, "ebit_batch_autotune: no velocity set");
+    if (!(b->have_u[0] && b->have_u[1] && b->have_u[2] && b->have_dt))
+        return bfail(b, EBIT_EINVAL, "ebit_batch_autotune: no velocity set");
     // trial sweeps run on a copy of the state, which is put back afterwards
     const long long cells = b->cells;
     const int par0 = b->parity;

@@ -56,48 +56,91 @@ __device__ __forceinline__ bool fragmented27(unsigned pos) {
     return r != pos;
 }
 
-// 3x3x3 block around cell (x, y, z); Youngs normal n = -grad C (1-2-1 weights,
-// b2 outer, b1 inner); reflect axes with n < 0; order axes by increasing |n|
-// (stable); write the 27 values in z-major order of the canonical axes, split
-// into bf16 head and tail.  Returns the fragment flag of the block.
-__device__ __forceinline__ bool canon_encode(const double *__restrict__ C, const Grid &g, int x, int y, int z,
-                                             __nv_bfloat16 out[MLP_IN]) {
-    double blk[3][3][3];
-#pragma unroll
-    for (int dz = -1; dz <= 1; dz++)
-#pragma unroll
-        for (int dy = -1; dy <= 1; dy++)
-#pragma unroll
-            for (int dx = -1; dx <= 1; dx++) blk[dz + 1][dy + 1][dx + 1] = __ldg(C + lin(g, x + dx, y + dy, z + dz));
-    const double w[3] = {1.0, 2.0, 1.0};
-    double n[3];
+// Youngs normal n = -grad C of a 3x3x3 block (1-2-1 weights, b2 outer, b1
+// inner), in the type T of the block values.
+template <typename T>
+__device__ __forceinline__ void youngs(const T (&v)[27], T n[3]) {
+    const T w[3] = {T(1), T(2), T(1)};
 #pragma unroll
     for (int d = 0; d < 3; d++) {
         const int t1 = (d == 0) ? 1 : 0, t2 = (d == 2) ? 1 : 2;
-        double gsum = 0.0;
+        T gsum = T(0);
 #pragma unroll
         for (int b2 = -1; b2 <= 1; b2++)
 #pragma unroll
             for (int b1 = -1; b1 <= 1; b1++) {
-                int op[3] = {0, 0, 0}, om[3] = {0, 0, 0};
-                op[d] = 1;
-                om[d] = -1;
+                int op[3] = {1, 1, 1}, om[3] = {1, 1, 1};
+                op[d] += 1;
+                om[d] -= 1;
                 op[t1] += b1;
                 om[t1] += b1;
                 op[t2] += b2;
                 om[t2] += b2;
-                gsum += (w[b1 + 1] * w[b2 + 1]) *
-                        (blk[op[2] + 1][op[1] + 1][op[0] + 1] - blk[om[2] + 1][om[1] + 1][om[0] + 1]);
+                gsum += (w[b1 + 1] * w[b2 + 1]) * (v[op[2] * 9 + op[1] * 3 + op[0]] - v[om[2] * 9 + om[1] * 3 + om[0]]);
             }
         n[d] = -gsum;
     }
-    const int sg[3] = {n[0] < 0.0 ? -1 : 1, n[1] < 0.0 ? -1 : 1, n[2] < 0.0 ? -1 : 1};
-    const double m[3] = {fabs(n[0]), fabs(n[1]), fabs(n[2])};
+}
+
+// Bound on |n_float - n| for values rounded to float: 8 additions below 64
+// (half an ulp, 2^-19, each) and the inputs' rounding (2^-25 each, weights
+// summing to 16, three roundings per difference) stay under 1.7e-5.
+constexpr float CANON_EPS = 3.0e-5f;
+
+// 3x3x3 block around cell (x, y, z); reflect the axes with n < 0; order the
+// axes by increasing |n| (stable); write the 27 values in z-major order of the
+// canonical axes, split into bf16 head and tail.  The normal is taken in float
+// and its decisions (signs, order) kept when every sign and comparison clears
+// twice the bound above, so they equal those of the double-precision normal;
+// otherwise the double-precision normal decides.  sf: this thread's column of
+// 27 floats (stride `stride`) in shared memory.  Returns the fragment flag.
+__device__ __forceinline__ bool canon_encode(const double *__restrict__ C, const Grid &g, int x, int y, int z,
+                                             __nv_bfloat16 out[MLP_IN], float *sf, int stride) {
+    float f[27];
+    unsigned pos = 0;
+#pragma unroll
+    for (int b = 0; b < 27; b++) {
+        const double c = __ldg(C + lin(g, x + b % 3 - 1, y + (b / 3) % 3 - 1, z + b / 9 - 1));
+        if (c > 0.0) pos |= 1u << b;
+        f[b] = (float)c;
+        sf[b * stride] = f[b];
+    }
+    float nf[3];
+    youngs<float>(f, nf);
+    const float a0 = fabsf(nf[0]), a1 = fabsf(nf[1]), a2 = fabsf(nf[2]);
+    int sg[3];
+    float m[3];
+    double md[3];
+    const bool sure = a0 > CANON_EPS && a1 > CANON_EPS && a2 > CANON_EPS && fabsf(a0 - a1) > 2.0f * CANON_EPS &&
+                      fabsf(a0 - a2) > 2.0f * CANON_EPS && fabsf(a1 - a2) > 2.0f * CANON_EPS;
     int o0 = 0, o1 = 1, o2 = 2, t;
-    if (m[o1] < m[o0]) { t = o0; o0 = o1; o1 = t; }
-    if (m[o2] < m[o1]) {
-        t = o1; o1 = o2; o2 = t;
+    if (sure) {
+#pragma unroll
+        for (int d = 0; d < 3; d++) sg[d] = nf[d] < 0.0f ? -1 : 1;
+        m[0] = a0;
+        m[1] = a1;
+        m[2] = a2;
         if (m[o1] < m[o0]) { t = o0; o0 = o1; o1 = t; }
+        if (m[o2] < m[o1]) {
+            t = o1; o1 = o2; o2 = t;
+            if (m[o1] < m[o0]) { t = o0; o0 = o1; o1 = t; }
+        }
+    } else {
+        double v[27];
+#pragma unroll
+        for (int b = 0; b < 27; b++) v[b] = __ldg(C + lin(g, x + b % 3 - 1, y + (b / 3) % 3 - 1, z + b / 9 - 1));
+        double n[3];
+        youngs<double>(v, n);
+#pragma unroll
+        for (int d = 0; d < 3; d++) {
+            sg[d] = n[d] < 0.0 ? -1 : 1;
+            md[d] = fabs(n[d]);
+        }
+        if (md[o1] < md[o0]) { t = o0; o0 = o1; o1 = t; }
+        if (md[o2] < md[o1]) {
+            t = o1; o1 = o2; o2 = t;
+            if (md[o1] < md[o0]) { t = o0; o0 = o1; o1 = t; }
+        }
     }
     int k = 0;
     for (int u2 = -1; u2 <= 1; u2++)
@@ -107,31 +150,31 @@ __device__ __forceinline__ bool canon_encode(const double *__restrict__ C, const
                 d[o0] = sg[o0] * u0;
                 d[o1] = sg[o1] * u1;
                 d[o2] = sg[o2] * u2;
-                const double c = __ldg(C + lin(g, x + d[0], y + d[1], z + d[2]));
-                const float f = (float)c;
-                const __nv_bfloat16 hi = __float2bfloat16_rn(f);
+                const float fv = sf[((d[2] + 1) * 9 + (d[1] + 1) * 3 + (d[0] + 1)) * stride];
+                const __nv_bfloat16 hi = __float2bfloat16_rn(fv);
                 out[k] = hi;
-                out[32 + k] = __float2bfloat16_rn(f - __bfloat162float(hi));
+                out[32 + k] = __float2bfloat16_rn(fv - __bfloat162float(hi));
                 k++;
             }
     for (int q = 27; q < 32; q++) {
         out[q] = __float2bfloat16_rn(0.0f);
         out[32 + q] = __float2bfloat16_rn(0.0f);
     }
-    unsigned pos = 0;
-#pragma unroll
-    for (int b = 0; b < 27; b++)
-        if (blk[b / 9][(b / 3) % 3][b % 3] > 0.0) pos |= 1u << b;
     return fragmented27(pos);
 }
 
-__global__ void mlp_gather_kernel(const double *__restrict__ C, Grid g, const int *__restrict__ cells, int m,
-                                  __nv_bfloat16 *__restrict__ X, uint8_t *__restrict__ frag) {
+constexpr int GATHER_THREADS = 128;
+
+__global__ void __launch_bounds__(GATHER_THREADS) mlp_gather_kernel(const double *__restrict__ C, Grid g,
+                                                                    const int *__restrict__ cells, int m,
+                                                                    __nv_bfloat16 *__restrict__ X,
+                                                                    uint8_t *__restrict__ frag) {
+    __shared__ float s_f[27 * GATHER_THREADS];
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < m; i += gridDim.x * blockDim.x) {
         const int id = cells[i];
         const int x = id % g.n[0], y = (id / g.n[0]) % g.n[1], z = id / (g.n[0] * g.n[1]);
         __nv_bfloat16 v[MLP_IN];
-        const bool fr = canon_encode(C, g, x, y, z, v);
+        const bool fr = canon_encode(C, g, x, y, z, v, s_f + threadIdx.x, GATHER_THREADS);
         if (frag) frag[i] = fr ? 1 : 0;
         uint4 *dst = reinterpret_cast<uint4 *>(X + (long long)i * MLP_IN);
         const uint4 *src = reinterpret_cast<const uint4 *>(v);
@@ -269,16 +312,22 @@ struct MlpArgs {
 };
 
 // ------------------------------------------------------------ forward
-// smem: X [128][72] | W1 [128][72] | H1 [128][136] | W2 [128][136] | fragment flags [128]
-constexpr int FWD_SMEM = (128 * LD64 * 2 + 128 * LD128 * 2) * 2 + 128;
+// smem: X [128][72] | W1 [128][72] | W2 [128][136] | fragment flags [128].  The
+// layer-1 activations stay in registers: the accumulator fragments of two
+// adjacent 8-column tiles are exactly the A fragment of one 16-wide k step.
+constexpr int FWD_SMEM = (2 * 128 * LD64 + 128 * LD128) * 2 + 128;
+
+__device__ __forceinline__ uint32_t pack_bf16x2(float lo, float hi) {
+    __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
+    return *reinterpret_cast<uint32_t *>(&v);
+}
 
 template <bool GATHER, bool CURV>
 __global__ void __launch_bounds__(128) mlp_fwd_kernel(MlpArgs a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __nv_bfloat16 *sX = reinterpret_cast<__nv_bfloat16 *>(smem_raw);
     __nv_bfloat16 *sW1 = sX + 128 * LD64;
-    __nv_bfloat16 *sH1 = sW1 + 128 * LD64;
-    __nv_bfloat16 *sW2 = sH1 + 128 * LD128;
+    __nv_bfloat16 *sW2 = sW1 + 128 * LD64;
     uint8_t *sFrag = reinterpret_cast<uint8_t *>(sW2 + 128 * LD128);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31, g = lane >> 2, t4 = lane & 3;
     load_row(sW1, LD64, tid, a.w1b, tid, MLP_IN, MLP_H);
@@ -295,7 +344,8 @@ __global__ void __launch_bounds__(128) mlp_fwd_kernel(MlpArgs a) {
             if (live) {
                 const int cell = a.cells[row];
                 const int x = cell % a.g.n[0], y = (cell / a.g.n[0]) % a.g.n[1], z = cell / (a.g.n[0] * a.g.n[1]);
-                sFrag[tid] = canon_encode(a.C, a.g, x, y, z, v) ? 1 : 0;
+                // the block values are staged in this thread's own input row
+                sFrag[tid] = canon_encode(a.C, a.g, x, y, z, v, reinterpret_cast<float *>(sX + tid * LD64), 1) ? 1 : 0;
             } else {
                 for (int q = 0; q < MLP_IN; q++) v[q] = __float2bfloat16_rn(0.0f);
             }
@@ -309,29 +359,45 @@ __global__ void __launch_bounds__(128) mlp_fwd_kernel(MlpArgs a) {
                 if (MLP_S(d + q, 16, 10)) d[q] = make_uint4(0, 0, 0, 0);
         }
         __syncthreads();
-        // ---- layer 1 -> H1 (bf16)
+        // ---- layer 1 -> H1 as bf16 A fragments in registers: h1[mt][kk][2 half + (row + 8)]
+        uint32_t h1[2][8][4];
+#pragma unroll
         for (int c = 0; c < 4; c++) {
             float acc[2][4][4];
             warp_gemm32<MLP_IN, LD64, LD64>(sX, sW1, m0, c * 32, acc);
 #pragma unroll
             for (int mt = 0; mt < 2; mt++)
 #pragma unroll
-                for (int nt = 0; nt < 4; nt++)
-#pragma unroll
-                    for (int hh = 0; hh < 2; hh++) {
-                        const int r = m0 + mt * 16 + g + 8 * hh, col = c * 32 + nt * 8 + 2 * t4;
-                        const float h0 = fmaxf(acc[mt][nt][2 * hh] + ldp(a.params, P_B1 + col), 0.0f);
-                        const float h1 = fmaxf(acc[mt][nt][2 * hh + 1] + ldp(a.params, P_B1 + col + 1), 0.0f);
-                        __nv_bfloat162 *dst = reinterpret_cast<__nv_bfloat162 *>(sH1 + r * LD128 + col);
-                        if (MLP_S(dst, 4, 4)) *dst = __floats2bfloat162_rn(h0, h1);
-                    }
+                for (int nt = 0; nt < 4; nt++) {
+                    const int col = c * 32 + nt * 8 + 2 * t4;
+                    const float b0 = ldp(a.params, P_B1 + col), b1 = ldp(a.params, P_B1 + col + 1);
+                    const int kk = 2 * c + (nt >> 1), half = nt & 1;
+                    h1[mt][kk][2 * half] = pack_bf16x2(fmaxf(acc[mt][nt][0] + b0, 0.0f), fmaxf(acc[mt][nt][1] + b1, 0.0f));
+                    h1[mt][kk][2 * half + 1] =
+                        pack_bf16x2(fmaxf(acc[mt][nt][2] + b0, 0.0f), fmaxf(acc[mt][nt][3] + b1, 0.0f));
+                }
         }
-        __syncthreads();
-        // ---- layer 2 and output
+        // ---- layer 2 (A from registers, B = W2 rows in shared memory) and output
         float yp[2][2] = {{0.0f, 0.0f}, {0.0f, 0.0f}};
+#pragma unroll
         for (int c = 0; c < 4; c++) {
             float acc[2][4][4];
-            warp_gemm32<MLP_H, LD128, LD128>(sH1, sW2, m0, c * 32, acc);
+#pragma unroll
+            for (int i = 0; i < 2; i++)
+#pragma unroll
+                for (int j = 0; j < 4; j++)
+#pragma unroll
+                    for (int e = 0; e < 4; e++) acc[i][j][e] = 0.0f;
+#pragma unroll
+            for (int kk = 0; kk < 8; kk++) {
+#pragma unroll
+                for (int nt = 0; nt < 4; nt++) {
+                    const __nv_bfloat16 *rb = sW2 + (c * 32 + nt * 8 + g) * LD128 + kk * 16 + 2 * t4;
+                    const uint32_t b0 = ld32s(rb), b1 = ld32s(rb + 8);
+#pragma unroll
+                    for (int mt = 0; mt < 2; mt++) mma16816(acc[mt][nt], h1[mt][kk], b0, b1);
+                }
+            }
 #pragma unroll
             for (int mt = 0; mt < 2; mt++)
 #pragma unroll

@@ -108,7 +108,8 @@ def load(build_if_missing: bool = True):
     lib.ebit_batch_instance.argtypes = [P, I]
     lib.ebit_batch_instance.restype = P
     lib.ebit_batch_set_velocity.argtypes = [P, ctypes.POINTER(ctypes.c_void_p), ctypes.POINTER(ctypes.c_double)]
-    lib.ebit_batch_advect_sweep.argtypes = [P, I]
+    lib.ebit_batch_advect_sweep.argtypes = [P, I, ctypes.POINTER(ctypes.c_void_p), ctypes.POINTER(ctypes.c_double)]
+    lib.ebit_mlp_load.argtypes = [P, P, ctypes.c_size_t]
     lib.ebit_batch_run.argtypes = [P, I, I, I]
     lib.ebit_batch_graph_active.argtypes = [P]
     lib.ebit_batch_graph_note.argtypes = [P]
@@ -327,6 +328,14 @@ def ebit_mlp_sync(mlp):
     return _mcheck(mlp, load().ebit_mlp_sync(mlp))
 
 
+def ebit_mlp_load(ctx, params):
+    p = torch.as_tensor(params, dtype=torch.float32).contiguous()
+    n = ebit_mlp_nparams()
+    if p.numel() != n:
+        raise ValueError(f"params: need {n} floats")
+    return _check(ctx, load().ebit_mlp_load(ctx, ctypes.c_void_p(p.data_ptr()), 4 * n))
+
+
 def ebit_set_mlp(ctx, mlp):
     return _check(ctx, load().ebit_set_mlp(ctx, mlp))
 
@@ -443,8 +452,19 @@ class Batch:
         self._u = [tuple(u) for u in u_fields]  # keep the device fields alive
         return ebit_batch_set_velocity(self.b, self.n3s, self._u, dts)
 
-    def sweep(self, d):
-        return _bcheck(self.b, load().ebit_batch_advect_sweep(self.b, int(d)))
+    def sweep(self, d, u=None, dts=None):
+        """One split sweep along d; ``u`` (instance i's u_d device tensor at u[i])
+        and ``dts`` replace the stored velocity of d and the time steps."""
+        up = dp = None
+        if u is not None:
+            up = (ctypes.c_void_p * len(self.n3s))()
+            for i, n3 in enumerate(self.n3s):
+                up[i] = _dev(u[i], torch.float64, n3[0] * n3[1] * n3[2], "u_face").value
+                self._keep = getattr(self, "_keep", {})
+                self._keep[(d, i)] = u[i]
+        if dts is not None:
+            dp = (ctypes.c_double * len(self.n3s))(*[float(v) for v in dts])
+        return _bcheck(self.b, load().ebit_batch_advect_sweep(self.b, int(d), up, dp))
 
     def run(self, first_step, steps, graph=True):
         return _bcheck(self.b, load().ebit_batch_run(self.b, int(first_step), int(steps), int(bool(graph))))
@@ -566,6 +586,10 @@ class Grid:
 
     def set_mlp(self, mlp):
         return ebit_set_mlp(self.ctx, None if mlp is None else mlp.h)
+
+    def load_mlp(self, params):
+        """Parameters (float32, host or device) into a network the context owns."""
+        return ebit_mlp_load(self.ctx, params)
 
     def profile(self, enable=True):
         return ebit_profile(self.ctx, enable)

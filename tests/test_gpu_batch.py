@@ -127,3 +127,24 @@ def test_instance_context_refuses_its_own_sweep():
     with pytest.raises(ebit.EbitError):
         g.sweep(0, dev(insts[0][3][0]), 0.5 / 16)
     b.close()
+
+
+def test_per_call_velocity_matches_stored_velocity():
+    insts = instances(8, [16, 24])
+    a = make_batch(insts)
+    b = ebit.Batch([(n, n, n) for n, *_ in insts])
+    for i, (n, phi, faces, u) in enumerate(insts):
+        b.instance(i).init(dev(phi), dev(faces))
+    us = [[dev(u[d]) for d in range(3)] for (_, _, _, u) in insts]
+    dts = [0.5 / n for n, *_ in insts]
+    for d in (0, 1, 2, 2, 1, 0):
+        a.sweep(d)
+        b.sweep(d, [us[i][d] for i in range(len(insts))], dts)
+    a.sync()
+    b.sync()
+    for i in range(len(insts)):
+        ca, sa = a.instance(i).get_state()
+        cb_, sb = b.instance(i).get_state()
+        assert torch.equal(ca, cb_) and torch.equal(sa, sb)
+    a.close()
+    b.close()

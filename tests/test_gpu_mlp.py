@@ -1,6 +1,8 @@
 """Learned curvature on the GPU (bf16 tensor-core kernels, through the C ABI) against the
 FP64 oracle of oracle/mlp.py: canonical stencils bit-exact, forward pass and
 gradients within the stated tolerances (bf16 operands, FP32 accumulation)."""
+import ctypes
+
 import numpy as np
 import pytest
 import torch
@@ -185,4 +187,26 @@ def test_curvature_mode_uses_the_network():
     assert np.array_equal(np.nonzero(st_h)[0], np.sort(cells))
     assert np.allclose(kh.cpu().numpy().ravel()[cells], y, rtol=0, atol=1e-6)
     g.close()
+    m.close()
+
+
+def test_context_owned_network_equals_attached_network():
+    n3, C, cells = sphere_fractions()
+    p = omlp.init_params(3).astype(np.float32)
+    m = ebit.Mlp(p.astype(np.float64))
+    g1, g2 = ebit.Grid(*n3), ebit.Grid(*n3)
+    g1.set_mlp(m)
+    g2.load_mlp(p)
+    Cd = dev(C)
+    outs = []
+    for g in (g1, g2):
+        kh = torch.zeros_like(Cd)
+        st = torch.zeros(Cd.shape, dtype=torch.uint8, device="cuda")
+        g.curvature(Cd, kh, st, mode=ebit.EBIT_CURV_MLP, flags=ebit.EBIT_FULL)
+        outs.append((kh, st))
+    assert torch.equal(outs[0][0], outs[1][0]) and torch.equal(outs[0][1], outs[1][1])
+    short = torch.zeros(5, dtype=torch.float32)
+    assert ebit.load().ebit_mlp_load(g2.ctx, ctypes.c_void_p(short.data_ptr()), 20) == ebit.EBIT_EINVAL
+    g1.close()
+    g2.close()
     m.close()
