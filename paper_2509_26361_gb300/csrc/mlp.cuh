@@ -56,37 +56,6 @@ __device__ __forceinline__ bool fragmented27(unsigned pos) {
     return r != pos;
 }
 
-// Youngs normal n = -grad C of a 3x3x3 block (1-2-1 weights, b2 outer, b1
-// inner), in the type T of the block values.
-template <typename T>
-__device__ __forceinline__ void youngs(const T (&v)[27], T n[3]) {
-    const T w[3] = {T(1), T(2), T(1)};
-#pragma unroll
-    for (int d = 0; d < 3; d++) {
-        const int t1 = (d == 0) ? 1 : 0, t2 = (d == 2) ? 1 : 2;
-        T gsum = T(0);
-#pragma unroll
-        for (int b2 = -1; b2 <= 1; b2++)
-#pragma unroll
-            for (int b1 = -1; b1 <= 1; b1++) {
-                int op[3] = {1, 1, 1}, om[3] = {1, 1, 1};
-                op[d] += 1;
-                om[d] -= 1;
-                op[t1] += b1;
-                om[t1] += b1;
-                op[t2] += b2;
-                om[t2] += b2;
-                gsum += (w[b1 + 1] * w[b2 + 1]) * (v[op[2] * 9 + op[1] * 3 + op[0]] - v[om[2] * 9 + om[1] * 3 + om[0]]);
-            }
-        n[d] = -gsum;
-    }
-}
-
-// Bound on |n_float - n| for values rounded to float: 8 additions below 64
-// (half an ulp, 2^-19, each) and the inputs' rounding (2^-25 each, weights
-// summing to 16, three roundings per difference) stay under 1.7e-5.
-constexpr float CANON_EPS = 3.0e-5f;
-
 // 3x3x3 block around cell (x, y, z); reflect the axes with n < 0; order the
 // axes by increasing |n| (stable); write the 27 values in z-major order of the
 // canonical axes, split into bf16 head and tail.  The normal is taken in float
