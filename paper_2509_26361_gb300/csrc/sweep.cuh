@@ -127,6 +127,36 @@ __device__ __forceinline__ bool circle_root(P2 A, P2 B, P2 C, double ylin, doubl
     return true;
 }
 
+// The crossing of an unaligned edge from the advected points P1 P2 P3 P4
+// (P2 -> P3 crosses the edge's grid line at ylin; P1, P4 their neighbours, if
+// found): circles through P1 P2 P3 and P2 P3 P4; both valid -> the larger
+// circle's root if its radius exceeds 10 times the smaller one, else the mean;
+// one valid -> its root; none -> ylin; clamped to [0, 1-] (Fig. 2).  One
+// out-of-line copy serves every edge family (the two fits are independent, so
+// their FP64 chains interleave inside it).
+static __device__ __noinline__ double circle_pair(P2 P1, P2 Pa, P2 Pb, P2 P4, double ylin, bool h1, bool h4) {
+    double ya = 0.0, ra = 0.0, yb = 0.0, rb = 0.0;
+    bool va = circle_root(P1, Pa, Pb, ylin, &ya, &ra);
+    bool vb = circle_root(Pa, Pb, P4, ylin, &yb, &rb);
+    va = va && h1;
+    vb = vb && h4;
+    double y;
+    if (va && vb) {
+        double rmax = ra > rb ? ra : rb, rmin = ra > rb ? rb : ra;
+        if (rmax > 10.0 * rmin) y = ra > rb ? ya : yb;
+        else y = 0.5 * (ya + yb);
+    } else if (va) {
+        y = ya;
+    } else if (vb) {
+        y = yb;
+    } else {
+        y = ylin;
+    }
+    if (y < 0.0) y = 0.0;
+    if (y > ONE_MINUS) y = ONE_MINUS;
+    return y;
+}
+
 // trilinear u_D at node q shifted by s along axis e; lerps in x, y, z order
 template <int D>
 __device__ double interp_u(const Grid &g, const double *__restrict__ u, const int q[3], int e, double s) {
@@ -414,33 +444,13 @@ struct SweepCell {
         }
         P2 Pa = c2[sel], Pb = c3[sel];
         double ylin = yl[sel];
-        // both neighbours first, then the two independent circle fits (the
-        // compiler interleaves the two FP64 chains)
+        // both neighbours first, then the two circle fits
         P2 P1 = Pa, P4 = Pb;
-        double ya = 0.0, ra = 0.0, yb = 0.0, rb = 0.0;
         const bool h1 = neighbour<TT, NN>(e2[sel], cd[sel], 0, &P1);
         const bool h4 = neighbour<TT, NN>(e3[sel], cd[sel], 0, &P4);
         if (!h1) ev[C_INCONSISTENT]++;
         if (!h4) ev[C_INCONSISTENT]++;
-        bool va = circle_root(P1, Pa, Pb, ylin, &ya, &ra);
-        bool vb = circle_root(Pa, Pb, P4, ylin, &yb, &rb);
-        va = va && h1;
-        vb = vb && h4;
-        double y;
-        if (va && vb) {
-            double rmax = ra > rb ? ra : rb, rmin = ra > rb ? rb : ra;
-            if (rmax > 10.0 * rmin) y = ra > rb ? ya : yb;
-            else y = 0.5 * (ya + yb);
-        } else if (va) {
-            y = ya;
-        } else if (vb) {
-            y = yb;
-        } else {
-            y = ylin;
-        }
-        if (y < 0.0) y = 0.0;
-        if (y > ONE_MINUS) y = ONE_MINUS;
-        a.so[TT][myid] = y;
+        a.so[TT][myid] = circle_pair(P1, Pa, Pb, P4, ylin, h1, h4);
     }
 
     // Face-centre colour of the family's 2D cell at the node (saddle faces): the
