@@ -319,7 +319,24 @@ def curvature_block():
                        "mlp_all_cells": r["rms_mlp"], "mlp_hf_all_cells": r["rms_mlp_hf"]},
             "hf_no_value_cells": r["hf_no_value"], "mlp_hf_fallback_cells": r["mlp_hf_fallback"],
             "dtype": "bf16 MMA, fp32 accumulate (HF: f64)",
-            "ms_per_pass": r["ms"]}
+            "ms_per_pass": r["ms"], "training": training_record()}
+
+
+def training_record():
+    """Throughput of the run that made the shipped parameters (its report sits
+    next to them): stencil passes (forward + backward + Adam) per second."""
+    from paper_2509_26361_gb300 import learned
+
+    path = os.path.join(os.path.dirname(learned.PARAMS_FILE), "mlp_curvature_train_report.json")
+    try:
+        with open(path) as f:
+            rep = json.load(f)
+    except OSError:
+        return None
+    steps = rep["stencils"] // rep["batch"] * rep["batch"] * rep["epochs"]
+    return {"stencils": rep["stencils"], "epochs": rep["epochs"], "batch": rep["batch"],
+            "train_seconds": rep["train_seconds"], "stencil_passes_per_s": steps / rep["train_seconds"],
+            "final_loss": rep["loss_per_epoch"][-1], "source": "data/mlp_curvature_train_report.json"}
 
 
 def batched_block(steps=256, warmup=4):
