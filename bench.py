@@ -257,10 +257,10 @@ def run_e2e(args, g, w, dev, C, kh, st):
             "h2d_bytes_per_step": 3 * nc * 8, "d2h_bytes_per_step": 2 * nc * 8}
 
 
-# DRAM bytes (read + write) per launch of the split-sweep kernels, one ncu
+# DRAM bytes (read + write) per launch of the split-sweep kernels (sweep along x), one ncu
 # capture each (--set full, cold caches) of the same 128^3 workload; see
 # profiles/kernels_fourier_spheres_128.md.  None once the kernels change.
-NCU_TRAFFIC = {"advect": 3467776.0, "sweep": 2865920.0, "fp64": 3277056.0}
+NCU_TRAFFIC = {"advect": 2948096.0, "sweep": 2346240.0, "fp64": 3277568.0, "band": 24064.0}
 # per band cell of one split sweep and of Front2VOF (the scope table's figures)
 SWEEP_BYTES_PER_CELL = 62.75
 F2V_BYTES_PER_CELL = 36.4
