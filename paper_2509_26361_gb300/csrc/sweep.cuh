@@ -663,7 +663,7 @@ __device__ __forceinline__ void sweep_tile(const SweepArgs &a, int tile, uint8_t
 }
 
 template <int D>
-__global__ void __launch_bounds__(256) sweep_kernel(SweepArgs a) {
+__global__ void __launch_bounds__(256, 4) sweep_kernel(SweepArgs a) {
     __shared__ unsigned s_flag;
     __shared__ uint8_t s_b[RA * R1 * R2];
     const int ntl = *a.count;
