@@ -242,8 +242,16 @@ int ebit_mlp_gradient(ebit_mlp *mlp, const uint16_t *X, const float *t, int batc
 int ebit_mlp_train_step(ebit_mlp *mlp, const uint16_t *X, const float *t, const int *idx, int batch, float lr,
                         float *loss_out);
 /* Wait for the network's stream; EBIT_ECUDA (message in ebit_mlp_last_error)
- * if a launch or copy on it failed. */
+ * if a launch or copy on it failed, EBIT_ETIMEOUT if a tensor-core wait of the
+ * tcgen05 path gave up (the kernel then freed its tensor memory and left). */
 int ebit_mlp_sync(ebit_mlp *mlp);
+/* Inference path of ebit_mlp_forward and ebit_curvature:
+ * EBIT_MLP_PATH_MMA (default): warp-level BF16 MMA (mma.sync m16n8k16), the
+ * layer-1 activations in registers; EBIT_MLP_PATH_TCGEN05: 5th-generation
+ * tensor cores, one thread issuing tcgen05.mma from shared memory into tensor
+ * memory.  Both compute the same network in bf16 with FP32 accumulation. */
+enum { EBIT_MLP_PATH_MMA = 0, EBIT_MLP_PATH_TCGEN05 = 1 };
+int ebit_mlp_set_path(ebit_mlp *mlp, int path);
 const char *ebit_mlp_last_error(const ebit_mlp *mlp);
 /* Network used by ebit_curvature in modes EBIT_CURV_MLP and EBIT_CURV_MLP_HF
  * (NULL detaches).  EBIT_CURV_MLP writes the learned value (status

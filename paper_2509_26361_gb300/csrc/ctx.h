@@ -18,7 +18,10 @@ struct ebit_mlp {
     __nv_bfloat16 *w1b, *w2b;  // bf16 copies for the tensor cores
     float *loss;               // summed weighted squared error of the last step
     int step;
-    int fwd_blocks;            // co-resident forward blocks per SM
+    int fwd_blocks;            // co-resident forward blocks per SM (warp-level MMA kernel)
+    int fwd_tc_blocks;         // the same for the tcgen05 kernel
+    int path;                  // EBIT_MLP_PATH_MMA or EBIT_MLP_PATH_TCGEN05
+    int *err;                  // set by a tcgen05 kernel whose bounded wait gave up
     std::string errmsg;
 };
 

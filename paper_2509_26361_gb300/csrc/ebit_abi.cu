@@ -503,7 +503,11 @@ int ebit_curvature(ebit_ctx *ctx, const double *C, double *kappa_h, uint8_t *sta
         int r;
         {
             ProfScope pm(ctx, EBIT_PROF_MLP);
-            mlp_fwd_kernel<true, true><<<ctx->mlp->fwd_blocks * ctx->sms, 128, FWD_SMEM, ctx->stream>>>(m);
+            m.err = ctx->mlp->err;
+            if (ctx->mlp->path == EBIT_MLP_PATH_TCGEN05)
+                mlp_fwd_tc_kernel<true, true><<<ctx->mlp->fwd_tc_blocks * ctx->sms, 128, FWD_TC_SMEM, ctx->stream>>>(m);
+            else
+                mlp_fwd_kernel<true, true><<<ctx->mlp->fwd_blocks * ctx->sms, 128, FWD_SMEM, ctx->stream>>>(m);
             r = launch_check(ctx, "mlp_fwd_kernel");
         }
         if (r) return r;
@@ -636,6 +640,7 @@ int ebit_mlp_create(void *cuda_stream, ebit_mlp **out) {
     mlp->stream = (cudaStream_t)cuda_stream;
     mlp->p = mlp->g = mlp->m = mlp->v = mlp->loss = nullptr;
     mlp->w1b = mlp->w2b = nullptr;
+    mlp->err = nullptr;
     mlp->step = 0;
     int dev = 0;
     cudaGetDevice(&dev);
@@ -646,7 +651,7 @@ int ebit_mlp_create(void *cuda_stream, ebit_mlp **out) {
               cudaMalloc((void **)&mlp->v, MLP_NP * 4) == cudaSuccess &&
               cudaMalloc((void **)&mlp->w1b, MLP_H * MLP_IN * 2) == cudaSuccess &&
               cudaMalloc((void **)&mlp->w2b, MLP_H * MLP_H * 2) == cudaSuccess &&
-              cudaMalloc((void **)&mlp->loss, 4) == cudaSuccess;
+              cudaMalloc((void **)&mlp->loss, 4) == cudaSuccess && cudaMalloc((void **)&mlp->err, 4) == cudaSuccess;
     if (!ok) {
         cudaGetLastError();
         ebit_mlp_destroy(mlp);
@@ -657,7 +662,11 @@ int ebit_mlp_create(void *cuda_stream, ebit_mlp **out) {
         cudaFuncSetAttribute(mlp_fwd_kernel<true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, FWD_SMEM) !=
             cudaSuccess ||
         cudaFuncSetAttribute(mlp_train_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, TRAIN_SMEM) !=
-            cudaSuccess) {
+            cudaSuccess ||
+        cudaFuncSetAttribute(mlp_fwd_tc_kernel<false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             FWD_TC_SMEM) != cudaSuccess ||
+        cudaFuncSetAttribute(mlp_fwd_tc_kernel<true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             FWD_TC_SMEM) != cudaSuccess) {
         cudaGetLastError();
         ebit_mlp_destroy(mlp);
         return EBIT_ECUDA;
@@ -665,6 +674,13 @@ int ebit_mlp_create(void *cuda_stream, ebit_mlp **out) {
     mlp->fwd_blocks = 1;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&mlp->fwd_blocks, mlp_fwd_kernel<true, true>, 128, FWD_SMEM);
     mlp->fwd_blocks = std::max(1, mlp->fwd_blocks);
+    mlp->fwd_tc_blocks = 1;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&mlp->fwd_tc_blocks, mlp_fwd_tc_kernel<true, true>, 128,
+                                                  FWD_TC_SMEM);
+    // each block holds 128 TMEM columns: at most 4 per SM
+    mlp->fwd_tc_blocks = std::max(1, std::min(mlp->fwd_tc_blocks, 4));
+    mlp->path = EBIT_MLP_PATH_MMA;
+    cudaMemsetAsync(mlp->err, 0, sizeof(int), mlp->stream);
     cudaMemsetAsync(mlp->p, 0, MLP_NP * 4, mlp->stream);
     cudaMemsetAsync(mlp->g, 0, MLP_NP * 4, mlp->stream);
     cudaMemsetAsync(mlp->m, 0, MLP_NP * 4, mlp->stream);
@@ -687,6 +703,7 @@ void ebit_mlp_destroy(ebit_mlp *mlp) {
     cudaFree(mlp->w1b);
     cudaFree(mlp->w2b);
     cudaFree(mlp->loss);
+    cudaFree(mlp->err);
     delete mlp;
 }
 
@@ -735,7 +752,12 @@ int ebit_mlp_forward(ebit_mlp *mlp, const uint16_t *X, int m, float *y) {
     a.w2b = mlp->w2b;
     a.y = y;
     const int ntile = (m + 127) / 128;
-    mlp_fwd_kernel<false, false><<<std::min(ntile, mlp->fwd_blocks * mlp->sms), 128, FWD_SMEM, mlp->stream>>>(a);
+    a.err = mlp->err;
+    if (mlp->path == EBIT_MLP_PATH_TCGEN05)
+        mlp_fwd_tc_kernel<false, false><<<std::min(ntile, mlp->fwd_tc_blocks * mlp->sms), 128, FWD_TC_SMEM,
+                                          mlp->stream>>>(a);
+    else
+        mlp_fwd_kernel<false, false><<<std::min(ntile, mlp->fwd_blocks * mlp->sms), 128, FWD_SMEM, mlp->stream>>>(a);
     MCU(cudaGetLastError());
     return EBIT_OK;
 }
@@ -784,7 +806,19 @@ int ebit_mlp_train_step(ebit_mlp *mlp, const uint16_t *X, const float *t, const 
 
 int ebit_mlp_sync(ebit_mlp *mlp) {
     if (!mlp) return EBIT_EINVAL;
+    int e = 0;
+    MCU(cudaMemcpyAsync(&e, mlp->err, sizeof(int), cudaMemcpyDeviceToHost, mlp->stream));
     MCU(cudaStreamSynchronize(mlp->stream));
+    if (e) {
+        mlp->errmsg = e == 2 ? "tensor memory allocation outside the expected range" : "a tensor-core wait gave up";
+        return EBIT_ETIMEOUT;
+    }
+    return EBIT_OK;
+}
+
+int ebit_mlp_set_path(ebit_mlp *mlp, int path) {
+    if (!mlp || (path != EBIT_MLP_PATH_MMA && path != EBIT_MLP_PATH_TCGEN05)) return EBIT_EINVAL;
+    mlp->path = path;
     return EBIT_OK;
 }
 

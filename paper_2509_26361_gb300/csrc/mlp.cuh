@@ -18,6 +18,7 @@
 #include <cuda_bf16.h>
 
 #include "common.cuh"
+#include "tc.cuh"
 
 namespace ebit {
 
@@ -278,6 +279,7 @@ struct MlpArgs {
     const int *idx;             // training rows X[idx[r]], t[idx[r]] (null: rows 0..batch-1)
     unsigned *fb;               // cells left to height functions (curvature mode 2)
     int *nfb;                   // their number
+    int *err;                   // set when a bounded tensor-core wait gives up
 };
 
 // ------------------------------------------------------------ forward
@@ -414,6 +416,153 @@ __global__ void __launch_bounds__(128) mlp_fwd_kernel(MlpArgs a) {
         }
         __syncthreads();
     }
+}
+
+// ------------------------------------------------- forward on tcgen05 (TMEM)
+// One 128-stencil tile per iteration; one elected thread issues the MMAs
+// (M = N = 128, K = 16 per instruction) from K-major, unswizzled shared tiles
+// (8x8 core matrices of 128 bytes, see tc.cuh) into 128 TMEM columns, which
+// both layers reuse.  Thread t owns row t: TMEM lane t, read back with
+// tcgen05.ld by its warp.
+// smem (1024-aligned): X 16 KB | W1 16 KB | H1 32 KB (also the gather's
+// staging) | W2 32 KB | mbarrier | TMEM base | fragment flags [128]
+constexpr int TCF_X = 0, TCF_W1 = 16384, TCF_H1 = 32768, TCF_W2 = 65536, TCF_MBAR = 98304, TCF_TB = 98320,
+              TCF_FRAG = 98336;
+constexpr int FWD_TC_SMEM = TCF_FRAG + 128 + 1024;
+constexpr long long MLP_WAIT = 1LL << 20;  // mbarrier polls before a wait gives up
+
+__device__ __forceinline__ void load_row_kmaj(unsigned char *tile, const __nv_bfloat16 *__restrict__ src, int tr,
+                                              long long r, int cols) {
+    const uint4 *s = reinterpret_cast<const uint4 *>(src + r * cols);
+    for (int q = 0; q < cols / 8; q++) *reinterpret_cast<uint4 *>(tile + tc::kmaj_off(tr, q * 8, cols)) = s[q];
+}
+
+template <bool GATHER, bool CURV>
+__global__ void __launch_bounds__(128) mlp_fwd_tc_kernel(MlpArgs a) {
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    unsigned char *base = (unsigned char *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    unsigned char *sX = base + TCF_X, *sW1 = base + TCF_W1, *sH1 = base + TCF_H1, *sW2 = base + TCF_W2;
+    uint64_t *mbar = reinterpret_cast<uint64_t *>(base + TCF_MBAR);
+    uint32_t *tbase = reinterpret_cast<uint32_t *>(base + TCF_TB);
+    uint8_t *sFrag = base + TCF_FRAG;
+    const int tid = threadIdx.x, warp = tid >> 5;
+    const uint32_t mb = tc::smem_u32(mbar);
+    if (tid == 0) {
+        tc::mbar_init(mb, 1);
+        tc::fence_mbar_init();
+    }
+    if (warp == 0) tc::tmem_alloc(tc::smem_u32(tbase), 128);
+    load_row_kmaj(sW1, a.w1b, tid, tid, MLP_IN);
+    load_row_kmaj(sW2, a.w2b, tid, tid, MLP_H);
+    tc::fence_proxy_async();
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    const uint32_t tm = *tbase;
+    const uint32_t lane_base = tm + ((uint32_t)(warp * 32) << 16);
+    const int m = a.ncells ? *a.ncells : a.m;
+    // the allocation must start at lane 0 with its 128 columns inside TMEM
+    const bool tm_ok = (tm >> 16) == 0 && (tm & 0xFFFF) + 128 <= 512;
+    const int ntile = tm_ok ? (m + 127) / 128 : 0;
+    if (!tm_ok && tid == 0) atomicExch(a.err, 2);
+    const uint32_t idesc = tc::idesc_bf16(128, 128);
+    uint32_t phase = 0;
+    bool ok = true;
+    for (int tile = blockIdx.x; tile < ntile; tile += gridDim.x) {
+        const int row = tile * 128 + tid;
+        const bool live = row < m;
+        int cell = 0;
+        // ---- inputs: row tid of the tile
+        {
+            __nv_bfloat16 v[MLP_IN];
+            if (GATHER && live) {
+                cell = a.cells[row];
+                const int x = cell % a.g.n[0], y = (cell / a.g.n[0]) % a.g.n[1], z = cell / (a.g.n[0] * a.g.n[1]);
+                // the block values are staged in the H1 tile (free until layer 1)
+                sFrag[tid] = canon_encode(a.C, a.g, x, y, z, v, reinterpret_cast<float *>(sH1 + tid * 112), 1) ? 1 : 0;
+            } else if (!GATHER && live) {
+                const uint4 *s4 = reinterpret_cast<const uint4 *>(a.X + (long long)row * MLP_IN);
+                for (int q = 0; q < MLP_IN / 8; q++) reinterpret_cast<uint4 *>(v)[q] = s4[q];
+            } else {
+                for (int q = 0; q < MLP_IN; q++) v[q] = __float2bfloat16_rn(0.0f);
+            }
+            for (int q = 0; q < MLP_IN / 8; q++)
+                *reinterpret_cast<uint4 *>(sX + tc::kmaj_off(tid, q * 8, MLP_IN)) = reinterpret_cast<uint4 *>(v)[q];
+        }
+        tc::fence_proxy_async();
+        tc::fence_before_sync();
+        __syncthreads();
+        // ---- layer 1: D = X W1^T
+        if (tid == 0) {
+            tc::fence_after_sync();
+            const uint32_t ax = tc::smem_u32(sX), aw = tc::smem_u32(sW1);
+#pragma unroll
+            for (int kk = 0; kk < MLP_IN / 16; kk++)
+                tc::mma_bf16(tm, tc::smem_desc(ax + kk * 256, 128, 1024), tc::smem_desc(aw + kk * 256, 128, 1024),
+                             idesc, kk > 0);
+            tc::mma_commit(mb);
+        }
+        ok = __syncthreads_and(tc::mbar_wait(mb, phase, MLP_WAIT)) != 0;  // the same decision in every thread
+        if (!ok) break;
+        phase ^= 1;
+        tc::fence_after_sync();
+        for (int c = 0; c < 4; c++) {
+            float v[32];
+            tc::tmem_ld32(lane_base + c * 32, v);
+#pragma unroll
+            for (int j = 0; j < 32; j++) v[j] = fmaxf(v[j] + ldp(a.params, P_B1 + c * 32 + j), 0.0f);
+#pragma unroll
+            for (int q = 0; q < 4; q++)
+                *reinterpret_cast<uint4 *>(sH1 + tc::kmaj_off(tid, c * 32 + q * 8, MLP_H)) = tc::pack8_bf16(v + q * 8);
+        }
+        tc::fence_proxy_async();
+        tc::fence_before_sync();
+        __syncthreads();
+        // ---- layer 2: D = H1 W2^T (the same TMEM columns)
+        if (tid == 0) {
+            tc::fence_after_sync();
+            const uint32_t ah = tc::smem_u32(sH1), aw = tc::smem_u32(sW2);
+#pragma unroll
+            for (int kk = 0; kk < MLP_H / 16; kk++)
+                tc::mma_bf16(tm, tc::smem_desc(ah + kk * 256, 128, 2048), tc::smem_desc(aw + kk * 256, 128, 2048),
+                             idesc, kk > 0);
+            tc::mma_commit(mb);
+        }
+        ok = __syncthreads_and(tc::mbar_wait(mb, phase, MLP_WAIT)) != 0;
+        if (!ok) break;
+        phase ^= 1;
+        tc::fence_after_sync();
+        float yv = 0.0f;
+        for (int c = 0; c < 4; c++) {
+            float v[32];
+            tc::tmem_ld32(lane_base + c * 32, v);
+#pragma unroll
+            for (int j = 0; j < 32; j++)
+                yv += fmaxf(v[j] + ldp(a.params, P_B2 + c * 32 + j), 0.0f) * ldp(a.params, P_W3 + c * 32 + j);
+        }
+        yv += ldp(a.params, P_B3);
+        if (live) {
+            if (CURV) {
+                if (a.mode == 2 && (fabsf(yv) > 1.0f || sFrag[tid])) {
+                    a.fb[atomicAdd(a.nfb, 1)] = (unsigned)cell;
+                } else {
+                    a.kh[cell] = (double)yv;
+                    a.st[cell] = 5;
+                }
+            } else {
+                a.y[row] = yv;
+            }
+        }
+        tc::fence_before_sync();
+        __syncthreads();
+    }
+    if (!ok) {
+        if (tid == 0) atomicExch(a.err, 1);
+        tc::mbar_wait(mb, phase, MLP_WAIT);  // an MMA still in flight finishes before the columns are freed
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+    if (warp == 0 && tm_ok) tc::tmem_dealloc(tm, 128);
 }
 
 // ------------------------------------------------------------ training

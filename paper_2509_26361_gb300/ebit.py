@@ -32,6 +32,7 @@ EBIT_CURV_MLP_HF = 2
 EBIT_DESC_DENSE = 1
 
 ST_NONE, ST_HF_X, ST_HF_Y, ST_HF_Z, ST_NO_HF, ST_MLP = 0, 1, 2, 3, 4, 5
+EBIT_MLP_PATH_MMA, EBIT_MLP_PATH_TCGEN05 = 0, 1
 
 COUNTER_NAMES = ("markers", "annihilate", "multi", "inconsistent", "cfl")
 
@@ -96,6 +97,7 @@ def load(build_if_missing: bool = True):
     lib.ebit_mlp_gradient.argtypes = [P, P, P, I, P]
     lib.ebit_mlp_train_step.argtypes = [P, P, P, P, I, ctypes.c_float, P]
     lib.ebit_mlp_sync.argtypes = [P]
+    lib.ebit_mlp_set_path.argtypes = [P, I]
     lib.ebit_mlp_last_error.argtypes = [P]
     lib.ebit_mlp_last_error.restype = ctypes.c_char_p
     lib.ebit_set_mlp.argtypes = [P, P]
@@ -345,6 +347,7 @@ class Mlp:
 
     def __init__(self, params=None, stream=None):
         self.h = ebit_mlp_create(stream)
+        self.path = EBIT_MLP_PATH_MMA
         self.nparams = ebit_mlp_nparams()
         if params is not None:
             self.set_params(params)
@@ -390,6 +393,12 @@ class Mlp:
 
     def sync(self):
         return ebit_mlp_sync(self.h)
+
+    def set_path(self, path):
+        """EBIT_MLP_PATH_MMA (warp-level MMA) or EBIT_MLP_PATH_TCGEN05."""
+        r = _mcheck(self.h, load().ebit_mlp_set_path(self.h, int(path)))
+        self.path = int(path)
+        return r
 
 
 # ----------------------------------------------------------------- batches

@@ -135,13 +135,15 @@ def _rms(e):
     return float(np.sqrt(np.mean(e * e))) if len(e) else float("nan")
 
 
-def evaluate(mlp, seed=33, n=256, count=64, amin=4.0, amax=32.0, repeats=5):
+def evaluate(mlp, seed=33, n=256, count=64, amin=4.0, amax=32.0, repeats=5, path=None):
     """The learned-curvature benchmark grid: ``count`` seeded ellipsoids with
     semi-axes U[amin, amax] cells and random rotations.  RMS kappa*h error
     against the analytic labels for height functions (where they give a value),
     the network alone, and the network with height-function fallback; binned
     by the local radius 2/|kappa| in cells; and stencils per second of the
     height-function pass and the learned pass on the same interface list."""
+    if path is not None:
+        mlp.set_path(path)
     rng = np.random.default_rng(seed)
     ells = D.random_ellipsoids(rng, count, amin, amax, n)
     st = stencil_set(n, ells, mlp, 1, with_hf=True)
@@ -166,7 +168,20 @@ def evaluate(mlp, seed=33, n=256, count=64, amin=4.0, amax=32.0, repeats=5):
         g.profile(False)
         times[name] = {k: v[0] / repeats for k, v in prof.items()}
         vals[name] = (kh.reshape(-1)[idx].cpu().numpy(), stt.reshape(-1)[idx].cpu().numpy())
+    # the tcgen05 inference path on the same list (same network, same values)
+    prev = getattr(mlp, "path", ebit.EBIT_MLP_PATH_MMA)
+    mlp.set_path(ebit.EBIT_MLP_PATH_TCGEN05)
+    g.curvature(C, kh, stt, mode=ebit.EBIT_CURV_MLP, flags=ebit.EBIT_FULL)
+    g.profile(True)
+    for _ in range(repeats):
+        g.curvature(C, kh, stt, mode=ebit.EBIT_CURV_MLP, flags=ebit.EBIT_FULL)
+    prof = g.profile_read()
+    g.profile(False)
+    times["mlp_tcgen05"] = {k: v[0] / repeats for k, v in prof.items()}
+    tc_kh = kh.reshape(-1)[idx].cpu().numpy()
+    mlp.set_path(prev)
     g.close()
+    res["tcgen05_max_abs_diff"] = float(np.max(np.abs(tc_kh - vals["mlp"][0]))) if len(cells) else 0.0
     hf_k, hf_s = vals["hf"]
     hf_ok = ok & (hf_s >= 1) & (hf_s <= 3)
     res["hf_no_value"] = int(np.sum(ok & ~((hf_s >= 1) & (hf_s <= 3))))
@@ -196,6 +211,8 @@ def evaluate(mlp, seed=33, n=256, count=64, amin=4.0, amax=32.0, repeats=5):
     res["hf_stencils_per_s"] = m / (t_hf * 1e-3)
     res["mlp_stencils_per_s"] = m / ((t_list + t_mlp) * 1e-3)
     res["mlp_hf_stencils_per_s"] = m / (t_mlp_hf * 1e-3)
+    t_tc = times["mlp_tcgen05"].get("hf", 0.0) + times["mlp_tcgen05"].get("mlp", float("nan"))
+    res["mlp_tcgen05_stencils_per_s"] = m / (t_tc * 1e-3)
     return res
 
 

@@ -62,12 +62,17 @@ def _random_inputs(n, rng):
     return omlp.encode(omlp.canonical_stencil(blk))
 
 
-def test_forward_matches_oracle():
+PATHS = [ebit.EBIT_MLP_PATH_MMA, ebit.EBIT_MLP_PATH_TCGEN05]
+
+
+@pytest.mark.parametrize("path", PATHS)
+def test_forward_matches_oracle(path):
     rng = np.random.default_rng(1)
     p = omlp.init_params(2) + rng.normal(scale=0.02, size=omlp.N_PARAMS)
     p = p.astype(np.float32).astype(np.float64)
     X = _random_inputs(1000, rng)  # ragged tail: 1000 = 7 tiles of 128 + 104
     m = ebit.Mlp(p)
+    m.set_path(path)
     y = m.forward(dev(X).to(torch.bfloat16)).cpu().numpy()
     m.sync()
     yr, _ = omlp.forward(p, X, emulate=True)
@@ -135,7 +140,8 @@ def test_indexed_training_step_equals_the_gathered_batch():
     b.close()
 
 
-def test_curvature_mode_with_height_function_fallback_matches_oracle():
+@pytest.mark.parametrize("path", PATHS)
+def test_curvature_mode_with_height_function_fallback_matches_oracle(path):
     n3, C, _ = sphere_fractions()
     C = with_satellites(C, np.random.default_rng(6))
     rng = np.random.default_rng(8)
@@ -149,6 +155,7 @@ def test_curvature_mode_with_height_function_fallback_matches_oracle():
     cells, kh_ref, st_ref, y_ref, frag = omlp.learned_curvature(C, p, 2, hf_kh, hf_st)
     assert frag.any() and (np.abs(y_ref) > 1.0).any() and (np.abs(y_ref) <= 1.0).any()
     m = ebit.Mlp(p)
+    m.set_path(path)
     g = ebit.Grid(*n3)
     g.set_mlp(m)
     Cd = dev(C)
@@ -209,4 +216,27 @@ def test_context_owned_network_equals_attached_network():
     assert ebit.load().ebit_mlp_load(g2.ctx, ctypes.c_void_p(short.data_ptr()), 20) == ebit.EBIT_EINVAL
     g1.close()
     g2.close()
+    m.close()
+
+
+def test_tensor_paths_agree_on_the_curvature_field():
+    n3, C, cells = sphere_fractions()
+    C = with_satellites(C, np.random.default_rng(11))
+    p = omlp.init_params(9) + np.random.default_rng(3).normal(scale=0.01, size=omlp.N_PARAMS)
+    m = ebit.Mlp(p)
+    g = ebit.Grid(*n3)
+    g.set_mlp(m)
+    Cd = dev(C)
+    out = []
+    for path in PATHS:
+        m.set_path(path)
+        kh = torch.zeros_like(Cd)
+        st = torch.zeros(Cd.shape, dtype=torch.uint8, device="cuda")
+        g.curvature(Cd, kh, st, mode=ebit.EBIT_CURV_MLP, flags=ebit.EBIT_FULL)
+        assert m.sync() == 0
+        out.append((kh.cpu().numpy(), st.cpu().numpy()))
+    assert np.array_equal(out[0][1], out[1][1])
+    # the same bf16 products, FP32 sums in a different order
+    assert np.max(np.abs(out[0][0] - out[1][0])) <= 1e-5
+    g.close()
     m.close()
