@@ -314,12 +314,14 @@ def curvature_block():
     return {"workload": "ellipsoids_256 (64 ellipsoids, semi-axes U[4,32] cells, random rotations, seed 33)",
             "interface_cells": r["interface_cells"], "unit": "stencils/s",
             "mlp": r["mlp_stencils_per_s"], "hf": r["hf_stencils_per_s"], "mlp_hf": r["mlp_hf_stencils_per_s"],
-            "mlp_tcgen05": r["mlp_tcgen05_stencils_per_s"], "tcgen05_max_abs_diff": r["tcgen05_max_abs_diff"],
+            "mlp_path": r["path"], "mlp_other_path": {"path": r["other_path"],
+                                                       "stencils_per_s": r["mlp_other_path_stencils_per_s"],
+                                                       "max_abs_diff": r["paths_max_abs_diff"]},
             "mlp_over_hf": r["mlp_stencils_per_s"] / r["hf_stencils_per_s"],
             "rms_kh": {"hf_on_hf_cells": r["rms_hf"], "mlp_on_hf_cells": r["rms_mlp_on_hf_cells"],
                        "mlp_all_cells": r["rms_mlp"], "mlp_hf_all_cells": r["rms_mlp_hf"]},
             "hf_no_value_cells": r["hf_no_value"], "mlp_hf_fallback_cells": r["mlp_hf_fallback"],
-            "dtype": "bf16 MMA (mma.sync default; tcgen05 path beside it), fp32 accumulate (HF: f64)",
+            "dtype": "bf16 tensor cores (tcgen05; mma.sync path beside it), fp32 accumulate (HF: f64)",
             "ms_per_pass": r["ms"], "training": training_record()}
 
 

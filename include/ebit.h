@@ -246,10 +246,11 @@ int ebit_mlp_train_step(ebit_mlp *mlp, const uint16_t *X, const float *t, const 
  * tcgen05 path gave up (the kernel then freed its tensor memory and left). */
 int ebit_mlp_sync(ebit_mlp *mlp);
 /* Inference path of ebit_mlp_forward and ebit_curvature:
- * EBIT_MLP_PATH_MMA (default): warp-level BF16 MMA (mma.sync m16n8k16), the
- * layer-1 activations in registers; EBIT_MLP_PATH_TCGEN05: 5th-generation
- * tensor cores, one thread issuing tcgen05.mma from shared memory into tensor
- * memory.  Both compute the same network in bf16 with FP32 accumulation. */
+ * EBIT_MLP_PATH_TCGEN05 (default): 5th-generation tensor cores, a persistent
+ * block per SM with three pipelines, each issuing tcgen05.mma from shared
+ * memory into its tensor-memory columns; EBIT_MLP_PATH_MMA: warp-level BF16
+ * MMA (mma.sync m16n8k16), the layer-1 activations in registers.  Both compute
+ * the same network in bf16 with FP32 accumulation. */
 enum { EBIT_MLP_PATH_MMA = 0, EBIT_MLP_PATH_TCGEN05 = 1 };
 int ebit_mlp_set_path(ebit_mlp *mlp, int path);
 const char *ebit_mlp_last_error(const ebit_mlp *mlp);

@@ -505,7 +505,7 @@ int ebit_curvature(ebit_ctx *ctx, const double *C, double *kappa_h, uint8_t *sta
             ProfScope pm(ctx, EBIT_PROF_MLP);
             m.err = ctx->mlp->err;
             if (ctx->mlp->path == EBIT_MLP_PATH_TCGEN05)
-                mlp_fwd_tc_kernel<true, true><<<ctx->mlp->fwd_tc_blocks * ctx->sms, 128, FWD_TC_SMEM, ctx->stream>>>(m);
+                mlp_fwd_tc_kernel<true, true><<<ctx->sms, TC_THREADS, FWD_TC_SMEM, ctx->stream>>>(m);
             else
                 mlp_fwd_kernel<true, true><<<ctx->mlp->fwd_blocks * ctx->sms, 128, FWD_SMEM, ctx->stream>>>(m);
             r = launch_check(ctx, "mlp_fwd_kernel");
@@ -675,11 +675,11 @@ int ebit_mlp_create(void *cuda_stream, ebit_mlp **out) {
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&mlp->fwd_blocks, mlp_fwd_kernel<true, true>, 128, FWD_SMEM);
     mlp->fwd_blocks = std::max(1, mlp->fwd_blocks);
     mlp->fwd_tc_blocks = 1;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&mlp->fwd_tc_blocks, mlp_fwd_tc_kernel<true, true>, 128,
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&mlp->fwd_tc_blocks, mlp_fwd_tc_kernel<true, true>, TC_THREADS,
                                                   FWD_TC_SMEM);
-    // each block holds 128 TMEM columns: at most 4 per SM
-    mlp->fwd_tc_blocks = std::max(1, std::min(mlp->fwd_tc_blocks, 4));
-    mlp->path = EBIT_MLP_PATH_MMA;
+    // a block holds all 512 TMEM columns (one per SM)
+    mlp->fwd_tc_blocks = 1;
+    mlp->path = EBIT_MLP_PATH_TCGEN05;
     cudaMemsetAsync(mlp->err, 0, sizeof(int), mlp->stream);
     cudaMemsetAsync(mlp->p, 0, MLP_NP * 4, mlp->stream);
     cudaMemsetAsync(mlp->g, 0, MLP_NP * 4, mlp->stream);
@@ -754,8 +754,8 @@ int ebit_mlp_forward(ebit_mlp *mlp, const uint16_t *X, int m, float *y) {
     const int ntile = (m + 127) / 128;
     a.err = mlp->err;
     if (mlp->path == EBIT_MLP_PATH_TCGEN05)
-        mlp_fwd_tc_kernel<false, false><<<std::min(ntile, mlp->fwd_tc_blocks * mlp->sms), 128, FWD_TC_SMEM,
-                                          mlp->stream>>>(a);
+        mlp_fwd_tc_kernel<false, false><<<std::min((ntile + TC_GROUPS - 1) / TC_GROUPS, mlp->sms), TC_THREADS,
+                                          FWD_TC_SMEM, mlp->stream>>>(a);
     else
         mlp_fwd_kernel<false, false><<<std::min(ntile, mlp->fwd_blocks * mlp->sms), 128, FWD_SMEM, mlp->stream>>>(a);
     MCU(cudaGetLastError());

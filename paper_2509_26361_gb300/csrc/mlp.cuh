@@ -419,16 +419,25 @@ __global__ void __launch_bounds__(128) mlp_fwd_kernel(MlpArgs a) {
 }
 
 // ------------------------------------------------- forward on tcgen05 (TMEM)
-// One 128-stencil tile per iteration; one elected thread issues the MMAs
-// (M = N = 128, K = 16 per instruction) from K-major, unswizzled shared tiles
-// (8x8 core matrices of 128 bytes, see tc.cuh) into 128 TMEM columns, which
-// both layers reuse.  Thread t owns row t: TMEM lane t, read back with
-// tcgen05.ld by its warp.
-// smem (1024-aligned): X 16 KB | W1 16 KB | H1 32 KB (also the gather's
-// staging) | W2 32 KB | mbarrier | TMEM base | fragment flags [128]
-constexpr int TCF_X = 0, TCF_W1 = 16384, TCF_H1 = 32768, TCF_W2 = 65536, TCF_MBAR = 98304, TCF_TB = 98320,
-              TCF_FRAG = 98336;
-constexpr int FWD_TC_SMEM = TCF_FRAG + 128 + 1024;
+// A kernel that uses tensor memory runs one block per SM, so the block holds
+// TC_GROUPS independent 128-thread pipelines (warpgroups), each with its own
+// input and H1 tiles, mbarrier and 128 TMEM columns; the weights are loaded once
+// per SM.  A group processes one 128-stencil tile at a time: its elected thread
+// issues the MMAs (M = N = 128, K = 16 per instruction) from K-major, unswizzled
+// shared tiles (8x8 core matrices of 128 bytes, see tc.cuh) into the group's
+// TMEM columns, which both layers reuse; thread t of the group owns row t (TMEM
+// lane t), read back with tcgen05.ld by its warp.  Groups synchronise on their
+// own named barrier.
+// smem (1024-aligned): W1 16 KB | W2 32 KB | per group: X 16 KB, H1 32 KB (also
+// the gather's staging) | mbarriers | TMEM base | fragment flags | wait flags
+constexpr int TC_GROUPS = 3;
+constexpr int TCF_W1 = 0, TCF_W2 = 16384, TCF_G0 = 49152, TCF_GSTRIDE = 49152;
+constexpr int TCF_MBAR = TCF_G0 + TC_GROUPS * TCF_GSTRIDE;          // 8 B per group
+constexpr int TCF_TB = TCF_MBAR + 8 * TC_GROUPS;
+constexpr int TCF_FRAG = TCF_TB + 16;                                // 128 B per group
+constexpr int TCF_BAD = TCF_FRAG + 128 * TC_GROUPS;                  // int per group
+constexpr int FWD_TC_SMEM = TCF_BAD + 4 * TC_GROUPS + 1024;
+constexpr int TC_THREADS = 128 * TC_GROUPS;
 constexpr long long MLP_WAIT = 1LL << 20;  // mbarrier polls before a wait gives up
 
 __device__ __forceinline__ void load_row_kmaj(unsigned char *tile, const __nv_bfloat16 *__restrict__ src, int tr,
@@ -437,49 +446,60 @@ __device__ __forceinline__ void load_row_kmaj(unsigned char *tile, const __nv_bf
     for (int q = 0; q < cols / 8; q++) *reinterpret_cast<uint4 *>(tile + tc::kmaj_off(tr, q * 8, cols)) = s[q];
 }
 
+// barrier of one 128-thread group (named barrier 1 + group)
+__device__ __forceinline__ void group_sync(int grp) {
+    asm volatile("bar.sync %0, 128;" ::"r"(1 + grp) : "memory");
+}
+
 template <bool GATHER, bool CURV>
-__global__ void __launch_bounds__(128) mlp_fwd_tc_kernel(MlpArgs a) {
+__global__ void __launch_bounds__(TC_THREADS) mlp_fwd_tc_kernel(MlpArgs a) {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     unsigned char *base = (unsigned char *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-    unsigned char *sX = base + TCF_X, *sW1 = base + TCF_W1, *sH1 = base + TCF_H1, *sW2 = base + TCF_W2;
-    uint64_t *mbar = reinterpret_cast<uint64_t *>(base + TCF_MBAR);
+    const int tid = threadIdx.x, grp = tid >> 7, t = tid & 127, wq = (tid >> 5) & 3;
+    unsigned char *sW1 = base + TCF_W1, *sW2 = base + TCF_W2;
+    unsigned char *sX = base + TCF_G0 + grp * TCF_GSTRIDE, *sH1 = sX + 16384;
+    uint64_t *mbar = reinterpret_cast<uint64_t *>(base + TCF_MBAR) + grp;
     uint32_t *tbase = reinterpret_cast<uint32_t *>(base + TCF_TB);
-    uint8_t *sFrag = base + TCF_FRAG;
-    const int tid = threadIdx.x, warp = tid >> 5;
+    uint8_t *sFrag = base + TCF_FRAG + 128 * grp;
+    volatile int *sBad = reinterpret_cast<volatile int *>(base + TCF_BAD) + grp;
     const uint32_t mb = tc::smem_u32(mbar);
-    if (tid == 0) {
+    if (t == 0) {
         tc::mbar_init(mb, 1);
         tc::fence_mbar_init();
+        *sBad = 0;
     }
-    if (warp == 0) tc::tmem_alloc(tc::smem_u32(tbase), 128);
-    load_row_kmaj(sW1, a.w1b, tid, tid, MLP_IN);
-    load_row_kmaj(sW2, a.w2b, tid, tid, MLP_H);
+    if (tid < 32) tc::tmem_alloc(tc::smem_u32(tbase), 512);
+    if (tid < 128) {
+        load_row_kmaj(sW1, a.w1b, tid, tid, MLP_IN);
+        load_row_kmaj(sW2, a.w2b, tid, tid, MLP_H);
+    }
     tc::fence_proxy_async();
     tc::fence_before_sync();
     __syncthreads();
     tc::fence_after_sync();
-    const uint32_t tm = *tbase;
-    const uint32_t lane_base = tm + ((uint32_t)(warp * 32) << 16);
+    const uint32_t tm0 = *tbase;
+    const uint32_t tm = tm0 + (uint32_t)(grp * 128);          // this group's columns
+    const uint32_t lane_base = tm + ((uint32_t)(wq * 32) << 16);
     const int m = a.ncells ? *a.ncells : a.m;
-    // the allocation must start at lane 0 with its 128 columns inside TMEM
-    const bool tm_ok = (tm >> 16) == 0 && (tm & 0xFFFF) + 128 <= 512;
+    // the allocation must be the whole of tensor memory, from lane 0, column 0
+    const bool tm_ok = tm0 == 0;
     const int ntile = tm_ok ? (m + 127) / 128 : 0;
     if (!tm_ok && tid == 0) atomicExch(a.err, 2);
     const uint32_t idesc = tc::idesc_bf16(128, 128);
     uint32_t phase = 0;
     bool ok = true;
-    for (int tile = blockIdx.x; tile < ntile; tile += gridDim.x) {
-        const int row = tile * 128 + tid;
+    for (int tile = blockIdx.x * TC_GROUPS + grp; tile < ntile; tile += gridDim.x * TC_GROUPS) {
+        const int row = tile * 128 + t;
         const bool live = row < m;
         int cell = 0;
-        // ---- inputs: row tid of the tile
+        // ---- inputs: row t of the group's tile
         {
             __nv_bfloat16 v[MLP_IN];
             if (GATHER && live) {
                 cell = a.cells[row];
                 const int x = cell % a.g.n[0], y = (cell / a.g.n[0]) % a.g.n[1], z = cell / (a.g.n[0] * a.g.n[1]);
-                // the block values are staged in the H1 tile (free until layer 1)
-                sFrag[tid] = canon_encode(a.C, a.g, x, y, z, v, reinterpret_cast<float *>(sH1 + tid * 112), 1) ? 1 : 0;
+                // the block values are staged in the group's H1 tile (free until layer 1)
+                sFrag[t] = canon_encode(a.C, a.g, x, y, z, v, reinterpret_cast<float *>(sH1 + t * 112), 1) ? 1 : 0;
             } else if (!GATHER && live) {
                 const uint4 *s4 = reinterpret_cast<const uint4 *>(a.X + (long long)row * MLP_IN);
                 for (int q = 0; q < MLP_IN / 8; q++) reinterpret_cast<uint4 *>(v)[q] = s4[q];
@@ -487,13 +507,13 @@ __global__ void __launch_bounds__(128) mlp_fwd_tc_kernel(MlpArgs a) {
                 for (int q = 0; q < MLP_IN; q++) v[q] = __float2bfloat16_rn(0.0f);
             }
             for (int q = 0; q < MLP_IN / 8; q++)
-                *reinterpret_cast<uint4 *>(sX + tc::kmaj_off(tid, q * 8, MLP_IN)) = reinterpret_cast<uint4 *>(v)[q];
+                *reinterpret_cast<uint4 *>(sX + tc::kmaj_off(t, q * 8, MLP_IN)) = reinterpret_cast<uint4 *>(v)[q];
         }
         tc::fence_proxy_async();
         tc::fence_before_sync();
-        __syncthreads();
+        group_sync(grp);
         // ---- layer 1: D = X W1^T
-        if (tid == 0) {
+        if (t == 0) {
             tc::fence_after_sync();
             const uint32_t ax = tc::smem_u32(sX), aw = tc::smem_u32(sW1);
 #pragma unroll
@@ -502,7 +522,9 @@ __global__ void __launch_bounds__(128) mlp_fwd_tc_kernel(MlpArgs a) {
                              idesc, kk > 0);
             tc::mma_commit(mb);
         }
-        ok = __syncthreads_and(tc::mbar_wait(mb, phase, MLP_WAIT)) != 0;  // the same decision in every thread
+        if (!tc::mbar_wait(mb, phase, MLP_WAIT)) *sBad = 1;
+        group_sync(grp);
+        ok = *sBad == 0;  // the same decision in every thread of the group
         if (!ok) break;
         phase ^= 1;
         tc::fence_after_sync();
@@ -513,13 +535,13 @@ __global__ void __launch_bounds__(128) mlp_fwd_tc_kernel(MlpArgs a) {
             for (int j = 0; j < 32; j++) v[j] = fmaxf(v[j] + ldp(a.params, P_B1 + c * 32 + j), 0.0f);
 #pragma unroll
             for (int q = 0; q < 4; q++)
-                *reinterpret_cast<uint4 *>(sH1 + tc::kmaj_off(tid, c * 32 + q * 8, MLP_H)) = tc::pack8_bf16(v + q * 8);
+                *reinterpret_cast<uint4 *>(sH1 + tc::kmaj_off(t, c * 32 + q * 8, MLP_H)) = tc::pack8_bf16(v + q * 8);
         }
         tc::fence_proxy_async();
         tc::fence_before_sync();
-        __syncthreads();
+        group_sync(grp);
         // ---- layer 2: D = H1 W2^T (the same TMEM columns)
-        if (tid == 0) {
+        if (t == 0) {
             tc::fence_after_sync();
             const uint32_t ah = tc::smem_u32(sH1), aw = tc::smem_u32(sW2);
 #pragma unroll
@@ -528,7 +550,9 @@ __global__ void __launch_bounds__(128) mlp_fwd_tc_kernel(MlpArgs a) {
                              idesc, kk > 0);
             tc::mma_commit(mb);
         }
-        ok = __syncthreads_and(tc::mbar_wait(mb, phase, MLP_WAIT)) != 0;
+        if (!tc::mbar_wait(mb, phase, MLP_WAIT)) *sBad = 1;
+        group_sync(grp);
+        ok = *sBad == 0;
         if (!ok) break;
         phase ^= 1;
         tc::fence_after_sync();
@@ -543,7 +567,7 @@ __global__ void __launch_bounds__(128) mlp_fwd_tc_kernel(MlpArgs a) {
         yv += ldp(a.params, P_B3);
         if (live) {
             if (CURV) {
-                if (a.mode == 2 && (fabsf(yv) > 1.0f || sFrag[tid])) {
+                if (a.mode == 2 && (fabsf(yv) > 1.0f || sFrag[t])) {
                     a.fb[atomicAdd(a.nfb, 1)] = (unsigned)cell;
                 } else {
                     a.kh[cell] = (double)yv;
@@ -554,15 +578,15 @@ __global__ void __launch_bounds__(128) mlp_fwd_tc_kernel(MlpArgs a) {
             }
         }
         tc::fence_before_sync();
-        __syncthreads();
+        group_sync(grp);
     }
     if (!ok) {
-        if (tid == 0) atomicExch(a.err, 1);
+        if (t == 0) atomicExch(a.err, 1);
         tc::mbar_wait(mb, phase, MLP_WAIT);  // an MMA still in flight finishes before the columns are freed
     }
     tc::fence_before_sync();
     __syncthreads();
-    if (warp == 0 && tm_ok) tc::tmem_dealloc(tm, 128);
+    if (tid < 32 && tm_ok) tc::tmem_dealloc(tm0, 512);
 }
 
 // ------------------------------------------------------------ training

@@ -347,7 +347,7 @@ class Mlp:
 
     def __init__(self, params=None, stream=None):
         self.h = ebit_mlp_create(stream)
-        self.path = EBIT_MLP_PATH_MMA
+        self.path = EBIT_MLP_PATH_TCGEN05
         self.nparams = ebit_mlp_nparams()
         if params is not None:
             self.set_params(params)
