@@ -323,6 +323,21 @@ int ebit_batch_set_launch_shape(ebit_batch *b, int ctas_per_sm);
  * the time of each shape, index ctas_per_sm - 1.  Allocates a state copy. */
 int ebit_batch_autotune(ebit_batch *b, int sweeps, double *ms_out);
 const char *ebit_batch_last_error(const ebit_batch *b);
+/* Self-test of the bounded device waits (the grid barrier of the batched
+ * sweep and the mbarrier waits of the tensor-core kernels), run on
+ * cuda_stream (NULL: the legacy default stream).  Each wait runs twice in a
+ * tiny kernel with a short poll limit: once where the awaited event comes
+ * (two blocks both reach the barrier; one arrival on the mbarrier), once
+ * where it never comes (one block leaves without arriving; nobody arrives),
+ * so that the wait must give up.  The second case shows, without any fault
+ * or hang, that a wait which runs out returns, sets the error flag the host
+ * reads, and leaves the device usable.  report (host, may be NULL) gets six
+ * ints: barrier result and error flag when both blocks arrive (1, 0), barrier
+ * result and error flag when one is absent (0, 1), mbarrier result with and
+ * without the arrival (1, 0).  Returns EBIT_OK when all six are as stated,
+ * EBIT_ETIMEOUT otherwise, EBIT_ENOMEM / EBIT_ECUDA if its 64-byte buffer
+ * cannot be allocated or a launch or copy fails. */
+int ebit_selftest_bounded_waits(void *cuda_stream, int *report);
 
 /* One split advection sweep that allocates no device memory.
  * The paper has no counterpart: this entry point exists for callers that

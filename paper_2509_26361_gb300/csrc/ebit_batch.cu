@@ -31,6 +31,7 @@
 #include "common.cuh"
 #include "ctx.h"
 #include "sweep.cuh"
+#include "tc.cuh"
 
 namespace ebit {
 
@@ -56,8 +57,9 @@ struct BatchParams {
     int *err;
 };
 
-// Grid-wide barrier of a cooperative launch (all blocks co-resident).
-__device__ bool grid_barrier(const BatchParams &p, int *s_ok) {
+// Grid-wide barrier of a cooperative launch (all blocks co-resident); gives up
+// after max_polls polls, sets the error flag and returns false.
+__device__ bool grid_barrier(const BatchParams &p, int *s_ok, long long max_polls = BAR_POLLS) {
     __syncthreads();
     if (threadIdx.x == 0) {
         int ok = 1;
@@ -72,7 +74,7 @@ __device__ bool grid_barrier(const BatchParams &p, int *s_ok) {
         } else {
             long long it = 0;
             while (*gen == g0) {
-                if (++it > BAR_POLLS) {
+                if (++it > max_polls) {
                     atomicExch(p.err, 1);
                     ok = 0;
                     break;
@@ -202,6 +204,35 @@ __global__ void __launch_bounds__(BATCH_THREADS, 4) batch_sweep_kernel(BatchPara
             for (int k = 0; k < C_N; k++)
                 if (k != C_MARKERS && ev[k]) atomicAdd(p.inst[i].a.ctr + k, (unsigned long long)ev[k]);
         }
+    }
+}
+
+// Self-tests of the bounded waits.  Each makes one wait either succeed or wait
+// for an event that never comes, with a short poll limit, and records whether
+// it returned true; nothing faults and nothing hangs.
+//
+// Two blocks meet at the grid barrier; with `absent` set, block 1 leaves
+// without arriving, so block 0 waits for a generation that never comes.
+__global__ void selftest_barrier_kernel(BatchParams p, int absent, long long polls, int *ok_out) {
+    __shared__ int s_ok;
+    if (absent && blockIdx.x == 1) return;
+    const bool ok = grid_barrier(p, &s_ok, polls);
+    if (blockIdx.x == 0 && threadIdx.x == 0) *ok_out = ok ? 1 : 0;
+}
+
+// An mbarrier expecting one arrival; with `arrive` clear nobody arrives, so
+// the wait on its first phase never succeeds.
+__global__ void selftest_mbarrier_kernel(int arrive, long long polls, int *ok_out) {
+    __shared__ __align__(8) uint64_t mbar;
+    const uint32_t mb = tc::smem_u32(&mbar);
+    if (threadIdx.x == 0) {
+        tc::mbar_init(mb, 1);
+        tc::fence_mbar_init();
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        if (arrive) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(mb) : "memory");
+        *ok_out = tc::mbar_wait(mb, 0, polls) ? 1 : 0;
     }
 }
 
@@ -819,5 +850,48 @@ int ebit_batch_autotune(ebit_batch *b, int sweeps, double *ms_out) {
 }
 
 const char *ebit_batch_last_error(const ebit_batch *b) { return b ? b->errmsg.c_str() : "null batch"; }
+
+int ebit_selftest_bounded_waits(void *cuda_stream, int *report) {
+    cudaStream_t st = (cudaStream_t)cuda_stream;
+    int *d = nullptr;
+    if (cudaMalloc((void **)&d, 16 * sizeof(int)) != cudaSuccess) {
+        cudaGetLastError();
+        return EBIT_ENOMEM;
+    }
+    // slots: 0..3 results; 4..5 / 8..9 barrier words; 6 / 10 error flags
+    int h[16] = {0};
+    bool ok = cudaMemsetAsync(d, 0, 16 * sizeof(int), st) == cudaSuccess;
+    for (int absent = 0; absent < 2 && ok; absent++) {
+        BatchParams p{};
+        p.bar = (unsigned *)(d + 4 + 4 * absent);
+        p.err = d + 6 + 4 * absent;
+        int *out = d + absent;
+        long long polls = absent ? 4096 : (1LL << 20);
+        void *args[] = {&p, &absent, &polls, &out};
+        ok = cudaLaunchCooperativeKernel((const void *)selftest_barrier_kernel, dim3(2), dim3(32), args, 0, st) ==
+             cudaSuccess;
+    }
+    if (ok) {
+        selftest_mbarrier_kernel<<<1, 32, 0, st>>>(1, 1 << 20, d + 2);
+        selftest_mbarrier_kernel<<<1, 32, 0, st>>>(0, 64, d + 3);
+        ok = cudaGetLastError() == cudaSuccess &&
+             cudaMemcpyAsync(h, d, sizeof(h), cudaMemcpyDeviceToHost, st) == cudaSuccess &&
+             cudaStreamSynchronize(st) == cudaSuccess;
+    }
+    // the device still takes work after the waits gave up
+    ok = ok && cudaMemsetAsync(d, 0, 16 * sizeof(int), st) == cudaSuccess && cudaStreamSynchronize(st) == cudaSuccess;
+    cudaFree(d);
+    if (!ok) {
+        cudaGetLastError();
+        return EBIT_ECUDA;
+    }
+    if (report) {
+        const int r[6] = {h[0], h[6], h[1], h[10], h[2], h[3]};
+        std::memcpy(report, r, sizeof(r));
+    }
+    const bool met = h[0] == 1 && h[6] == 0 && h[2] == 1;      // the waits that can succeed did
+    const bool gave_up = h[1] == 0 && h[10] == 1 && h[3] == 0; // the others gave up and said so
+    return met && gave_up ? EBIT_OK : EBIT_ETIMEOUT;
+}
 
 }  // extern "C"

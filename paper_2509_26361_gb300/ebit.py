@@ -105,6 +105,7 @@ def load(build_if_missing: bool = True):
     lib.ebit_last_error.restype = ctypes.c_char_p
     lib.ebit_batch_create.argtypes = [I, ctypes.POINTER(_Desc), ctypes.POINTER(ctypes.c_void_p)]
     lib.ebit_batch_destroy.argtypes = [P]
+    lib.ebit_selftest_bounded_waits.argtypes = [P, P]
     lib.ebit_batch_destroy.restype = None
     lib.ebit_batch_size.argtypes = [P]
     lib.ebit_batch_instance.argtypes = [P, I]
@@ -251,6 +252,17 @@ def ebit_advect_sweep_noalloc(n3, h, d, cb_in, s_in, u_face, dt, cb_out, s_out, 
 
 def ebit_last_error(ctx):
     return load().ebit_last_error(ctx).decode()
+
+
+def ebit_selftest_bounded_waits(stream=None):
+    """Runs the self-test of the bounded device waits (see include/ebit.h);
+    returns (code, report) with report the six ints it fills."""
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    sp = stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream)
+    rep = (ctypes.c_int * 6)()
+    code = load().ebit_selftest_bounded_waits(ctypes.c_void_p(sp), rep)
+    return code, list(rep)
 
 
 # ------------------------------------------------------- learned curvature
