@@ -177,25 +177,37 @@ def run_gpu(args, rank, world):
     st = torch.zeros(g.shape, dtype=torch.uint8, device=dev)
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)  # 256 MiB > L2
 
-    def one_step(n):
+    def one_step(n, sweep_ev=None):
+        """One step; with sweep_ev, CUDA events on the context's stream bracket
+        each split-sweep call (band + advect + integer pass + FP64 lists)."""
         dt = w.lam(n) * g.h
-        g.step(n, ud, dt)
+        for j, d in enumerate((0, 1, 2) if n % 2 == 0 else (2, 1, 0)):
+            if sweep_ev is not None:
+                sweep_ev[j][0].record()
+            g.sweep(d, ud[d], dt)
+            if sweep_ev is not None:
+                sweep_ev[j][1].record()
         g.front2vof(C)
         g.curvature(C, kh, st)
 
-    g.init(phi, faces)
-    g.front2vof(C, ebit.EBIT_FULL)
-    g.curvature(C, kh, st, flags=ebit.EBIT_FULL)
-    for n in range(args.warmup):
-        one_step(n)
-    torch.cuda.synchronize()
-    g.reset_counters()
-    g.profile(True)
+    def start():
+        g.init(phi, faces)
+        g.front2vof(C, ebit.EBIT_FULL)
+        g.curvature(C, kh, st, flags=ebit.EBIT_FULL)
+        for n in range(args.warmup):
+            one_step(n)
+        torch.cuda.synchronize()
+        g.reset_counters()
+
+    E = lambda: torch.cuda.Event(enable_timing=True)
+    # ---- timed region: value, and the split sweep's duration for the roofline
+    start()
     clocks = ClockSampler()
     if rank == 0:
         clocks.start()
         time.sleep(0.3)
-    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    evs = [(E(), E()) for _ in range(args.steps)]
+    sev = [[(E(), E()) for _ in range(3)] for _ in range(args.steps)]
     if world > 1:
         import torch.distributed as dist
         dist.barrier()
@@ -204,16 +216,15 @@ def run_gpu(args, rank, world):
     for i in range(args.steps):
         flush.zero_()
         evs[i][0].record()
-        one_step(args.warmup + i)
+        one_step(args.warmup + i, sev[i])
         evs[i][1].record()
     torch.cuda.synchronize()
     wall1 = time.perf_counter()
     if world > 1:
         dist.barrier()
     step_ms = [a.elapsed_time(b) for a, b in evs]
+    sweep_ms = [a.elapsed_time(b) for r in sev for a, b in r]
     total_ms = float(sum(step_ms))
-    prof = g.profile_read()
-    g.profile(False)
     cnt = g.counters()
     total_ms = max_over_ranks(total_ms, world, dev)
 
@@ -223,8 +234,21 @@ def run_gpu(args, rank, world):
         e2e = run_e2e(args, g, w, dev, C, kh, st)
     clk = clocks.summary(wall0, wall1) if rank == 0 else None
     clocks.stop()
+
+    # ---- instrumented pass over the same steps: an event pair around every
+    # kernel launch of the library (per-kernel times and launch counts; the
+    # events slow the step, so none of its times enter value or roofline)
+    start()
+    g.profile(True)
+    for i in range(args.steps):
+        flush.zero_()
+        one_step(args.warmup + i)
+    torch.cuda.synchronize()
+    prof = g.profile_read()
+    g.profile(False)
     g.close()
-    return dict(total_ms=total_ms, step_ms=step_ms, prof=prof, cnt=cnt, nc=nc, w=w, e2e=e2e, clk=clk)
+    return dict(total_ms=total_ms, step_ms=step_ms, sweep_ms=sweep_ms, prof=prof, cnt=cnt, nc=nc, w=w, e2e=e2e,
+                clk=clk)
 
 
 def run_e2e(args, g, w, dev, C, kh, st):
@@ -269,23 +293,23 @@ F2V_BYTES_PER_CELL = 36.4
 def roofline_block(res):
     """The dominant stage is the split sweep (its band, advect, integer-pass and
     FP64-list launches; the scope table defines its algorithmic bytes per band
-    cell).  achieved = 62.75 B x band cells per sweep / device time per sweep,
-    summed from CUDA events around each of its launches on the context's
-    stream.  The marker-level minimum (colour bytes of the band, offsets and
-    one velocity sample per marker) is given beside it."""
+    cell).  achieved = 62.75 B x band cells per sweep / mean duration of a
+    split-sweep call, from the CUDA events that bracket each call on the
+    context's stream inside the timed region.  The marker-level minimum (colour
+    bytes of the band, offsets and one velocity sample per marker) is given
+    beside it; per-kernel times come from the instrumented pass."""
     hbm, src = peaks()
     prof = res["prof"]
     cnt = res["cnt"]
-    nsweeps = prof["sweep"][1]
-    stage_ms = sum(prof[k][0] for k in ("band", "advect", "sweep", "fp64") if k in prof)
-    per_sweep_s = stage_ms * 1e-3 / nsweeps
+    nsweeps = len(res["sweep_ms"])
+    per_sweep_s = float(np.mean(res["sweep_ms"])) * 1e-3
     band_cells = cnt["tiles"] / nsweeps * 512.0
     markers = cnt["markers"] / nsweeps
     alg = SWEEP_BYTES_PER_CELL * band_cells
     alg_min = 2.0 * band_cells + 24.0 * markers
     achieved = alg / per_sweep_s / 1e9
     traffic = sum(NCU_TRAFFIC.values()) if NCU_TRAFFIC else None
-    stages = {"split_sweep": stage_ms,
+    stages = {"split_sweep": sum(prof[k][0] for k in ("band", "advect", "sweep", "fp64") if k in prof),
               "front2vof": prof.get("f2v", (0.0, 0))[0],
               "curvature": prof.get("hf", (0.0, 0))[0] + prof.get("scan", (0.0, 0))[0]}
     return {"bound": "hbm", "kernel": "split sweep (band + advect + integer pass + FP64 lists)",
@@ -294,8 +318,9 @@ def roofline_block(res):
             "band_cells_per_sweep": band_cells, "markers_per_sweep": markers,
             "min_bytes_per_sweep": alg_min, "min_frac": alg_min / per_sweep_s / 1e9 / hbm,
             "avg_sweep_us": per_sweep_s * 1e6,
-            "stage_ms": {k: round(v, 4) for k, v in stages.items()},
-            "kernel_ms": {k: round(v[0], 4) for k, v in prof.items()},
+            "timing": "CUDA events around each split-sweep call in the timed region",
+            "instrumented_stage_ms": {k: round(v, 4) for k, v in stages.items()},
+            "instrumented_kernel_ms": {k: round(v[0], 4) for k, v in prof.items()},
             "kernel_launches": {k: v[1] for k, v in prof.items()}}
 
 
@@ -403,8 +428,10 @@ def large_block(steps=20, warmup=3):
     """The 512^3 configuration: two seeded ellipsoidal drops (semi-axes U[40, 80]
     cells) driven together by a Fourier field plus a converging cellular mode,
     dt = 0.5 h; one step = 3 split sweeps + Front2VOF + learned curvature with
-    height-function fallback.  Timed with CUDA events per step after an L2
-    flush; the band roofline of the split sweep, and the dense-equivalent rate
+    height-function fallback.  Timed with CUDA events per step (and per
+    split-sweep call, for the roofline) after an L2 flush; per-kernel times
+    come from an instrumented pass over the following steps.  Reported: the
+    band roofline of the split sweep, and the dense-equivalent rate
     (the scope table's 224.6 B per cell-step of advection + Front2VOF over all
     512^3 cells) for comparison with a dense implementation."""
     import torch
@@ -427,38 +454,51 @@ def large_block(steps=20, warmup=3):
     st = torch.zeros(g.shape, dtype=torch.uint8, device="cuda")
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
 
-    def one(n):
-        g.step(n, ud, w.lam(n) * g.h)
+    def one(n, sweep_ev=None):
+        dt = w.lam(n) * g.h
+        for j, d in enumerate((0, 1, 2) if n % 2 == 0 else (2, 1, 0)):
+            if sweep_ev is not None:
+                sweep_ev[j][0].record()
+            g.sweep(d, ud[d], dt)
+            if sweep_ev is not None:
+                sweep_ev[j][1].record()
         g.front2vof(C)
         g.curvature(C, kh, st, mode=mode)
 
+    E = lambda: torch.cuda.Event(enable_timing=True)
     g.front2vof(C, ebit.EBIT_FULL)
     g.curvature(C, kh, st, mode=mode, flags=ebit.EBIT_FULL)
     for n in range(warmup):
         one(n)
     torch.cuda.synchronize()
     g.reset_counters()
-    g.profile(True)
-    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    evs = [(E(), E()) for _ in range(steps)]
+    sev = [[(E(), E()) for _ in range(3)] for _ in range(steps)]
     for i in range(steps):
         flush.zero_()
         evs[i][0].record()
-        one(warmup + i)
+        one(warmup + i, sev[i])
         evs[i][1].record()
     torch.cuda.synchronize()
     ms = sum(a.elapsed_time(b) for a, b in evs)
+    sweep_ms = [a.elapsed_time(b) for r in sev for a, b in r]
+    cnt = g.counters()
+    # instrumented pass over the following steps: per-kernel times
+    g.profile(True)
+    for i in range(steps):
+        flush.zero_()
+        one(warmup + steps + i)
+    torch.cuda.synchronize()
     prof = g.profile_read()
     g.profile(False)
-    cnt = g.counters()
     g.close()
     if mlp is not None:
         mlp.close()
     cells = 512 ** 3
-    nsw = prof["sweep"][1]
-    stage_ms = sum(prof[k][0] for k in ("band", "advect", "sweep", "fp64") if k in prof)
+    nsw = len(sweep_ms)
     band_cells = cnt["tiles"] / nsw * 512.0
     hbm, src = peaks()
-    achieved = SWEEP_BYTES_PER_CELL * band_cells / (stage_ms * 1e-3 / nsw) / 1e9
+    achieved = SWEEP_BYTES_PER_CELL * band_cells / (float(np.mean(sweep_ms)) * 1e-3) / 1e9
     dense = (3 * SWEEP_BYTES_PER_CELL + F2V_BYTES_PER_CELL) * cells * steps / (ms * 1e-3) / 1e9
     return {"workload": "merging_drops_512 (two ellipsoids, semi-axes U[40,80] cells, gap 8 cells, seed 5)",
             "value": cells * steps / (ms * 1e-3), "unit": "cell-steps/s", "steps": steps, "warmup": warmup,
@@ -468,7 +508,8 @@ def large_block(steps=20, warmup=3):
                          "frac": achieved / hbm, "peak_source": src},
             "dense_equivalent": {"achieved": dense, "unit": "GB/s", "frac": dense / hbm,
                                  "rule": "224.6 B per cell-step over all 512^3 cells"},
-            "kernel_ms": {k: round(v[0], 3) for k, v in prof.items()},
+            "avg_sweep_us": float(np.mean(sweep_ms)) * 1e3,
+            "kernel_ms_instrumented": {k: round(v[0], 3) for k, v in prof.items()},
             "l2": "flushed (256 MiB write) before every timed step, outside its events"}
 
 
@@ -516,7 +557,8 @@ def main():
         return 0
     value = job_value(res["nc"], args.steps, world, res["total_ms"])
     prof = res["prof"]
-    # every profiled scope brackets exactly one kernel launch
+    # every profiled scope brackets exactly one kernel launch; the instrumented
+    # pass runs the same steps from the same state as the timed region
     launches = sum(v[1] for v in prof.values())
     line = {"metric": METRIC, "value": value, "unit": "cell-steps/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": res["total_ms"] / args.steps, "higher_is_better": True,
