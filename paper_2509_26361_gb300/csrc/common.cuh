@@ -12,6 +12,19 @@
 
 namespace ebit {
 
+// Programmatic dependent launch.  The kernels of a step are launched with
+// programmatic stream serialization, so the next kernel in the stream is
+// launched as the blocks of the current one exit, overlapping its launch with
+// the current kernel's tail.  Every such kernel calls pdl_wait() before its
+// first access to global memory: it returns once the preceding kernel has
+// completed and its writes are visible (and so, by induction, every earlier
+// one).  None of them releases its dependents early
+// (griddepcontrol.launch_dependents): grids sized to full occupancy then had
+// the next kernel's waiting blocks take the slots of exiting ones unevenly,
+// which measured slower than the release at exit.  For an ordinary launch
+// pdl_wait() is a no-op.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
 constexpr double ONE_MINUS = 0.99999999999999988898;  // 1 - 2^-53, largest offset below 1
 constexpr int TILE = 8;                               // tile edge (cells)
 constexpr int TILE_CELLS = TILE * TILE * TILE;

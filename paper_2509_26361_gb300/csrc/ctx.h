@@ -38,8 +38,11 @@ struct ebit_ctx {
     int cur;
     uint32_t *tile_marker;    // per tile: proximity mask of its markers (see near_bits)
     uint8_t *tile_dirty, *tile_cchg;
-    int *band_list, *band_count;
-    int *work_list, *work_count;
+    int *band_list, *band_count;  // band_count[2]: one slot per sweep parity
+    int band_par;                 // slot of the next sweep's band list (0 on entry)
+    int band_last;                // slot of the last sweep's band list
+    int *work_list, *work_count;  // work_count[2]: one slot per incremental Front2VOF parity
+    int f2v_par;
     int *all_list, *all_count;
     unsigned long long *ctr;  // C_N event counters + Front2VOF inconsistencies
     double *scratch;          // 3N doubles, allocated on first ebit_get_state
@@ -50,8 +53,9 @@ struct ebit_ctx {
     unsigned *cut;            // cells cut by the interface at the last Front2VOF
     int *ncut;
     unsigned *iface[2];       // interface cells of the last two curvature calls
-    int *niface;              // [2]
-    int cur_if;
+    int *niface;              // [3] list lengths, one slot per curvature call modulo 3
+    int cur_if;               // list buffer of the last curvature call
+    int if_slot;              // length slot of the next call (0 on entry)
     unsigned *scan;           // interface cells found by a full curvature scan
     int *nscan;
     int *zero;                // a device int that stays 0

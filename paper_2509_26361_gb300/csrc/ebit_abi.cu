@@ -45,6 +45,34 @@ int launch_check(ebit_ctx *ctx, const char *what) {
     return EBIT_OK;
 }
 
+// Launch with programmatic stream serialization: the kernel is launched as
+// the previous kernel's blocks exit, and waits (pdl_wait) for that kernel's
+// completion before it touches global memory.  Counters that a
+// launch appends to are cleared by an earlier kernel of the chain (in its
+// zero arguments) instead of by memsets, which would break the overlap.
+template <typename... KArgs, typename... Args>
+cudaError_t launch_pdl(void (*kernel)(KArgs...), int grid, int block, size_t smem, cudaStream_t st, Args... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(block);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kernel, args...);
+}
+
+int launched(ebit_ctx *ctx, cudaError_t e, const char *what) {
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(ctx, EBIT_ECUDA, std::string(what) + ": " + cudaGetErrorString(e));
+    }
+    return launch_check(ctx, what);
+}
+
 int mark_all(ebit_ctx *ctx) {
     ctx->sweeps_since_f2v = 1;
     CU(cudaMemsetAsync(ctx->tile_marker, 0xFF, ctx->g.ntiles * sizeof(uint32_t), ctx->stream));
@@ -109,19 +137,16 @@ template <int D>
 int sweep_launch(ebit_ctx *ctx, const SweepArgs &args) {
     {
         ProfScope ps(ctx, EBIT_PROF_ADVECT);
-        advect_kernel<D><<<ctx->grid_adv, 256, 0, ctx->stream>>>(args);
-        int r = launch_check(ctx, "advect_kernel");
+        int r = launched(ctx, launch_pdl(advect_kernel<D>, ctx->grid_adv, 256, 0, ctx->stream, args), "advect_kernel");
         if (r) return r;
     }
     {
         ProfScope ps(ctx, EBIT_PROF_SWEEP);
-        sweep_kernel<D><<<ctx->grid_sweep, 256, 0, ctx->stream>>>(args);
-        int r = launch_check(ctx, "sweep_kernel");
+        int r = launched(ctx, launch_pdl(sweep_kernel<D>, ctx->grid_sweep, 256, 0, ctx->stream, args), "sweep_kernel");
         if (r) return r;
     }
     ProfScope ps(ctx, EBIT_PROF_FP64);
-    fp64_kernel<D><<<ctx->grid_fp64, 128, 0, ctx->stream>>>(args);
-    return launch_check(ctx, "fp64_kernel");
+    return launched(ctx, launch_pdl(fp64_kernel<D>, ctx->grid_fp64, 128, 0, ctx->stream, args), "fp64_kernel");
 }
 
 }  // namespace
@@ -150,6 +175,9 @@ static int create_ctx(const ebit_desc *desc, const ebit_state_arrays *st, ebit_c
     ctx->wcount = ctx->ncut = ctx->niface = ctx->nscan = ctx->zero = nullptr;
     ctx->cut = ctx->scan = nullptr;
     ctx->cur_if = 0;
+    ctx->if_slot = 0;
+    ctx->band_par = ctx->band_last = 0;
+    ctx->f2v_par = 0;
     ctx->sweeps_since_f2v = 0;
     ctx->mlp = nullptr;
     ctx->own_mlp = nullptr;
@@ -203,11 +231,11 @@ static int create_ctx(const ebit_desc *desc, const ebit_state_arrays *st, ebit_c
     ok = ok && alloc((void **)&ctx->cut, ctx->N * sizeof(unsigned)) && alloc((void **)&ctx->scan, ctx->N * sizeof(unsigned)) &&
          alloc((void **)&ctx->iface[0], ctx->N * sizeof(unsigned)) &&
          alloc((void **)&ctx->iface[1], ctx->N * sizeof(unsigned)) &&
-         alloc((void **)&ctx->ncut, sizeof(int)) && alloc((void **)&ctx->niface, 2 * sizeof(int)) &&
+         alloc((void **)&ctx->ncut, sizeof(int)) && alloc((void **)&ctx->niface, 3 * sizeof(int)) &&
          alloc((void **)&ctx->nscan, sizeof(int)) && alloc((void **)&ctx->zero, sizeof(int));
     ok = ok && alloc((void **)&ctx->tile_cchg, nt) && alloc((void **)&ctx->band_list, nt * sizeof(int)) &&
-         alloc((void **)&ctx->band_count, sizeof(int)) && alloc((void **)&ctx->work_list, nt * sizeof(int)) &&
-         alloc((void **)&ctx->work_count, sizeof(int)) && alloc((void **)&ctx->all_list, nt * sizeof(int)) &&
+         alloc((void **)&ctx->band_count, 2 * sizeof(int)) && alloc((void **)&ctx->work_list, nt * sizeof(int)) &&
+         alloc((void **)&ctx->work_count, 2 * sizeof(int)) && alloc((void **)&ctx->all_list, nt * sizeof(int)) &&
          alloc((void **)&ctx->all_count, sizeof(int));
     if (!ok) {
         cudaGetLastError();
@@ -231,7 +259,9 @@ static int create_ctx(const ebit_desc *desc, const ebit_state_arrays *st, ebit_c
     ctx->grid_hfl = ctx->sms * std::max(occ, 1);
     cudaMemsetAsync(ctx->wcount, 0, 4 * sizeof(int), ctx->stream);
     cudaMemsetAsync(ctx->ncut, 0, sizeof(int), ctx->stream);
-    cudaMemsetAsync(ctx->niface, 0, 2 * sizeof(int), ctx->stream);
+    cudaMemsetAsync(ctx->niface, 0, 3 * sizeof(int), ctx->stream);
+    cudaMemsetAsync(ctx->band_count, 0, 2 * sizeof(int), ctx->stream);
+    cudaMemsetAsync(ctx->work_count, 0, 2 * sizeof(int), ctx->stream);
     cudaMemsetAsync(ctx->nscan, 0, sizeof(int), ctx->stream);
     cudaMemsetAsync(ctx->zero, 0, sizeof(int), ctx->stream);
     iota_kernel<<<blocks_for(nt, 256, ctx->sms), 256, 0, ctx->stream>>>(ctx->all_list, nt, ctx->all_count);
@@ -346,14 +376,20 @@ int ebit_advect_sweep(ebit_ctx *ctx, int dir, const double *u_face, double dt) {
         list = ctx->all_list;
         count = ctx->all_count;
     } else {
+        // band_count[bp] is 0 (cleared by the previous sweep's band kernel,
+        // or at creation); this one clears the other slot for the next sweep
         ProfScope ps(ctx, EBIT_PROF_BAND);
-        CU(cudaMemsetAsync(ctx->band_count, 0, sizeof(int), ctx->stream));
-        band_kernel<<<blocks_for(ctx->g.ntiles, 256, ctx->sms), 256, 0, ctx->stream>>>(
-            ctx->g, ctx->tile_marker, ctx->band_list, ctx->band_count);
-        int r = launch_check(ctx, "band_kernel");
+        const int bp = ctx->band_par;
+        int r = launched(ctx,
+                         launch_pdl(band_kernel, blocks_for(ctx->g.ntiles, 256, ctx->sms), 256, 0, ctx->stream, ctx->g,
+                                    (const uint32_t *)ctx->tile_marker, ctx->band_list, ctx->band_count + bp,
+                                    ctx->band_count + (bp ^ 1)),
+                         "band_kernel");
         if (r) return r;
         list = ctx->band_list;
-        count = ctx->band_count;
+        count = ctx->band_count + bp;
+        ctx->band_last = bp;
+        ctx->band_par = bp ^ 1;
     }
     SweepArgs a;
     a.g = ctx->g;
@@ -393,20 +429,26 @@ int ebit_front2vof(ebit_ctx *ctx, double *C, int flags) {
     bool full = (flags & EBIT_FULL) || ctx->dense || C != ctx->last_C;
     // nothing was swept since the last call on this buffer: C is current
     if (!full && ctx->sweeps_since_f2v == 0) return EBIT_OK;
-    CU(cudaMemsetAsync(ctx->ncut, 0, sizeof(int), ctx->stream));
     if (full) {
+        CU(cudaMemsetAsync(ctx->ncut, 0, sizeof(int), ctx->stream));
         CU(cudaMemsetAsync(ctx->tile_dirty, 0, ctx->g.ntiles, ctx->stream));
         list = ctx->all_list;
         count = ctx->all_count;
     } else {
+        // work_count[fp] is 0; the tile-list kernel clears the other slot for
+        // the next incremental call, and the cut-cell count (its readers, the
+        // previous Front2VOF and curvature, are complete)
         ProfScope ps(ctx, EBIT_PROF_F2V);
-        CU(cudaMemsetAsync(ctx->work_count, 0, sizeof(int), ctx->stream));
-        take_flagged_kernel<<<blocks_for(ctx->g.ntiles, 256, ctx->sms), 256, 0, ctx->stream>>>(
-            ctx->g, ctx->tile_dirty, ctx->work_list, ctx->work_count);
-        int r = launch_check(ctx, "take_flagged_kernel");
+        const int fp = ctx->f2v_par;
+        int r = launched(ctx,
+                         launch_pdl(take_flagged_kernel, blocks_for(ctx->g.ntiles, 256, ctx->sms), 256, 0, ctx->stream,
+                                    ctx->g, ctx->tile_dirty, ctx->work_list, ctx->work_count + fp,
+                                    ctx->work_count + (fp ^ 1), ctx->ncut),
+                         "take_flagged_kernel");
         if (r) return r;
         list = ctx->work_list;
-        count = ctx->work_count;
+        count = ctx->work_count + fp;
+        ctx->f2v_par = fp ^ 1;
     }
     F2VArgs a;
     a.g = ctx->g;
@@ -422,14 +464,12 @@ int ebit_front2vof(ebit_ctx *ctx, double *C, int flags) {
     int r;
     {
         ProfScope ps(ctx, EBIT_PROF_F2V);
-        f2v_band_kernel<<<ctx->grid_f2v, 256, 0, ctx->stream>>>(a);
-        r = launch_check(ctx, "f2v_band_kernel");
+        r = launched(ctx, launch_pdl(f2v_band_kernel, ctx->grid_f2v, 256, 0, ctx->stream, a), "f2v_band_kernel");
     }
     if (r) return r;
     {
         ProfScope ps(ctx, EBIT_PROF_F2V);
-        f2v_list_kernel<<<ctx->grid_f2vl, 128, 0, ctx->stream>>>(a);
-        r = launch_check(ctx, "f2v_list_kernel");
+        r = launched(ctx, launch_pdl(f2v_list_kernel, ctx->grid_f2vl, 128, 0, ctx->stream, a), "f2v_list_kernel");
     }
     if (r) return r;
     ctx->last_C = C;
@@ -445,22 +485,28 @@ int ebit_curvature(ebit_ctx *ctx, const double *C, double *kappa_h, uint8_t *sta
     bool full = (flags & EBIT_FULL) || ctx->dense || C != ctx->last_C || kappa_h != ctx->last_kh ||
                 status != ctx->last_st;
     const int nw = ctx->cur_if ^ 1;
+    // list lengths rotate over three slots: this call appends to slot cs
+    // (0, cleared by the previous call), reads the previous call's length in
+    // slot cprev, and clears slot cnext (last read by the previous call) for
+    // the next call
+    const int cs = ctx->if_slot, cnext = (cs + 1) % 3, cprev = (cs + 2) % 3;
     HFArgs a;
     a.g = ctx->g;
     a.C = C;
     a.kh = kappa_h;
     a.st = status;
     a.iface = ctx->iface[nw];
-    a.niface = ctx->niface + nw;
+    a.niface = ctx->niface + cs;
     a.list = ctx->all_list;
     a.count = ctx->all_count;
-    CU(cudaMemsetAsync(ctx->niface + nw, 0, sizeof(int), ctx->stream));
+    a.zero[0] = ctx->niface + cnext;
+    a.zero[1] = nullptr;
     if (full) {
         // any C: scan every tile, reset non-interface cells, list the interface cells
         ProfScope ps(ctx, EBIT_PROF_SCAN);
         CU(cudaMemsetAsync(ctx->nscan, 0, sizeof(int), ctx->stream));
-        hf_scan_kernel<<<ctx->grid_hf, 256, 0, ctx->stream>>>(a, ctx->scan, ctx->nscan);
-        int r = launch_check(ctx, "hf_scan_kernel");
+        int r = launched(ctx, launch_pdl(hf_scan_kernel, ctx->grid_hf, 256, 0, ctx->stream, a, ctx->scan, ctx->nscan),
+                         "hf_scan_kernel");
         if (r) return r;
         a.prev = ctx->iface[ctx->cur_if];
         a.nprev = ctx->zero;
@@ -469,18 +515,19 @@ int ebit_curvature(ebit_ctx *ctx, const double *C, double *kappa_h, uint8_t *sta
     } else {
         // C is this context's Front2VOF output: its cut cells hold every interface cell
         a.prev = ctx->iface[ctx->cur_if];
-        a.nprev = ctx->niface + ctx->cur_if;
+        a.nprev = ctx->niface + cprev;
         a.cand = ctx->cut;
         a.ncand = ctx->ncut;
+        // the fallback list of the learned pass below starts empty
+        if (mode != EBIT_CURV_HF) a.zero[1] = ctx->nscan;
     }
     {
         // height functions on every interface cell (mode HF), or only the list
         ProfScope ps(ctx, EBIT_PROF_HF);
-        if (mode == EBIT_CURV_HF)
-            hf_list_kernel<true><<<ctx->grid_hfl, 128, 0, ctx->stream>>>(a);
-        else
-            hf_list_kernel<false><<<ctx->grid_hfl, 128, 0, ctx->stream>>>(a);
-        int r = launch_check(ctx, "hf_list_kernel");
+        cudaError_t e = (mode == EBIT_CURV_HF)
+                            ? launch_pdl(hf_list_kernel<true>, ctx->grid_hfl, 128, 0, ctx->stream, a)
+                            : launch_pdl(hf_list_kernel<false>, ctx->grid_hfl, 128, 0, ctx->stream, a);
+        int r = launched(ctx, e, "hf_list_kernel");
         if (r) return r;
     }
     if (mode != EBIT_CURV_HF) {
@@ -490,7 +537,7 @@ int ebit_curvature(ebit_ctx *ctx, const double *C, double *kappa_h, uint8_t *sta
         m.g = ctx->g;
         m.C = C;
         m.cells = reinterpret_cast<const int *>(ctx->iface[nw]);
-        m.ncells = ctx->niface + nw;
+        m.ncells = ctx->niface + cs;
         m.params = ctx->mlp->p;
         m.w1b = ctx->mlp->w1b;
         m.w2b = ctx->mlp->w2b;
@@ -499,16 +546,17 @@ int ebit_curvature(ebit_ctx *ctx, const double *C, double *kappa_h, uint8_t *sta
         m.mode = mode;
         m.fb = ctx->scan;  // free again: the listing pass above has consumed it
         m.nfb = ctx->nscan;
-        CU(cudaMemsetAsync(ctx->nscan, 0, sizeof(int), ctx->stream));
+        if (full) CU(cudaMemsetAsync(ctx->nscan, 0, sizeof(int), ctx->stream));
         int r;
         {
             ProfScope pm(ctx, EBIT_PROF_MLP);
             m.err = ctx->mlp->err;
-            if (ctx->mlp->path == EBIT_MLP_PATH_TCGEN05)
-                mlp_fwd_tc_kernel<true, true><<<ctx->sms, TC_THREADS, FWD_TC_SMEM, ctx->stream>>>(m);
-            else
-                mlp_fwd_kernel<true, true><<<ctx->mlp->fwd_blocks * ctx->sms, 128, FWD_SMEM, ctx->stream>>>(m);
-            r = launch_check(ctx, "mlp_fwd_kernel");
+            cudaError_t e =
+                (ctx->mlp->path == EBIT_MLP_PATH_TCGEN05)
+                    ? launch_pdl(mlp_fwd_tc_kernel<true, true>, ctx->sms, TC_THREADS, FWD_TC_SMEM, ctx->stream, m)
+                    : launch_pdl(mlp_fwd_kernel<true, true>, ctx->mlp->fwd_blocks * ctx->sms, 128, FWD_SMEM,
+                                 ctx->stream, m);
+            r = launched(ctx, e, "mlp_fwd_kernel");
         }
         if (r) return r;
         if (mode == EBIT_CURV_MLP_HF) {
@@ -520,13 +568,15 @@ int ebit_curvature(ebit_ctx *ctx, const double *C, double *kappa_h, uint8_t *sta
             f.ncand = ctx->nscan;
             f.iface = nullptr;
             f.niface = nullptr;
+            f.zero[0] = f.zero[1] = nullptr;
             ProfScope pf(ctx, EBIT_PROF_MLP);
-            hf_list_kernel<true><<<ctx->grid_hfl, 128, 0, ctx->stream>>>(f);
-            r = launch_check(ctx, "hf_list_kernel");
+            r = launched(ctx, launch_pdl(hf_list_kernel<true>, ctx->grid_hfl, 128, 0, ctx->stream, f),
+                         "hf_list_kernel");
             if (r) return r;
         }
     }
     ctx->cur_if = nw;
+    ctx->if_slot = cnext;
     ctx->last_kh = kappa_h;
     ctx->last_st = status;
     return EBIT_OK;
@@ -566,7 +616,7 @@ int ebit_band_tiles(ebit_ctx *ctx) {
     if (!ctx) return -1;
     if (ctx->dense) return ctx->g.ntiles;
     int n = -1;
-    if (cudaMemcpyAsync(&n, ctx->band_count, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream) != cudaSuccess) return -1;
+    if (cudaMemcpyAsync(&n, ctx->band_count + ctx->band_last, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream) != cudaSuccess) return -1;
     if (cudaStreamSynchronize(ctx->stream) != cudaSuccess) return -1;
     return n;
 }

@@ -175,6 +175,7 @@ __device__ __forceinline__ void cell_ids(const Grid &g, int x, int y, int z, int
 // marker and its fraction is that colour (written as a bit pattern); the other
 // cells go to the global cut list.
 __global__ void __launch_bounds__(256) f2v_band_kernel(F2VArgs a) {
+    pdl_wait();
     const int ntl = *a.count;
     for (int li = blockIdx.x; li < ntl; li += gridDim.x) {
         const int tile = a.list[li];
@@ -364,6 +365,7 @@ __device__ double cell_fraction_fast(int K, const int Fc[6], const double *sE, i
 // FP64 pass: one thread per cut cell, full warps.
 __global__ void __launch_bounds__(128) f2v_list_kernel(F2VArgs a) {
     __shared__ double sE[12 * 128];
+    pdl_wait();
     const int n = *a.ncut;
     unsigned nbad = 0;
     const int stride = gridDim.x * blockDim.x;

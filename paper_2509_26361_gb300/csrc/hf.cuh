@@ -29,6 +29,7 @@ struct HFArgs {
     const int *__restrict__ ncand;
     unsigned *__restrict__ iface;       // interface cells of this call (output list, may be null)
     int *__restrict__ niface;
+    int *zero[2];                       // counters of later launches to clear (may be null)
     const int *__restrict__ list;       // tiles, for the full scan
     const int *__restrict__ count;
 };
@@ -164,6 +165,11 @@ __device__ __noinline__ int hf_cell(const HFArgs &a, int x, int y, int z, double
 // them next).
 template <bool COMPUTE>
 __global__ void __launch_bounds__(128) hf_list_kernel(HFArgs a) {
+    pdl_wait();
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        if (a.zero[0]) *a.zero[0] = 0;
+        if (a.zero[1]) *a.zero[1] = 0;
+    }
     const int np = *a.nprev, nc = *a.ncand;
     const int total = np + nc;
     const int stride = gridDim.x * blockDim.x;
@@ -209,6 +215,7 @@ __global__ void __launch_bounds__(128) hf_list_kernel(HFArgs a) {
 // Full scan of the listed tiles (any C): non-interface cells are reset, the
 // interface cells are appended to the candidate list for hf_list_kernel.
 __global__ void __launch_bounds__(256) hf_scan_kernel(HFArgs a, unsigned *cand, int *ncand) {
+    pdl_wait();
     const int ntl = *a.count;
     for (int li = blockIdx.x; li < ntl; li += gridDim.x) {
         const int tile = a.list[li];

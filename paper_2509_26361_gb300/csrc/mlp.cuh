@@ -295,6 +295,7 @@ __device__ __forceinline__ uint32_t pack_bf16x2(float lo, float hi) {
 
 template <bool GATHER, bool CURV>
 __global__ void __launch_bounds__(128) mlp_fwd_kernel(MlpArgs a) {
+    pdl_wait();
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __nv_bfloat16 *sX = reinterpret_cast<__nv_bfloat16 *>(smem_raw);
     __nv_bfloat16 *sW1 = sX + 128 * LD64;
@@ -453,6 +454,7 @@ __device__ __forceinline__ void group_sync(int grp) {
 
 template <bool GATHER, bool CURV>
 __global__ void __launch_bounds__(TC_THREADS) mlp_fwd_tc_kernel(MlpArgs a) {
+    pdl_wait();
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     unsigned char *base = (unsigned char *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     const int tid = threadIdx.x, grp = tid >> 7, t = tid & 127, wq = (tid >> 5) & 3;

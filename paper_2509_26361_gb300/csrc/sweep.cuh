@@ -261,6 +261,7 @@ __global__ void __launch_bounds__(256) advect_kernel(SweepArgs a) {
     __shared__ uint16_t s_mk[3 * TILE_CELLS];
     __shared__ uint8_t s_c[9 * 9 * 9];  // node colours of the tile and its +1 layer
     __shared__ int s_n;
+    pdl_wait();
     const int ntl = *a.count;
     if (blockIdx.x == 0 && threadIdx.x < 4) a.wcount[threadIdx.x] = 0;
     for (int li = blockIdx.x; li < ntl; li += gridDim.x) advect_tile<D>(a, a.u, a.lam, a.list[li], s_mk, s_c, &s_n);
@@ -666,6 +667,7 @@ template <int D>
 __global__ void __launch_bounds__(256, 4) sweep_kernel(SweepArgs a) {
     __shared__ unsigned s_flag;
     __shared__ uint8_t s_b[RA * R1 * R2];
+    pdl_wait();
     const int ntl = *a.count;
     for (int li = blockIdx.x; li < ntl; li += gridDim.x) sweep_tile<D, false>(a, a.list[li], s_b, &s_flag);
     if (blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(a.ctr + C_TILES, (unsigned long long)ntl);
@@ -701,6 +703,7 @@ __device__ __forceinline__ void fp64_item(const SweepArgs &a, int kind, int k, u
 
 template <int D>
 __global__ void __launch_bounds__(128) fp64_kernel(SweepArgs a) {
+    pdl_wait();
     const int n0 = a.wcount[0], n1 = a.wcount[1], n2 = a.wcount[2], n3 = a.wcount[3];
     const int total = n0 + n1 + n2 + n3;
     unsigned ev[C_N] = {0, 0, 0, 0, 0};
