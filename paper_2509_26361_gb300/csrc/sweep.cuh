@@ -102,8 +102,9 @@ __device__ __forceinline__ int cell_segs(int c00, int c10, int c01, int c11, int
 }
 
 // Circle through A, B, C meeting the grid line x = 0; only roots on the edge
-// (0 <= y <= 1) count, the one nearest ylin is kept (Fig. 2).
-__device__ __forceinline__ bool circle_root(P2 A, P2 B, P2 C, double ylin, double *root, double *rad) {
+// (0 <= y <= 1) count, the one nearest ylin is kept (Fig. 2).  rad2 gets the
+// squared radius.
+__device__ __forceinline__ bool circle_root(P2 A, P2 B, P2 C, double ylin, double *root, double *rad2) {
     double bx = B.x - A.x, by = B.y - A.y;
     double cx = C.x - A.x, cy = C.y - A.y;
     double b2 = bx * bx + by * by;
@@ -123,8 +124,20 @@ __device__ __forceinline__ bool circle_root(P2 A, P2 B, P2 C, double ylin, doubl
     if (!okp && !okm) return false;
     if (okp && okm) *root = (fabs(yp - ylin) <= fabs(ym - ylin)) ? yp : ym;
     else *root = okp ? yp : ym;
-    *rad = sqrt(r2);
+    *rad2 = r2;
     return true;
+}
+
+// The ratio rule's test rmax > 10 rmin with rmax = sqrt(r2max), rmin =
+// sqrt(r2min), both rounded, as the method states it.  Away from the threshold
+// the squared radii decide it (r2max against 100 r2min with a relative margin of
+// 1e-12, far above the few units of rounding in the radii and the product), so
+// the square roots are taken only within that margin.
+__device__ __forceinline__ bool ratio_above_10(double r2max, double r2min) {
+    const double t = 100.0 * r2min;
+    if (r2max > t * (1.0 + 1e-12)) return true;
+    if (r2max < t * (1.0 - 1e-12)) return false;
+    return sqrt(r2max) > 10.0 * sqrt(r2min);
 }
 
 // The crossing of an unaligned edge from the advected points P1 P2 P3 P4
@@ -135,15 +148,17 @@ __device__ __forceinline__ bool circle_root(P2 A, P2 B, P2 C, double ylin, doubl
 // out-of-line copy serves every edge family (the two fits are independent, so
 // their FP64 chains interleave inside it).
 static __device__ __noinline__ double circle_pair(P2 P1, P2 Pa, P2 Pb, P2 P4, double ylin, bool h1, bool h4) {
-    double ya = 0.0, ra = 0.0, yb = 0.0, rb = 0.0;
-    bool va = circle_root(P1, Pa, Pb, ylin, &ya, &ra);
-    bool vb = circle_root(Pa, Pb, P4, ylin, &yb, &rb);
+    double ya = 0.0, ra2 = 0.0, yb = 0.0, rb2 = 0.0;
+    bool va = circle_root(P1, Pa, Pb, ylin, &ya, &ra2);
+    bool vb = circle_root(Pa, Pb, P4, ylin, &yb, &rb2);
     va = va && h1;
     vb = vb && h4;
     double y;
     if (va && vb) {
-        double rmax = ra > rb ? ra : rb, rmin = ra > rb ? rb : ra;
-        if (rmax > 10.0 * rmin) y = ra > rb ? ya : yb;
+        // above the ratio the radii differ, so the larger squared radius names
+        // the larger circle
+        const double r2max = ra2 > rb2 ? ra2 : rb2, r2min = ra2 > rb2 ? rb2 : ra2;
+        if (ratio_above_10(r2max, r2min)) y = ra2 > rb2 ? ya : yb;
         else y = 0.5 * (ya + yb);
     } else if (va) {
         y = ya;
