@@ -25,6 +25,16 @@ namespace ebit {
 // pdl_wait() is a no-op.
 __device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
 
+// Entry of a compacted work list for this thread in iteration `it` of a
+// grid-stride loop over the list.  Whole warps of consecutive entries are dealt
+// to the blocks in turn (warp slot 0 of every block, then slot 1, ...), so a
+// list much shorter than the grid spreads over all SMs instead of filling the
+// first blocks; every entry maps to one thread of one iteration.
+__device__ __forceinline__ int list_item(int it) {
+    const int gw = (it * (int)(blockDim.x >> 5) + (int)(threadIdx.x >> 5)) * (int)gridDim.x + (int)blockIdx.x;
+    return gw * 32 + (int)(threadIdx.x & 31);
+}
+
 constexpr double ONE_MINUS = 0.99999999999999988898;  // 1 - 2^-53, largest offset below 1
 constexpr int TILE = 8;                               // tile edge (cells)
 constexpr int TILE_CELLS = TILE * TILE * TILE;

@@ -372,7 +372,7 @@ __global__ void __launch_bounds__(128) f2v_list_kernel(F2VArgs a) {
     const int iters = (n + stride - 1) / stride;
     double *myE = sE + threadIdx.x;
     for (int it = 0; it < iters; it++) {
-        int t = it * stride + blockIdx.x * blockDim.x + threadIdx.x;
+        const int t = list_item(it);
         if (t >= n) continue;
         const int id = (int)a.cut[t];
         const int x = id % a.g.n[0], y = (id / a.g.n[0]) % a.g.n[1], z = id / (a.g.n[0] * a.g.n[1]);

@@ -175,7 +175,7 @@ __global__ void __launch_bounds__(128) hf_list_kernel(HFArgs a) {
     const int stride = gridDim.x * blockDim.x;
     const int iters = (total + stride - 1) / stride;
     for (int it = 0; it < iters; it++) {
-        int t = it * stride + blockIdx.x * blockDim.x + threadIdx.x;
+        const int t = list_item(it);
         bool keep = false;
         int id = 0;
         if (t < total) {

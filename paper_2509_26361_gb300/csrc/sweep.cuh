@@ -726,7 +726,7 @@ __global__ void __launch_bounds__(128) fp64_kernel(SweepArgs a) {
     // uniform trip count so that every lane reaches the warp reductions
     const int iters = (total + stride - 1) / stride;
     for (int it = 0; it < iters; it++) {
-        int t = it * stride + blockIdx.x * blockDim.x + threadIdx.x;
+        const int t = list_item(it);
         if (t >= total) continue;
         int k, kind;
         if (t < n0) { kind = 0; k = t; }
