@@ -414,56 +414,80 @@ struct SweepCell {
         return false;
     }
 
+    // Crossings of the advected polyline of cells (-1, 0) and (0, 0) with the
+    // grid line x = 0, in scan order (cell da = -1 then 0, segment 0 then 1):
+    // their number, and for the first three their left and right endpoint
+    // edges and cell (scalars, so that nothing lives in local memory).
+    struct Crossings {
+        int n;
+        int el0, er0, da0, el1, er1, da1, el2, er2, da2;
+    };
+    template <int TT, int NN>
+    __device__ __forceinline__ Crossings crossings() const {
+        Crossings c{};
+#pragma unroll
+        for (int da = -1; da <= 0; da++) {
+            int seg[2][2];
+            const int ns = psegs<TT, NN>(da, 0, seg);
+#pragma unroll
+            for (int k = 0; k < 2; k++) {
+                if (k >= ns) continue;
+                const bool l0 = pleft<TT, NN>(seg[k][0], da, 0, 0), l1 = pleft<TT, NN>(seg[k][1], da, 0, 0);
+                if (l0 == l1) continue;
+                const int el = l0 ? seg[k][0] : seg[k][1], er = l0 ? seg[k][1] : seg[k][0];
+                if (c.n == 0) { c.el0 = el; c.er0 = er; c.da0 = da; }
+                else if (c.n == 1) { c.el1 = el; c.er1 = er; c.da1 = da; }
+                else if (c.n == 2) { c.el2 = el; c.er2 = er; c.da2 = da; }
+                c.n++;
+            }
+        }
+        return c;
+    }
+    // the crossing's advected endpoints and its linear crossing height
+    template <int TT, int NN>
+    __device__ __forceinline__ double crossing_line(int el, int er, int cda, P2 &Pa, P2 &Pb) const {
+        Pa = ppos<TT, NN>(el, cda, 0);
+        Pb = ppos<TT, NN>(er, cda, 0);
+        const double tt = (0.0 - Pa.x) / (Pb.x - Pa.x);
+        return Pa.y + tt * (Pb.y - Pa.y);
+    }
+
     // Unaligned edge of family (TT, NN) at the cell's node (carries a marker):
     // crossings of the advected polyline with the grid line x = 0 in strip 0
     // (Fig. 1c), then the two circle fits with the ratio rule (Fig. 2).
     template <int TT, int NN>
     __device__ void unaligned(unsigned ev[C_N]) const {
-        P2 c2[4], c3[4];
-        int e2[4], e3[4], cd[4];
-        int nc = 0;
-        for (int da = -1; da <= 0; da++) {
-            int seg[2][2];
-            int ns = psegs<TT, NN>(da, 0, seg);
-            for (int k = 0; k < ns; k++) {
-                bool l0 = pleft<TT, NN>(seg[k][0], da, 0, 0), l1 = pleft<TT, NN>(seg[k][1], da, 0, 0);
-                if (l0 == l1) continue;
-                int el = l0 ? seg[k][0] : seg[k][1], er = l0 ? seg[k][1] : seg[k][0];
-                c2[nc] = ppos<TT, NN>(el, da, 0);
-                c3[nc] = ppos<TT, NN>(er, da, 0);
-                e2[nc] = el;
-                e3[nc] = er;
-                cd[nc] = da;
-                nc++;
-            }
-        }
+        const Crossings c = crossings<TT, NN>();
         const int myid = lin3(a.g, p);
         ev[C_MARKERS]++;
-        if ((nc & 1) == 0) {
+        if ((c.n & 1) == 0) {
             ev[C_INCONSISTENT]++;
             a.so[TT][myid] = 0.5;
             return;
         }
-        double yl[4];
-        for (int k = 0; k < nc; k++) {
-            double tt = (0.0 - c2[k].x) / (c3[k].x - c2[k].x);
-            yl[k] = c2[k].y + tt * (c3[k].y - c2[k].y);
-        }
-        int sel = 0;
-        if (nc == 3) {
+        int el = c.el0, er = c.er0, cda = c.da0;
+        P2 Pa, Pb;
+        double ylin = crossing_line<TT, NN>(el, er, cda, Pa, Pb);
+        if (c.n == 3) {
+            // a fold of the polyline: the crossing with the median linear
+            // height, by the same three compare-exchanges as the oracle
+            P2 A1, B1, A2, B2;
+            const double y1 = crossing_line<TT, NN>(c.el1, c.er1, c.da1, A1, B1);
+            const double y2 = crossing_line<TT, NN>(c.el2, c.er2, c.da2, A2, B2);
+            // (v_k tracks yl[o_k], so the comparisons are the oracle's)
+            double v0 = ylin, v1 = y1, v2 = y2, tv;
             int o0 = 0, o1 = 1, o2 = 2, tmp;
-            if (yl[o0] > yl[o1]) { tmp = o0; o0 = o1; o1 = tmp; }
-            if (yl[o1] > yl[o2]) { tmp = o1; o1 = o2; o2 = tmp; }
-            if (yl[o0] > yl[o1]) { tmp = o0; o0 = o1; o1 = tmp; }
-            sel = o1;
+            if (v0 > v1) { tmp = o0; o0 = o1; o1 = tmp; tv = v0; v0 = v1; v1 = tv; }
+            if (v1 > v2) { tmp = o1; o1 = o2; o2 = tmp; tv = v1; v1 = v2; v2 = tv; }
+            if (v0 > v1) { tmp = o0; o0 = o1; o1 = tmp; tv = v0; v0 = v1; v1 = tv; }
+            if (o1 == 1) { el = c.el1; er = c.er1; cda = c.da1; Pa = A1; Pb = B1; ylin = y1; }
+            else if (o1 == 2) { el = c.el2; er = c.er2; cda = c.da2; Pa = A2; Pb = B2; ylin = y2; }
             ev[C_MULTI]++;
         }
-        P2 Pa = c2[sel], Pb = c3[sel];
-        double ylin = yl[sel];
         // both neighbours first, then the two circle fits
         P2 P1 = Pa, P4 = Pb;
-        const bool h1 = neighbour<TT, NN>(e2[sel], cd[sel], 0, &P1);
-        const bool h4 = neighbour<TT, NN>(e3[sel], cd[sel], 0, &P4);
+        const bool h1 = neighbour<TT, NN>(el, cda, 0, &P1);
+        const bool h4 = neighbour<TT, NN>(er, cda, 0, &P4);
         if (!h1) ev[C_INCONSISTENT]++;
         if (!h4) ev[C_INCONSISTENT]++;
         a.so[TT][myid] = circle_pair(P1, Pa, Pb, P4, ylin, h1, h4);
