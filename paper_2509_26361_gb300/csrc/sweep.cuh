@@ -172,6 +172,38 @@ static __device__ __noinline__ double circle_pair(P2 P1, P2 Pa, P2 Pb, P2 P4, do
     return y;
 }
 
+// circle_pair with one fit per lane of a lane pair (adjacent lanes of a warp;
+// lane parity `half`: 0 fits P1 Pa Pb, 1 fits Pa Pb P4).  The pair exchanges
+// root, squared radius and validity, and both lanes return the crossing
+// circle_pair returns (the same operations, in the same order, per fit).
+static __device__ __noinline__ double circle_pair_split(P2 P1, P2 Pa, P2 Pb, P2 P4, double ylin, bool h1, bool h4,
+                                                        int half) {
+    const unsigned pm = 3u << ((threadIdx.x & 31) & ~1u);
+    const P2 A = half ? Pa : P1, B = half ? Pb : Pa, Cc = half ? P4 : Pb;
+    double y = 0.0, r2 = 0.0;
+    bool v = circle_root(A, B, Cc, ylin, &y, &r2);
+    v = v && (half ? h4 : h1);
+    const double yo = __shfl_xor_sync(pm, y, 1), r2o = __shfl_xor_sync(pm, r2, 1);
+    const bool vo = __shfl_xor_sync(pm, (int)v, 1) != 0;
+    const double ya = half ? yo : y, ra2 = half ? r2o : r2, yb = half ? y : yo, rb2 = half ? r2 : r2o;
+    const bool va = half ? vo : v, vb = half ? v : vo;
+    double res;
+    if (va && vb) {
+        const double r2max = ra2 > rb2 ? ra2 : rb2, r2min = ra2 > rb2 ? rb2 : ra2;
+        if (ratio_above_10(r2max, r2min)) res = ra2 > rb2 ? ya : yb;
+        else res = 0.5 * (ya + yb);
+    } else if (va) {
+        res = ya;
+    } else if (vb) {
+        res = yb;
+    } else {
+        res = ylin;
+    }
+    if (res < 0.0) res = 0.0;
+    if (res > ONE_MINUS) res = ONE_MINUS;
+    return res;
+}
+
 // trilinear u_D at node q shifted by s along axis e; lerps in x, y, z order
 template <int D>
 __device__ double interp_u(const Grid &g, const double *__restrict__ u, const int q[3], int e, double s) {
@@ -455,14 +487,19 @@ struct SweepCell {
     // Unaligned edge of family (TT, NN) at the cell's node (carries a marker):
     // crossings of the advected polyline with the grid line x = 0 in strip 0
     // (Fig. 1c), then the two circle fits with the ratio rule (Fig. 2).
+    // half: -1 one lane per edge; 0, 1 the lanes of a pair sharing the edge
+    // (the even lane counts and stores).
     template <int TT, int NN>
-    __device__ void unaligned(unsigned ev[C_N]) const {
+    __device__ void unaligned(unsigned ev[C_N], int half = -1) const {
         const Crossings c = crossings<TT, NN>();
         const int myid = lin3(a.g, p);
-        ev[C_MARKERS]++;
+        const bool lead = half <= 0;
+        if (lead) ev[C_MARKERS]++;
         if ((c.n & 1) == 0) {
-            ev[C_INCONSISTENT]++;
-            a.so[TT][myid] = 0.5;
+            if (lead) {
+                ev[C_INCONSISTENT]++;
+                a.so[TT][myid] = 0.5;
+            }
             return;
         }
         int el = c.el0, er = c.er0, cda = c.da0;
@@ -482,15 +519,20 @@ struct SweepCell {
             if (v0 > v1) { tmp = o0; o0 = o1; o1 = tmp; tv = v0; v0 = v1; v1 = tv; }
             if (o1 == 1) { el = c.el1; er = c.er1; cda = c.da1; Pa = A1; Pb = B1; ylin = y1; }
             else if (o1 == 2) { el = c.el2; er = c.er2; cda = c.da2; Pa = A2; Pb = B2; ylin = y2; }
-            ev[C_MULTI]++;
+            if (lead) ev[C_MULTI]++;
         }
         // both neighbours first, then the two circle fits
         P2 P1 = Pa, P4 = Pb;
         const bool h1 = neighbour<TT, NN>(el, cda, 0, &P1);
         const bool h4 = neighbour<TT, NN>(er, cda, 0, &P4);
-        if (!h1) ev[C_INCONSISTENT]++;
-        if (!h4) ev[C_INCONSISTENT]++;
-        a.so[TT][myid] = circle_pair(P1, Pa, Pb, P4, ylin, h1, h4);
+        if (lead && !h1) ev[C_INCONSISTENT]++;
+        if (lead && !h4) ev[C_INCONSISTENT]++;
+        if (half < 0) {
+            a.so[TT][myid] = circle_pair(P1, Pa, Pb, P4, ylin, h1, h4);
+        } else {
+            const double y = circle_pair_split(P1, Pa, Pb, P4, ylin, h1, h4, half);
+            if (lead) a.so[TT][myid] = y;
+        }
     }
 
     // Face-centre colour of the family's 2D cell at the node (saddle faces): the
@@ -717,17 +759,18 @@ __global__ void __launch_bounds__(256, 4) sweep_kernel(SweepArgs a) {
 // Entry k of list `kind` (0, 1: unaligned edges of families 1, 2; 2, 3: saddle
 // faces of families 1, 2).
 template <int D, bool F>
-__device__ __forceinline__ void fp64_item(const SweepArgs &a, int kind, int k, unsigned ev[C_N]) {
+__device__ __forceinline__ void fp64_item(const SweepArgs &a, int kind, int k, unsigned ev[C_N], int half = -1) {
     constexpr int T1 = (D + 1) % 3, T2 = (D + 2) % 3;
+    if (kind >= 2 && half > 0) return;  // saddle faces: one lane
     const int id = (int)ld_in<F>(a.work[kind] + k);
     const int x = id % a.g.n[0], y = (id / a.g.n[0]) % a.g.n[1], z = id / (a.g.n[0] * a.g.n[1]);
     SweepCell<D, F> cell(a, x, y, z);
     if ((kind & 1) == 0) cell.template loadw<T1, T2>();
     else cell.template loadw<T2, T1>();
     if (kind == 0) {
-        cell.template unaligned<T1, T2>(ev);
+        cell.template unaligned<T1, T2>(ev, half);
     } else if (kind == 1) {
-        cell.template unaligned<T2, T1>(ev);
+        cell.template unaligned<T2, T1>(ev, half);
     } else {
         int ncol0 = ld_in<F>(a.cbo + id) & 1;
         int bit = (kind == 2) ? (cell.template face_phase<T1, T2>(ncol0) << (1 + T2))
@@ -747,17 +790,23 @@ __global__ void __launch_bounds__(128) fp64_kernel(SweepArgs a) {
     const int total = n0 + n1 + n2 + n3;
     unsigned ev[C_N] = {0, 0, 0, 0, 0};
     const int stride = gridDim.x * blockDim.x;
-    // uniform trip count so that every lane reaches the warp reductions
-    const int iters = (total + stride - 1) / stride;
+    // A short list (one round of the grid even at two lanes per entry) gets two
+    // adjacent lanes per entry, the circle fits split between them: a shorter
+    // chain per warp where few warps run.  A long list keeps one lane per entry,
+    // since the pairs repeat the work before the fits.  The trip count is uniform
+    // so that every lane reaches the warp reductions.
+    const bool pairs = 2 * total <= stride;
+    const int iters = ((pairs ? 2 : 1) * total + stride - 1) / stride;
     for (int it = 0; it < iters; it++) {
-        const int t = list_item(it);
+        const int t2 = list_item(it);
+        const int t = pairs ? t2 >> 1 : t2, half = pairs ? (t2 & 1) : -1;
         if (t >= total) continue;
         int k, kind;
         if (t < n0) { kind = 0; k = t; }
         else if (t < n0 + n1) { kind = 1; k = t - n0; }
         else if (t < n0 + n1 + n2) { kind = 2; k = t - n0 - n1; }
         else { kind = 3; k = t - n0 - n1 - n2; }
-        fp64_item<D, false>(a, kind, k, ev);
+        fp64_item<D, false>(a, kind, k, ev, half);
     }
 #pragma unroll
     for (int k = 0; k < C_N; k++) {
