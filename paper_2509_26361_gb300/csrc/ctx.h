@@ -11,6 +11,10 @@
 
 using ebit::Grid;
 
+// work lists of a context's sweep: unaligned edges and saddle faces of the two
+// face families, and the annihilation checks of the two families
+constexpr int NLISTS = 6;
+
 struct ebit_mlp {
     cudaStream_t stream;
     int sms;
@@ -48,8 +52,8 @@ struct ebit_ctx {
     double *scratch;          // 3N doubles, allocated on first ebit_get_state
     double *adv[3];           // advected marker coordinates of the current sweep (scratch)
     int8_t *bin[3];           // floor(2 adv) (scratch)
-    unsigned *work[4];        // FP64 work lists of a sweep (scratch)
-    int *wcount;              // [4]
+    unsigned *work[NLISTS];   // work lists of a sweep (scratch; a batch view has the first 4)
+    int *wcount;              // [NLISTS] list lengths ([4] in a batch view)
     unsigned *cut;            // cells cut by the interface at the last Front2VOF
     int *ncut;
     unsigned *iface[2];       // interface cells of the last two curvature calls

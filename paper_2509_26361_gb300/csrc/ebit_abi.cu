@@ -137,16 +137,19 @@ template <int D>
 int sweep_launch(ebit_ctx *ctx, const SweepArgs &args) {
     {
         ProfScope ps(ctx, EBIT_PROF_ADVECT);
-        int r = launched(ctx, launch_pdl(advect_kernel<D>, ctx->grid_adv, 256, 0, ctx->stream, args), "advect_kernel");
+        int r = launched(ctx, launch_pdl(advect_kernel<D, NLISTS>, ctx->grid_adv, 256, 0, ctx->stream, args),
+                         "advect_kernel");
         if (r) return r;
     }
     {
         ProfScope ps(ctx, EBIT_PROF_SWEEP);
-        int r = launched(ctx, launch_pdl(sweep_kernel<D>, ctx->grid_sweep, 256, 0, ctx->stream, args), "sweep_kernel");
+        int r = launched(ctx, launch_pdl(sweep_kernel<D, NLISTS>, ctx->grid_sweep, 256, 0, ctx->stream, args),
+                         "sweep_kernel");
         if (r) return r;
     }
     ProfScope ps(ctx, EBIT_PROF_FP64);
-    return launched(ctx, launch_pdl(fp64_kernel<D>, ctx->grid_fp64, 128, 0, ctx->stream, args), "fp64_kernel");
+    return launched(ctx, launch_pdl(fp64_kernel<D, NLISTS>, ctx->grid_fp64, 128, 0, ctx->stream, args),
+                    "fp64_kernel");
 }
 
 }  // namespace
@@ -170,7 +173,7 @@ static int create_ctx(const ebit_desc *desc, const ebit_state_arrays *st, ebit_c
         ctx->adv[a] = nullptr;
         ctx->bin[a] = nullptr;
     }
-    for (int k = 0; k < 4; k++) ctx->work[k] = nullptr;
+    for (int k = 0; k < NLISTS; k++) ctx->work[k] = nullptr;
     ctx->iface[0] = ctx->iface[1] = nullptr;
     ctx->wcount = ctx->ncut = ctx->niface = ctx->nscan = ctx->zero = nullptr;
     ctx->cut = ctx->scan = nullptr;
@@ -224,8 +227,8 @@ static int create_ctx(const ebit_desc *desc, const ebit_state_arrays *st, ebit_c
         }
         for (int a = 0; a < 3 && ok; a++)
             ok = ok && alloc((void **)&ctx->adv[a], ctx->N * sizeof(double)) && alloc((void **)&ctx->bin[a], ctx->N);
-        for (int k = 0; k < 4 && ok; k++) ok = ok && alloc((void **)&ctx->work[k], ctx->N * sizeof(unsigned));
-        ok = ok && alloc((void **)&ctx->wcount, 4 * sizeof(int)) && alloc((void **)&ctx->tile_marker, nt * sizeof(uint32_t)) &&
+        for (int k = 0; k < NLISTS && ok; k++) ok = ok && alloc((void **)&ctx->work[k], ctx->N * sizeof(unsigned));
+        ok = ok && alloc((void **)&ctx->wcount, NLISTS * sizeof(int)) && alloc((void **)&ctx->tile_marker, nt * sizeof(uint32_t)) &&
              alloc((void **)&ctx->tile_dirty, nt) && alloc((void **)&ctx->ctr, C_TOTAL * sizeof(unsigned long long));
     }
     ok = ok && alloc((void **)&ctx->cut, ctx->N * sizeof(unsigned)) && alloc((void **)&ctx->scan, ctx->N * sizeof(unsigned)) &&
@@ -243,11 +246,11 @@ static int create_ctx(const ebit_desc *desc, const ebit_state_arrays *st, ebit_c
         return EBIT_ENOMEM;
     }
     int occ = 1;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, sweep_kernel<0>, 256, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, sweep_kernel<0, NLISTS>, 256, 0);
     ctx->grid_sweep = std::max(1, std::min(nt, ctx->sms * std::max(occ, 1)));
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, advect_kernel<0>, 256, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, advect_kernel<0, NLISTS>, 256, 0);
     ctx->grid_adv = std::max(1, std::min(nt, ctx->sms * std::max(occ, 1)));
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fp64_kernel<0>, 128, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fp64_kernel<0, NLISTS>, 128, 0);
     ctx->grid_fp64 = ctx->sms * std::max(occ, 1);
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, f2v_band_kernel, 256, 0);
     ctx->grid_f2v = std::max(1, std::min(nt, ctx->sms * std::max(occ, 1)));
@@ -257,7 +260,7 @@ static int create_ctx(const ebit_desc *desc, const ebit_state_arrays *st, ebit_c
     ctx->grid_hf = std::max(1, std::min(nt, ctx->sms * std::max(occ, 1)));
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, hf_list_kernel<true>, 128, 0);
     ctx->grid_hfl = ctx->sms * std::max(occ, 1);
-    cudaMemsetAsync(ctx->wcount, 0, 4 * sizeof(int), ctx->stream);
+    cudaMemsetAsync(ctx->wcount, 0, (ctx->owns_state ? NLISTS : 4) * sizeof(int), ctx->stream);
     cudaMemsetAsync(ctx->ncut, 0, sizeof(int), ctx->stream);
     cudaMemsetAsync(ctx->niface, 0, 3 * sizeof(int), ctx->stream);
     cudaMemsetAsync(ctx->band_count, 0, 2 * sizeof(int), ctx->stream);
@@ -306,7 +309,7 @@ void ebit_destroy(ebit_ctx *ctx) {
             cudaFree(ctx->adv[a]);
             cudaFree(ctx->bin[a]);
         }
-        for (int k = 0; k < 4; k++) cudaFree(ctx->work[k]);
+        for (int k = 0; k < NLISTS; k++) cudaFree(ctx->work[k]);
         cudaFree(ctx->wcount);
     }
     cudaFree(ctx->tile_cchg);
@@ -402,7 +405,7 @@ int ebit_advect_sweep(ebit_ctx *ctx, int dir, const double *u_face, double dt) {
         a.adv[k] = ctx->adv[k];
         a.bin[k] = ctx->bin[k];
     }
-    for (int k = 0; k < 4; k++) a.work[k] = ctx->work[k];
+    for (int k = 0; k < NLISTS; k++) a.work[k] = ctx->work[k];
     a.wcount = ctx->wcount;
     a.u = u_face;
     a.lam = dt / ctx->h;

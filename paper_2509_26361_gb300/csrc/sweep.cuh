@@ -51,8 +51,9 @@ struct SweepArgs {
     int8_t *__restrict__ bin[3];     // floor(2 adv) (scratch)
     const int *__restrict__ list;    // band tile ids
     const int *__restrict__ count;   // number of band tiles (device)
-    unsigned *__restrict__ work[4];  // FP64 work lists: unaligned fam.1, fam.2, saddle fam.1, fam.2
-    int *__restrict__ wcount;        // [4] list lengths (device)
+    unsigned *__restrict__ work[6];  // work lists: unaligned fam.1, fam.2, saddle fam.1, fam.2
+                                     // (and, with six lists, annihilation checks fam.1, fam.2)
+    int *__restrict__ wcount;        // [4] or [6] list lengths (device)
     unsigned long long *ctr;         // event counters
     uint32_t *tile_marker;           // per tile: proximity mask of its markers in the input or the output
     uint8_t *tile_dirty;             // per tile: processed since the last Front2VOF
@@ -303,14 +304,14 @@ __device__ __forceinline__ void advect_tile(const SweepArgs &a, const double *__
     __syncthreads();
 }
 
-template <int D>
+template <int D, int NL = 4>
 __global__ void __launch_bounds__(256) advect_kernel(SweepArgs a) {
     __shared__ uint16_t s_mk[3 * TILE_CELLS];
     __shared__ uint8_t s_c[9 * 9 * 9];  // node colours of the tile and its +1 layer
     __shared__ int s_n;
     pdl_wait();
     const int ntl = *a.count;
-    if (blockIdx.x == 0 && threadIdx.x < 4) a.wcount[threadIdx.x] = 0;
+    if (blockIdx.x == 0 && threadIdx.x < NL) a.wcount[threadIdx.x] = 0;
     for (int li = blockIdx.x; li < ntl; li += gridDim.x) advect_tile<D>(a, a.u, a.lam, a.list[li], s_mk, s_c, &s_n);
 }
 
@@ -573,7 +574,10 @@ __device__ __forceinline__ bool saddle4(int c00, int c10, int c01, int c11) {
 constexpr int RA = 11, R1 = 9, R2 = 9;
 
 // One band tile, all threads of the block; s_b/s_flag are its shared staging.
-template <int D, bool F>
+// NL = 6: an unaligned edge without a marker whose window shows a colour change
+// goes to work list 4 or 5 (the crossing count of the annihilation counter is
+// taken by the FP64-list kernel, with full warps); NL = 4: counted here.
+template <int D, bool F, int NL = 4>
 __device__ __forceinline__ void sweep_tile(const SweepArgs &a, int tile, uint8_t *s_b, unsigned *s_flag) {
     constexpr int A = D, T1 = (D + 1) % 3, T2 = (D + 2) % 3;
     {
@@ -594,7 +598,7 @@ __device__ __forceinline__ void sweep_tile(const SweepArgs &a, int tile, uint8_t
         for (int c = threadIdx.x; c < TILE_CELLS; c += blockDim.x) {
             int x = o[0] + (c & 7), y = o[1] + ((c >> 3) & 7), z = o[2] + (c >> 6);
             bool valid = x < a.g.n[0] && y < a.g.n[1] && z < a.g.n[2];
-            bool push[4] = {false, false, false, false};
+            bool push[6] = {false, false, false, false, false, false};
             int myid = 0;
             if (valid) {
                 SweepCell<D, F> cell(a, x, y, z);
@@ -699,14 +703,19 @@ __device__ __forceinline__ void sweep_tile(const SweepArgs &a, int tile, uint8_t
                     const bool pres2 = n0 != nc[0][0][1];
                     push[0] = pres1;
                     push[1] = pres2;
-                    if (!pres1 && ((col[1][0][0] ^ m) | (col[2][0][0] ^ m) | (col[0][1][0] ^ m) |
-                                   (col[1][1][0] ^ m) | (col[2][1][0] ^ m)))
-                        if ((cell.template loadw<T1, T2>(), cell.template count_crossings<T1, T2>()) >= 2)
+                    const bool chk1 = !pres1 && ((col[1][0][0] ^ m) | (col[2][0][0] ^ m) | (col[0][1][0] ^ m) |
+                                                 (col[1][1][0] ^ m) | (col[2][1][0] ^ m));
+                    const bool chk2 = !pres2 && ((col[1][0][0] ^ m) | (col[2][0][0] ^ m) | (col[0][0][1] ^ m) |
+                                                 (col[1][0][1] ^ m) | (col[2][0][1] ^ m));
+                    if (NL == 6) {
+                        push[4] = chk1;
+                        push[5] = chk2;
+                    } else {
+                        if (chk1 && (cell.template loadw<T1, T2>(), cell.template count_crossings<T1, T2>()) >= 2)
                             ev[C_ANNIHILATE]++;
-                    if (!pres2 && ((col[1][0][0] ^ m) | (col[2][0][0] ^ m) | (col[0][0][1] ^ m) |
-                                   (col[1][0][1] ^ m) | (col[2][0][1] ^ m)))
-                        if ((cell.template loadw<T2, T1>(), cell.template count_crossings<T2, T1>()) >= 2)
+                        if (chk2 && (cell.template loadw<T2, T1>(), cell.template count_crossings<T2, T1>()) >= 2)
                             ev[C_ANNIHILATE]++;
+                    }
                     out_marker |= pres1 || pres2;
                     // face colours: family 1 faces are normal to T2, family 2 to T1
                     int byte = n0;
@@ -721,7 +730,7 @@ __device__ __forceinline__ void sweep_tile(const SweepArgs &a, int tile, uint8_t
                 }
             }
 #pragma unroll
-            for (int k = 0; k < 4; k++) {
+            for (int k = 0; k < NL; k++) {
                 int slot = warp_append(a.wcount + k, push[k]);
                 if (slot >= 0) a.work[k][slot] = (unsigned)myid;
             }
@@ -744,13 +753,13 @@ __device__ __forceinline__ void sweep_tile(const SweepArgs &a, int tile, uint8_t
     }
 }
 
-template <int D>
+template <int D, int NL = 4>
 __global__ void __launch_bounds__(256, 4) sweep_kernel(SweepArgs a) {
     __shared__ unsigned s_flag;
     __shared__ uint8_t s_b[RA * R1 * R2];
     pdl_wait();
     const int ntl = *a.count;
-    for (int li = blockIdx.x; li < ntl; li += gridDim.x) sweep_tile<D, false>(a, a.list[li], s_b, &s_flag);
+    for (int li = blockIdx.x; li < ntl; li += gridDim.x) sweep_tile<D, false, NL>(a, a.list[li], s_b, &s_flag);
     if (blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(a.ctr + C_TILES, (unsigned long long)ntl);
 }
 
@@ -761,13 +770,17 @@ __global__ void __launch_bounds__(256, 4) sweep_kernel(SweepArgs a) {
 template <int D, bool F>
 __device__ __forceinline__ void fp64_item(const SweepArgs &a, int kind, int k, unsigned ev[C_N], int half = -1) {
     constexpr int T1 = (D + 1) % 3, T2 = (D + 2) % 3;
-    if (kind >= 2 && half > 0) return;  // saddle faces: one lane
     const int id = (int)ld_in<F>(a.work[kind] + k);
     const int x = id % a.g.n[0], y = (id / a.g.n[0]) % a.g.n[1], z = id / (a.g.n[0] * a.g.n[1]);
     SweepCell<D, F> cell(a, x, y, z);
     if ((kind & 1) == 0) cell.template loadw<T1, T2>();
     else cell.template loadw<T2, T1>();
-    if (kind == 0) {
+    if (kind >= 4) {
+        // an even number (>= 2) of advected crossings met on an edge that keeps
+        // no marker (Fig. 5)
+        const int nc = (kind == 4) ? cell.template count_crossings<T1, T2>() : cell.template count_crossings<T2, T1>();
+        if (nc >= 2) ev[C_ANNIHILATE]++;
+    } else if (kind == 0) {
         cell.template unaligned<T1, T2>(ev, half);
     } else if (kind == 1) {
         cell.template unaligned<T2, T1>(ev, half);
@@ -783,29 +796,43 @@ __device__ __forceinline__ void fp64_item(const SweepArgs &a, int kind, int k, u
     }
 }
 
-template <int D>
+template <int D, int NL = 4>
 __global__ void __launch_bounds__(128) fp64_kernel(SweepArgs a) {
     pdl_wait();
     const int n0 = a.wcount[0], n1 = a.wcount[1], n2 = a.wcount[2], n3 = a.wcount[3];
-    const int total = n0 + n1 + n2 + n3;
+    const int n4 = NL == 6 ? a.wcount[4] : 0, n5 = NL == 6 ? a.wcount[5] : 0;
+    const int total = n0 + n1 + n2 + n3 + n4 + n5;
     unsigned ev[C_N] = {0, 0, 0, 0, 0};
     const int stride = gridDim.x * blockDim.x;
-    // A short list (one round of the grid even at two lanes per entry) gets two
-    // adjacent lanes per entry, the circle fits split between them: a shorter
-    // chain per warp where few warps run.  A long list keeps one lane per entry,
-    // since the pairs repeat the work before the fits.  The trip count is uniform
-    // so that every lane reaches the warp reductions.
-    const bool pairs = 2 * total <= stride;
-    const int iters = ((pairs ? 2 : 1) * total + stride - 1) / stride;
+    // Unaligned edges first, then saddle faces and annihilation checks, one lane
+    // each.  When the lists fit one round of the grid with two lanes per
+    // unaligned edge, each edge gets two adjacent lanes and the circle fits are
+    // split between them: a shorter chain per warp where few warps run.  Long
+    // lists keep one lane per edge, since the pairs repeat the work before the
+    // fits.  The trip count is uniform so that every lane reaches the warp
+    // reductions.
+    const int nu = n0 + n1, rest = total - nu;
+    const bool pairs = 2 * nu + rest <= stride;
+    const int lanes_u = pairs ? 2 * nu : nu;
+    const int iters = (lanes_u + rest + stride - 1) / stride;
     for (int it = 0; it < iters; it++) {
         const int t2 = list_item(it);
-        const int t = pairs ? t2 >> 1 : t2, half = pairs ? (t2 & 1) : -1;
+        int t, half;
+        if (t2 < lanes_u) {
+            t = pairs ? t2 >> 1 : t2;
+            half = pairs ? (t2 & 1) : -1;
+        } else {
+            t = nu + (t2 - lanes_u);
+            half = -1;
+        }
         if (t >= total) continue;
         int k, kind;
         if (t < n0) { kind = 0; k = t; }
         else if (t < n0 + n1) { kind = 1; k = t - n0; }
         else if (t < n0 + n1 + n2) { kind = 2; k = t - n0 - n1; }
-        else { kind = 3; k = t - n0 - n1 - n2; }
+        else if (t < n0 + n1 + n2 + n3) { kind = 3; k = t - n0 - n1 - n2; }
+        else if (t < n0 + n1 + n2 + n3 + n4) { kind = 4; k = t - n0 - n1 - n2 - n3; }
+        else { kind = 5; k = t - n0 - n1 - n2 - n3 - n4; }
         fp64_item<D, false>(a, kind, k, ev, half);
     }
 #pragma unroll
