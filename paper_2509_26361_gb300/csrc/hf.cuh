@@ -106,6 +106,43 @@ __device__ int hf_cell_impl(const CAccess<WRAP> &c, double *out) {
         for (int dy = -1; dy <= 1; dy++)
 #pragma unroll
             for (int dx = -1; dx <= 1; dx++) blk[dz + 1][dy + 1][dx + 1] = c(dx, dy, dz);
+    // The normal decides only the axis order and the side of the reference
+    // phase.  A float normal decides them when every |n_d| and every gap
+    // between two |n_d| clears the float rounding bound CANON_EPS with margin
+    // (then the FP64 sums, within 2e-14 of the exact ones, order and sign them
+    // the same); otherwise the FP64 sums below, in the oracle's order.
+    // (the bound holds for values in [+0, 1], checked on the bit patterns)
+    float fv[27];
+    bool unit = true;
+#pragma unroll
+    for (int dz = 0; dz < 3; dz++)
+#pragma unroll
+        for (int dy = 0; dy < 3; dy++)
+#pragma unroll
+            for (int dx = 0; dx < 3; dx++) {
+                unit = unit && (unsigned long long)__double_as_longlong(blk[dz][dy][dx]) <= 0x3FF0000000000000ull;
+                fv[dz * 9 + dy * 3 + dx] = (float)blk[dz][dy][dx];
+            }
+    float nf[3];
+    youngs<float>(fv, nf);
+    const float f0 = fabsf(nf[0]), f1 = fabsf(nf[1]), f2 = fabsf(nf[2]);
+    if (unit && f0 > CANON_EPS && f1 > CANON_EPS && f2 > CANON_EPS && fabsf(f0 - f1) > 2.0f * CANON_EPS &&
+        fabsf(f0 - f2) > 2.0f * CANON_EPS && fabsf(f1 - f2) > 2.0f * CANON_EPS) {
+        int o0 = 0, o1 = 1, o2 = 2, tmp;
+        const float fa[3] = {f0, f1, f2};
+        if (fa[o1] > fa[o0]) { tmp = o0; o0 = o1; o1 = tmp; }
+        if (fa[o2] > fa[o1]) {
+            tmp = o1; o1 = o2; o2 = tmp;
+            if (fa[o1] > fa[o0]) { tmp = o0; o0 = o1; o1 = tmp; }
+        }
+        const int ord[3] = {o0, o1, o2};
+        for (int oi = 0; oi < 3; oi++) {
+            const int d = ord[oi];
+            if (hf_axis<WRAP>(c, d, nf[d] > 0.0f, out)) return 1 + d;
+        }
+        *out = 0.0;
+        return 4;
+    }
     const double w[3] = {1.0, 2.0, 1.0};
     double n[3];
 #pragma unroll
