@@ -316,7 +316,7 @@ def run_e2e(args, g, w, dev, C, kh, st):
 # DRAM bytes (read + write) per launch of the split-sweep kernels (sweep along x), one ncu
 # capture each (--set full, cold caches) of the same 128^3 workload; see
 # profiles/kernels_fourier_spheres_128.md.  None once the kernels change.
-NCU_TRAFFIC = {"advect": 2950656.0, "sweep": 2351872.0, "fp64": 3362304.0, "band": 25600.0}
+NCU_TRAFFIC = {"advect": 2952704.0, "sweep": 1858304.0, "fp64": 3752960.0, "band": 25088.0}
 # per band cell of one split sweep and of Front2VOF (the scope table's figures)
 SWEEP_BYTES_PER_CELL = 62.75
 F2V_BYTES_PER_CELL = 36.4
