@@ -88,7 +88,11 @@ typedef struct ebit_ctx ebit_ctx;
 typedef struct {
     int nx, ny, nz;    /* cells per axis, periodic, each >= 8 */
     double h;          /* cell size (> 0); dt/h is the sweep's CFL factor */
-    void *cuda_stream; /* cudaStream_t used for every launch; NULL = legacy default stream */
+    void *cuda_stream; /* cudaStream_t used for every launch; NULL = legacy default stream.
+                          The kernels of a sweep, Front2VOF and curvature are launched with
+                          programmatic stream serialization: each waits for the preceding
+                          kernel on the stream to complete before it touches memory, so
+                          stream order holds as for ordinary launches. */
     int flags;         /* EBIT_DESC_DENSE: process every tile on every call (no band) */
 } ebit_desc;
 
