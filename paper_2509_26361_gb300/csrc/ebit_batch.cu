@@ -105,6 +105,7 @@ __global__ void __launch_bounds__(BATCH_THREADS, 4) batch_sweep_kernel(BatchPara
     __shared__ uint16_t s_mk[3 * TILE_CELLS];
     __shared__ uint8_t s_c[9 * 9 * 9];
     __shared__ uint8_t s_b[RA * R1 * R2];
+    __shared__ int8_t s_bn[RA * R1 * R2];
     __shared__ int s_n, s_ok;
     __shared__ unsigned s_flag;
     __shared__ int s_pre[4 * BATCH_MAX + 1];
@@ -148,7 +149,7 @@ __global__ void __launch_bounds__(BATCH_THREADS, 4) batch_sweep_kernel(BatchPara
         const int e = __ldcg(p.band + li);
         const int i = e >> 20;
         const SweepArgs &a = p.inst[i].a;
-        sweep_tile<D, true>(a, e & 0xFFFFF, s_b, &s_flag);
+        sweep_tile<D, true>(a, e & 0xFFFFF, s_b, s_bn, &s_flag);
         if (threadIdx.x == 0) atomicAdd(a.ctr + C_TILES, 1ull);
     }
     if (!grid_barrier(p, &s_ok)) return;

@@ -573,12 +573,14 @@ __device__ __forceinline__ bool saddle4(int c00, int c10, int c01, int c11) {
 // in [0, 8] relative to the tile origin
 constexpr int RA = 11, R1 = 9, R2 = 9;
 
-// One band tile, all threads of the block; s_b/s_flag are its shared staging.
+// One band tile, all threads of the block; s_b/s_n/s_flag are its shared
+// staging (colour bytes and the A-axis bins of the same window; a bin is read
+// only where its node owns a marker).
 // NL = 6: an unaligned edge without a marker whose window shows a colour change
 // goes to work list 4 or 5 (the crossing count of the annihilation counter is
 // taken by the FP64-list kernel, with full warps); NL = 4: counted here.
 template <int D, bool F, int NL = 4>
-__device__ __forceinline__ void sweep_tile(const SweepArgs &a, int tile, uint8_t *s_b, unsigned *s_flag) {
+__device__ __forceinline__ void sweep_tile(const SweepArgs &a, int tile, uint8_t *s_b, int8_t *s_n, unsigned *s_flag) {
     constexpr int A = D, T1 = (D + 1) % 3, T2 = (D + 2) % 3;
     {
         int o[3];
@@ -590,7 +592,9 @@ __device__ __forceinline__ void sweep_tile(const SweepArgs &a, int tile, uint8_t
             q[A] = o[A] + ka - 1;
             q[T1] = o[T1] + k1;
             q[T2] = o[T2] + k2;
-            s_b[r] = __ldg(a.cb + lin3(a.g, q));
+            const int id = lin3(a.g, q);
+            s_b[r] = __ldg(a.cb + id);
+            s_n[r] = ld_in<F>(a.bin[A] + id);
         }
         __syncthreads();
         unsigned ev[C_N] = {0, 0, 0, 0, 0};
@@ -635,7 +639,7 @@ __device__ __forceinline__ void sweep_tile(const SweepArgs &a, int tile, uint8_t
 #pragma unroll
                             for (int d2 = 0; d2 < 2; d2++) {
                                 has[da][d1][d2] = col[da][d1][d2] != col[da + 1][d1][d2];
-                                bn[da][d1][d2] = has[da][d1][d2] ? ld_in<F>(a.bin[A] + cell.id3(da - 1, d1, d2)) : 0;
+                                bn[da][d1][d2] = has[da][d1][d2] ? (int)s_n[sidx(da - 1, d1, d2)] : 0;
                             }
                     // new colours: X >= 1 <=> bin >= 2 (crossed the right node),
                     // X < 0 <=> bin < 0 (crossed the left node)  (Fig. 4)
@@ -757,9 +761,10 @@ template <int D, int NL = 4>
 __global__ void __launch_bounds__(256, 4) sweep_kernel(SweepArgs a) {
     __shared__ unsigned s_flag;
     __shared__ uint8_t s_b[RA * R1 * R2];
+    __shared__ int8_t s_n[RA * R1 * R2];
     pdl_wait();
     const int ntl = *a.count;
-    for (int li = blockIdx.x; li < ntl; li += gridDim.x) sweep_tile<D, false, NL>(a, a.list[li], s_b, &s_flag);
+    for (int li = blockIdx.x; li < ntl; li += gridDim.x) sweep_tile<D, false, NL>(a, a.list[li], s_b, s_n, &s_flag);
     if (blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(a.ctr + C_TILES, (unsigned long long)ntl);
 }
 
