@@ -178,15 +178,16 @@ def run_gpu(args, rank, world):
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)  # 256 MiB > L2
 
     def one_step(n, sweep_ev=None):
-        """One step; with sweep_ev, CUDA events on the context's stream bracket
-        each split-sweep call (band + advect + integer pass + FP64 lists)."""
+        """One step; with sweep_ev, a pair of CUDA events on the context's stream
+        brackets the step's three split-sweep calls (band + advect + integer
+        pass + FP64 lists each), which run back to back."""
         dt = w.lam(n) * g.h
-        for j, d in enumerate((0, 1, 2) if n % 2 == 0 else (2, 1, 0)):
-            if sweep_ev is not None:
-                sweep_ev[j][0].record()
+        if sweep_ev is not None:
+            sweep_ev[0].record()
+        for d in ((0, 1, 2) if n % 2 == 0 else (2, 1, 0)):
             g.sweep(d, ud[d], dt)
-            if sweep_ev is not None:
-                sweep_ev[j][1].record()
+        if sweep_ev is not None:
+            sweep_ev[1].record()
         g.front2vof(C)
         g.curvature(C, kh, st)
 
@@ -207,7 +208,7 @@ def run_gpu(args, rank, world):
         clocks.start()
         time.sleep(0.3)
     evs = [(E(), E()) for _ in range(args.steps)]
-    sev = [[(E(), E()) for _ in range(3)] for _ in range(args.steps)]
+    sev = [(E(), E()) for _ in range(args.steps)]
     if world > 1:
         import torch.distributed as dist
         dist.barrier()
@@ -223,7 +224,8 @@ def run_gpu(args, rank, world):
     if world > 1:
         dist.barrier()
     step_ms = [a.elapsed_time(b) for a, b in evs]
-    sweep_ms = [a.elapsed_time(b) for r in sev for a, b in r]
+    # per-sweep duration: the three sweeps of a step share one bracket
+    sweep_ms = [a.elapsed_time(b) / 3.0 for a, b in sev for _ in range(3)]
     total_ms = float(sum(step_ms))
     cnt = g.counters()
     total_ms = max_over_ranks(total_ms, world, dev)
@@ -316,7 +318,7 @@ def run_e2e(args, g, w, dev, C, kh, st):
 # DRAM bytes (read + write) per launch of the split-sweep kernels (sweep along x), one ncu
 # capture each (--set full, cold caches) of the same 128^3 workload; see
 # profiles/kernels_fourier_spheres_128.md.  None once the kernels change.
-NCU_TRAFFIC = {"advect": 2952704.0, "sweep": 1858304.0, "fp64": 3752960.0, "band": 25088.0}
+NCU_TRAFFIC = {"advect": 2953216.0, "sweep": 2512384.0, "fp64": 3747840.0, "band": 24832.0}
 # per band cell of one split sweep and of Front2VOF (the scope table's figures)
 SWEEP_BYTES_PER_CELL = 62.75
 F2V_BYTES_PER_CELL = 36.4
@@ -350,7 +352,7 @@ def roofline_block(res):
             "band_cells_per_sweep": band_cells, "markers_per_sweep": markers,
             "min_bytes_per_sweep": alg_min, "min_frac": alg_min / per_sweep_s / 1e9 / hbm,
             "avg_sweep_us": per_sweep_s * 1e6,
-            "timing": "CUDA events around each split-sweep call in the timed region",
+            "timing": "CUDA events around the three split-sweep calls of each step in the timed region",
             "instrumented_stage_ms": {k: round(v, 4) for k, v in stages.items()},
             "instrumented_kernel_ms": {k: round(v[0], 4) for k, v in prof.items()},
             "kernel_launches": {k: v[1] for k, v in prof.items()}}
@@ -488,12 +490,12 @@ def large_block(steps=20, warmup=3):
 
     def one(n, sweep_ev=None):
         dt = w.lam(n) * g.h
-        for j, d in enumerate((0, 1, 2) if n % 2 == 0 else (2, 1, 0)):
-            if sweep_ev is not None:
-                sweep_ev[j][0].record()
+        if sweep_ev is not None:
+            sweep_ev[0].record()
+        for d in ((0, 1, 2) if n % 2 == 0 else (2, 1, 0)):
             g.sweep(d, ud[d], dt)
-            if sweep_ev is not None:
-                sweep_ev[j][1].record()
+        if sweep_ev is not None:
+            sweep_ev[1].record()
         g.front2vof(C)
         g.curvature(C, kh, st, mode=mode)
 
@@ -505,7 +507,7 @@ def large_block(steps=20, warmup=3):
     torch.cuda.synchronize()
     g.reset_counters()
     evs = [(E(), E()) for _ in range(steps)]
-    sev = [[(E(), E()) for _ in range(3)] for _ in range(steps)]
+    sev = [(E(), E()) for _ in range(steps)]
     for i in range(steps):
         flush.zero_()
         evs[i][0].record()
@@ -513,7 +515,7 @@ def large_block(steps=20, warmup=3):
         evs[i][1].record()
     torch.cuda.synchronize()
     ms = sum(a.elapsed_time(b) for a, b in evs)
-    sweep_ms = [a.elapsed_time(b) for r in sev for a, b in r]
+    sweep_ms = [a.elapsed_time(b) / 3.0 for a, b in sev for _ in range(3)]
     cnt = g.counters()
     # instrumented pass over the following steps: per-kernel times
     g.profile(True)

@@ -228,3 +228,42 @@ def test_sweeps_on_random_colour_fields(seed):
     cnt = g.counters()
     assert [cnt[k] for k in ebit.COUNTER_NAMES] == list(ocnt), (cnt, ocnt)
     g.close()
+
+
+def _hf_case(C):
+    """Height functions of an arbitrary fraction field (full scan) against the oracle."""
+    nz, ny, nx = C.shape
+    g = ebit.Grid(nx, ny, nz)
+    Cd = to_dev(C)
+    kh = torch.zeros_like(Cd)
+    stt = torch.zeros(Cd.shape, dtype=torch.uint8, device="cuda")
+    g.curvature(Cd, kh, stt, flags=ebit.EBIT_FULL)
+    okh, ost = oracle.hf_curvature(C)
+    assert np.array_equal(stt.cpu().numpy(), ost)
+    assert np.abs(kh.cpu().numpy() - okh).max() <= TOL
+    g.close()
+    return ost
+
+
+def test_hf_normal_ties_and_ranges():
+    """Fields where the float normal cannot decide: a grid-aligned slab (two
+    normal components exactly zero), a diagonal plane (|n_x| = |n_y| exactly,
+    ties to the lower axis), and fractions outside [0, 1]; the FP64 sums must
+    give the oracle's statuses and curvature."""
+    n = 16
+    z = np.arange(n)[:, None, None] * np.ones((1, n, n))
+    slab = np.where((z >= 2) & (z < 7), 1.0, 0.0)
+    slab[7] = 0.3
+    slab[1] = 0.6
+    st = _hf_case(slab)
+    assert np.all(st[7] == 3) and np.all(st[1] == 3)  # columns along z
+    x = np.arange(n)[None, None, :] * np.ones((n, n, 1))
+    y = np.arange(n)[None, :, None] * np.ones((n, 1, n))
+    d = (x + y + 0.5) / np.sqrt(2.0) - 10.0 / np.sqrt(2.0)  # plane x + y = 9.5
+    diag = np.clip(0.5 - d, 0.0, 1.0)
+    st = _hf_case(diag)
+    assert np.any(st == 1)  # ties resolved to the lower axis, as the oracle does
+    rng = np.random.default_rng(5)
+    wild = np.clip(slab + rng.normal(0.0, 0.05, slab.shape), -0.2, 1.2)
+    wild[(wild > 0.0) & (wild < 1.0) & (z != 7) & (z != 1)] = 1.0
+    _hf_case(wild)
