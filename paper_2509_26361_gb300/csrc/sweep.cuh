@@ -24,9 +24,11 @@
 //   sweep_kernel  -- per band tile, one thread per cell, integer only: new node
 //                    colours, aligned edges, canonical face colours; unaligned
 //                    edges that carry a marker and saddle faces are appended to
-//                    global work lists.
-//   fp64_kernel   -- one thread per list entry: crossings, circle fits, face
-//                    phases.
+//                    global work lists (with six lists, also the unaligned
+//                    edges whose annihilation count needs their crossings).
+//   fp64_kernel   -- one thread per list entry (two per unaligned edge when
+//                    the lists are short, the circle fits split between them):
+//                    crossings, circle fits, face phases, crossing counts.
 // Every crossing decision compares an advected coordinate da + adv with 0 or
 // 1/2; for the integers da that occur the sum is exact near those thresholds,
 // so "da + adv < 0" equals "bin < -2 da" and "da + adv < 1/2" equals
