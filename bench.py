@@ -312,7 +312,8 @@ def run_e2e(args, g, w, dev, C, kh, st):
     nc = w.n3[0] * w.n3[1] * w.n3[2]
     return {"value": nc * steps / (ms * 1e-3), "unit": "cell-steps/s",
             "h2d_bytes_per_step": 3 * nc * 8, "d2h_bytes_per_step": 2 * nc * 8,
-            "overlap": "uploads and read-backs on two copy streams, overlapping the neighbouring steps"}
+            "overlap": "uploads and read-backs on two copy streams, overlapping the neighbouring steps",
+            "l2": "not flushed between these steps; the 84 MB of host copies per step pass through L2"}
 
 
 # DRAM bytes (read + write) per launch of the split-sweep kernels (sweep along x), one ncu
