@@ -39,9 +39,11 @@
  *   of its lowest corner; velocity by trilinear interpolation of the MAC
  *   component; periodic grid, at least 8 cells per axis; CFL < 1.
  *
- * Parity unpinned: the face-centre colour rule (phase of the advected polyline
- * at the face centre) is checked only by self-consistency and by GPU = oracle;
- * the paper fixes no value for it.
+ * The paper fixes no value for the face-centre colour rule (phase of the
+ * advected polyline at the face centre); the tests pin it by invariants:
+ * equivariance under reflections of the grid, independence of the path along
+ * which the phase is counted, and the colours of a surface moved by a uniform
+ * velocity.
  *
  * Layout (shared with the product only as a documented format): node/cell index
  * idx = (k*ny + j)*nx + i.  Colour byte cb[idx]: bit0 = node colour, bit(1+a) =
