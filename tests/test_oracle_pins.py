@@ -786,3 +786,83 @@ def test_saddle_face_colours_are_path_independent(seed):
                 assert ph == int(newbit[k, j, i]), f"sweep {d}, faces normal to {N}, node {q}"
                 checked += 1
     assert checked > 500, checked
+
+
+# ------------------------------------------------------ height-function axes
+def _sampled_fractions(n, inside, sub=8):
+    """Volume fractions by sub x sub x sub point sampling of an analytic region."""
+    g = np.arange(n, dtype=np.float64)
+    o = (np.arange(sub) + 0.5) / sub
+    C = np.zeros((n, n, n))
+    z, y, x = np.meshgrid(g, g, g, indexing="ij")
+    for a in o:
+        for b in o:
+            for c in o:
+                C += inside(x + a, y + b, z + c)
+    return C / sub ** 3
+
+
+def _columns_valid(C, k, j, i, d, below):
+    """The 3 x 3 columns of 9 cells along d around the cell end in pure cells of
+    the phases the reference side asks for."""
+    n = C.shape[0]
+    t1, t2 = [b for b in range(3) if b != d]
+    for b2 in (-1, 0, 1):
+        for b1 in (-1, 0, 1):
+            ends = []
+            for m in (-4, 4):
+                q = [i, j, k]
+                q[t1] += b1
+                q[t2] += b2
+                q[d] += m
+                ends.append(C[q[2] % n, q[1] % n, q[0] % n])
+            if ends != ([1.0, 0.0] if below else [0.0, 1.0]):
+                return False
+    return True
+
+
+def _first_valid_axis(C, k, j, i, nrm):
+    """1 + the first axis, by decreasing |normal component|, whose columns are
+    valid; 4 if none is."""
+    for ax in np.argsort(-np.abs(nrm), kind="stable"):
+        if nrm[ax] != 0.0 and _columns_valid(C, k, j, i, int(ax), nrm[ax] > 0):
+            return 1 + int(ax)
+    return 4
+
+
+def test_hf_axis_order_follows_the_surface_normal():
+    """Height functions take the axis of the largest normal component, then the
+    next ones where a column is not bounded by pure cells.  On spheres (analytic
+    normal, cells where the three components differ by 25 % or more) and on a
+    thin tilted plate (its z columns run into the other face, so cells fall back
+    to x), every status must be the first valid axis in the analytic order."""
+    n = 24
+    c = (12.3, 11.8, 12.1)
+    cases = []
+    for R in (4.2, 7.0):
+        C = _sampled_fractions(n, lambda x, y, z, R=R: ((x - c[0]) ** 2 + (y - c[1]) ** 2 + (z - c[2]) ** 2) < R * R)
+
+        def nrm(i, j, k):
+            v = np.array([i + 0.5 - c[0], j + 0.5 - c[1], k + 0.5 - c[2]])
+            return v / np.linalg.norm(v)
+        cases.append((C, nrm, True))
+
+    def plate_offset(x, z):
+        return (z - 0.5 * x - 7.3 + n / 2) % n - n / 2
+
+    Cp = _sampled_fractions(n, lambda x, y, z: np.abs(plate_offset(x, z)) < 1.9)
+    up = np.array([-0.5, 0.0, 1.0]) / np.sqrt(1.25)
+    cases.append((Cp, lambda i, j, k: up * np.sign(plate_offset(i + 0.5, k + 0.5)), False))
+    compared = fallbacks = 0
+    for C, nrm, need_clear in cases:
+        _, st = oracle.hf_curvature(C)
+        for k, j, i in zip(*np.nonzero((C > 0.0) & (C < 1.0))):
+            v = nrm(i, j, k)
+            a = np.sort(np.abs(v))[::-1]
+            if need_clear and not (a[0] >= 1.25 * a[1] and a[1] >= 1.25 * a[2]):
+                continue
+            want = _first_valid_axis(C, k, j, i, v)
+            assert st[k, j, i] == want, (k, j, i, st[k, j, i], want)
+            compared += 1
+            fallbacks += int(want != 4 and want != 1 + int(np.argmax(np.abs(v))))
+    assert compared > 1000 and fallbacks > 100, (compared, fallbacks)
