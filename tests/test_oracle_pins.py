@@ -866,3 +866,40 @@ def test_hf_axis_order_follows_the_surface_normal():
             compared += 1
             fallbacks += int(want != 4 and want != 1 + int(np.argmax(np.abs(v))))
     assert compared > 1000 and fallbacks > 100, (compared, fallbacks)
+
+
+# ------------------------------------------------------ velocity interpolation
+@pytest.mark.parametrize("d", [0, 1, 2])
+def test_aligned_markers_move_by_a_linear_field_exactly(d):
+    """Trilinear interpolation reproduces a linear field, so with u_d = a + b x +
+    c y + e z on the d-faces (MAC: on the nodes along d, half-way between them
+    along the other axes) every aligned marker that stays on its edge moves by
+    exactly lam u_d at its position (explicit Euler, Eq. 2), up to rounding.
+    Markers whose interpolation stencil wraps around the periodic grid are not
+    compared (the field is not linear across the seam)."""
+    n = 24
+    n3 = (n, n, n)
+    sp = [W.Sphere((0.5, 0.5, 0.5), 6.5 / n)]
+    phi, faces = W.sphere_phi_nodes_faces(n3, sp)
+    st = oracle.init(phi, faces, W.sphere_edge_roots(n3, sp))
+    coef = (0.3, 0.04, -0.03, 0.05)  # a, b, c, e: |u| < 1 on the grid
+    g = np.arange(n, dtype=np.float64)
+    pos = [g[None, None, :] + (0.0 if d == 0 else 0.5), g[None, :, None] + (0.0 if d == 1 else 0.5),
+           g[:, None, None] + (0.0 if d == 2 else 0.5)]
+    u = coef[0] + coef[1] * pos[0] + coef[2] * pos[1] + coef[3] * pos[2] + np.zeros((n, n, n))
+    lam = 0.7
+    new, _ = oracle.sweep(st, d, u, lam)
+    c0, c1 = st.cb & 1, new.cb & 1
+    ax = 2 - d
+    stay = (c0 != np.roll(c0, -1, axis=ax)) & (c1 != np.roll(c1, -1, axis=ax)) & (c0 == c1) & \
+        (np.roll(c0, -1, axis=ax) == np.roll(c1, -1, axis=ax))
+    kk, jj, ii = np.nonzero(stay)
+    q = np.stack([ii, jj, kk]).astype(np.float64)
+    inner = np.all((q >= 2) & (q <= n - 3), axis=0)
+    kk, jj, ii, q = kk[inner], jj[inner], ii[inner], q[:, inner]
+    s0 = st.s[d][kk, jj, ii]
+    q[d] += s0
+    expect = s0 + lam * (coef[0] + coef[1] * q[0] + coef[2] * q[1] + coef[3] * q[2])
+    moved = (expect >= 0.0) & (expect < 1.0)
+    assert moved.sum() > 50
+    assert np.max(np.abs(new.s[d][kk, jj, ii][moved] - expect[moved])) <= 1e-12
