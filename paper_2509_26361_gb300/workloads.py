@@ -176,6 +176,53 @@ def ellipsoid_phi_nodes_faces(n3, ells):
 
 
 # --------------------------------------------------------- velocity fields
+def gyroid_surface(n, waves, phases, c0, shift=0.0, axis=0):
+    """A gyroid-type triply periodic surface on an n^3 grid (cell units):
+    phi = sin X cos Y + sin Y cos Z + sin Z cos X + c0 with X = 2 pi waves[0] x / n
+    + phases[0] (and likewise Y, Z), moved by `shift` cells along `axis`.  Its
+    product terms give faces whose diagonal corners lie on the same side (saddle
+    faces), which a sum of one-axis terms never does.  Returns phi at the nodes,
+    phi at the three families of face centres, and the exact offsets of the
+    surface on the sign-change edges (bisection to 2^-60; NaN elsewhere)."""
+    k = [2.0 * np.pi * w / n for w in waves]
+    off = [0.0, 0.0, 0.0]
+    off[axis] = shift
+
+    def surf(x, y, z):
+        X = k[0] * (x - off[0]) + phases[0]
+        Y = k[1] * (y - off[1]) + phases[1]
+        Z = k[2] * (z - off[2]) + phases[2]
+        return np.sin(X) * np.cos(Y) + np.sin(Y) * np.cos(Z) + np.sin(Z) * np.cos(X) + c0
+
+    g = np.arange(n, dtype=np.float64)
+
+    def at(ox, oy, oz):
+        return surf(g[None, None, :] + ox, g[None, :, None] + oy, g[:, None, None] + oz)
+
+    phi = at(0.0, 0.0, 0.0)
+    faces = np.stack([at(0.0, 0.5, 0.5), at(0.5, 0.0, 0.5), at(0.5, 0.5, 0.0)])
+    roots = np.full((3,) + phi.shape, np.nan)
+    for a in range(3):
+        cross = (phi >= 0) != (np.roll(phi, -1, axis=2 - a) >= 0)
+        kk, jj, ii = np.nonzero(cross)
+        base = [ii.astype(np.float64), jj.astype(np.float64), kk.astype(np.float64)]
+        lo, hi = np.zeros(len(ii)), np.ones(len(ii))
+
+        def along(t):
+            p = [b.copy() for b in base]
+            p[a] = p[a] + t
+            return surf(p[0], p[1], p[2])
+
+        f0 = along(lo) >= 0
+        for _ in range(60):
+            mid = 0.5 * (lo + hi)
+            same = (along(mid) >= 0) == f0
+            lo = np.where(same, mid, lo)
+            hi = np.where(same, hi, mid)
+        roots[a][kk, jj, ii] = 0.5 * (lo + hi)
+    return phi, faces, roots
+
+
 def uniform_velocity(n3, u=(1.0, 1.0, 1.0)):
     nx, ny, nz = n3
     return np.stack([np.full((nz, ny, nx), float(u[a])) for a in range(3)])

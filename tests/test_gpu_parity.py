@@ -97,6 +97,19 @@ def test_fourier_spheres_small(seed):
     run_pair(w.n3, w.phi, w.phi_faces, w.u, w.lam, w.steps)
 
 
+@pytest.mark.parametrize("seed", [61, 62])
+def test_gyroid_surfaces_with_saddle_faces(seed):
+    """Smooth triply periodic surfaces whose faces include saddles (diagonal
+    corners on the same side), exact edge roots, a Fourier field: the saddle
+    face colours and segment pairings of every sweep against the oracle."""
+    rng = np.random.default_rng(seed)
+    n = 16
+    phi, faces, roots = W.gyroid_surface(n, rng.integers(4, 6, size=3), rng.uniform(0.0, 2.0 * np.pi, size=3),
+                                         rng.uniform(-0.3, 0.3))
+    u = W.fourier_velocity((n, n, n), rng)
+    run_pair((n, n, n), phi, faces, u, lambda k: 0.5, 4, s_exact=roots)
+
+
 @pytest.mark.parametrize("n3", [(20, 24, 28), (9, 17, 8)])
 def test_ragged_grid_random_blobs(n3):
     """Grids that are not multiples of the 8-cell tile, lumpy shapes with thin

@@ -613,51 +613,6 @@ def test_sweeps_commute_with_reflections(seed):
 
 
 # --------------------------------------------- face-centre colour, geometry
-def _periodic_surface(x, y, z, k, ph, c0):
-    """A gyroid-type triply periodic level set with wave numbers k and phases
-    ph per axis: its product terms make faces whose diagonal corners lie on the
-    same side (a sum of one-axis terms never does)."""
-    X, Y, Z = k[0] * x + ph[0], k[1] * y + ph[1], k[2] * z + ph[2]
-    return np.sin(X) * np.cos(Y) + np.sin(Y) * np.cos(Z) + np.sin(Z) * np.cos(X) + c0
-
-
-def _surface_state(n, shift, d, k, ph, c0):
-    """Nodes, face centres and exact edge roots of the surface moved by `shift`
-    cells along axis d."""
-    g = np.arange(n, dtype=np.float64)
-    off = [0.0, 0.0, 0.0]
-    off[d] = shift
-
-    def surf(x, y, z):
-        return _periodic_surface(x - off[0], y - off[1], z - off[2], k, ph, c0)
-
-    def phi_at(ox, oy, oz):
-        return surf(g[None, None, :] + ox, g[None, :, None] + oy, g[:, None, None] + oz)
-
-    phi = phi_at(0.0, 0.0, 0.0)
-    faces = np.stack([phi_at(0.0, 0.5, 0.5), phi_at(0.5, 0.0, 0.5), phi_at(0.5, 0.5, 0.0)])
-    roots = np.full((3,) + phi.shape, np.nan)
-    for a in range(3):
-        cross = (phi >= 0) != (np.roll(phi, -1, axis=2 - a) >= 0)
-        kk, jj, ii = np.nonzero(cross)
-        base = [ii.astype(float), jj.astype(float), kk.astype(float)]
-        lo, hi = np.zeros(len(ii)), np.ones(len(ii))
-
-        def f(t):
-            p = [b.copy() for b in base]
-            p[a] = p[a] + t
-            return surf(p[0], p[1], p[2])
-
-        f0 = f(lo)
-        for _ in range(60):
-            mid = 0.5 * (lo + hi)
-            same = (f(mid) >= 0) == (f0 >= 0)
-            lo = np.where(same, mid, lo)
-            hi = np.where(same, hi, mid)
-        roots[a][kk, jj, ii] = 0.5 * (lo + hi)
-    return phi, faces, roots
-
-
 @pytest.mark.parametrize("seed", [41, 42, 43, 44])
 def test_saddle_face_colours_follow_the_moved_surface(seed):
     """Moved by a uniform velocity (a fraction of a cell along each axis in
@@ -670,18 +625,18 @@ def test_saddle_face_colours_follow_the_moved_surface(seed):
     these surfaces (4-5 periods on 16 cells, random phases)."""
     rng = np.random.default_rng(seed)
     n = 16
-    k = 2.0 * np.pi * rng.integers(4, 6, size=3) / n
+    waves = rng.integers(4, 6, size=3)
     ph = rng.uniform(0.0, 2.0 * np.pi, size=3)
     c0 = rng.uniform(-0.3, 0.3)
     shift = rng.uniform(0.2, 0.45)
-    phi, faces, roots = _surface_state(n, 0.0, 0, k, ph, c0)
+    phi, faces, roots = W.gyroid_surface(n, waves, ph, c0)
     st0 = oracle.init(phi, faces, roots)
     compared = 0
     for d in range(3):
         u = [np.zeros((n, n, n)) for _ in range(3)]
         u[d][:] = 1.0
         st, _ = oracle.sweep(st0, d, u[d], shift)
-        phi1, faces1, _ = _surface_state(n, shift, d, k, ph, c0)
+        phi1, faces1, _ = W.gyroid_surface(n, waves, ph, c0, shift, d)
         far = np.abs(phi1) > 0.5
         assert np.array_equal((st.cb & 1)[far], (phi1 >= 0)[far]), f"sweep {d}: node colours"
         for a in range(3):
