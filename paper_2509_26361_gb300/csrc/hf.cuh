@@ -71,15 +71,19 @@ __device__ __forceinline__ bool hf_axis(const CAccess<WRAP> &c, int d, bool belo
 #pragma unroll
         for (int b1 = -1; b1 <= 1; b1++) {
             const int ox = b1 * e1[0] + b2 * e2[0], oy = b1 * e1[1] + b2 * e2[1], oz = b1 * e1[2] + b2 * e2[2];
-            double H = 0.0, lo = 0.0, hi = 0.0;
+            double H = 0.0;
+            unsigned long long lo = 0ull, hi = 0ull;
 #pragma unroll
             for (int m = -HFH; m <= HFH; m++) {
                 double cv = c(ox + m * ed[0], oy + m * ed[1], oz + m * ed[2]);
                 H += cv;
-                if (m == -HFH) lo = cv;
-                if (m == HFH) hi = cv;
+                if (m == -HFH) lo = (unsigned long long)__double_as_longlong(cv);
+                if (m == HFH) hi = (unsigned long long)__double_as_longlong(cv);
             }
-            ok = ok && (below ? (lo == 1.0 && hi == 0.0) : (lo == 0.0 && hi == 1.0));
+            // pure ends on the bit patterns: == 1.0 is one pattern, == 0.0 two (+0, -0)
+            const bool lo1 = lo == 0x3FF0000000000000ull, lo0 = (lo << 1) == 0ull;
+            const bool hi1 = hi == 0x3FF0000000000000ull, hi0 = (hi << 1) == 0ull;
+            ok = ok && (below ? (lo1 && hi0) : (lo0 && hi1));
             eta[b1 + 1][b2 + 1] = below ? H - (HFH + 0.5) : (HFH + 0.5) - H;
         }
     if (!ok) return false;
