@@ -5,8 +5,11 @@ on the 128^3 periodic workload: 8 non-overlapping spheres (R ~ U[0.05, 0.12]) in
 seeded 12-mode divergence-free Fourier field times cos(pi t / T), T = 2, CFL 0.5
 (512 steps for the full period).  Inputs are seeded and synthetic.
 
-Prints one JSON line (see the design doc for every key).  ``--impl reference`` times
-the CPU FP64 oracle on the same workload instead (a bounded sample of steps).
+Prints one JSON line: throughput (device-resident and end to end with host
+copies), the split sweep's HBM roofline, clocks, launch count, the CPU oracle
+baseline and the learned-curvature, batched and 512^3 blocks.  ``--impl
+reference`` times the CPU FP64 oracle on the same workload instead (a bounded
+sample of steps).
 """
 from __future__ import annotations
 

@@ -3,7 +3,7 @@
 The network (27 -> 128 -> 128 -> 1, ReLU, bf16 operands with FP32
 accumulation) maps the canonically oriented 3x3x3 volume-fraction stencil of an
 interface cell to kappa*h; height functions (Sec. 2.6) stay the fallback and
-the judge.  Every arithmetic step runs in the library's kernels: Front2VOF
+the reference it is measured against.  Every arithmetic step runs in the library's kernels: Front2VOF
 makes the fractions, the gather kernel encodes the stencils, the training
 kernel computes the loss gradient and the Adam kernel updates the weights.
 This module only orchestrates them and computes the analytic labels on the
