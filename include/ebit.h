@@ -352,7 +352,10 @@ int ebit_selftest_bounded_waits(void *cuda_stream, int *report);
  * velocity and the output buffers (all DEVICE pointers), and the sweep's
  * intermediate arrays live in one fixed file-scope device array.
  *   nx, ny, nz, h   grid as in ebit_desc; nx*ny*nz must not exceed 64^3 =
- *                   262144 cells (EBIT_EINVAL beyond), each axis >= 8.
+ *                   262144 cells (EBIT_EINVAL beyond), each axis >= 8.  The
+ *                   tile parts of the scratch hold 1620 tiles of 8^3, the
+ *                   most any such grid has (9 x 9 x 3236), so every grid
+ *                   within the cell limit is accepted.
  *   dir, u_face, dt as for ebit_advect_sweep.
  *   cb_in [N], s_in [3N]    state before the sweep (colour bytes, offsets).
  *   cb_out [N], s_out [3N]  state after the sweep (offsets 0 on edges without
@@ -360,11 +363,13 @@ int ebit_selftest_bounded_waits(void *cuda_stream, int *report);
  *   cuda_stream     cudaStream_t for every launch (NULL = default stream).
  * Every tile is processed (no active band).  Marker displacements of a full
  * cell or more are clamped and not reported (use ebit_advect_sweep for the
- * event counters).  The scratch array is about 11.6 MB and is held by every
+ * event counters).  The scratch array is about 11.3 MB and is held by every
  * GPU that loads the library until the process exits; its address is looked
  * up on the first call made on each device, so make that first call before
- * any stream capture.  All calls on a device share it: calls that overlap on
- * the GPU race and must be ordered by the caller.
+ * any stream capture.  The address is kept for the life of the device's
+ * primary context: do not call this entry point after a cudaDeviceReset.
+ * All calls on a device share it: calls that overlap on the GPU race and must
+ * be ordered by the caller.
  * Errors: EBIT_EINVAL (sizes, dir, null pointers, non-finite h or dt),
  * EBIT_ECUDA (a launch or copy failed). */
 int ebit_advect_sweep_noalloc(int nx, int ny, int nz, double h, int dir, const uint8_t *cb_in,

@@ -11,9 +11,12 @@
 // lives in one file-scope device array of fixed size, below.
 //
 // The scratch array is part of the library image: every GPU that loads the
-// library holds it (about 11.6 MB) until the process exits.  Its device address
+// library holds it (about 11.3 MB) until the process exits.  Its device address
 // is looked up once per device, on the first call made with that device
 // current; that first call should therefore come before any stream capture.
+// The address stays valid for the life of the device's primary context: a
+// process that resets the device (cudaDeviceReset) must not call this entry
+// point afterwards, because the cached address would be stale.
 // Every call on a device reuses the same array and leaves its contents there;
 // the parts that must start at zero are cleared by each call.  Two calls that
 // overlap on the GPU (on different streams without ordering, or from different
@@ -30,17 +33,19 @@ using namespace ebit;
 
 namespace {
 
-// largest grid the variant accepts: 64^3 cells (512 tiles of 8^3)
+// largest grid the variant accepts: 64^3 cells.  Axes that are not multiples
+// of 8 round their tile count up, so the tile parts are sized for the worst
+// grid of at most 64^3 cells with every axis >= 8: 9 x 9 x 3236 cells, 2 x 2 x
+// 405 = 1620 tiles of 8^3 (a brute-force search over all such grids).
 constexpr long long NA_MAX_CELLS = 64LL * 64 * 64;
-constexpr int NA_MAX_TILES = 512;
+constexpr int NA_MAX_TILES = 1620;
 
 // byte offsets inside the scratch array (each part 256-byte aligned)
 constexpr long long align256(long long x) { return (x + 255) & ~255LL; }
 constexpr long long OFF_ADV = 0;
 constexpr long long OFF_BIN = align256(OFF_ADV + 3 * NA_MAX_CELLS * 8);
 constexpr long long OFF_WORK = align256(OFF_BIN + 3 * NA_MAX_CELLS);
-constexpr long long OFF_CBO = align256(OFF_WORK + 4 * NA_MAX_CELLS * 4);
-constexpr long long OFF_LIST = align256(OFF_CBO + NA_MAX_CELLS + 8);
+constexpr long long OFF_LIST = align256(OFF_WORK + 4 * NA_MAX_CELLS * 4);
 constexpr long long OFF_INTS = align256(OFF_LIST + NA_MAX_TILES * 4);  // all_count, wcount[4]
 constexpr long long OFF_CTR = align256(OFF_INTS + 8 * 4);
 constexpr long long OFF_TILES = align256(OFF_CTR + C_TOTAL * 8);       // tile_marker (u32), tile_dirty
@@ -113,11 +118,11 @@ extern "C" int ebit_advect_sweep_noalloc(int nx, int ny, int nz, double h, int d
     g.n[2] = nz;
     for (int a = 0; a < 3; a++) g.td[a] = (g.n[a] + TILE - 1) / TILE;
     g.ntiles = g.td[0] * g.td[1] * g.td[2];
+    if (g.ntiles > NA_MAX_TILES) return EBIT_EINVAL;  // cannot happen within 64^3 cells; kept as a guard
 
     int *list = (int *)(base + OFF_LIST);
     int *ints = (int *)(base + OFF_INTS);
     unsigned long long *ctr = (unsigned long long *)(base + OFF_CTR);
-    uint8_t *cbo = base + OFF_CBO;
 
     // zero what must start at zero: list lengths and counters
     if (cudaMemsetAsync(ints, 0, 8 * sizeof(int), st) != cudaSuccess) return EBIT_ECUDA;
@@ -128,7 +133,7 @@ extern "C" int ebit_advect_sweep_noalloc(int nx, int ny, int nz, double h, int d
     SweepArgs a;
     a.g = g;
     a.cb = cb_in;
-    a.cbo = cbo;
+    a.cbo = cb_out;  // every tile is processed, so every colour byte is written
     for (int k = 0; k < 3; k++) {
         a.s[k] = s_in + k * N;
         a.so[k] = s_out + k * N;
@@ -154,8 +159,7 @@ extern "C" int ebit_advect_sweep_noalloc(int nx, int ny, int nz, double h, int d
     case 1: launch_all<1>(a, st, grid_tiles, sms * 4); break;
     default: launch_all<2>(a, st, grid_tiles, sms * 4); break;
     }
-    // new colour bytes to the caller; offsets of edges without a marker set to 0
-    if (cudaMemcpyAsync(cb_out, cbo, (size_t)N, cudaMemcpyDeviceToDevice, st) != cudaSuccess) return EBIT_ECUDA;
+    // offsets of edges without a marker set to 0
     na_zero_empty_kernel<<<(int)((N + 255) / 256), 256, 0, st>>>(g, cb_out, s_out);
     if (cudaGetLastError() != cudaSuccess) return EBIT_ECUDA;
     return EBIT_OK;
