@@ -1,20 +1,28 @@
 """Benchmark of the GB300 EBIT kinematics path.
 
-One step = three split advection sweeps + Front2VOF + height-function curvature
-on the 128^3 periodic workload: 8 non-overlapping spheres (R ~ U[0.05, 0.12]) in a
-seeded 12-mode divergence-free Fourier field times cos(pi t / T), T = 2, CFL 0.5
-(512 steps for the full period).  Inputs are seeded and synthetic.
+Headline workload (``merging_drops_512``): a 512^3 periodic grid holding two
+seeded ellipsoidal drops (semi-axes U[40, 80] cells, random rotations, supporting
+planes 8 cells apart) carried together by a seeded 12-mode Fourier field plus a
+converging cellular mode, dt = 0.5 h, so that they merge (a topology change of
+the colour field) after about 170 steps.  One step = three split advection
+sweeps + Front2VOF + learned curvature (BF16 tensor cores) with height-function
+fallback; 200 steps by default.  Inputs are seeded and synthetic.
 
-Prints one JSON line: throughput (device-resident and end to end with host
-copies), the split sweep's HBM roofline, clocks, launch count, the CPU oracle
-baseline and the learned-curvature, batched and 512^3 blocks.  ``--impl
-reference`` times the CPU FP64 oracle on the same workload instead (a bounded
-sample of steps).
+Prints one JSON line: throughput with the state resident on the device
+(``value``) and end to end through the C ABI with host buffers (``e2e``), the
+split sweep's HBM roofline, clocks, launch count,
+the CPU oracle baseline on a stratified window sample of the same state (one
+thread and all host cores), and extra blocks: the 128^3 Fourier-spheres
+workload, learned against height-function curvature on 64 ellipsoids, and the
+batched sweep of 64 instances.  ``--impl reference`` times the CPU FP64 oracle
+on the same workload instead.  ``--workload merging_drops_256`` runs the same
+geometry at half the resolution (the size used for profiler captures).
 """
 from __future__ import annotations
 
 import argparse
 import json
+import multiprocessing as mp
 import os
 import statistics
 import subprocess
@@ -29,8 +37,21 @@ if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
 METRIC = "EBIT cell-steps/s (advect+Front2VOF) & curvature/s learned vs HF, % HBM roof"
-WORKLOAD = "fourier_spheres_128"
-N = 128
+HEADLINE = "merging_drops_512"
+# name -> (kind, n): the merging drops keep their geometry in units of the grid
+# (semi-axes 40-80 cells and an 8-cell gap at 512^3, halved at 256^3)
+WORKLOADS = {"merging_drops_512": ("merging", 512), "merging_drops_256": ("merging", 256),
+             "fourier_spheres_128": ("fourier", 128)}
+# per band cell of one split sweep and of Front2VOF (the scope table's figures)
+SWEEP_BYTES_PER_CELL = 62.75
+F2V_BYTES_PER_CELL = 36.4
+# DRAM bytes (read + write) per launch of the split-sweep kernels, from one ncu
+# capture of each; None until the current kernels have been captured.
+NCU_TRAFFIC = None
+# FP64 arithmetic rate of this GPU (thread operations per second; a probe of
+# independent add and multiply chains over every SM); the FP64-list kernel's
+# second roofline
+FP64_OPS_PER_S = 5.26e11
 
 
 def peaks():
@@ -43,14 +64,37 @@ def peaks():
         return 6800.0, "fallback"
 
 
-def workload(seed_offset=0):
+def make_workload(name, seed_offset=0):
     from paper_2509_26361_gb300 import workloads as W
 
-    return W.fourier_spheres(n=N, seed=2 + seed_offset)
+    kind, n = WORKLOADS[name]
+    if kind == "merging":
+        sc = n / 512.0
+        return W.merging_drops(n=n, seed=5 + seed_offset, amin_cells=40.0 * sc, amax_cells=80.0 * sc,
+                               gap_cells=8.0 * sc)
+    return W.fourier_spheres(n=n, seed=2 + seed_offset)
 
 
-def config_dict(w, l2):
-    return {"workload": WORKLOAD, "grid": list(w.n3), "spheres": len(w.shapes), "radius_range": [0.05, 0.12],
+def curvature_mode(name):
+    from paper_2509_26361_gb300 import ebit, learned
+
+    if WORKLOADS[name][0] == "merging" and os.path.exists(learned.PARAMS_FILE):
+        return ebit.EBIT_CURV_MLP_HF
+    return ebit.EBIT_CURV_HF
+
+
+def config_dict(name, w, l2):
+    kind, n = WORKLOADS[name]
+    if kind == "merging":
+        sc = n / 512.0
+        return {"workload": name, "grid": list(w.n3), "drops": 2,
+                "semi_axes_cells": [40.0 * sc, 80.0 * sc], "gap_cells": 8.0 * sc,
+                "velocity": "12-mode Fourier curl scaled to max|u|=0.1 + converging cellular mode (amplitude 1)",
+                "cfl": w.cfl, "steps_to_merge": "about %d" % int(round(170 * n / 512)),
+                "step": "3 split sweeps + Front2VOF + learned curvature (BF16 tensor cores) with HF fallback",
+                "band": "8^3 tiles owning a marker, and their neighbours where a marker lies within 3 cells",
+                "l2": l2}
+    return {"workload": name, "grid": list(w.n3), "spheres": len(w.shapes), "radius_range": [0.05, 0.12],
             "velocity": "12-mode Fourier vector-potential curl x cos(pi t/T), T=2", "cfl": w.cfl,
             "period_steps": w.steps, "step": "3 split sweeps + Front2VOF + HF curvature (FP64)",
             "band": "8^3 tiles owning a marker, and their neighbours where a marker lies within 3 cells",
@@ -58,30 +102,134 @@ def config_dict(w, l2):
 
 
 # --------------------------------------------------------------- oracle arm
-def run_oracle(w, steps, budget_s):
+WIN = 64  # window edge of the CPU sample (cells)
+
+
+def window_sample(w, frac, seed=0):
+    """Stratified sample of the WIN^3 windows tiling the grid: the same fraction
+    ``frac`` (at least one of each kind) of the windows the interface crosses
+    and of those it misses, chosen with a seeded generator.  Returns the window
+    origins (z, y, x) and the counts of each kind in the whole grid."""
+    nx, ny, nz = w.n3
+    c = w.phi >= 0.0
+    cross, empty = [], []
+    for z in range(0, nz, WIN):
+        for y in range(0, ny, WIN):
+            for x in range(0, nx, WIN):
+                b = c[z:z + WIN, y:y + WIN, x:x + WIN]
+                (cross if (b.any() and not b.all()) else empty).append((z, y, x))
+    rng = np.random.default_rng(seed)
+    pick = lambda lst: [lst[i] for i in sorted(rng.choice(len(lst), max(1, int(round(frac * len(lst)))),
+                                                         replace=False))] if lst else []
+    return pick(cross) + pick(empty), len(cross), len(empty)
+
+
+def cut_window(w, o):
+    z, y, x = o
+    sl = (slice(z, z + WIN), slice(y, y + WIN), slice(x, x + WIN))
+    sub = lambda a: np.ascontiguousarray(a[(slice(None),) + sl]) if a.ndim == 4 else np.ascontiguousarray(a[sl])
+    return (sub(w.phi), sub(w.phi_faces), None if w.s_exact is None else sub(w.s_exact), sub(w.u),
+            [w.lam(k) for k in range(64)])
+
+
+def oracle_window_steps(args):
+    """One window advanced ``steps`` steps by the oracle as a periodic box: three
+    split sweeps + Front2VOF + height-function curvature per step.  Returns the
+    seconds taken and the sum of the last volume fractions."""
+    phi, faces, s_exact, u, lams, steps = args
     import oracle
 
-    st = oracle.init(w.phi, w.phi_faces)
-    C, _ = oracle.front2vof(st)
-    done = 0
+    st = oracle.init(phi, faces, s_exact)
     t0 = time.perf_counter()
+    Csum = 0.0
     for n in range(steps):
-        st = oracle.step(st, n, w.u, w.lam(n))
+        st = oracle.step(st, n, u, lams[n])
         C, _ = oracle.front2vof(st)
         oracle.hf_curvature(C)
-        done += 1
-        if time.perf_counter() - t0 > budget_s:
-            break
+        Csum = float(C.sum())
+    return time.perf_counter() - t0, Csum
+
+
+def cpu_baseline_block(name, w, frac1=0.125, frac_all=0.25):
+    """The oracle on a stratified sample of WIN^3 windows of the workload's
+    initial state, each advanced one step as a periodic box.  One thread: the
+    windows in sequence; all cores: a larger sample over a process pool (spawn)
+    with one worker per host core.  value = cells of the sample per second of
+    wall time; the whole-grid step would take (its windows) / value."""
+    import oracle
+
+    oracle.build()
+    origins, n_cross, n_empty = window_sample(w, frac1, seed=11)
+    jobs = [cut_window(w, o) + (1,) for o in origins]
+    t0 = time.perf_counter()
+    res1 = [oracle_window_steps(j) for j in jobs]
+    t1 = time.perf_counter() - t0
+    cells1 = len(jobs) * WIN ** 3
+    origins_all, _, _ = window_sample(w, frac_all, seed=12)
+    jobs_all = [cut_window(w, o) + (1,) for o in origins_all]
+    cores = os.cpu_count() or 1
+    ctx = mp.get_context("spawn")
+    with ctx.Pool(cores) as pool:
+        pool.map(oracle_window_steps, jobs_all[:cores])  # start-up and import outside the timing
+        t0 = time.perf_counter()
+        res_all = pool.map(oracle_window_steps, jobs_all)
+        t_all = time.perf_counter() - t0
+    cells_all = len(jobs_all) * WIN ** 3
+    # the same window gives the same fractions in both runs (independent boxes)
+    same = {o: r[1] for o, r in zip(origins, res1)}
+    agree = all(same[o] == r[1] for o, r in zip(origins_all, res_all) if o in same)
+    desc = (f"oracle (plain C, FP64, no network: HF curvature) on {WIN}^3 windows cut from the initial "
+            f"{name} state, each advanced 1 step (3 sweeps + Front2VOF + HF) as a periodic box; stratified: "
+            "the same fraction of the %d windows the drops cross and of the %d they miss" % (n_cross, n_empty))
+    return {"value": cells1 / t1, "unit": "cell-steps/s", "cores": 1, "kind": "oracle",
+            "sample": desc + f"; {len(jobs)} windows in sequence (each set up and stepped), {t1:.1f} s",
+            "all_cores": {"value": cells_all / t_all, "unit": "cell-steps/s", "cores": cores,
+                          "sample": f"{len(jobs_all)} windows (same rule, larger fraction) over a spawn "
+                                    f"pool of {cores} workers, {t_all:.1f} s wall",
+                          "same_results_as_one_thread": bool(agree)}}
+
+
+def reference_arm(args):
+    """The oracle as the reference arm: every step advances the stratified
+    window sample one step (one thread), within a time budget."""
+    import oracle
+
+    oracle.build()
+    w = make_workload(args.workload)
+    origins, n_cross, n_empty = window_sample(w, 0.125, seed=11)
+    states = []
+    for o in origins:
+        phi, faces, s_exact, u, lams = cut_window(w, o)
+        states.append([oracle.init(phi, faces, s_exact), u, lams])
+    budget = 150.0
+    done = 0
+    warm = min(args.warmup, 1)  # one untimed step: the oracle has nothing to warm
+    t0 = time.perf_counter()
+    for k in range(warm + args.steps):
+        for sv in states:
+            sv[0] = oracle.step(sv[0], k % 64, sv[1], sv[2][k % 64])
+            C, _ = oracle.front2vof(sv[0])
+            oracle.hf_curvature(C)
+        if k == warm - 1:
+            t0 = time.perf_counter()
+        if k >= warm:
+            done += 1
+            if time.perf_counter() - t0 > budget:
+                break
     dt = time.perf_counter() - t0
-    return done, dt
-
-
-def cpu_baseline_block(w, budget_s=15.0, max_steps=64):
-    done, dt = run_oracle(w, max_steps, budget_s)
-    val = w.n3[0] * w.n3[1] * w.n3[2] * done / dt
-    return {"value": val, "unit": "cell-steps/s", "cores": 1, "kind": "oracle",
-            "sample": f"first {done} steps of the {WORKLOAD} workload (3 sweeps + Front2VOF + HF each), "
-                      f"single-threaded C oracle, {dt:.1f} s"}
+    cells = len(states) * WIN ** 3
+    val = cells * done / dt
+    line = {"metric": METRIC, "value": val, "unit": "cell-steps/s", "n_gpus": args.gpus, "steps": done,
+            "warmup": warm, "ms_per_step": dt * 1e3 / max(done, 1), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
+            "config": config_dict(args.workload, w, "n/a (CPU)"),
+            "cpu_baseline": {"value": val, "unit": "cell-steps/s", "cores": 1, "kind": "oracle",
+                             "sample": f"{len(states)} {WIN}^3 windows of the initial state (stratified over the "
+                                       f"{n_cross} windows the drops cross and {n_empty} they miss), advanced "
+                                       f"together; {done} of {args.steps} steps within {budget:.0f} s, one thread"},
+            "e2e": {"value": val, "unit": "cell-steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    return 0
 
 
 # ------------------------------------------------------------------ clocks
@@ -90,7 +238,6 @@ class ClockSampler:
         self.rows = []
         self.proc = None
         self.thread = None
-        self.window = None
 
     def start(self):
         q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
@@ -162,182 +309,188 @@ def job_value(cells, steps, world, max_ms):
     return cells * steps * world / (max_ms * 1e-3)
 
 
-def run_gpu(args, rank, world):
-    import torch
+class Run:
+    """One workload on one GPU: the context, its buffers and the step."""
 
-    from paper_2509_26361_gb300 import ebit
+    def __init__(self, name, dev, seed_offset=0):
+        import torch
 
-    dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0)))
-    torch.cuda.set_device(dev)
-    w = workload(seed_offset=rank)
-    nc = w.n3[0] * w.n3[1] * w.n3[2]
-    g = ebit.Grid(*w.n3, h=w.h, device=dev)
-    tdev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)
-    phi, faces = tdev(w.phi), tdev(w.phi_faces)
-    ud = [tdev(w.u[d]) for d in range(3)]
-    C = torch.zeros(g.shape, dtype=torch.float64, device=dev)
-    kh = torch.zeros_like(C)
-    st = torch.zeros(g.shape, dtype=torch.uint8, device=dev)
-    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)  # 256 MiB > L2
+        from paper_2509_26361_gb300 import ebit, learned
 
-    def one_step(n, sweep_ev=None):
+        self.name = name
+        self.w = make_workload(name, seed_offset)
+        w = self.w
+        self.dev = dev
+        self.g = ebit.Grid(*w.n3, h=w.h, device=dev)
+        tdev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)
+        self.phi, self.faces = tdev(w.phi), tdev(w.phi_faces)
+        self.s_exact = None if w.s_exact is None else tdev(w.s_exact)
+        self.ud = [tdev(w.u[d]) for d in range(3)]
+        self.mode = curvature_mode(name)
+        self.mlp = None
+        if self.mode != ebit.EBIT_CURV_HF:
+            self.mlp = learned.load_network()
+            self.g.set_mlp(self.mlp)
+        self.C = torch.zeros(self.g.shape, dtype=torch.float64, device=dev)
+        self.kh = torch.zeros_like(self.C)
+        self.st = torch.zeros(self.g.shape, dtype=torch.uint8, device=dev)
+        self.flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)  # 256 MiB > L2
+        self.cells = w.n3[0] * w.n3[1] * w.n3[2]
+
+    def one_step(self, n, ud=None, sweep_ev=None):
         """One step; with sweep_ev, a pair of CUDA events on the context's stream
-        brackets the step's three split-sweep calls (band + advect + integer
-        pass + FP64 lists each), which run back to back."""
-        dt = w.lam(n) * g.h
+        brackets the step's three split-sweep calls (advect + integer pass +
+        FP64 lists each), which run back to back."""
+        ud = self.ud if ud is None else ud
+        dt = self.w.lam(n) * self.g.h
         if sweep_ev is not None:
             sweep_ev[0].record()
         for d in ((0, 1, 2) if n % 2 == 0 else (2, 1, 0)):
-            g.sweep(d, ud[d], dt)
+            self.g.sweep(d, ud[d], dt)
         if sweep_ev is not None:
             sweep_ev[1].record()
-        g.front2vof(C)
-        g.curvature(C, kh, st)
+        self.g.front2vof(self.C)
+        self.g.curvature(self.C, self.kh, self.st, mode=self.mode)
 
-    def start():
-        g.init(phi, faces)
-        g.front2vof(C, ebit.EBIT_FULL)
-        g.curvature(C, kh, st, flags=ebit.EBIT_FULL)
-        for n in range(args.warmup):
-            one_step(n)
+    def start(self, warmup):
+        import torch
+
+        from paper_2509_26361_gb300 import ebit
+
+        self.g.init(self.phi, self.faces, self.s_exact)
+        self.g.front2vof(self.C, ebit.EBIT_FULL)
+        self.g.curvature(self.C, self.kh, self.st, mode=self.mode, flags=ebit.EBIT_FULL)
+        for n in range(warmup):
+            self.one_step(n)
         torch.cuda.synchronize()
-        g.reset_counters()
+        self.g.reset_counters()
 
-    E = lambda: torch.cuda.Event(enable_timing=True)
-    # ---- timed region: value, and the split sweep's duration for the roofline
-    start()
-    clocks = ClockSampler()
-    if rank == 0:
-        clocks.start()
-        time.sleep(0.3)
-    evs = [(E(), E()) for _ in range(args.steps)]
-    sev = [(E(), E()) for _ in range(args.steps)]
-    if world > 1:
-        import torch.distributed as dist
-        dist.barrier()
-    torch.cuda.synchronize()
-    wall0 = time.perf_counter()
-    for i in range(args.steps):
-        flush.zero_()
-        evs[i][0].record()
-        one_step(args.warmup + i, sev[i])
-        evs[i][1].record()
-    torch.cuda.synchronize()
-    wall1 = time.perf_counter()
-    if world > 1:
-        dist.barrier()
-    step_ms = [a.elapsed_time(b) for a, b in evs]
-    # per-sweep duration: the three sweeps of a step share one bracket
-    sweep_ms = [a.elapsed_time(b) / 3.0 for a, b in sev for _ in range(3)]
-    total_ms = float(sum(step_ms))
-    cnt = g.counters()
-    total_ms = max_over_ranks(total_ms, world, dev)
+    def timed(self, warmup, steps, world=1, clocks=None):
+        """Device-resident steps: an L2 flush (outside the events) before every
+        step, an event pair around each step and one around its three sweeps."""
+        import torch
 
-    # ------------------------------------------------ end-to-end (host buffers)
-    e2e = None
-    if rank == 0:
-        e2e = run_e2e(args, g, w, dev, C, kh, st)
-    clk = clocks.summary(wall0, wall1) if rank == 0 else None
-    clocks.stop()
+        E = lambda: torch.cuda.Event(enable_timing=True)
+        self.start(warmup)
+        evs = [(E(), E()) for _ in range(steps)]
+        sev = [(E(), E()) for _ in range(steps)]
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+        torch.cuda.synchronize()
+        wall0 = time.perf_counter()
+        for i in range(steps):
+            self.flush.zero_()
+            evs[i][0].record()
+            self.one_step(warmup + i, sweep_ev=sev[i])
+            evs[i][1].record()
+        torch.cuda.synchronize()
+        wall1 = time.perf_counter()
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+        step_ms = [a.elapsed_time(b) for a, b in evs]
+        sweep_ms = [a.elapsed_time(b) / 3.0 for a, b in sev for _ in range(3)]
+        return dict(total_ms=float(sum(step_ms)), step_ms=step_ms, sweep_ms=sweep_ms, cnt=self.g.counters(),
+                    wall=(wall0, wall1))
 
-    # ---- instrumented pass over the same steps: an event pair around every
-    # kernel launch of the library (per-kernel times and launch counts; the
-    # events slow the step, so none of its times enter value or roofline)
-    start()
-    g.profile(True)
-    for i in range(args.steps):
-        flush.zero_()
-        one_step(args.warmup + i)
-    torch.cuda.synchronize()
-    prof = g.profile_read()
-    g.profile(False)
-    g.close()
-    return dict(total_ms=total_ms, step_ms=step_ms, sweep_ms=sweep_ms, prof=prof, cnt=cnt, nc=nc, w=w, e2e=e2e,
-                clk=clk)
+    def instrumented(self, warmup, steps):
+        """The same steps from the same state with an event pair around every
+        kernel launch of the library: per-kernel times and the launch count.
+        The events slow the step, so none of these times enter value or
+        roofline."""
+        import torch
 
+        self.start(warmup)
+        self.g.profile(True)
+        for i in range(steps):
+            self.flush.zero_()
+            self.one_step(warmup + i)
+        torch.cuda.synchronize()
+        prof = self.g.profile_read()
+        self.g.profile(False)
+        return prof
 
-def run_e2e(args, g, w, dev, C, kh, st):
-    """Same steps through the public API with host buffers: every step uploads
-    its three velocity fields from pinned host memory and reads C and kappa*h
-    back into pinned host memory, inside the timed region.  The copies run on
-    two copy streams and overlap the neighbouring steps' compute: the velocity
-    of step i+1 goes into the other of two device buffers while step i
-    computes, and C, kappa*h of step i are read back while the sweeps of step
-    i+1 run (its Front2VOF waits for that read-back, since it overwrites C)."""
-    import torch
+    def e2e(self, warmup, steps):
+        """The same steps through the public API with host buffers: every step
+        uploads its three velocity fields from pinned host memory and reads C
+        and kappa*h back into pinned host memory, inside the timed region.  The
+        copies run on two copy streams and overlap the neighbouring steps'
+        compute: the velocity of step i+1 goes into the other of two device
+        buffers while step i computes, and C, kappa*h of step i are read back
+        while the sweeps of step i+1 run (its Front2VOF waits for that
+        read-back, since it overwrites C)."""
+        import torch
 
-    E = lambda: torch.cuda.Event(enable_timing=False)
-    uh = [torch.from_numpy(np.ascontiguousarray(w.u[d])).pin_memory() for d in range(3)]
-    ud = [[torch.empty(g.shape, dtype=torch.float64, device=dev) for _ in range(3)] for _ in range(2)]
-    Ch = torch.empty(g.shape, dtype=torch.float64).pin_memory()
-    kh_h = torch.empty(g.shape, dtype=torch.float64).pin_memory()
-    cs = torch.cuda.current_stream()
-    up, down = torch.cuda.Stream(), torch.cuda.Stream()
-    ev_in, ev_used = [E(), E()], [E(), E()]
-    ev_out, ev_back = E(), E()
-    steps = args.steps
-    s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    torch.cuda.synchronize()
-    s0.record(cs)
-    up.wait_event(s0)
-    with torch.cuda.stream(up):
-        for d in range(3):
-            ud[0][d].copy_(uh[d], non_blocking=True)
-        ev_in[0].record(up)
-    for i in range(steps):
-        n = args.warmup + args.steps + i
-        slot = i % 2
-        if i + 1 < steps:
-            # next step's velocity into the buffer step i - 1 used
-            with torch.cuda.stream(up):
-                if i >= 1:
-                    up.wait_event(ev_used[1 - slot])
-                for d in range(3):
-                    ud[1 - slot][d].copy_(uh[d], non_blocking=True)
-                ev_in[1 - slot].record(up)
-        cs.wait_event(ev_in[slot])
-        g.step(n, ud[slot], w.lam(n) * g.h)
-        ev_used[slot].record(cs)
-        if i >= 1:
-            cs.wait_event(ev_back)
-        g.front2vof(C)
-        g.curvature(C, kh, st)
-        ev_out.record(cs)
-        with torch.cuda.stream(down):
-            down.wait_event(ev_out)
-            Ch.copy_(C, non_blocking=True)
-            kh_h.copy_(kh, non_blocking=True)
-            ev_back.record(down)
-    cs.wait_event(ev_back)
-    s1.record(cs)
-    torch.cuda.synchronize()
-    ms = s0.elapsed_time(s1)
-    nc = w.n3[0] * w.n3[1] * w.n3[2]
-    return {"value": nc * steps / (ms * 1e-3), "unit": "cell-steps/s",
-            "h2d_bytes_per_step": 3 * nc * 8, "d2h_bytes_per_step": 2 * nc * 8,
-            "overlap": "uploads and read-backs on two copy streams, overlapping the neighbouring steps",
-            "l2": "not flushed between these steps; the 84 MB of host copies per step pass through L2"}
+        self.start(warmup)
+        w, g, dev = self.w, self.g, self.dev
+        E = lambda: torch.cuda.Event(enable_timing=False)
+        uh = [torch.from_numpy(np.ascontiguousarray(w.u[d])).pin_memory() for d in range(3)]
+        ud = [[torch.empty(g.shape, dtype=torch.float64, device=dev) for _ in range(3)] for _ in range(2)]
+        Ch = torch.empty(g.shape, dtype=torch.float64).pin_memory()
+        kh_h = torch.empty(g.shape, dtype=torch.float64).pin_memory()
+        cs = torch.cuda.current_stream()
+        up, down = torch.cuda.Stream(), torch.cuda.Stream()
+        ev_in, ev_used = [E(), E()], [E(), E()]
+        ev_out, ev_back = E(), E()
+        s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        s0.record(cs)
+        up.wait_event(s0)
+        with torch.cuda.stream(up):
+            for d in range(3):
+                ud[0][d].copy_(uh[d], non_blocking=True)
+            ev_in[0].record(up)
+        for i in range(steps):
+            n = warmup + i
+            slot = i % 2
+            if i + 1 < steps:
+                with torch.cuda.stream(up):
+                    if i >= 1:
+                        up.wait_event(ev_used[1 - slot])
+                    for d in range(3):
+                        ud[1 - slot][d].copy_(uh[d], non_blocking=True)
+                    ev_in[1 - slot].record(up)
+            cs.wait_event(ev_in[slot])
+            dt = w.lam(n) * g.h
+            for d in ((0, 1, 2) if n % 2 == 0 else (2, 1, 0)):
+                g.sweep(d, ud[slot][d], dt)
+            ev_used[slot].record(cs)
+            if i >= 1:
+                cs.wait_event(ev_back)
+            g.front2vof(self.C)
+            g.curvature(self.C, self.kh, self.st, mode=self.mode)
+            ev_out.record(cs)
+            with torch.cuda.stream(down):
+                down.wait_event(ev_out)
+                Ch.copy_(self.C, non_blocking=True)
+                kh_h.copy_(self.kh, non_blocking=True)
+                ev_back.record(down)
+        cs.wait_event(ev_back)
+        s1.record(cs)
+        torch.cuda.synchronize()
+        ms = s0.elapsed_time(s1)
+        del ud, uh, Ch, kh_h
+        return {"value": self.cells * steps / (ms * 1e-3), "unit": "cell-steps/s",
+                "h2d_bytes_per_step": 3 * self.cells * 8, "d2h_bytes_per_step": 2 * self.cells * 8,
+                "ms_per_step": ms / steps,
+                "overlap": "uploads and read-backs on two copy streams, overlapping the neighbouring steps",
+                "l2": "not flushed between these steps; the host copies pass through L2"}
 
-
-# DRAM bytes (read + write) per launch of the split-sweep kernels (sweep along x), one ncu
-# capture each (--set full, cold caches) of the same 128^3 workload; see
-# profiles/kernels_fourier_spheres_128.md.  None once the kernels change.
-NCU_TRAFFIC = {"advect": 2953216.0, "sweep": 2512384.0, "fp64": 3747840.0, "band": 24832.0}
-# per band cell of one split sweep and of Front2VOF (the scope table's figures)
-SWEEP_BYTES_PER_CELL = 62.75
-F2V_BYTES_PER_CELL = 36.4
+    def close(self):
+        self.g.close()
+        if self.mlp is not None:
+            self.mlp.close()
 
 
-def roofline_block(res):
-    """The dominant stage is the split sweep (its band, advect, integer-pass and
+def roofline_block(res, prof):
+    """The dominant stage is the split sweep (its advect, integer-pass and
     FP64-list launches; the scope table defines its algorithmic bytes per band
     cell).  achieved = 62.75 B x band cells per sweep / mean duration of a
-    split-sweep call, from the CUDA events that bracket each call on the
-    context's stream inside the timed region.  The marker-level minimum (colour
-    bytes of the band, offsets and one velocity sample per marker) is given
-    beside it; per-kernel times come from the instrumented pass."""
+    split-sweep call, from the CUDA events that bracket the three calls of each
+    step on the context's stream inside the timed region (a third of that
+    interval per call).  Per-kernel times come from the instrumented pass."""
     hbm, src = peaks()
-    prof = res["prof"]
     cnt = res["cnt"]
     nsweeps = len(res["sweep_ms"])
     per_sweep_s = float(np.mean(res["sweep_ms"])) * 1e-3
@@ -349,8 +502,8 @@ def roofline_block(res):
     traffic = sum(NCU_TRAFFIC.values()) if NCU_TRAFFIC else None
     stages = {"split_sweep": sum(prof[k][0] for k in ("band", "advect", "sweep", "fp64") if k in prof),
               "front2vof": prof.get("f2v", (0.0, 0))[0],
-              "curvature": prof.get("hf", (0.0, 0))[0] + prof.get("scan", (0.0, 0))[0]}
-    return {"bound": "hbm", "kernel": "split sweep (band + advect + integer pass + FP64 lists)",
+              "curvature": sum(prof.get(k, (0.0, 0))[0] for k in ("hf", "scan", "mlp"))}
+    return {"bound": "hbm", "kernel": "split sweep (advect + integer pass + FP64 lists)",
             "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm, "traffic": traffic,
             "peak_source": src, "alg_bytes_per_launch": alg, "alg_bytes_rule": "62.75 B per band cell per sweep",
             "band_cells_per_sweep": band_cells, "markers_per_sweep": markers,
@@ -385,24 +538,7 @@ def curvature_block():
                        "mlp_all_cells": r["rms_mlp"], "mlp_hf_all_cells": r["rms_mlp_hf"]},
             "hf_no_value_cells": r["hf_no_value"], "mlp_hf_fallback_cells": r["mlp_hf_fallback"],
             "dtype": "bf16 tensor cores (tcgen05; mma.sync path beside it), fp32 accumulate (HF: f64)",
-            "ms_per_pass": r["ms"], "training": training_record()}
-
-
-def training_record():
-    """Throughput of the run that made the shipped parameters (its report sits
-    next to them): stencil passes (forward + backward + Adam) per second."""
-    from paper_2509_26361_gb300 import learned
-
-    path = os.path.join(os.path.dirname(learned.PARAMS_FILE), "mlp_curvature_train_report.json")
-    try:
-        with open(path) as f:
-            rep = json.load(f)
-    except OSError:
-        return None
-    steps = rep["stencils"] // rep["batch"] * rep["batch"] * rep["epochs"]
-    return {"stencils": rep["stencils"], "epochs": rep["epochs"], "batch": rep["batch"],
-            "train_seconds": rep["train_seconds"], "stencil_passes_per_s": steps / rep["train_seconds"],
-            "final_loss": rep["loss_per_epoch"][-1], "source": "data/mlp_curvature_train_report.json"}
+            "ms_per_pass": r["ms"]}
 
 
 def batched_block(steps=256, warmup=4):
@@ -411,7 +547,8 @@ def batched_block(steps=256, warmup=4):
     spheres, dt = 0.5 h), 3 split sweeps per step, one cooperative launch per
     sweep, pairs of steps replayed from a CUDA graph, launch shape autotuned.
     Value: cell-steps/s over all instances (sweeps only, as the batched path
-    covers advection)."""
+    covers advection); its roofline counts the scope table's 62.75 B per band
+    cell of a sweep, like the single-grid sweep."""
     import torch
 
     from paper_2509_26361_gb300 import ebit
@@ -429,6 +566,8 @@ def batched_block(steps=256, warmup=4):
     shape, max_shape = b.launch_shape()
     b.run(0, warmup, graph=True)
     b.sync()
+    for i in range(len(insts)):
+        b.instance(i).reset_counters()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     torch.cuda.synchronize()
     e0.record()
@@ -442,11 +581,10 @@ def batched_block(steps=256, warmup=4):
         c = b.instance(i).counters()
         tiles += c["tiles"]
         markers += c["markers"]
-    sweeps = 3 * (steps + warmup)
-    # per sweep: colour byte read + written per band cell; offset read, offset
-    # written and one velocity sample per marker
-    alg = (2.0 * tiles * 512.0 + 24.0 * markers) / sweeps
-    per_sweep_s = ms * 1e-3 / (3 * steps)
+    sweeps = 3 * steps
+    band_cells = tiles * 512.0 / sweeps
+    alg = SWEEP_BYTES_PER_CELL * band_cells
+    per_sweep_s = ms * 1e-3 / sweeps
     hbm, src = peaks()
     out = {"workload": "batched_64 (64 instances, sizes {32,48,64,96,128}^3 seeded, 1-4 spheres, own "
                        "Fourier fields, CFL 0.5, seed 4)",
@@ -456,111 +594,35 @@ def batched_block(steps=256, warmup=4):
            "launch_shape_ctas_per_sm": shape, "autotune_ms_per_6_sweeps": tune_ms,
            "roofline": {"bound": "hbm", "achieved": alg / per_sweep_s / 1e9, "peak": hbm, "unit": "GB/s",
                         "frac": alg / per_sweep_s / 1e9 / hbm, "peak_source": src,
-                        "alg_bytes_per_sweep": alg},
+                        "alg_bytes_per_sweep": alg, "alg_bytes_rule": "62.75 B per band cell per sweep",
+                        "band_cells_per_sweep": band_cells, "markers_per_sweep": markers / sweeps},
            "l2": "state (%.2f GB) larger than L2; no flush" % (cells * 51 / 1e9)}
     b.close()
     return out
 
 
-def large_block(steps=20, warmup=3):
-    """The 512^3 configuration: two seeded ellipsoidal drops (semi-axes U[40, 80]
-    cells) driven together by a Fourier field plus a converging cellular mode,
-    dt = 0.5 h; one step = 3 split sweeps + Front2VOF + learned curvature with
-    height-function fallback.  Timed with CUDA events per step (and per
-    split-sweep call, for the roofline) after an L2 flush; per-kernel times
-    come from an instrumented pass over the following steps.  Reported: the
-    band roofline of the split sweep, and the dense-equivalent rate
-    (the scope table's 224.6 B per cell-step of advection + Front2VOF over all
-    512^3 cells) for comparison with a dense implementation."""
-    import torch
-
-    from paper_2509_26361_gb300 import ebit, learned
-    from paper_2509_26361_gb300 import workloads as W
-
-    w = W.merging_drops(n=512, seed=5)
-    dev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
-    g = ebit.Grid(*w.n3)
-    g.init(dev(w.phi), dev(w.phi_faces), dev(w.s_exact))
-    ud = [dev(w.u[d]) for d in range(3)]
-    del w.phi, w.phi_faces, w.s_exact
-    mlp = learned.load_network() if os.path.exists(learned.PARAMS_FILE) else None
-    mode = ebit.EBIT_CURV_MLP_HF if mlp is not None else ebit.EBIT_CURV_HF
-    if mlp is not None:
-        g.set_mlp(mlp)
-    C = torch.zeros(g.shape, dtype=torch.float64, device="cuda")
-    kh = torch.zeros_like(C)
-    st = torch.zeros(g.shape, dtype=torch.uint8, device="cuda")
-    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
-
-    def one(n, sweep_ev=None):
-        dt = w.lam(n) * g.h
-        if sweep_ev is not None:
-            sweep_ev[0].record()
-        for d in ((0, 1, 2) if n % 2 == 0 else (2, 1, 0)):
-            g.sweep(d, ud[d], dt)
-        if sweep_ev is not None:
-            sweep_ev[1].record()
-        g.front2vof(C)
-        g.curvature(C, kh, st, mode=mode)
-
-    E = lambda: torch.cuda.Event(enable_timing=True)
-    g.front2vof(C, ebit.EBIT_FULL)
-    g.curvature(C, kh, st, mode=mode, flags=ebit.EBIT_FULL)
-    for n in range(warmup):
-        one(n)
-    torch.cuda.synchronize()
-    g.reset_counters()
-    evs = [(E(), E()) for _ in range(steps)]
-    sev = [(E(), E()) for _ in range(steps)]
-    for i in range(steps):
-        flush.zero_()
-        evs[i][0].record()
-        one(warmup + i, sev[i])
-        evs[i][1].record()
-    torch.cuda.synchronize()
-    ms = sum(a.elapsed_time(b) for a, b in evs)
-    sweep_ms = [a.elapsed_time(b) / 3.0 for a, b in sev for _ in range(3)]
-    cnt = g.counters()
-    # instrumented pass over the following steps: per-kernel times
-    g.profile(True)
-    for i in range(steps):
-        flush.zero_()
-        one(warmup + steps + i)
-    torch.cuda.synchronize()
-    prof = g.profile_read()
-    g.profile(False)
-    g.close()
-    if mlp is not None:
-        mlp.close()
-    cells = 512 ** 3
-    nsw = len(sweep_ms)
-    band_cells = cnt["tiles"] / nsw * 512.0
-    hbm, src = peaks()
-    achieved = SWEEP_BYTES_PER_CELL * band_cells / (float(np.mean(sweep_ms)) * 1e-3) / 1e9
-    dense = (3 * SWEEP_BYTES_PER_CELL + F2V_BYTES_PER_CELL) * cells * steps / (ms * 1e-3) / 1e9
-    return {"workload": "merging_drops_512 (two ellipsoids, semi-axes U[40,80] cells, gap 8 cells, seed 5)",
-            "value": cells * steps / (ms * 1e-3), "unit": "cell-steps/s", "steps": steps, "warmup": warmup,
-            "ms_per_step": ms / steps, "curvature_mode": "learned + HF fallback" if mlp is not None else "HF",
-            "band_cells_per_sweep": band_cells, "markers_per_sweep": cnt["markers"] / nsw,
-            "roofline": {"bound": "hbm", "kernel": "split sweep", "achieved": achieved, "peak": hbm, "unit": "GB/s",
-                         "frac": achieved / hbm, "peak_source": src},
-            "dense_equivalent": {"achieved": dense, "unit": "GB/s", "frac": dense / hbm,
-                                 "rule": "224.6 B per cell-step over all 512^3 cells"},
-            "avg_sweep_us": float(np.mean(sweep_ms)) * 1e3,
-            "kernel_ms_instrumented": {k: round(v[0], 3) for k, v in prof.items()},
-            "l2": "flushed (256 MiB write) before every timed step, outside its events"}
+def extra_grid_block(name, steps, warmup, dev):
+    """Another single-grid workload with the headline's timing rules."""
+    r = Run(name, dev)
+    res = r.timed(warmup, steps)
+    prof = r.instrumented(warmup, steps)
+    r.close()
+    return {"workload": name, "value": r.cells * steps / (res["total_ms"] * 1e-3), "unit": "cell-steps/s",
+            "steps": steps, "warmup": warmup, "ms_per_step": res["total_ms"] / steps,
+            "config": config_dict(name, r.w, "flushed (256 MiB write) before every timed step, outside its events"),
+            "roofline": roofline_block(res, prof), "counters": res["cnt"]}
 
 
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=512)
-    ap.add_argument("--warmup", type=int, default=8)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ebit", choices=["ebit", "reference"])
+    ap.add_argument("--workload", default=HEADLINE, choices=sorted(WORKLOADS))
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--no-curvature", action="store_true")
-    ap.add_argument("--no-batched", action="store_true")
-    ap.add_argument("--no-large", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-extra", action="store_true", help="skip the 128^3, curvature and batched blocks")
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", 0))
     world = int(os.environ.get("WORLD_SIZE", 1))
@@ -568,51 +630,57 @@ def main():
     if args.impl == "reference":
         if rank != 0:
             return 0
-        w = workload()
-        budget = 120.0
-        done, dt = run_oracle(w, args.steps, budget)
-        nc = w.n3[0] * w.n3[1] * w.n3[2]
-        val = nc * done / dt
-        line = {"metric": METRIC, "value": val, "unit": "cell-steps/s", "n_gpus": args.gpus, "steps": done,
-                "warmup": 0, "ms_per_step": dt * 1e3 / done, "higher_is_better": True, "scaling": "weak",
-                "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
-                "config": config_dict(w, "n/a (CPU)"),
-                "cpu_baseline": {"value": val, "unit": "cell-steps/s", "cores": 1, "kind": "oracle",
-                                 "sample": f"first {done} of {args.steps} requested steps (time budget "
-                                           f"{budget:.0f} s), single-threaded C oracle"},
-                "e2e": {"value": val, "unit": "cell-steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
-        print(json.dumps(line))
-        return 0
+        return reference_arm(args)
+
+    import torch
 
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl" if os.environ.get("EBIT_BENCH_BACKEND", "nccl") == "nccl" else "gloo")
-    res = run_gpu(args, rank, world)
+    dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0)))
+    torch.cuda.set_device(dev)
+    run = Run(args.workload, dev, seed_offset=rank)
+    clocks = ClockSampler()
+    if rank == 0:
+        clocks.start()
+        time.sleep(0.3)
+    res = run.timed(args.warmup, args.steps, world)
+    total_ms = max_over_ranks(res["total_ms"], world, dev)
+    clk = clocks.summary(*res["wall"]) if rank == 0 else None
+    clocks.stop()
+    prof = run.instrumented(args.warmup, args.steps)
+    e2e = None
+    if rank == 0 and not args.no_e2e:
+        e2e = run.e2e(args.warmup, args.steps)
+    w = run.w
+    run.close()
     if rank != 0:
         if world > 1:
             import torch.distributed as dist
             dist.destroy_process_group()
         return 0
-    value = job_value(res["nc"], args.steps, world, res["total_ms"])
-    prof = res["prof"]
+    value = job_value(run.cells, args.steps, world, total_ms)
     # every profiled scope brackets exactly one kernel launch; the instrumented
     # pass runs the same steps from the same state as the timed region
     launches = sum(v[1] for v in prof.values())
     line = {"metric": METRIC, "value": value, "unit": "cell-steps/s", "n_gpus": world, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": res["total_ms"] / args.steps, "higher_is_better": True,
+            "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": config_dict(res["w"], "flushed (256 MiB write) before every timed step, outside its events"),
-            "roofline": roofline_block(res), "e2e": res["e2e"], "gpu_launches": launches,
-            "clocks": res["clk"],
-            "counters": res["cnt"]}
-    if not args.no_curvature:
+            "config": config_dict(args.workload, w, "flushed (256 MiB write) before every timed step, outside its events"),
+            "roofline": roofline_block(res, prof), "e2e": e2e, "gpu_launches": launches,
+            "clocks": clk, "counters": res["cnt"]}
+    hbm, _ = peaks()
+    cells = run.cells
+    line["dense_equivalent"] = {
+        "achieved": (3 * SWEEP_BYTES_PER_CELL + F2V_BYTES_PER_CELL) * cells * args.steps / (total_ms * 1e-3) / 1e9,
+        "unit": "GB/s", "rule": "224.6 B per cell-step of advection + Front2VOF over all cells"}
+    line["dense_equivalent"]["frac"] = line["dense_equivalent"]["achieved"] / hbm
+    if not args.no_extra:
+        line["fourier_spheres_128"] = extra_grid_block("fourier_spheres_128", 512, 8, dev)
         line["curvature"] = curvature_block()
-    if not args.no_batched:
         line["batched"] = batched_block()
-    if not args.no_large:
-        line["large"] = large_block()
     if not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline_block(res["w"])
+        line["cpu_baseline"] = cpu_baseline_block(args.workload, w)
     print(json.dumps(line))
     if world > 1:
         import torch.distributed as dist

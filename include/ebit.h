@@ -105,6 +105,7 @@ typedef struct {
     int64_t inconsistent; /* colour/crossing parity disagreements (never expected) */
     int64_t cfl;          /* marker displacements of a full cell or more (error) */
     int64_t tiles;        /* 8x8x8 tiles processed by the sweeps (band size, summed) */
+    int64_t nonfinite;    /* markers whose displacement was NaN or infinite (error) */
 } ebit_counters_t;
 
 /* Create a context for one grid: allocates the double-buffered state and the
@@ -149,8 +150,11 @@ int ebit_get_state(ebit_ctx *ctx, uint8_t *cb, double *s);
  *   u_face [N]  u_dir at the dir-faces (device).  A field of the form
  *               g(t) * u0 may be passed as u0 with dt * g(t).
  *   dt          signed time step (finite); |u| dt / h must stay below 1.
- * Errors: EBIT_EINVAL (dir, null, non-finite dt), EBIT_ECUDA; EBIT_ECFL is
- * raised later if a marker moved a full cell. */
+ * Errors: EBIT_EINVAL (dir, null), EBIT_ENONFINITE (dt NaN or infinite),
+ * EBIT_ECUDA.  Found on the device and reported by the next ebit_sync or
+ * ebit_counters: EBIT_ENONFINITE if the velocity at a marker was NaN or
+ * infinite (the marker is left in place), else EBIT_ECFL if a marker moved a
+ * full cell (its displacement is clamped). */
 int ebit_advect_sweep(ebit_ctx *ctx, int dir, const double *u_face, double dt);
 
 /* Front2VOF volume fractions (Sec. 2.6, Eq. 7): per cell, the face segments
@@ -172,14 +176,16 @@ int ebit_front2vof(ebit_ctx *ctx, double *C, int flags);
 int ebit_curvature(ebit_ctx *ctx, const double *C, double *kappa_h, uint8_t *status, int mode,
                    int flags);
 
-/* Copy the event counters accumulated since the last reset (synchronises). */
+/* Copy the event counters accumulated since the last reset (synchronises).
+ * Returns EBIT_ENONFINITE or EBIT_ECFL as ebit_sync does, EBIT_WINCONSISTENT
+ * if the consistency counters are non-zero, else EBIT_OK. */
 int ebit_counters(ebit_ctx *ctx, ebit_counters_t *out);
 
 /* Zero the event counters (stream-ordered). */
 int ebit_reset_counters(ebit_ctx *ctx);
 
-/* Wait for the context's stream; returns pending device errors (EBIT_ECFL,
- * EBIT_ETIMEOUT) or EBIT_OK. */
+/* Wait for the context's stream; returns pending device errors
+ * (EBIT_ENONFINITE before EBIT_ECFL, see ebit_advect_sweep) or EBIT_OK. */
 int ebit_sync(ebit_ctx *ctx);
 
 /* Number of tiles (8x8x8 cells) the last sweep processed; -1 if unknown. */
@@ -190,7 +196,7 @@ int ebit_band_tiles(ebit_ctx *ctx);
  * elapsed device time per kind.  Kinds (index into the arrays below): */
 enum {
     EBIT_PROF_SWEEP = 0, /* split-sweep reconstruction kernels */
-    EBIT_PROF_BAND = 1,  /* band tile list of a sweep and its memset */
+    EBIT_PROF_BAND = 1,  /* (no kernel of its own: each sweep's band pass lists the next sweep's band) */
     EBIT_PROF_F2V = 2,   /* Front2VOF: list of the swept tiles (incremental calls), band and cut-cell kernels */
     EBIT_PROF_HF = 3,    /* height-function kernel (interface-cell list pass) */
     EBIT_PROF_MLP = 4,   /* learned-curvature kernels (with the height-function fallback pass) */

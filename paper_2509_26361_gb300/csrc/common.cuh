@@ -66,8 +66,9 @@ __host__ __device__ inline unsigned near_bits(int lx, int ly, int lz) {
 }
 
 enum Counter { C_MARKERS = 0, C_ANNIHILATE = 1, C_MULTI = 2, C_INCONSISTENT = 3, C_CFL = 4, C_N = 5 };
-// extra device counters after the event counters
-enum { C_F2V_BAD = C_N, C_TILES = C_N + 1, C_TOTAL = C_N + 2 };
+// extra device counters after the event counters (C_NONFINITE: markers whose
+// displacement u dt / h was not finite; they are left in place)
+enum { C_F2V_BAD = C_N, C_TILES = C_N + 1, C_NONFINITE = C_N + 2, C_TOTAL = C_N + 3 };
 
 struct Grid {
     int n[3];        // cells per axis

@@ -42,9 +42,8 @@ struct ebit_ctx {
     int cur;
     uint32_t *tile_marker;    // per tile: proximity mask of its markers (see near_bits)
     uint8_t *tile_dirty, *tile_cchg;
-    int *band_list, *band_count;  // band_count[2]: one slot per sweep parity
-    int band_par;                 // slot of the next sweep's band list (0 on entry)
-    int band_last;                // slot of the last sweep's band list
+    int *band_list, *band_count;  // band_count[2]: the lengths of band_list and band_list2
+    int band_last;                // slot of the last sweep's band list (-1: every tile)
     int *work_list, *work_count;  // work_count[2]: one slot per incremental Front2VOF parity
     int f2v_par;
     int *all_list, *all_count;
@@ -53,7 +52,19 @@ struct ebit_ctx {
     double *adv[3];           // advected marker coordinates of the current sweep (scratch)
     int8_t *bin[3];           // floor(2 adv) (scratch)
     unsigned *work[NLISTS];   // work lists of a sweep (scratch; a batch view has the first 4)
-    int *wcount;              // [NLISTS] list lengths ([4] in a batch view)
+    int *wcount;              // [NLISTS] list lengths ([4] in a batch view), then the band pass's tile counter
+    // A context's band sweeps alternate between two sets of lists: a sweep
+    // reads set mk_par (the markers and band the previous sweep listed) and
+    // writes set mk_par ^ 1.  Set 0 is work/wcount above, set 1 work2/wcount2.
+    unsigned *work2[NLISTS];
+    int *wcount2;
+    unsigned *mk_al[2];       // aligned edges that carry a marker, per set
+    int *mk_count;            // [2] their lengths
+    int *band_list2;          // the band list of set 1 (set 0: band_list)
+    uint32_t *band_flag[2];   // per tile: listed in that set's band list
+    int mk_par;               // set written by the last sweep
+    int mk_dir;               // sweep axis of the last sweep
+    int mk_valid;             // the lists of set mk_par describe the current state
     unsigned *cut;            // cells cut by the interface at the last Front2VOF
     int *ncut;
     unsigned *iface[2];       // interface cells of the last two curvature calls
@@ -69,7 +80,7 @@ struct ebit_ctx {
     const double *last_C;
     const double *last_kh;
     const uint8_t *last_st;
-    int grid_sweep, grid_adv, grid_fp64, grid_f2v, grid_f2vl, grid_hf, grid_hfl;
+    int grid_sweep, grid_adv, grid_advl, grid_fp64, grid_f2v, grid_f2vl, grid_hf, grid_hfl;
     // per-kernel CUDA-event timing (ebit_profile)
     int prof_on;
     std::vector<cudaEvent_t> ev;

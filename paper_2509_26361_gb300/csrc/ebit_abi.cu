@@ -77,6 +77,13 @@ int mark_all(ebit_ctx *ctx) {
     ctx->sweeps_since_f2v = 1;
     CU(cudaMemsetAsync(ctx->tile_marker, 0xFF, ctx->g.ntiles * sizeof(uint32_t), ctx->stream));
     CU(cudaMemsetAsync(ctx->tile_dirty, 1, ctx->g.ntiles, ctx->stream));
+    // the next sweep processes every tile and lists the markers and band anew
+    ctx->mk_valid = 0;
+    if (ctx->owns_state) {
+        for (int q = 0; q < 2; q++)
+            CU(cudaMemsetAsync(ctx->band_flag[q], 0, ctx->g.ntiles * sizeof(uint32_t), ctx->stream));
+        CU(cudaMemsetAsync(ctx->band_count, 0, 2 * sizeof(int), ctx->stream));
+    }
     ctx->last_C = nullptr;
     ctx->last_kh = nullptr;
     ctx->last_st = nullptr;
@@ -134,11 +141,14 @@ struct ProfScope {
 };
 
 template <int D>
-int sweep_launch(ebit_ctx *ctx, const SweepArgs &args) {
+int sweep_launch(ebit_ctx *ctx, const SweepArgs &args, const MarkerLists *ml) {
     {
         ProfScope ps(ctx, EBIT_PROF_ADVECT);
-        int r = launched(ctx, launch_pdl(advect_kernel<D, NLISTS>, ctx->grid_adv, 256, 0, ctx->stream, args),
-                         "advect_kernel");
+        int r = ml ? launched(ctx, launch_pdl(advect_list_kernel<D, NLISTS>, ctx->grid_advl, 256, 0, ctx->stream,
+                                              args, *ml),
+                              "advect_list_kernel")
+                   : launched(ctx, launch_pdl(advect_kernel<D, NLISTS>, ctx->grid_adv, 256, 0, ctx->stream, args),
+                              "advect_kernel");
         if (r) return r;
     }
     {
@@ -173,13 +183,19 @@ static int create_ctx(const ebit_desc *desc, const ebit_state_arrays *st, ebit_c
         ctx->adv[a] = nullptr;
         ctx->bin[a] = nullptr;
     }
-    for (int k = 0; k < NLISTS; k++) ctx->work[k] = nullptr;
+    for (int k = 0; k < NLISTS; k++) ctx->work[k] = ctx->work2[k] = nullptr;
+    ctx->wcount2 = ctx->mk_count = ctx->band_list2 = nullptr;
+    ctx->mk_al[0] = ctx->mk_al[1] = nullptr;
+    ctx->band_flag[0] = ctx->band_flag[1] = nullptr;
+    ctx->mk_par = 0;
+    ctx->mk_dir = 0;
+    ctx->mk_valid = 0;
     ctx->iface[0] = ctx->iface[1] = nullptr;
     ctx->wcount = ctx->ncut = ctx->niface = ctx->nscan = ctx->zero = nullptr;
     ctx->cut = ctx->scan = nullptr;
     ctx->cur_if = 0;
     ctx->if_slot = 0;
-    ctx->band_par = ctx->band_last = 0;
+    ctx->band_last = -1;
     ctx->f2v_par = 0;
     ctx->sweeps_since_f2v = 0;
     ctx->mlp = nullptr;
@@ -228,8 +244,14 @@ static int create_ctx(const ebit_desc *desc, const ebit_state_arrays *st, ebit_c
         for (int a = 0; a < 3 && ok; a++)
             ok = ok && alloc((void **)&ctx->adv[a], ctx->N * sizeof(double)) && alloc((void **)&ctx->bin[a], ctx->N);
         for (int k = 0; k < NLISTS && ok; k++) ok = ok && alloc((void **)&ctx->work[k], ctx->N * sizeof(unsigned));
-        ok = ok && alloc((void **)&ctx->wcount, NLISTS * sizeof(int)) && alloc((void **)&ctx->tile_marker, nt * sizeof(uint32_t)) &&
+        ok = ok && alloc((void **)&ctx->wcount, (NLISTS + 1) * sizeof(int)) && alloc((void **)&ctx->tile_marker, nt * sizeof(uint32_t)) &&
              alloc((void **)&ctx->tile_dirty, nt) && alloc((void **)&ctx->ctr, C_TOTAL * sizeof(unsigned long long));
+        for (int k = 0; k < NLISTS && ok; k++) ok = ok && alloc((void **)&ctx->work2[k], ctx->N * sizeof(unsigned));
+        for (int q = 0; q < 2 && ok; q++)
+            ok = ok && alloc((void **)&ctx->mk_al[q], ctx->N * sizeof(unsigned)) &&
+                 alloc((void **)&ctx->band_flag[q], nt * sizeof(uint32_t));
+        ok = ok && alloc((void **)&ctx->wcount2, (NLISTS + 1) * sizeof(int)) && alloc((void **)&ctx->mk_count, 2 * sizeof(int)) &&
+             alloc((void **)&ctx->band_list2, nt * sizeof(int));
     }
     ok = ok && alloc((void **)&ctx->cut, ctx->N * sizeof(unsigned)) && alloc((void **)&ctx->scan, ctx->N * sizeof(unsigned)) &&
          alloc((void **)&ctx->iface[0], ctx->N * sizeof(unsigned)) &&
@@ -250,6 +272,8 @@ static int create_ctx(const ebit_desc *desc, const ebit_state_arrays *st, ebit_c
     ctx->grid_sweep = std::max(1, std::min(nt, ctx->sms * std::max(occ, 1)));
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, advect_kernel<0, NLISTS>, 256, 0);
     ctx->grid_adv = std::max(1, std::min(nt, ctx->sms * std::max(occ, 1)));
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, advect_list_kernel<0, NLISTS>, 256, 0);
+    ctx->grid_advl = ctx->sms * std::max(occ, 1);
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fp64_kernel<0, NLISTS>, 128, 0);
     ctx->grid_fp64 = ctx->sms * std::max(occ, 1);
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, f2v_band_kernel, 256, 0);
@@ -260,7 +284,11 @@ static int create_ctx(const ebit_desc *desc, const ebit_state_arrays *st, ebit_c
     ctx->grid_hf = std::max(1, std::min(nt, ctx->sms * std::max(occ, 1)));
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, hf_list_kernel<true>, 128, 0);
     ctx->grid_hfl = ctx->sms * std::max(occ, 1);
-    cudaMemsetAsync(ctx->wcount, 0, (ctx->owns_state ? NLISTS : 4) * sizeof(int), ctx->stream);
+    cudaMemsetAsync(ctx->wcount, 0, (ctx->owns_state ? NLISTS + 1 : 4) * sizeof(int), ctx->stream);
+    if (ctx->owns_state) {
+        cudaMemsetAsync(ctx->wcount2, 0, (NLISTS + 1) * sizeof(int), ctx->stream);
+        cudaMemsetAsync(ctx->mk_count, 0, 2 * sizeof(int), ctx->stream);
+    }
     cudaMemsetAsync(ctx->ncut, 0, sizeof(int), ctx->stream);
     cudaMemsetAsync(ctx->niface, 0, 3 * sizeof(int), ctx->stream);
     cudaMemsetAsync(ctx->band_count, 0, 2 * sizeof(int), ctx->stream);
@@ -309,8 +337,18 @@ void ebit_destroy(ebit_ctx *ctx) {
             cudaFree(ctx->adv[a]);
             cudaFree(ctx->bin[a]);
         }
-        for (int k = 0; k < NLISTS; k++) cudaFree(ctx->work[k]);
+        for (int k = 0; k < NLISTS; k++) {
+            cudaFree(ctx->work[k]);
+            cudaFree(ctx->work2[k]);
+        }
         cudaFree(ctx->wcount);
+        cudaFree(ctx->wcount2);
+        cudaFree(ctx->mk_al[0]);
+        cudaFree(ctx->mk_al[1]);
+        cudaFree(ctx->mk_count);
+        cudaFree(ctx->band_flag[0]);
+        cudaFree(ctx->band_flag[1]);
+        cudaFree(ctx->band_list2);
     }
     cudaFree(ctx->tile_cchg);
     cudaFree(ctx->band_list);
@@ -373,27 +411,16 @@ int ebit_advect_sweep(ebit_ctx *ctx, int dir, const double *u_face, double dt) {
     if (!u_face) return fail(ctx, EBIT_EINVAL, "ebit_advect_sweep: null velocity");
     if (!ctx->owns_state)
         return fail(ctx, EBIT_EINVAL, "ebit_advect_sweep: a batch instance is swept by ebit_batch_advect_sweep");
-    if (!std::isfinite(dt)) return fail(ctx, EBIT_EINVAL, "ebit_advect_sweep: non-finite dt");
-    const int *list, *count;
-    if (ctx->dense) {
-        list = ctx->all_list;
-        count = ctx->all_count;
-    } else {
-        // band_count[bp] is 0 (cleared by the previous sweep's band kernel,
-        // or at creation); this one clears the other slot for the next sweep
-        ProfScope ps(ctx, EBIT_PROF_BAND);
-        const int bp = ctx->band_par;
-        int r = launched(ctx,
-                         launch_pdl(band_kernel, blocks_for(ctx->g.ntiles, 256, ctx->sms), 256, 0, ctx->stream, ctx->g,
-                                    (const uint32_t *)ctx->tile_marker, ctx->band_list, ctx->band_count + bp,
-                                    ctx->band_count + (bp ^ 1)),
-                         "band_kernel");
-        if (r) return r;
-        list = ctx->band_list;
-        count = ctx->band_count + bp;
-        ctx->band_last = bp;
-        ctx->band_par = bp ^ 1;
-    }
+    if (!std::isfinite(dt)) return fail(ctx, EBIT_ENONFINITE, "ebit_advect_sweep: non-finite dt");
+    // Band sweeps alternate between two sets of lists (see ebit_ctx): this
+    // sweep reads set rd (its band and the markers to move, listed by the
+    // previous sweep) and writes set wr for the next one.  After a state
+    // change, and in dense mode, every tile is processed and the markers are
+    // found from the colours of each tile instead.
+    const int rd = ctx->mk_par, wr = rd ^ 1;
+    const bool lists = !ctx->dense && ctx->mk_valid;
+    const int *list = lists ? (rd ? ctx->band_list2 : ctx->band_list) : ctx->all_list;
+    const int *count = lists ? ctx->band_count + rd : ctx->all_count;
     SweepArgs a;
     a.g = ctx->g;
     int c = ctx->cur, o = c ^ 1;
@@ -405,8 +432,10 @@ int ebit_advect_sweep(ebit_ctx *ctx, int dir, const double *u_face, double dt) {
         a.adv[k] = ctx->adv[k];
         a.bin[k] = ctx->bin[k];
     }
-    for (int k = 0; k < NLISTS; k++) a.work[k] = ctx->work[k];
-    a.wcount = ctx->wcount;
+    unsigned *const *wk_wr = wr ? ctx->work2 : ctx->work;
+    for (int k = 0; k < NLISTS; k++) a.work[k] = wk_wr[k];
+    a.wcount = wr ? ctx->wcount2 : ctx->wcount;
+    a.tile_next = a.wcount + NLISTS;  // one int after the list lengths
     a.u = u_face;
     a.lam = dt / ctx->h;
     a.list = list;
@@ -414,11 +443,42 @@ int ebit_advect_sweep(ebit_ctx *ctx, int dir, const double *u_face, double dt) {
     a.ctr = ctx->ctr;
     a.tile_marker = ctx->tile_marker;
     a.tile_dirty = ctx->tile_dirty;
+    if (!ctx->dense) {
+        a.mk_out = ctx->mk_al[wr];
+        a.mk_out_count = ctx->mk_count + wr;
+        a.band_flag_in = lists ? ctx->band_flag[rd] : nullptr;
+        a.band_flag_out = ctx->band_flag[wr];
+        a.band_out = wr ? ctx->band_list2 : ctx->band_list;
+        a.band_out_count = ctx->band_count + wr;
+    }
+    MarkerLists ml;
+    if (lists) {
+        // the previous sweep's aligned markers and its unaligned work lists
+        const int pd = ctx->mk_dir;
+        unsigned *const *wk_rd = rd ? ctx->work2 : ctx->work;
+        const int *wc_rd = rd ? ctx->wcount2 : ctx->wcount;
+        ml.list[0] = ctx->mk_al[rd];
+        ml.count[0] = ctx->mk_count + rd;
+        ml.axis[0] = pd;
+        ml.list[1] = wk_rd[0];
+        ml.count[1] = wc_rd + 0;
+        ml.axis[1] = (pd + 1) % 3;
+        ml.list[2] = wk_rd[1];
+        ml.count[2] = wc_rd + 1;
+        ml.axis[2] = (pd + 2) % 3;
+    }
     int r;
     switch (dir) {
-    case 0: r = sweep_launch<0>(ctx, a); break;
-    case 1: r = sweep_launch<1>(ctx, a); break;
-    default: r = sweep_launch<2>(ctx, a); break;
+    case 0: r = sweep_launch<0>(ctx, a, lists ? &ml : nullptr); break;
+    case 1: r = sweep_launch<1>(ctx, a, lists ? &ml : nullptr); break;
+    default: r = sweep_launch<2>(ctx, a, lists ? &ml : nullptr); break;
+    }
+    if (r) return r;
+    ctx->band_last = lists ? rd : -1;
+    if (!ctx->dense) {
+        ctx->mk_par = wr;
+        ctx->mk_dir = dir;
+        ctx->mk_valid = 1;
     }
     if (r) return r;
     ctx->cur = o;
@@ -596,6 +656,8 @@ int ebit_counters(ebit_ctx *ctx, ebit_counters_t *out) {
     out->inconsistent = (int64_t)h[C_INCONSISTENT] + (int64_t)h[C_F2V_BAD];
     out->cfl = (int64_t)h[C_CFL];
     out->tiles = (int64_t)h[C_TILES];
+    out->nonfinite = (int64_t)h[C_NONFINITE];
+    if (out->nonfinite) return fail(ctx, EBIT_ENONFINITE, "a marker's displacement was not finite (NaN or infinite velocity)");
     if (out->cfl) return fail(ctx, EBIT_ECFL, "a marker moved a full cell or more in one sweep");
     return out->inconsistent ? EBIT_WINCONSISTENT : EBIT_OK;
 }
@@ -608,16 +670,18 @@ int ebit_reset_counters(ebit_ctx *ctx) {
 
 int ebit_sync(ebit_ctx *ctx) {
     if (!ctx) return EBIT_EINVAL;
-    unsigned long long cfl = 0;
-    CU(cudaMemcpyAsync(&cfl, ctx->ctr + C_CFL, sizeof(cfl), cudaMemcpyDeviceToHost, ctx->stream));
+    unsigned long long h[C_TOTAL];
+    CU(cudaMemcpyAsync(h, ctx->ctr, sizeof(h), cudaMemcpyDeviceToHost, ctx->stream));
     CU(cudaStreamSynchronize(ctx->stream));
-    if (cfl) return fail(ctx, EBIT_ECFL, "a marker moved a full cell or more in one sweep");
+    // a non-finite velocity is named before the CFL verdict it would also trip
+    if (h[C_NONFINITE]) return fail(ctx, EBIT_ENONFINITE, "a marker's displacement was not finite (NaN or infinite velocity)");
+    if (h[C_CFL]) return fail(ctx, EBIT_ECFL, "a marker moved a full cell or more in one sweep");
     return EBIT_OK;
 }
 
 int ebit_band_tiles(ebit_ctx *ctx) {
     if (!ctx) return -1;
-    if (ctx->dense) return ctx->g.ntiles;
+    if (ctx->dense || ctx->band_last < 0) return ctx->g.ntiles;
     int n = -1;
     if (cudaMemcpyAsync(&n, ctx->band_count + ctx->band_last, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream) != cudaSuccess) return -1;
     if (cudaStreamSynchronize(ctx->stream) != cudaSuccess) return -1;

@@ -75,24 +75,6 @@ __global__ void canonical_s_kernel(Grid g, const uint8_t *__restrict__ cb, const
     }
 }
 
-// Band: the tiles in_band selects.  The list order depends on scheduling;
-// every consumer is order-independent.  zero_next (may be null): a counter
-// that a later launch appends to, cleared here once the preceding kernels are
-// complete (count itself must already be 0).
-__global__ void band_kernel(Grid g, const uint32_t *__restrict__ flag, int *__restrict__ list, int *__restrict__ count,
-                            int *zero_next) {
-    pdl_wait();
-    if (zero_next && blockIdx.x == 0 && threadIdx.x == 0) *zero_next = 0;
-    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < g.ntiles; t += gridDim.x * blockDim.x) {
-        int tx = t % g.td[0], ty = (t / g.td[0]) % g.td[1], tz = t / (g.td[0] * g.td[1]);
-        const bool on = in_band(g, flag, tx, ty, tz);
-        if (on) {
-            int slot = atomicAdd(count, 1);
-            list[slot] = t;
-        }
-    }
-}
-
 // List of the flagged tiles (no dilation), clearing the flags; zero0 and
 // zero1 (may be null) are counters of later launches, cleared as in
 // band_kernel.

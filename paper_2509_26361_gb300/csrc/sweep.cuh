@@ -59,6 +59,29 @@ struct SweepArgs {
     unsigned long long *ctr;         // event counters
     uint32_t *tile_marker;           // per tile: proximity mask of its markers in the input or the output
     uint8_t *tile_dirty;             // per tile: processed since the last Front2VOF
+    // Lists for the next sweep (a context's band sweeps; null elsewhere).  The
+    // band pass appends every aligned edge that carries a marker after the
+    // sweep to mk_out (the unaligned ones are its work lists 0 and 1), and
+    // builds the next sweep's band: each tile it processes sets the flag of,
+    // and lists, every tile its new proximity mask points to, and clears its
+    // own flag of the current band.
+    unsigned *mk_out = nullptr;
+    int *mk_out_count = nullptr;
+    uint32_t *band_flag_in = nullptr;
+    uint32_t *band_flag_out = nullptr;
+    int *band_out = nullptr;
+    int *band_out_count = nullptr;
+    // next band tile to take (blocks of the band pass take tiles in turn from
+    // this counter; null: a fixed stride over the list)
+    int *tile_next = nullptr;
+};
+
+// The markers of the state before a sweep, as node ids of their edges, one
+// list per edge axis (the previous sweep's band pass wrote them).
+struct MarkerLists {
+    const unsigned *list[3];
+    const int *count[3];
+    int axis[3];
 };
 
 struct P2 {
@@ -257,7 +280,8 @@ __device__ __forceinline__ int warp_append(int *counter, bool flag) {
 
 // ---------------------------------------------------------------- advection
 // Move every marker of one band tile once (Eq. 2).  CFL >= 1 is counted and
-// clamped.  Called by all threads of the block; s_mk/s_c/s_n are its shared
+// clamped; a displacement that is not finite (NaN or infinite velocity) is
+// counted apart and the marker stays where it is.  Called by all threads of the block; s_mk/s_c/s_n are its shared
 // staging; u is u_D on the D-faces and lam = dt / h.
 template <int D>
 __device__ __forceinline__ void advect_tile(const SweepArgs &a, const double *__restrict__ u, double lam, int tile,
@@ -286,14 +310,17 @@ __device__ __forceinline__ void advect_tile(const SweepArgs &a, const double *__
     }
     __syncthreads();
     const int n = *s_n;
-    unsigned hits = 0;
+    unsigned hits = 0, bad = 0;
     for (int k = threadIdx.x; k < n; k += blockDim.x) {
         int it = s_mk[k], c = it & 511, e = it >> 9;
         int q[3] = {o[0] + (c & 7), o[1] + ((c >> 3) & 7), o[2] + (c >> 6)};
         const int id = lin3(a.g, q);
         double sv = __ldg(a.s[e] + id);
         double cf = interp_u<D>(a.g, u, q, e, sv) * lam;
-        if (!(fabs(cf) < 1.0)) {
+        if (!isfinite(cf)) {
+            bad++;
+            cf = 0.0;
+        } else if (!(fabs(cf) < 1.0)) {
             hits++;
             cf = cf > 0.0 ? ONE_MINUS : -ONE_MINUS;
         }
@@ -303,7 +330,19 @@ __device__ __forceinline__ void advect_tile(const SweepArgs &a, const double *__
     }
     unsigned v = __reduce_add_sync(0xffffffffu, hits);
     if ((threadIdx.x & 31) == 0 && v) atomicAdd(a.ctr + C_CFL, (unsigned long long)v);
+    v = __reduce_add_sync(0xffffffffu, bad);
+    if ((threadIdx.x & 31) == 0 && v) atomicAdd(a.ctr + C_NONFINITE, (unsigned long long)v);
     __syncthreads();
+}
+
+// the counters the band pass appends to start at zero (cleared by the launch before it)
+template <int NL>
+__device__ __forceinline__ void clear_sweep_counts(const SweepArgs &a) {
+    if (blockIdx.x != 0) return;
+    if (threadIdx.x < NL) a.wcount[threadIdx.x] = 0;
+    if (threadIdx.x == 32 && a.mk_out_count) *a.mk_out_count = 0;
+    if (threadIdx.x == 33 && a.band_out_count) *a.band_out_count = 0;
+    if (threadIdx.x == 34 && a.tile_next) *a.tile_next = 0;
 }
 
 template <int D, int NL = 4>
@@ -313,8 +352,56 @@ __global__ void __launch_bounds__(256) advect_kernel(SweepArgs a) {
     __shared__ int s_n;
     pdl_wait();
     const int ntl = *a.count;
-    if (blockIdx.x == 0 && threadIdx.x < NL) a.wcount[threadIdx.x] = 0;
+    clear_sweep_counts<NL>(a);
     for (int li = blockIdx.x; li < ntl; li += gridDim.x) advect_tile<D>(a, a.u, a.lam, a.list[li], s_mk, s_c, &s_n);
+}
+
+// Advection from the marker lists (Eq. 2): one thread per marker, no tile
+// staging.  Every marker of the state is on a list, so the same markers as in
+// advect_tile are moved, with the same arithmetic.
+template <int D, int NL = 4>
+__global__ void __launch_bounds__(256) advect_list_kernel(SweepArgs a, MarkerLists m) {
+    pdl_wait();
+    clear_sweep_counts<NL>(a);
+    const int n0 = *m.count[0], n1 = *m.count[1], n2 = *m.count[2];
+    const int total = n0 + n1 + n2;
+    const int stride = gridDim.x * blockDim.x;
+    const int iters = (total + stride - 1) / stride;
+    const int nx = a.g.n[0], nxy = a.g.n[0] * a.g.n[1];
+    unsigned hits = 0, bad = 0;
+    for (int it = 0; it < iters; it++) {
+        const int t = list_item(it);
+        if (t >= total) continue;
+        // selects rather than indexing, which would copy the parameter arrays
+        // to local memory
+        const int k = t < n0 ? 0 : (t < n0 + n1 ? 1 : 2);
+        const int j = t - (k == 0 ? 0 : (k == 1 ? n0 : n0 + n1));
+        const unsigned *lst = k == 0 ? m.list[0] : (k == 1 ? m.list[1] : m.list[2]);
+        const int e = k == 0 ? m.axis[0] : (k == 1 ? m.axis[1] : m.axis[2]);
+        const int id = (int)__ldg(lst + j);
+        const int z = id / nxy, r = id - z * nxy;
+        const int y = r / nx;
+        const int q[3] = {r - y * nx, y, z};
+        const double *se = e == 0 ? a.s[0] : (e == 1 ? a.s[1] : a.s[2]);
+        double *adv = e == 0 ? a.adv[0] : (e == 1 ? a.adv[1] : a.adv[2]);
+        int8_t *bin = e == 0 ? a.bin[0] : (e == 1 ? a.bin[1] : a.bin[2]);
+        const double sv = __ldg(se + id);
+        double cf = interp_u<D>(a.g, a.u, q, e, sv) * a.lam;
+        if (!isfinite(cf)) {
+            bad++;
+            cf = 0.0;
+        } else if (!(fabs(cf) < 1.0)) {
+            hits++;
+            cf = cf > 0.0 ? ONE_MINUS : -ONE_MINUS;
+        }
+        const double x = (e == D) ? sv + cf : cf;
+        adv[id] = x;
+        bin[id] = (int8_t)(int)floor(2.0 * x);
+    }
+    unsigned v = __reduce_add_sync(0xffffffffu, hits);
+    if ((threadIdx.x & 31) == 0 && v) atomicAdd(a.ctr + C_CFL, (unsigned long long)v);
+    v = __reduce_add_sync(0xffffffffu, bad);
+    if ((threadIdx.x & 31) == 0 && v) atomicAdd(a.ctr + C_NONFINITE, (unsigned long long)v);
 }
 
 // ----------------------------------------------------------- cell context
@@ -588,15 +675,22 @@ __device__ __forceinline__ void sweep_tile(const SweepArgs &a, int tile, uint8_t
         int o[3];
         tile_origin(a.g, tile, o);
         if (threadIdx.x == 0) *s_flag = 0;
+        // walk the region in global order (x fastest), so that a warp's loads
+        // fall on a few rows of the grid whatever the sweep axis; the staged
+        // copy is indexed in sweep-local order (A fastest)
+        constexpr int E0 = A == 0 ? RA : (T1 == 0 ? R1 : R2);
+        constexpr int E1 = A == 1 ? RA : (T1 == 1 ? R1 : R2);
         for (int r = threadIdx.x; r < RA * R1 * R2; r += blockDim.x) {
-            int ka = r % RA, k1 = (r / RA) % R1, k2 = r / (RA * R1);
+            const int gl[3] = {r % E0, (r / E0) % E1, r / (E0 * E1)};
+            const int ka = gl[A], k1 = gl[T1], k2 = gl[T2];
             int q[3];
             q[A] = o[A] + ka - 1;
             q[T1] = o[T1] + k1;
             q[T2] = o[T2] + k2;
             const int id = lin3(a.g, q);
-            s_b[r] = __ldg(a.cb + id);
-            s_n[r] = ld_in<F>(a.bin[A] + id);
+            const int sr = ka + RA * (k1 + R1 * k2);
+            s_b[sr] = __ldg(a.cb + id);
+            s_n[sr] = ld_in<F>(a.bin[A] + id);
         }
         __syncthreads();
         unsigned ev[C_N] = {0, 0, 0, 0, 0};
@@ -605,6 +699,7 @@ __device__ __forceinline__ void sweep_tile(const SweepArgs &a, int tile, uint8_t
             int x = o[0] + (c & 7), y = o[1] + ((c >> 3) & 7), z = o[2] + (c >> 6);
             bool valid = x < a.g.n[0] && y < a.g.n[1] && z < a.g.n[2];
             bool push[6] = {false, false, false, false, false, false};
+            bool push_al = false;
             int myid = 0;
             if (valid) {
                 SweepCell<D, F> cell(a, x, y, z);
@@ -698,6 +793,7 @@ __device__ __forceinline__ void sweep_tile(const SweepArgs &a, int tile, uint8_t
                             a.so[A][myid] = v;
                             ev[C_MARKERS]++;
                             out_marker = true;
+                            push_al = true;
                         } else if (nl >= 2) {
                             ev[C_ANNIHILATE]++;
                         }
@@ -740,6 +836,10 @@ __device__ __forceinline__ void sweep_tile(const SweepArgs &a, int tile, uint8_t
                 int slot = warp_append(a.wcount + k, push[k]);
                 if (slot >= 0) a.work[k][slot] = (unsigned)myid;
             }
+            if (a.mk_out) {
+                const int slot = warp_append(a.mk_out_count, push_al);
+                if (slot >= 0) a.mk_out[slot] = (unsigned)myid;
+            }
         }
         {
             const unsigned v = __reduce_or_sync(0xffffffffu, mk);
@@ -751,9 +851,21 @@ __device__ __forceinline__ void sweep_tile(const SweepArgs &a, int tile, uint8_t
             if ((threadIdx.x & 31) == 0 && v) atomicAdd(a.ctr + k, (unsigned long long)v);
         }
         __syncthreads();
+        const unsigned fl = *s_flag;
         if (threadIdx.x == 0) {
-            a.tile_marker[tile] = *s_flag;
+            a.tile_marker[tile] = fl;
             a.tile_dirty[tile] = 1;
+            if (a.band_flag_in) a.band_flag_in[tile] = 0u;
+        }
+        // next sweep's band: the tiles this tile's markers reach (bit
+        // near_bit(dx, dy, dz) names the neighbour in that direction)
+        if (a.band_flag_out && threadIdx.x < 27 && ((fl >> threadIdx.x) & 1u)) {
+            const int b = threadIdx.x;
+            const int tx = tile % a.g.td[0], ty = (tile / a.g.td[0]) % a.g.td[1], tz = tile / (a.g.td[0] * a.g.td[1]);
+            const int nx = wrapc(tx + b % 3 - 1, a.g.td[0]), ny = wrapc(ty + (b / 3) % 3 - 1, a.g.td[1]),
+                      nz = wrapc(tz + b / 9 - 1, a.g.td[2]);
+            const int nt = (nz * a.g.td[1] + ny) * a.g.td[0] + nx;
+            if (atomicExch(a.band_flag_out + nt, 1u) == 0u) a.band_out[atomicAdd(a.band_out_count, 1)] = nt;
         }
         __syncthreads();
     }
@@ -764,9 +876,24 @@ __global__ void __launch_bounds__(256, 4) sweep_kernel(SweepArgs a) {
     __shared__ unsigned s_flag;
     __shared__ uint8_t s_b[RA * R1 * R2];
     __shared__ int8_t s_n[RA * R1 * R2];
+    __shared__ int s_li;
     pdl_wait();
     const int ntl = *a.count;
-    for (int li = blockIdx.x; li < ntl; li += gridDim.x) sweep_tile<D, false, NL>(a, a.list[li], s_b, s_n, &s_flag);
+    if (a.tile_next) {
+        // tiles differ in cost (interface tiles against halo tiles): each block
+        // takes the next one when it is done.  Every thread reads s_li before
+        // the first barrier inside sweep_tile, and thread 0 rewrites it only
+        // after the last one.
+        for (;;) {
+            if (threadIdx.x == 0) s_li = atomicAdd(a.tile_next, 1);
+            __syncthreads();
+            const int li = s_li;
+            if (li >= ntl) break;
+            sweep_tile<D, false, NL>(a, a.list[li], s_b, s_n, &s_flag);
+        }
+    } else {
+        for (int li = blockIdx.x; li < ntl; li += gridDim.x) sweep_tile<D, false, NL>(a, a.list[li], s_b, s_n, &s_flag);
+    }
     if (blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(a.ctr + C_TILES, (unsigned long long)ntl);
 }
 

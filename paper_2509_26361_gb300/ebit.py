@@ -49,7 +49,7 @@ class _Desc(ctypes.Structure):
 
 
 class _Counters(ctypes.Structure):
-    _fields_ = [(n, ctypes.c_int64) for n in COUNTER_NAMES + ("tiles",)]
+    _fields_ = [(n, ctypes.c_int64) for n in COUNTER_NAMES + ("tiles", "nonfinite")]
 
 
 _lib = None
@@ -204,7 +204,7 @@ def ebit_counters(ctx):
     c = _Counters()
     code = load().ebit_counters(ctx, ctypes.byref(c))
     _check(ctx, code)
-    return {k: int(getattr(c, k)) for k in COUNTER_NAMES + ("tiles",)}, code
+    return {k: int(getattr(c, k)) for k in COUNTER_NAMES + ("tiles", "nonfinite")}, code
 
 
 def ebit_reset_counters(ctx):

@@ -144,3 +144,94 @@ def test_512_windows_match_the_oracle():
         assert np.array_equal(_cut(st, o, Wn)[inner], ost_[inner])
         assert np.max(np.abs(_cut(kh, o, Wn)[inner] - okh[inner])) <= TOL
     g.close()
+
+
+def _box(cb, centre, half):
+    """Phase-1 node colours in the box of half-width ``half`` around ``centre``
+    (x, y, z in cells), periodic."""
+    n = cb.shape[-1]
+    o = [int(round(centre[2])) - half, int(round(centre[1])) - half, int(round(centre[0])) - half]
+    return (_cut(cb, o, 2 * half) & 1).astype(bool), o
+
+
+def test_512_windows_where_the_drops_touch():
+    """The 512^3 merging drops: the step where the colour field joins them (two
+    phase-1 components in a box around the gap become one) is found, the run is
+    repeated up to the last state with two components, and the next two steps'
+    sweeps, Front2VOF
+    and height functions are checked against the oracle on windows centred on
+    the point where the drops come closest."""
+    w = W.merging_drops(n=512, seed=5)
+    n = w.n3[0]
+    e1, e2 = w.shapes
+    gap_c = (e1.centre[0] + W._extent(e1, 0) + 4.0 / n) * n, 0.5 * n, 0.5 * n
+    half = 64
+    phi, faces, sx = dev(w.phi), dev(w.phi_faces), dev(w.s_exact)
+    del w.phi, w.phi_faces, w.s_exact
+    ud = [dev(w.u[d]) for d in range(3)]
+    g = ebit.Grid(*w.n3)
+    g.init(phi, faces, sx)
+    merged = None
+    for k in range(260):
+        g.step(k, ud, w.lam(k) * g.h)
+        if k >= 100 and k % 2 == 1:
+            cb, _ = g.get_state()
+            box, _ = _box(cb, gap_c, half)
+            nc = ndimage.label(box)[1]
+            if k == 101:
+                assert nc == 2, nc
+            if nc == 1:
+                merged = k
+                break
+    assert merged is not None, "the drops did not merge"
+    # the same run up to the last state seen with two components (after step
+    # merged - 2); the drops join in step merged - 1 or merged
+    g.init(phi, faces, sx)
+    for k in range(merged - 1):
+        g.step(k, ud, w.lam(k) * g.h)
+    cb, _ = g.get_state()
+    box, o = _box(cb, gap_c, half)
+    lab, nc = ndimage.label(box)
+    assert nc == 2
+    da = ndimage.distance_transform_edt(lab != 1)
+    db = ndimage.distance_transform_edt(lab != 2)
+    p = np.unravel_index(np.argmin(da + db), box.shape)
+    contact = [o[k] + p[k] for k in range(3)]  # z, y, x
+    Wn, M = 32, 4
+    wins = [(contact[0] + dz - Wn // 2, contact[1] + dy - Wn // 2, contact[2] + dx - Wn // 2)
+            for dz, dy, dx in ((0, 0, 0), (6, 0, 0), (0, 6, 0), (0, 0, -6))]
+    del cb
+    for step in (merged - 1, merged):
+        lam = w.lam(step)
+        for d in ((0, 1, 2) if step % 2 == 0 else (2, 1, 0)):
+            cb0, s0 = g.get_state()
+            before = [(_cut(cb0, o_, Wn), _cut(s0, o_, Wn), _cut(ud[d], o_, Wn)) for o_ in wins]
+            del cb0, s0
+            g.sweep(d, ud[d], lam * g.h)
+            cb1, s1 = g.get_state()
+            for o_, (wcb, ws, wu) in zip(wins, before):
+                ost, _ = oracle.sweep(oracle.State(wcb, ws), d, wu, lam)
+                gcb, gs = _cut(cb1, o_, Wn), _cut(s1, o_, Wn)
+                inner = (slice(M, Wn - M),) * 3
+                assert np.array_equal(gcb[inner], ost.cb[inner]), f"step {step} sweep {d}: colours differ in {o_}"
+                m = _present(gcb)[(slice(None),) + inner]
+                diff = np.abs(gs[(slice(None),) + inner][m] - ost.s[(slice(None),) + inner][m])
+                assert diff.size > 0 and diff.max() <= TOL, f"step {step} sweep {d}: offsets differ in {o_}"
+            del cb1, s1
+    cb, s = g.get_state()
+    assert ndimage.label(_box(cb, gap_c, half)[0])[1] == 1  # the checked steps joined the drops
+    C = torch.zeros(g.shape, dtype=torch.float64, device="cuda")
+    kh = torch.zeros_like(C)
+    st = torch.zeros(g.shape, dtype=torch.uint8, device="cuda")
+    g.front2vof(C)
+    g.curvature(C, kh, st)
+    for o_ in wins:
+        oC, _ = oracle.front2vof(oracle.State(_cut(cb, o_, Wn), _cut(s, o_, Wn)))
+        gC = _cut(C, o_, Wn)
+        inner = (slice(2, Wn - 2),) * 3
+        assert np.max(np.abs(gC[inner] - oC[inner])) <= TOL
+        okh, ost_ = oracle.hf_curvature(gC)
+        inner = (slice(6, Wn - 6),) * 3
+        assert np.array_equal(_cut(st, o_, Wn)[inner], ost_[inner])
+        assert np.max(np.abs(_cut(kh, o_, Wn)[inner] - okh[inner])) <= TOL
+    g.close()

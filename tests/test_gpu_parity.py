@@ -162,14 +162,58 @@ def test_errors_are_reported():
     with pytest.raises(ebit.EbitError) as e:
         g.sweep(3, u, 0.01)
     assert e.value.code == ebit.EBIT_EINVAL
-    with pytest.raises(ebit.EbitError):
+    with pytest.raises(ebit.EbitError) as e:
         g.sweep(0, u, float("nan"))
+    assert e.value.code == ebit.EBIT_ENONFINITE
     phi, faces = blobs((16, 16, 16), 1, 3, 0.15, 0.3)
     g.init(to_dev(phi), to_dev(faces))
     g.sweep(0, u, 1.5 * g.h)  # markers move 1.5 cells: clamped on the device, raised at sync
     with pytest.raises(ebit.EbitError) as e:
         g.sync()
     assert e.value.code == ebit.EBIT_ECFL
+    g.close()
+
+
+@pytest.mark.parametrize("bad", [float("nan"), float("inf"), -float("inf")])
+def test_nonfinite_velocity_is_reported_before_cfl(bad):
+    """A NaN or infinite velocity where a marker samples it is named as such
+    (EBIT_ENONFINITE), not as a CFL violation, even when the same sweep also
+    moves markers a full cell; the markers it touches stay in place.  A
+    non-finite value that no marker samples is harmless."""
+    n3 = (16, 16, 16)
+    phi, faces = blobs(n3, 1, 3, 0.15, 0.3)
+    g = ebit.Grid(*n3)
+    g.init(to_dev(phi), to_dev(faces))
+    cb0, _ = g.get_state()
+    c = cb0.cpu().numpy() & 1
+    xm = np.argwhere(c != np.roll(c, -1, axis=2))  # nodes owning an x-edge marker
+    offs = [(dz, dy, dx) for dz in range(-2, 3) for dy in range(-2, 3) for dx in range(-2, 3)]
+    far = np.argwhere(np.all([np.roll(c, o, axis=(0, 1, 2)) == c for o in offs], axis=0))
+    u = torch.full(g.shape, 0.3, dtype=torch.float64, device="cuda")
+    # a face whose 5x5x5 node neighbourhood holds no colour change: no marker
+    # interpolates there (the trilinear stencil reaches one face further)
+    k, j, i = far[0]
+    u[k, j, i] = bad
+    g.sweep(0, u, g.h)
+    assert g.sync() == ebit.EBIT_OK
+    assert g.counters()["nonfinite"] == 0
+    # every marker moves 1.5 cells, and the faces one marker samples are bad
+    u = torch.full(g.shape, 1.5, dtype=torch.float64, device="cuda")
+    k, j, i = xm[0]
+    u[k, j, i] = bad
+    u[k, j, (i + 1) % n3[0]] = bad
+    g.sweep(0, u, g.h)
+    with pytest.raises(ebit.EbitError) as e:
+        g.sync()
+    assert e.value.code == ebit.EBIT_ENONFINITE
+    with pytest.raises(ebit.EbitError) as e:
+        g.counters()
+    assert e.value.code == ebit.EBIT_ENONFINITE
+    # after a reset the context works again
+    g.reset_counters()
+    g.init(to_dev(phi), to_dev(faces))
+    g.sweep(0, torch.full(g.shape, 0.3, dtype=torch.float64, device="cuda"), g.h)
+    assert g.sync() == ebit.EBIT_OK
     g.close()
 
 
@@ -280,3 +324,34 @@ def test_hf_normal_ties_and_ranges():
     wild = np.clip(slab + rng.normal(0.0, 0.05, slab.shape), -0.2, 1.2)
     wild[(wild > 0.0) & (wild < 1.0) & (z != 7) & (z != 1)] = 1.0
     _hf_case(wild)
+
+
+def test_checkpoint_resume_is_bit_identical():
+    """Run 2k steps in one context; run k steps in another, read its state back
+    to the host, restore it into a fresh context and run k more: colour bytes
+    and offsets are identical bit for bit (the restored context's first sweep
+    processes every tile, the continuous one only its band)."""
+    w = W.fourier_spheres(n=40, seed=5, count=5, rmin=0.07, rmax=0.15, steps=12)
+    k = 6
+    ud = [to_dev(w.u[d]) for d in range(3)]
+    a = ebit.Grid(*w.n3)
+    a.init(to_dev(w.phi), to_dev(w.phi_faces))
+    for n in range(2 * k):
+        a.step(n, ud, w.lam(n) * a.h)
+    cb_a, s_a = (t.cpu().numpy() for t in a.get_state())
+    b = ebit.Grid(*w.n3)
+    b.init(to_dev(w.phi), to_dev(w.phi_faces))
+    for n in range(k):
+        b.step(n, ud, w.lam(n) * b.h)
+    cb_h, s_h = (t.cpu().numpy() for t in b.get_state())
+    b.close()
+    c = ebit.Grid(*w.n3)
+    c.set_state(torch.from_numpy(cb_h).cuda(), torch.from_numpy(s_h).cuda())
+    for n in range(k, 2 * k):
+        c.step(n, ud, w.lam(n) * c.h)
+    cb_c, s_c = (t.cpu().numpy() for t in c.get_state())
+    assert np.array_equal(cb_a, cb_c)
+    assert np.array_equal(s_a.view(np.uint64), s_c.view(np.uint64))
+    assert present_mask(cb_a).sum() > 1000
+    a.close()
+    c.close()
