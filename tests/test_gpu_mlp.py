@@ -94,9 +94,13 @@ def test_gradient_matches_oracle_backprop():
     _, gr = omlp.loss_and_grad(p, X, t, emulate=True)
     blocks = [("W1", 0, 128 * 64), ("b1", 8192, 8320), ("W2", 8320, 8320 + 16384), ("b2", 24704, 24832),
               ("w3", 24832, 24960), ("b3", 24960, 24961)]
+    # element by element: |g - g_ref| <= 1e-2 |g_ref| + 1e-3 max|g_ref| in each
+    # block (the kernel rounds the backward operands to bf16 for the tensor
+    # cores; the oracle passes the roundings straight through)
     for name, a, b in blocks:
-        rel = np.linalg.norm(g[a:b] - gr[a:b]) / max(np.linalg.norm(gr[a:b]), 1e-12)
-        assert rel <= 2e-2, (name, rel)
+        err = np.abs(g[a:b] - gr[a:b])
+        bound = 1e-2 * np.abs(gr[a:b]) + 1e-3 * np.abs(gr[a:b]).max()
+        assert np.all(err <= bound), (name, int(np.sum(err > bound)), float(np.max(err / bound)))
     m.close()
 
 

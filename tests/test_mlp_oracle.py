@@ -169,3 +169,89 @@ def test_learned_curvature_fallback_selection():
     assert frag.any() and not frag.all()
     cells1, kh1, st1, y1, _ = mlp.learned_curvature(C, p, 1, hf_kh, hf_st)
     assert np.array_equal(kh1, y1) and np.all(st1 == 5)
+
+
+def test_bf16_round_matches_torch_bfloat16():
+    """bf16_round against the bfloat16 conversion of torch (round to nearest,
+    ties to even) on random floats over many magnitudes and on exact ties."""
+    import torch
+
+    rng = np.random.default_rng(21)
+    x = (rng.normal(size=20000) * 10.0 ** rng.uniform(-8, 8, size=20000)).astype(np.float32)
+    # exact ties: low 16 bits 0x8000, with even and odd bit 16
+    u = rng.integers(0x3F000000, 0x47000000, size=4000, dtype=np.uint64).astype(np.uint32)
+    ties = ((u & 0xFFFF0000) | 0x8000).view(np.float32)
+    for v in (x, ties, -ties):
+        ref = torch.from_numpy(v).to(torch.bfloat16).to(torch.float32).numpy().astype(np.float64)
+        assert np.array_equal(mlp.bf16_round(v), ref)
+
+
+def _net(units):
+    """Parameters of a network given as a few non-zero entries:
+    units = dict(W1={(j, i): w}, b1={j: b}, W2={(k, j): w}, b2={k: b}, w3={k: w}, b3=b)."""
+    W1 = np.zeros((mlp.H, mlp.D_IN))
+    b1, W2, b2, w3 = np.zeros(mlp.H), np.zeros((mlp.H, mlp.H)), np.zeros(mlp.H), np.zeros(mlp.H)
+    for (j, i), v in units.get("W1", {}).items():
+        W1[j, i] = v
+    for j, v in units.get("b1", {}).items():
+        b1[j] = v
+    for (k, j), v in units.get("W2", {}).items():
+        W2[k, j] = v
+    for k, v in units.get("b2", {}).items():
+        b2[k] = v
+    for k, v in units.get("w3", {}).items():
+        w3[k] = v
+    return mlp.pack(W1, b1, W2, b2, w3, np.array([units.get("b3", 0.0)]))
+
+
+def test_forward_of_closed_form_networks():
+    """Networks built to compute known functions of two inputs (all values
+    exact in bfloat16, so the emulated roundings change nothing): |x0 - x1|,
+    max(x0, x1) for x1 >= 0, a shifted ramp with biases, a layer-2 weight off
+    the diagonal (a transposed W2 gives another function), and an input in the
+    tail half of the vector."""
+    rng = np.random.default_rng(22)
+    B = 257
+    X = np.zeros((B, mlp.D_IN))
+    x0 = rng.integers(-64, 65, B) / 64.0
+    x1 = rng.integers(0, 65, B) / 64.0
+    X[:, 3], X[:, 40] = x0, x1
+    nets = [
+        # |x0 - x1| = relu(x0 - x1) + relu(x1 - x0)
+        (dict(W1={(0, 3): 1.0, (0, 40): -1.0, (1, 3): -1.0, (1, 40): 1.0}, W2={(0, 0): 1.0, (1, 1): 1.0},
+              w3={0: 1.0, 1: 1.0}), np.abs(x0 - x1)),
+        # max(x0, x1) = relu(x0 - x1) + relu(x1), x1 >= 0
+        (dict(W1={(5, 3): 1.0, (5, 40): -1.0, (9, 40): 1.0}, W2={(2, 5): 1.0, (7, 9): 1.0}, w3={2: 1.0, 7: 1.0}),
+         np.maximum(x0, x1)),
+        # relu(x0 - 1/2) + 1/4 with the shift in b1 and b3; b2 of an idle unit is cut by its ReLU
+        (dict(W1={(0, 3): 1.0}, b1={0: -0.5}, W2={(0, 0): 1.0}, b2={3: -2.0}, w3={0: 1.0, 3: 5.0}, b3=0.25),
+         np.maximum(x0 - 0.5, 0.0) + 0.25),
+        # 2 relu(x1) read through W2[1][0] (row: layer-2 unit, column: layer-1 unit) and b2
+        (dict(W1={(0, 40): 1.0}, W2={(1, 0): 2.0}, b2={1: 0.125}, w3={1: 1.0}), 2.0 * x1 + 0.125),
+    ]
+    for units, ref in nets:
+        p = _net(units)
+        for emulate in (True, False):
+            y, _ = mlp.forward(p, X, emulate=emulate)
+            assert np.array_equal(y, ref), units
+
+
+def test_forward_emulation_rounds_weights_and_layer1_only():
+    """With emulation the layer-1 and layer-2 weights and the layer-1 activation
+    are rounded to bfloat16 (8 significant bits: 1 + 2^-9 rounds to 1), the
+    biases, the output weights and the layer-2 activation are not."""
+    X = np.zeros((1, mlp.D_IN))
+    X[0, 0] = 1.0
+    e = 2.0 ** -9
+    cases = [
+        # a layer-1 weight 1 + e: rounded to 1
+        (dict(W1={(0, 0): 1.0 + e}, W2={(0, 0): 1.0}, w3={0: 1.0}), 1.0, 1.0 + e),
+        # layer-1 activation 1 + e from its bias: rounded to 1 before layer 2
+        (dict(W1={(0, 0): 1.0}, b1={0: e}, W2={(0, 0): 1.0}, w3={0: 1.0}), 1.0, 1.0 + e),
+        # layer-2 bias and output weight keep their bits
+        (dict(W1={(0, 0): 1.0}, W2={(0, 0): 1.0}, b2={0: e}, w3={0: 1.0 + e}), (1.0 + e) ** 2, (1.0 + e) ** 2),
+    ]
+    for units, want_emu, want_exact in cases:
+        p = _net(units)
+        assert mlp.forward(p, X, emulate=True)[0][0] == want_emu
+        assert mlp.forward(p, X, emulate=False)[0][0] == want_exact
