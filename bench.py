@@ -477,6 +477,42 @@ class Run:
                 "overlap": "uploads and read-backs on two copy streams, overlapping the neighbouring steps",
                 "l2": "not flushed between these steps; the host copies pass through L2"}
 
+    def precision(self):
+        """The learned pass on the interface cells of the current fractions:
+        the tensor-core network against the unrounded FP64 network."""
+        import torch
+
+        from paper_2509_26361_gb300 import learned
+
+        if self.mlp is None:
+            return None
+        cells = torch.nonzero(((self.C > 0) & (self.C < 1)).reshape(-1)).reshape(-1).to(torch.int32)
+        X = self.mlp.gather(self.C, self.w.n3, cells)
+        return dict(learned.precision_error(self.mlp, X), note="kappa*h of the tensor-core pass against the same "
+                    "network evaluated in FP64 without bf16 rounding, on the interface cells after the timed steps")
+
+    def shape_error(self):
+        """E_shape (Eq. 10) and E_mass (Eq. 9) over one period of a reversing
+        field: the run from t = 0 for the workload's period, the fractions
+        summed after every step."""
+        import torch
+
+        from paper_2509_26361_gb300 import ebit
+
+        self.g.init(self.phi, self.faces, self.s_exact)
+        self.g.front2vof(self.C, ebit.EBIT_FULL)
+        C0 = self.C.clone()
+        sums = torch.zeros(self.w.steps, dtype=torch.float64, device=self.dev)
+        for n in range(self.w.steps):
+            dt = self.w.lam(n) * self.g.h
+            for d in ((0, 1, 2) if n % 2 == 0 else (2, 1, 0)):
+                self.g.sweep(d, self.ud[d], dt)
+            self.g.front2vof(self.C)
+            sums[n] = self.C.sum()
+        V0 = float(C0.sum())
+        return {"E_shape": float((self.C - C0).abs().sum()) / V0, "E_mass": float((sums - V0).abs().mean()) / V0,
+                "steps": self.w.steps, "t_end": self.w.steps * self.w.cfl * self.g.h, "period": self.w.period}
+
     def close(self):
         self.g.close()
         if self.mlp is not None:
@@ -525,7 +561,7 @@ def curvature_block():
     if not os.path.exists(learned.PARAMS_FILE):
         return {"unavailable": "no trained parameters"}
     mlp = learned.load_network()
-    r = learned.evaluate(mlp, repeats=10)
+    r = learned.evaluate(mlp, repeats=10, train_steps=200)
     mlp.close()
     return {"workload": "ellipsoids_256 (64 ellipsoids, semi-axes U[4,32] cells, random rotations, seed 33)",
             "interface_cells": r["interface_cells"], "unit": "stencils/s",
@@ -538,6 +574,10 @@ def curvature_block():
                        "mlp_all_cells": r["rms_mlp"], "mlp_hf_all_cells": r["rms_mlp_hf"]},
             "hf_no_value_cells": r["hf_no_value"], "mlp_hf_fallback_cells": r["mlp_hf_fallback"],
             "dtype": "bf16 tensor cores (tcgen05; mma.sync path beside it), fp32 accumulate (HF: f64)",
+            "bf16_vs_fp64": dict(r["bf16_vs_fp64"], note="kappa*h of the tensor-core pass against the same "
+                                 "network evaluated in FP64 without bf16 rounding, on this grid's stencils"),
+            "training": dict(r["training"], note="forward + backward + Adam per step, rows through a random "
+                             "index array, on this grid's labelled stencils, timed live with CUDA events"),
             "ms_per_pass": r["ms"]}
 
 
@@ -606,11 +646,12 @@ def extra_grid_block(name, steps, warmup, dev):
     r = Run(name, dev)
     res = r.timed(warmup, steps)
     prof = r.instrumented(warmup, steps)
+    shape = r.shape_error() if r.w.period is not None else None
     r.close()
     return {"workload": name, "value": r.cells * steps / (res["total_ms"] * 1e-3), "unit": "cell-steps/s",
             "steps": steps, "warmup": warmup, "ms_per_step": res["total_ms"] / steps,
             "config": config_dict(name, r.w, "flushed (256 MiB write) before every timed step, outside its events"),
-            "roofline": roofline_block(res, prof), "counters": res["cnt"]}
+            "roofline": roofline_block(res, prof), "counters": res["cnt"], "errors_at_period": shape}
 
 
 def main():
@@ -645,6 +686,7 @@ def main():
         clocks.start()
         time.sleep(0.3)
     res = run.timed(args.warmup, args.steps, world)
+    precision = run.precision() if rank == 0 else None
     total_ms = max_over_ranks(res["total_ms"], world, dev)
     clk = clocks.summary(*res["wall"]) if rank == 0 else None
     clocks.stop()
@@ -668,7 +710,7 @@ def main():
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": config_dict(args.workload, w, "flushed (256 MiB write) before every timed step, outside its events"),
             "roofline": roofline_block(res, prof), "e2e": e2e, "gpu_launches": launches,
-            "clocks": clk, "counters": res["cnt"]}
+            "clocks": clk, "counters": res["cnt"], "learned_bf16_vs_fp64": precision}
     hbm, _ = peaks()
     cells = run.cells
     line["dense_equivalent"] = {

@@ -60,8 +60,10 @@ struct ebit_ctx {
     int *wcount2;
     unsigned *mk_al[2];       // aligned edges that carry a marker, per set
     int *mk_count;            // [2] their lengths
+    int *mtiles[2];           // tiles whose proximity mask is not empty, per set
+    int *mt_count;            // [2] their lengths
     int *band_list2;          // the band list of set 1 (set 0: band_list)
-    uint32_t *band_flag[2];   // per tile: listed in that set's band list
+    uint32_t *band_flag;      // per tile: in the band list being built or processed
     int mk_par;               // set written by the last sweep
     int mk_dir;               // sweep axis of the last sweep
     int mk_valid;             // the lists of set mk_par describe the current state

@@ -80,8 +80,7 @@ int mark_all(ebit_ctx *ctx) {
     // the next sweep processes every tile and lists the markers and band anew
     ctx->mk_valid = 0;
     if (ctx->owns_state) {
-        for (int q = 0; q < 2; q++)
-            CU(cudaMemsetAsync(ctx->band_flag[q], 0, ctx->g.ntiles * sizeof(uint32_t), ctx->stream));
+        CU(cudaMemsetAsync(ctx->band_flag, 0, ctx->g.ntiles * sizeof(uint32_t), ctx->stream));
         CU(cudaMemsetAsync(ctx->band_count, 0, 2 * sizeof(int), ctx->stream));
     }
     ctx->last_C = nullptr;
@@ -184,9 +183,10 @@ static int create_ctx(const ebit_desc *desc, const ebit_state_arrays *st, ebit_c
         ctx->bin[a] = nullptr;
     }
     for (int k = 0; k < NLISTS; k++) ctx->work[k] = ctx->work2[k] = nullptr;
-    ctx->wcount2 = ctx->mk_count = ctx->band_list2 = nullptr;
+    ctx->wcount2 = ctx->mk_count = ctx->mt_count = ctx->band_list2 = nullptr;
     ctx->mk_al[0] = ctx->mk_al[1] = nullptr;
-    ctx->band_flag[0] = ctx->band_flag[1] = nullptr;
+    ctx->mtiles[0] = ctx->mtiles[1] = nullptr;
+    ctx->band_flag = nullptr;
     ctx->mk_par = 0;
     ctx->mk_dir = 0;
     ctx->mk_valid = 0;
@@ -249,9 +249,10 @@ static int create_ctx(const ebit_desc *desc, const ebit_state_arrays *st, ebit_c
         for (int k = 0; k < NLISTS && ok; k++) ok = ok && alloc((void **)&ctx->work2[k], ctx->N * sizeof(unsigned));
         for (int q = 0; q < 2 && ok; q++)
             ok = ok && alloc((void **)&ctx->mk_al[q], ctx->N * sizeof(unsigned)) &&
-                 alloc((void **)&ctx->band_flag[q], nt * sizeof(uint32_t));
+                 alloc((void **)&ctx->mtiles[q], nt * sizeof(int));
         ok = ok && alloc((void **)&ctx->wcount2, (NLISTS + 1) * sizeof(int)) && alloc((void **)&ctx->mk_count, 2 * sizeof(int)) &&
-             alloc((void **)&ctx->band_list2, nt * sizeof(int));
+             alloc((void **)&ctx->mt_count, 2 * sizeof(int)) && alloc((void **)&ctx->band_list2, nt * sizeof(int)) &&
+             alloc((void **)&ctx->band_flag, nt * sizeof(uint32_t));
     }
     ok = ok && alloc((void **)&ctx->cut, ctx->N * sizeof(unsigned)) && alloc((void **)&ctx->scan, ctx->N * sizeof(unsigned)) &&
          alloc((void **)&ctx->iface[0], ctx->N * sizeof(unsigned)) &&
@@ -288,6 +289,7 @@ static int create_ctx(const ebit_desc *desc, const ebit_state_arrays *st, ebit_c
     if (ctx->owns_state) {
         cudaMemsetAsync(ctx->wcount2, 0, (NLISTS + 1) * sizeof(int), ctx->stream);
         cudaMemsetAsync(ctx->mk_count, 0, 2 * sizeof(int), ctx->stream);
+        cudaMemsetAsync(ctx->mt_count, 0, 2 * sizeof(int), ctx->stream);
     }
     cudaMemsetAsync(ctx->ncut, 0, sizeof(int), ctx->stream);
     cudaMemsetAsync(ctx->niface, 0, 3 * sizeof(int), ctx->stream);
@@ -346,8 +348,10 @@ void ebit_destroy(ebit_ctx *ctx) {
         cudaFree(ctx->mk_al[0]);
         cudaFree(ctx->mk_al[1]);
         cudaFree(ctx->mk_count);
-        cudaFree(ctx->band_flag[0]);
-        cudaFree(ctx->band_flag[1]);
+        cudaFree(ctx->mtiles[0]);
+        cudaFree(ctx->mtiles[1]);
+        cudaFree(ctx->mt_count);
+        cudaFree(ctx->band_flag);
         cudaFree(ctx->band_list2);
     }
     cudaFree(ctx->tile_cchg);
@@ -413,8 +417,9 @@ int ebit_advect_sweep(ebit_ctx *ctx, int dir, const double *u_face, double dt) {
         return fail(ctx, EBIT_EINVAL, "ebit_advect_sweep: a batch instance is swept by ebit_batch_advect_sweep");
     if (!std::isfinite(dt)) return fail(ctx, EBIT_ENONFINITE, "ebit_advect_sweep: non-finite dt");
     // Band sweeps alternate between two sets of lists (see ebit_ctx): this
-    // sweep reads set rd (its band and the markers to move, listed by the
-    // previous sweep) and writes set wr for the next one.  After a state
+    // sweep reads set rd (the markers to move and the tiles with markers
+    // nearby, listed by the previous sweep), builds its band into band list
+    // rd from the latter, and writes set wr for the next one.  After a state
     // change, and in dense mode, every tile is processed and the markers are
     // found from the colours of each tile instead.
     const int rd = ctx->mk_par, wr = rd ^ 1;
@@ -446,10 +451,10 @@ int ebit_advect_sweep(ebit_ctx *ctx, int dir, const double *u_face, double dt) {
     if (!ctx->dense) {
         a.mk_out = ctx->mk_al[wr];
         a.mk_out_count = ctx->mk_count + wr;
-        a.band_flag_in = lists ? ctx->band_flag[rd] : nullptr;
-        a.band_flag_out = ctx->band_flag[wr];
-        a.band_out = wr ? ctx->band_list2 : ctx->band_list;
-        a.band_out_count = ctx->band_count + wr;
+        a.mt_out = ctx->mtiles[wr];
+        a.mt_out_count = ctx->mt_count + wr;
+        a.band_flag = lists ? ctx->band_flag : nullptr;
+        a.band_next_count = ctx->band_count + wr;
     }
     MarkerLists ml;
     if (lists) {
@@ -466,6 +471,10 @@ int ebit_advect_sweep(ebit_ctx *ctx, int dir, const double *u_face, double dt) {
         ml.list[2] = wk_rd[1];
         ml.count[2] = wc_rd + 1;
         ml.axis[2] = (pd + 2) % 3;
+        ml.mtiles = ctx->mtiles[rd];
+        ml.mtiles_count = ctx->mt_count + rd;
+        ml.band = rd ? ctx->band_list2 : ctx->band_list;
+        ml.band_count = ctx->band_count + rd;
     }
     int r;
     switch (dir) {

@@ -61,27 +61,35 @@ struct SweepArgs {
     uint8_t *tile_dirty;             // per tile: processed since the last Front2VOF
     // Lists for the next sweep (a context's band sweeps; null elsewhere).  The
     // band pass appends every aligned edge that carries a marker after the
-    // sweep to mk_out (the unaligned ones are its work lists 0 and 1), and
-    // builds the next sweep's band: each tile it processes sets the flag of,
-    // and lists, every tile its new proximity mask points to, and clears its
-    // own flag of the current band.
+    // sweep to mk_out (the unaligned ones are its work lists 0 and 1) and every
+    // tile whose new proximity mask is not empty to mt_out; it clears the band
+    // flag of each tile it processes.  The next sweep's advection builds that
+    // sweep's band from mt_out and the masks.
     unsigned *mk_out = nullptr;
     int *mk_out_count = nullptr;
-    uint32_t *band_flag_in = nullptr;
-    uint32_t *band_flag_out = nullptr;
-    int *band_out = nullptr;
-    int *band_out_count = nullptr;
+    int *mt_out = nullptr;
+    int *mt_out_count = nullptr;
+    uint32_t *band_flag = nullptr;
+    // the count of the band list the following sweep builds (cleared here)
+    int *band_next_count = nullptr;
     // next band tile to take (blocks of the band pass take tiles in turn from
     // this counter; null: a fixed stride over the list)
     int *tile_next = nullptr;
 };
 
 // The markers of the state before a sweep, as node ids of their edges, one
-// list per edge axis (the previous sweep's band pass wrote them).
+// list per edge axis, and the tiles whose proximity mask is not empty (the
+// previous sweep's band pass wrote them); the band this sweep processes is
+// built from the latter into band / band_count, with band_flag against
+// duplicates.
 struct MarkerLists {
     const unsigned *list[3];
     const int *count[3];
     int axis[3];
+    const int *mtiles;
+    const int *mtiles_count;
+    int *band;
+    int *band_count;
 };
 
 struct P2 {
@@ -341,8 +349,9 @@ __device__ __forceinline__ void clear_sweep_counts(const SweepArgs &a) {
     if (blockIdx.x != 0) return;
     if (threadIdx.x < NL) a.wcount[threadIdx.x] = 0;
     if (threadIdx.x == 32 && a.mk_out_count) *a.mk_out_count = 0;
-    if (threadIdx.x == 33 && a.band_out_count) *a.band_out_count = 0;
+    if (threadIdx.x == 33 && a.mt_out_count) *a.mt_out_count = 0;
     if (threadIdx.x == 34 && a.tile_next) *a.tile_next = 0;
+    if (threadIdx.x == 35 && a.band_next_count) *a.band_next_count = 0;
 }
 
 template <int D, int NL = 4>
@@ -363,6 +372,18 @@ template <int D, int NL = 4>
 __global__ void __launch_bounds__(256) advect_list_kernel(SweepArgs a, MarkerLists m) {
     pdl_wait();
     clear_sweep_counts<NL>(a);
+    // this sweep's band: every tile a listed tile's mask points to (bit
+    // near_bit(dx, dy, dz) names the neighbour in that direction), listed once
+    const int nmt = *m.mtiles_count;
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < 27 * nmt; t += gridDim.x * blockDim.x) {
+        const int tile = __ldg(m.mtiles + t / 27), b = t % 27;
+        if (!((__ldg(a.tile_marker + tile) >> b) & 1u)) continue;
+        const int tx = tile % a.g.td[0], ty = (tile / a.g.td[0]) % a.g.td[1], tz = tile / (a.g.td[0] * a.g.td[1]);
+        const int nx = wrapc(tx + b % 3 - 1, a.g.td[0]), ny = wrapc(ty + (b / 3) % 3 - 1, a.g.td[1]),
+                  nz = wrapc(tz + b / 9 - 1, a.g.td[2]);
+        const int nt = (nz * a.g.td[1] + ny) * a.g.td[0] + nx;
+        if (atomicExch(a.band_flag + nt, 1u) == 0u) m.band[atomicAdd(m.band_count, 1)] = nt;
+    }
     const int n0 = *m.count[0], n1 = *m.count[1], n2 = *m.count[2];
     const int total = n0 + n1 + n2;
     const int stride = gridDim.x * blockDim.x;
@@ -669,7 +690,7 @@ constexpr int RA = 11, R1 = 9, R2 = 9;
 // goes to work list 4 or 5 (the crossing count of the annihilation counter is
 // taken by the FP64-list kernel, with full warps); NL = 4: counted here.
 template <int D, bool F, int NL = 4>
-__device__ __forceinline__ void sweep_tile(const SweepArgs &a, int tile, uint8_t *s_b, int8_t *s_n, unsigned *s_flag) {
+__device__ __forceinline__ int sweep_tile(const SweepArgs &a, int tile, uint8_t *s_b, int8_t *s_n, unsigned *s_flag) {
     constexpr int A = D, T1 = (D + 1) % 3, T2 = (D + 2) % 3;
     {
         int o[3];
@@ -831,14 +852,33 @@ __device__ __forceinline__ void sweep_tile(const SweepArgs &a, int tile, uint8_t
                     if (in_marker || out_marker) mk |= near_bits(l[0], l[1], l[2]);
                 }
             }
+            // the warp's appends to the NL work lists and the marker list: all
+            // ballots first, then lane 0 reserves every list's slots with
+            // independent atomics (one round trip to L2 for all of them)
+            {
+                const unsigned full = 0xffffffffu;
+                const int lane = threadIdx.x & 31;
+                unsigned m[NL + 1];
+                int base[NL + 1];
 #pragma unroll
-            for (int k = 0; k < NL; k++) {
-                int slot = warp_append(a.wcount + k, push[k]);
-                if (slot >= 0) a.work[k][slot] = (unsigned)myid;
-            }
-            if (a.mk_out) {
-                const int slot = warp_append(a.mk_out_count, push_al);
-                if (slot >= 0) a.mk_out[slot] = (unsigned)myid;
+                for (int k = 0; k < NL; k++) m[k] = __ballot_sync(full, push[k]);
+                m[NL] = a.mk_out ? __ballot_sync(full, push_al) : 0u;
+#pragma unroll
+                for (int k = 0; k <= NL; k++) base[k] = 0;
+                if (lane == 0) {
+#pragma unroll
+                    for (int k = 0; k < NL; k++)
+                        if (m[k]) base[k] = atomicAdd(a.wcount + k, __popc(m[k]));
+                    if (m[NL]) base[NL] = atomicAdd(a.mk_out_count, __popc(m[NL]));
+                }
+                const unsigned below = (1u << lane) - 1u;
+#pragma unroll
+                for (int k = 0; k < NL; k++) {
+                    const int b = __shfl_sync(full, base[k], 0);
+                    if (push[k]) a.work[k][b + __popc(m[k] & below)] = (unsigned)myid;
+                }
+                const int b = __shfl_sync(full, base[NL], 0);
+                if (push_al && a.mk_out) a.mk_out[b + __popc(m[NL] & below)] = (unsigned)myid;
             }
         }
         {
@@ -851,23 +891,18 @@ __device__ __forceinline__ void sweep_tile(const SweepArgs &a, int tile, uint8_t
             if ((threadIdx.x & 31) == 0 && v) atomicAdd(a.ctr + k, (unsigned long long)v);
         }
         __syncthreads();
-        const unsigned fl = *s_flag;
+        int pending = -1;
         if (threadIdx.x == 0) {
+            const unsigned fl = *s_flag;
             a.tile_marker[tile] = fl;
             a.tile_dirty[tile] = 1;
-            if (a.band_flag_in) a.band_flag_in[tile] = 0u;
-        }
-        // next sweep's band: the tiles this tile's markers reach (bit
-        // near_bit(dx, dy, dz) names the neighbour in that direction)
-        if (a.band_flag_out && threadIdx.x < 27 && ((fl >> threadIdx.x) & 1u)) {
-            const int b = threadIdx.x;
-            const int tx = tile % a.g.td[0], ty = (tile / a.g.td[0]) % a.g.td[1], tz = tile / (a.g.td[0] * a.g.td[1]);
-            const int nx = wrapc(tx + b % 3 - 1, a.g.td[0]), ny = wrapc(ty + (b / 3) % 3 - 1, a.g.td[1]),
-                      nz = wrapc(tz + b / 9 - 1, a.g.td[2]);
-            const int nt = (nz * a.g.td[1] + ny) * a.g.td[0] + nx;
-            if (atomicExch(a.band_flag_out + nt, 1u) == 0u) a.band_out[atomicAdd(a.band_out_count, 1)] = nt;
+            if (a.band_flag) a.band_flag[tile] = 0u;
+            // a slot on the list of tiles with markers nearby; the caller
+            // stores the tile id there later, so that nothing waits for it
+            if (a.mt_out && fl) pending = atomicAdd(a.mt_out_count, 1);
         }
         __syncthreads();
+        return pending;
     }
 }
 
@@ -879,21 +914,35 @@ __global__ void __launch_bounds__(256, 4) sweep_kernel(SweepArgs a) {
     __shared__ int s_li;
     pdl_wait();
     const int ntl = *a.count;
+    // the previous tile's slot on the marker-tile list (thread 0), stored one
+    // tile later so that the atomic that reserved it is not waited for
+    int pending = -1, pending_tile = 0;
     if (a.tile_next) {
         // tiles differ in cost (interface tiles against halo tiles): each block
-        // takes the next one when it is done.  Every thread reads s_li before
-        // the first barrier inside sweep_tile, and thread 0 rewrites it only
-        // after the last one.
+        // takes the next one when it is done, the counter read one tile ahead.
+        // Every thread reads s_li before the first barrier inside sweep_tile,
+        // and thread 0 rewrites it only after the last one.
+        int next = threadIdx.x == 0 ? atomicAdd(a.tile_next, 1) : 0;
         for (;;) {
-            if (threadIdx.x == 0) s_li = atomicAdd(a.tile_next, 1);
+            if (threadIdx.x == 0) s_li = next;
             __syncthreads();
             const int li = s_li;
             if (li >= ntl) break;
-            sweep_tile<D, false, NL>(a, a.list[li], s_b, s_n, &s_flag);
+            if (threadIdx.x == 0) {
+                next = atomicAdd(a.tile_next, 1);
+                if (pending >= 0) a.mt_out[pending] = pending_tile;
+            }
+            pending_tile = a.list[li];
+            pending = sweep_tile<D, false, NL>(a, pending_tile, s_b, s_n, &s_flag);
         }
     } else {
-        for (int li = blockIdx.x; li < ntl; li += gridDim.x) sweep_tile<D, false, NL>(a, a.list[li], s_b, s_n, &s_flag);
+        for (int li = blockIdx.x; li < ntl; li += gridDim.x) {
+            if (threadIdx.x == 0 && pending >= 0) a.mt_out[pending] = pending_tile;
+            pending_tile = a.list[li];
+            pending = sweep_tile<D, false, NL>(a, pending_tile, s_b, s_n, &s_flag);
+        }
     }
+    if (threadIdx.x == 0 && pending >= 0) a.mt_out[pending] = pending_tile;
     if (blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(a.ctr + C_TILES, (unsigned long long)ntl);
 }
 

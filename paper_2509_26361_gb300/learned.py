@@ -135,13 +135,69 @@ def _rms(e):
     return float(np.sqrt(np.mean(e * e))) if len(e) else float("nan")
 
 
-def evaluate(mlp, seed=33, n=256, count=64, amin=4.0, amax=32.0, repeats=5, path=None):
+def fp64_network(params, X):
+    """The network evaluated in FP64 from the FP32 master parameters, with no
+    bfloat16 rounding of weights or activations: the function the tensor-core
+    pass approximates.  Used only to state that pass's precision error.
+    X: encoded stencils (bf16 [m, 64], device); returns kappa*h (FP64, host)."""
+    p = np.asarray(params, dtype=np.float64)
+    W1 = p[:8192].reshape(128, 64)
+    b1 = p[8192:8320]
+    W2 = p[8320:24704].reshape(128, 128)
+    b2, w3, b3 = p[24704:24832], p[24832:24960], p[24960]
+    x = X.float().cpu().numpy().astype(np.float64)
+    h1 = np.maximum(x @ W1.T + b1, 0.0)
+    h2 = np.maximum(h1 @ W2.T + b2, 0.0)
+    return h2 @ w3 + b3
+
+
+def precision_error(mlp, X):
+    """kappa*h of the tensor-core pass (bf16 operands, FP32 accumulation)
+    against the unrounded FP64 network on the same encoded stencils."""
+    y = mlp.forward(X).double().cpu().numpy()
+    ref = fp64_network(mlp.get_params().cpu().numpy(), X)
+    d = y - ref
+    return {"stencils": int(len(y)), "rms": _rms(d), "max_abs": float(np.max(np.abs(d))) if len(d) else 0.0,
+            "rms_ref": _rms(ref)}
+
+
+def time_training(X, t, steps=200, batch=16384, warmup=10, seed=0):
+    """Training throughput of the library's kernels (forward, backward and
+    Adam per step, rows read through a random index array as in train()):
+    stencil passes per second over ``steps`` steps of a fresh network, timed
+    with CUDA events on the network's stream."""
+    mlp = ebit.Mlp(init_params(seed))
+    rng = np.random.default_rng(seed)
+    m = t.numel()
+    idx = [_dev(rng.integers(0, m, batch).astype(np.int32)) for _ in range(8)]
+    loss = torch.zeros(1, dtype=torch.float32, device="cuda")
+    for k in range(warmup):
+        mlp.train_step(X, t, 1e-3, loss, idx=idx[k % 8], batch=batch)
+    mlp.sync()
+    # the network was created on the default stream, which is torch's current one here
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for k in range(steps):
+        mlp.train_step(X, t, 1e-3, loss, idx=idx[k % 8], batch=batch)
+    e1.record()
+    mlp.sync()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    mlp.close()
+    return {"steps": steps, "batch": batch, "ms_per_step": ms / steps,
+            "stencil_passes_per_s": steps * batch / (ms * 1e-3),
+            "flops_per_stencil_pass": 1.2e5, "tflops": steps * batch * 1.2e5 / (ms * 1e-3) / 1e12}
+
+
+def evaluate(mlp, seed=33, n=256, count=64, amin=4.0, amax=32.0, repeats=5, path=None, train_steps=0):
     """The learned-curvature benchmark grid: ``count`` seeded ellipsoids with
     semi-axes U[amin, amax] cells and random rotations.  RMS kappa*h error
     against the analytic labels for height functions (where they give a value),
     the network alone, and the network with height-function fallback; binned
-    by the local radius 2/|kappa| in cells; and stencils per second of the
-    height-function pass and the learned pass on the same interface list."""
+    by the local radius 2/|kappa| in cells; stencils per second of the
+    height-function pass and the learned pass on the same interface list; the
+    tensor-core pass against the unrounded FP64 network; and, with
+    ``train_steps``, the training throughput on this grid's labelled stencils."""
     if path is not None:
         mlp.set_path(path)
     rng = np.random.default_rng(seed)
@@ -216,6 +272,12 @@ def evaluate(mlp, seed=33, n=256, count=64, amin=4.0, amax=32.0, repeats=5, path
     res["mlp_hf_stencils_per_s"] = m / (t_mlp_hf * 1e-3)
     t_o = times["mlp_other_path"].get("hf", 0.0) + times["mlp_other_path"].get("mlp", float("nan"))
     res["mlp_other_path_stencils_per_s"] = m / (t_o * 1e-3)
+    res["bf16_vs_fp64"] = precision_error(mlp, st["X"])
+    if train_steps:
+        keep = np.nonzero(ok & ~st["frag"] & (np.abs(lab) <= 1.0))[0]
+        kidx = _dev(keep.astype(np.int64))
+        res["training"] = time_training(st["X"][kidx].contiguous(), _dev(lab[keep].astype(np.float32)),
+                                        steps=train_steps)
     return res
 
 
