@@ -303,6 +303,18 @@ def max_over_ranks(ms, world, device):
     return float(t.item())
 
 
+def sum_over_ranks(values, world, device):
+    """Element-wise sum of a list of numbers over the ranks."""
+    if world <= 1:
+        return [float(v) for v in values]
+    import torch
+    import torch.distributed as dist
+
+    t = torch.tensor([float(v) for v in values], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return [float(v) for v in t.tolist()]
+
+
 def job_value(cells, steps, world, max_ms):
     """Whole-job throughput: every rank advances its own replica of ``cells``
     cells by ``steps`` steps; the job takes the slowest rank's time."""
@@ -337,10 +349,14 @@ class Run:
         self.flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)  # 256 MiB > L2
         self.cells = w.n3[0] * w.n3[1] * w.n3[2]
 
-    def one_step(self, n, ud=None, sweep_ev=None):
+    def one_step(self, n, ud=None, sweep_ev=None, asynch=False, before_f2v=None):
         """One step; with sweep_ev, a pair of CUDA events on the context's stream
         brackets the step's three split-sweep calls (advect + integer pass +
-        FP64 lists each), which run back to back."""
+        FP64 lists each), which run back to back.  With asynch, Front2VOF and
+        curvature run on the context's side stream (EBIT_ASYNC), overlapping
+        the next step's sweeps; before_f2v (an event) is waited for first."""
+        from paper_2509_26361_gb300 import ebit
+
         ud = self.ud if ud is None else ud
         dt = self.w.lam(n) * self.g.h
         if sweep_ev is not None:
@@ -349,10 +365,14 @@ class Run:
             self.g.sweep(d, ud[d], dt)
         if sweep_ev is not None:
             sweep_ev[1].record()
-        self.g.front2vof(self.C)
-        self.g.curvature(self.C, self.kh, self.st, mode=self.mode)
+        if before_f2v is not None:
+            import torch
+            torch.cuda.current_stream().wait_event(before_f2v)
+        fl = ebit.EBIT_ASYNC if asynch else ebit.EBIT_INCREMENTAL
+        self.g.front2vof(self.C, fl)
+        self.g.curvature(self.C, self.kh, self.st, mode=self.mode, flags=fl)
 
-    def start(self, warmup):
+    def start(self, warmup, asynch=False):
         import torch
 
         from paper_2509_26361_gb300 import ebit
@@ -361,13 +381,46 @@ class Run:
         self.g.front2vof(self.C, ebit.EBIT_FULL)
         self.g.curvature(self.C, self.kh, self.st, mode=self.mode, flags=ebit.EBIT_FULL)
         for n in range(warmup):
-            self.one_step(n)
+            self.one_step(n, asynch=asynch)
+        self.g.join()
         torch.cuda.synchronize()
         self.g.reset_counters()
 
-    def timed(self, warmup, steps, world=1, clocks=None):
-        """Device-resident steps: an L2 flush (outside the events) before every
-        step, an event pair around each step and one around its three sweeps."""
+    def timed(self, warmup, steps, world=1):
+        """Device-resident steps back to back, Front2VOF and curvature of each
+        step on the side stream overlapping the next step's sweeps; one event
+        pair around all steps (the side stream joined before the last event)
+        and one around each step's three sweeps.  No L2 flush: the state and
+        the velocity fields are far larger than L2."""
+        import torch
+
+        E = lambda: torch.cuda.Event(enable_timing=True)
+        self.start(warmup, asynch=True)
+        e0, e1 = E(), E()
+        sev = [(E(), E()) for _ in range(steps)]
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+        torch.cuda.synchronize()
+        wall0 = time.perf_counter()
+        e0.record()
+        for i in range(steps):
+            self.one_step(warmup + i, sweep_ev=sev[i], asynch=True)
+        self.g.join()
+        e1.record()
+        torch.cuda.synchronize()
+        wall1 = time.perf_counter()
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+        total = e0.elapsed_time(e1)
+        sweep_ms = [a.elapsed_time(b) / 3.0 for a, b in sev for _ in range(3)]
+        return dict(total_ms=float(total), sweep_ms=sweep_ms, cnt=self.g.counters(), wall=(wall0, wall1))
+
+    def timed_sync(self, warmup, steps, world=1):
+        """Device-resident steps in order (Front2VOF and curvature on the
+        context's stream): an L2 flush (outside the events) before every step,
+        an event pair around each step and one around its three sweeps."""
         import torch
 
         E = lambda: torch.cuda.Event(enable_timing=True)
@@ -401,11 +454,11 @@ class Run:
         roofline."""
         import torch
 
-        self.start(warmup)
+        self.start(warmup, asynch=True)
         self.g.profile(True)
         for i in range(steps):
-            self.flush.zero_()
-            self.one_step(warmup + i)
+            self.one_step(warmup + i, asynch=True)
+        self.g.join()
         torch.cuda.synchronize()
         prof = self.g.profile_read()
         self.g.profile(False)
@@ -418,11 +471,14 @@ class Run:
         copies run on two copy streams and overlap the neighbouring steps'
         compute: the velocity of step i+1 goes into the other of two device
         buffers while step i computes, and C, kappa*h of step i are read back
-        while the sweeps of step i+1 run (its Front2VOF waits for that
-        read-back, since it overwrites C)."""
+        (once its Front2VOF and curvature on the side stream are done) while
+        the sweeps of step i+1 run (its Front2VOF waits for that read-back,
+        since it overwrites C)."""
         import torch
 
-        self.start(warmup)
+        from paper_2509_26361_gb300 import ebit
+
+        self.start(warmup, asynch=True)
         w, g, dev = self.w, self.g, self.dev
         E = lambda: torch.cuda.Event(enable_timing=False)
         uh = [torch.from_numpy(np.ascontiguousarray(w.u[d])).pin_memory() for d in range(3)]
@@ -458,15 +514,16 @@ class Run:
             ev_used[slot].record(cs)
             if i >= 1:
                 cs.wait_event(ev_back)
-            g.front2vof(self.C)
-            g.curvature(self.C, self.kh, self.st, mode=self.mode)
-            ev_out.record(cs)
+            g.front2vof(self.C, ebit.EBIT_ASYNC)
+            g.curvature(self.C, self.kh, self.st, mode=self.mode, flags=ebit.EBIT_ASYNC)
+            g.record_done(ev_out)
             with torch.cuda.stream(down):
                 down.wait_event(ev_out)
                 Ch.copy_(self.C, non_blocking=True)
                 kh_h.copy_(self.kh, non_blocking=True)
                 ev_back.record(down)
         cs.wait_event(ev_back)
+        g.join()
         s1.record(cs)
         torch.cuda.synchronize()
         ms = s0.elapsed_time(s1)
@@ -551,6 +608,17 @@ def roofline_block(res, prof):
             "kernel_launches": {k: v[1] for k, v in prof.items()}}
 
 
+def overlapped(res):
+    """The split sweep's rate in the overlapped timed region (Front2VOF and
+    curvature of the previous step sharing the GPU)."""
+    hbm, _ = peaks()
+    nsw = len(res["sweep_ms"])
+    per_sweep_s = float(np.mean(res["sweep_ms"])) * 1e-3
+    alg = SWEEP_BYTES_PER_CELL * res["cnt"]["tiles"] / nsw * 512.0
+    return {"achieved": alg / per_sweep_s / 1e9, "frac": alg / per_sweep_s / 1e9 / hbm,
+            "avg_sweep_us": per_sweep_s * 1e6}
+
+
 def curvature_block():
     """Learned vs height-function curvature on the 256^3 grid of 64 seeded
     ellipsoids (semi-axes U[4, 32] cells, random rotations, seed 33): stencils
@@ -581,21 +649,27 @@ def curvature_block():
             "ms_per_pass": r["ms"]}
 
 
-def batched_block(steps=256, warmup=4):
+def batched_block(device, rank=0, world=1, steps=256, warmup=4):
     """The batched workload: 64 independent instances (seeded sizes from
     {32, 48, 64, 96, 128}^3, each with its own 12-mode Fourier field and 1-4
     spheres, dt = 0.5 h), 3 split sweeps per step, one cooperative launch per
     sweep, pairs of steps replayed from a CUDA graph, launch shape autotuned.
-    Value: cell-steps/s over all instances (sweeps only, as the batched path
-    covers advection); its roofline counts the scope table's 62.75 B per band
-    cell of a sweep, like the single-grid sweep."""
+    On N ranks every rank runs its own shard of the instances (balanced by
+    cells, no communication on the data path); the job takes the slowest
+    rank's time and counts every rank's cells.  Value: cell-steps/s over all
+    instances (sweeps only, as the batched path covers advection); its roofline
+    counts the scope table's 62.75 B per band cell of a sweep, like the
+    single-grid sweep."""
     import torch
 
-    from paper_2509_26361_gb300 import ebit
+    from paper_2509_26361_gb300 import ebit, sharding
     from paper_2509_26361_gb300 import workloads as W
 
-    insts = W.batched_instances()
-    dev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
+    every = W.batched_instances()
+    mine = sharding.owned_by([n ** 3 for n, *_ in every], rank, world)
+    insts = [every[i] for i in mine]
+    del every
+    dev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(device)
     b = ebit.Batch([(n, n, n) for n, *_ in insts])
     uf = []
     for i, (n, phi, faces, u, dt) in enumerate(insts):
@@ -609,18 +683,22 @@ def batched_block(steps=256, warmup=4):
     for i in range(len(insts)):
         b.instance(i).reset_counters()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
     torch.cuda.synchronize()
     e0.record()
     b.run(warmup, steps, graph=True)
     e1.record()
     b.sync()
-    ms = e0.elapsed_time(e1)
-    cells = sum(n ** 3 for n, *_ in insts)
+    ms = max_over_ranks(e0.elapsed_time(e1), world, device)
     tiles = markers = 0
     for i in range(len(insts)):
         c = b.instance(i).counters()
         tiles += c["tiles"]
         markers += c["markers"]
+    cells, tiles, markers, ninst = sum_over_ranks([sum(n ** 3 for n, *_ in insts), tiles, markers, len(insts)],
+                                                  world, device)
     sweeps = 3 * steps
     band_cells = tiles * 512.0 / sweeps
     alg = SWEEP_BYTES_PER_CELL * band_cells
@@ -628,7 +706,8 @@ def batched_block(steps=256, warmup=4):
     hbm, src = peaks()
     out = {"workload": "batched_64 (64 instances, sizes {32,48,64,96,128}^3 seeded, 1-4 spheres, own "
                        "Fourier fields, CFL 0.5, seed 4)",
-           "instances": len(insts), "cells": cells, "steps": steps, "warmup": warmup,
+           "instances": int(ninst), "cells": int(cells), "steps": steps, "warmup": warmup, "ranks": world,
+           "sharding": "instances split over the ranks by cell count, no data-path collective",
            "value": cells * steps / (ms * 1e-3), "unit": "cell-steps/s", "ms_per_step": ms / steps,
            "launches_per_sweep": 1, "graph": b.graph_active(), "graph_note": b.graph_note(),
            "launch_shape_ctas_per_sm": shape, "autotune_ms_per_6_sweeps": tune_ms,
@@ -645,13 +724,18 @@ def extra_grid_block(name, steps, warmup, dev):
     """Another single-grid workload with the headline's timing rules."""
     r = Run(name, dev)
     res = r.timed(warmup, steps)
+    res_sync = r.timed_sync(warmup, steps)
     prof = r.instrumented(warmup, steps)
     shape = r.shape_error() if r.w.period is not None else None
     r.close()
     return {"workload": name, "value": r.cells * steps / (res["total_ms"] * 1e-3), "unit": "cell-steps/s",
             "steps": steps, "warmup": warmup, "ms_per_step": res["total_ms"] / steps,
             "config": config_dict(name, r.w, "flushed (256 MiB write) before every timed step, outside its events"),
-            "roofline": roofline_block(res, prof), "counters": res["cnt"], "errors_at_period": shape}
+            "roofline": dict(roofline_block(res_sync, prof), overlapped=overlapped(res)),
+            "counters": res["cnt"], "errors_at_period": shape,
+            "sync_flushed": {"value": r.cells * steps / (res_sync["total_ms"] * 1e-3),
+                             "ms_per_step": res_sync["total_ms"] / steps,
+                             "note": "steps in order, L2 flushed before each"}}
 
 
 def main():
@@ -688,6 +772,7 @@ def main():
     res = run.timed(args.warmup, args.steps, world)
     precision = run.precision() if rank == 0 else None
     total_ms = max_over_ranks(res["total_ms"], world, dev)
+    res_sync = run.timed_sync(args.warmup, args.steps, world)
     clk = clocks.summary(*res["wall"]) if rank == 0 else None
     clocks.stop()
     prof = run.instrumented(args.warmup, args.steps)
@@ -696,6 +781,7 @@ def main():
         e2e = run.e2e(args.warmup, args.steps)
     w = run.w
     run.close()
+    batched = None if args.no_extra else batched_block(dev, rank, world)
     if rank != 0:
         if world > 1:
             import torch.distributed as dist
@@ -708,8 +794,13 @@ def main():
     line = {"metric": METRIC, "value": value, "unit": "cell-steps/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": config_dict(args.workload, w, "flushed (256 MiB write) before every timed step, outside its events"),
-            "roofline": roofline_block(res, prof), "e2e": e2e, "gpu_launches": launches,
+            "config": config_dict(args.workload, w, "not flushed: the steps run back to back (Front2VOF and curvature "
+                                  "overlapping the next sweeps); the state (149 B per node) and the velocity "
+                                  "fields are far larger than L2"),
+            "roofline": dict(roofline_block(res_sync, prof), overlapped=overlapped(res),
+                             timing="CUDA events around the three split-sweep calls of each step of the ordered "
+                                    "pass (the sweeps alone on the GPU, L2 flushed before every step)"),
+            "e2e": e2e, "gpu_launches": launches,
             "clocks": clk, "counters": res["cnt"], "learned_bf16_vs_fp64": precision}
     hbm, _ = peaks()
     cells = run.cells
@@ -717,10 +808,15 @@ def main():
         "achieved": (3 * SWEEP_BYTES_PER_CELL + F2V_BYTES_PER_CELL) * cells * args.steps / (total_ms * 1e-3) / 1e9,
         "unit": "GB/s", "rule": "224.6 B per cell-step of advection + Front2VOF over all cells"}
     line["dense_equivalent"]["frac"] = line["dense_equivalent"]["achieved"] / hbm
+    line["sync_flushed"] = {
+        "value": run.cells * args.steps / (res_sync["total_ms"] * 1e-3), "unit": "cell-steps/s",
+        "ms_per_step": res_sync["total_ms"] / args.steps,
+        "note": "the same steps in order (Front2VOF and curvature on the context's stream), L2 flushed before "
+                "every step outside its events, an event pair per step"}
     if not args.no_extra:
         line["fourier_spheres_128"] = extra_grid_block("fourier_spheres_128", 512, 8, dev)
         line["curvature"] = curvature_block()
-        line["batched"] = batched_block()
+        line["batched"] = batched
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline_block(args.workload, w)
     print(json.dumps(line))

@@ -60,10 +60,11 @@ enum {
     EBIT_WINCONSISTENT = 1 /* consistency counters are non-zero (warning) */
 };
 
-/* flags for ebit_front2vof / ebit_curvature */
+/* flags for ebit_front2vof / ebit_curvature (EBIT_ASYNC may be OR-ed in) */
 enum {
     EBIT_INCREMENTAL = 0, /* recompute only the cells the sweeps may have changed */
-    EBIT_FULL = 1         /* recompute every cell */
+    EBIT_FULL = 1,        /* recompute every cell */
+    EBIT_ASYNC = 2        /* run on the context's side stream (see ebit_join) */
 };
 
 /* curvature modes */
@@ -185,8 +186,32 @@ int ebit_counters(ebit_ctx *ctx, ebit_counters_t *out);
 int ebit_reset_counters(ebit_ctx *ctx);
 
 /* Wait for the context's stream; returns pending device errors
- * (EBIT_ENONFINITE before EBIT_ECFL, see ebit_advect_sweep) or EBIT_OK. */
+ * (EBIT_ENONFINITE before EBIT_ECFL, see ebit_advect_sweep) or EBIT_OK.
+ * Joins the side stream first (ebit_join). */
 int ebit_sync(ebit_ctx *ctx);
+
+/* Asynchronous Front2VOF and curvature.  Not in the paper: its per-step
+ * pipeline (advection, then volume fractions, then curvature; Sec. 2.6) is
+ * kept, only overlapped.  With EBIT_ASYNC in flags, ebit_front2vof and
+ * ebit_curvature run on a side stream the context creates on first use, after
+ * the work already issued on the context's stream, and return at once; the
+ * next sweeps then run on the context's stream alongside them.  The library
+ * orders what depends on them: a sweep that would overwrite the state an
+ * asynchronous Front2VOF is reading waits for it (with the two buffers of a
+ * split step that is the step's second sweep), the sweeps mark their tiles
+ * for the following Front2VOF in a second set of tile flags, and every other
+ * call that reads or writes the state, the counters or C (ebit_init,
+ * ebit_set_state, ebit_get_state, ebit_counters, ebit_reset_counters,
+ * ebit_sync, a call without EBIT_ASYNC) first makes the context's stream
+ * wait for the side stream.  Callers that read C, kappa_h or status must do
+ * the same: ebit_join makes the context's stream wait for all side-stream
+ * work so far (no host synchronisation); ebit_event_record records
+ * cuda_event (a cudaEvent_t) where the last Front2VOF/curvature output is
+ * complete, so that another stream (a device-to-host copy) can wait for it
+ * without holding back the context's stream.  Not for batch instances
+ * (EBIT_EINVAL).  Errors: EBIT_EINVAL (null), EBIT_ECUDA. */
+int ebit_join(ebit_ctx *ctx);
+int ebit_event_record(ebit_ctx *ctx, void *cuda_event);
 
 /* Number of tiles (8x8x8 cells) the last sweep processed; -1 if unknown. */
 int ebit_band_tiles(ebit_ctx *ctx);

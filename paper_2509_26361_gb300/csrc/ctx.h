@@ -42,6 +42,17 @@ struct ebit_ctx {
     int cur;
     uint32_t *tile_marker;    // per tile: proximity mask of its markers (see near_bits)
     uint8_t *tile_dirty, *tile_cchg;
+    // Front2VOF and curvature may run on a side stream (EBIT_ASYNC), overlapping
+    // the next sweeps.  The sweeps mark processed tiles in dirty set dirty_set;
+    // each Front2VOF call consumes that set and the next sweeps mark the other
+    // (tile_dirty2 is set 1; a batch view keeps one set).
+    uint8_t *tile_dirty2;
+    int dirty_set;
+    cudaStream_t side;        // created on the first EBIT_ASYNC call
+    cudaEvent_t ev_main, ev_side, ev_f2v;
+    int side_pending;         // side-stream work not yet joined into the main stream
+    int f2v_pending;          // an async Front2VOF may still read state buffer f2v_buf
+    int f2v_buf;
     int *band_list, *band_count;  // band_count[2]: the lengths of band_list and band_list2
     int band_last;                // slot of the last sweep's band list (-1: every tile)
     int *work_list, *work_count;  // work_count[2]: one slot per incremental Front2VOF parity

@@ -76,7 +76,9 @@ int launched(ebit_ctx *ctx, cudaError_t e, const char *what) {
 int mark_all(ebit_ctx *ctx) {
     ctx->sweeps_since_f2v = 1;
     CU(cudaMemsetAsync(ctx->tile_marker, 0xFF, ctx->g.ntiles * sizeof(uint32_t), ctx->stream));
-    CU(cudaMemsetAsync(ctx->tile_dirty, 1, ctx->g.ntiles, ctx->stream));
+    CU(cudaMemsetAsync(ctx->dirty_set ? ctx->tile_dirty2 : ctx->tile_dirty, 1, ctx->g.ntiles, ctx->stream));
+    if (ctx->tile_dirty2)
+        CU(cudaMemsetAsync(ctx->dirty_set ? ctx->tile_dirty : ctx->tile_dirty2, 0, ctx->g.ntiles, ctx->stream));
     // the next sweep processes every tile and lists the markers and band anew
     ctx->mk_valid = 0;
     if (ctx->owns_state) {
@@ -86,6 +88,38 @@ int mark_all(ebit_ctx *ctx) {
     ctx->last_C = nullptr;
     ctx->last_kh = nullptr;
     ctx->last_st = nullptr;
+    return EBIT_OK;
+}
+
+// The main stream waits for everything issued on the side stream so far.
+int join_side(ebit_ctx *ctx) {
+    if (!ctx->side_pending) return EBIT_OK;
+    CU(cudaEventRecord(ctx->ev_side, ctx->side));
+    CU(cudaStreamWaitEvent(ctx->stream, ctx->ev_side, 0));
+    ctx->side_pending = 0;
+    ctx->f2v_pending = 0;
+    return EBIT_OK;
+}
+
+// The stream for a Front2VOF or curvature call: the side stream (after the
+// main stream's work so far) for EBIT_ASYNC, else the main stream (after any
+// side-stream work).
+int call_stream(ebit_ctx *ctx, int flags, cudaStream_t *st) {
+    if (!(flags & EBIT_ASYNC)) {
+        *st = ctx->stream;
+        return join_side(ctx);
+    }
+    if (!ctx->owns_state) return fail(ctx, EBIT_EINVAL, "EBIT_ASYNC: not for batch instances");
+    if (!ctx->side) {
+        CU(cudaStreamCreateWithFlags(&ctx->side, cudaStreamNonBlocking));
+        CU(cudaEventCreateWithFlags(&ctx->ev_main, cudaEventDisableTiming));
+        CU(cudaEventCreateWithFlags(&ctx->ev_side, cudaEventDisableTiming));
+        CU(cudaEventCreateWithFlags(&ctx->ev_f2v, cudaEventDisableTiming));
+    }
+    CU(cudaEventRecord(ctx->ev_main, ctx->stream));
+    CU(cudaStreamWaitEvent(ctx->side, ctx->ev_main, 0));
+    ctx->side_pending = 1;
+    *st = ctx->side;
     return EBIT_OK;
 }
 
@@ -110,6 +144,7 @@ int blocks_for(long long n, int threads, int sms) {
 int prof_drain(ebit_ctx *ctx) {
     if (ctx->ev_used == 0) return EBIT_OK;
     CU(cudaStreamSynchronize(ctx->stream));
+    if (ctx->side) CU(cudaStreamSynchronize(ctx->side));
     for (int i = 0; i < ctx->ev_used; i++) {
         float ms = 0.f;
         CU(cudaEventElapsedTime(&ms, ctx->ev[2 * i], ctx->ev[2 * i + 1]));
@@ -124,16 +159,17 @@ struct ProfScope {
     ebit_ctx *ctx;
     int kind;
     bool on;
-    ProfScope(ebit_ctx *c, int k) : ctx(c), kind(k), on(c->prof_on != 0) {
+    cudaStream_t st;
+    ProfScope(ebit_ctx *c, int k, cudaStream_t s = nullptr) : ctx(c), kind(k), on(c->prof_on != 0), st(s ? s : c->stream) {
         if (!on) return;
         if (ctx->ev_used * 2 + 2 > (int)ctx->ev.size()) {
             if (prof_drain(ctx) != EBIT_OK) { on = false; return; }
         }
-        cudaEventRecord(ctx->ev[2 * ctx->ev_used], ctx->stream);
+        cudaEventRecord(ctx->ev[2 * ctx->ev_used], st);
     }
     ~ProfScope() {
         if (!on) return;
-        cudaEventRecord(ctx->ev[2 * ctx->ev_used + 1], ctx->stream);
+        cudaEventRecord(ctx->ev[2 * ctx->ev_used + 1], st);
         ctx->ev_kind[ctx->ev_used] = kind;
         ctx->ev_used++;
     }
@@ -187,6 +223,11 @@ static int create_ctx(const ebit_desc *desc, const ebit_state_arrays *st, ebit_c
     ctx->mk_al[0] = ctx->mk_al[1] = nullptr;
     ctx->mtiles[0] = ctx->mtiles[1] = nullptr;
     ctx->band_flag = nullptr;
+    ctx->tile_dirty2 = nullptr;
+    ctx->dirty_set = 0;
+    ctx->side = nullptr;
+    ctx->ev_main = ctx->ev_side = ctx->ev_f2v = nullptr;
+    ctx->side_pending = ctx->f2v_pending = ctx->f2v_buf = 0;
     ctx->mk_par = 0;
     ctx->mk_dir = 0;
     ctx->mk_valid = 0;
@@ -252,7 +293,7 @@ static int create_ctx(const ebit_desc *desc, const ebit_state_arrays *st, ebit_c
                  alloc((void **)&ctx->mtiles[q], nt * sizeof(int));
         ok = ok && alloc((void **)&ctx->wcount2, (NLISTS + 1) * sizeof(int)) && alloc((void **)&ctx->mk_count, 2 * sizeof(int)) &&
              alloc((void **)&ctx->mt_count, 2 * sizeof(int)) && alloc((void **)&ctx->band_list2, nt * sizeof(int)) &&
-             alloc((void **)&ctx->band_flag, nt * sizeof(uint32_t));
+             alloc((void **)&ctx->band_flag, nt * sizeof(uint32_t)) && alloc((void **)&ctx->tile_dirty2, nt);
     }
     ok = ok && alloc((void **)&ctx->cut, ctx->N * sizeof(unsigned)) && alloc((void **)&ctx->scan, ctx->N * sizeof(unsigned)) &&
          alloc((void **)&ctx->iface[0], ctx->N * sizeof(unsigned)) &&
@@ -326,6 +367,13 @@ int ebit_create(const ebit_desc *desc, ebit_ctx **out) { return create_ctx(desc,
 void ebit_destroy(ebit_ctx *ctx) {
     if (!ctx) return;
     cudaStreamSynchronize(ctx->stream);
+    if (ctx->side) {
+        cudaStreamSynchronize(ctx->side);
+        cudaStreamDestroy(ctx->side);
+        cudaEventDestroy(ctx->ev_main);
+        cudaEventDestroy(ctx->ev_side);
+        cudaEventDestroy(ctx->ev_f2v);
+    }
     if (ctx->own_mlp) ebit_mlp_destroy(ctx->own_mlp);
     if (ctx->owns_state) {
         for (int b = 0; b < 2; b++) {
@@ -352,6 +400,7 @@ void ebit_destroy(ebit_ctx *ctx) {
         cudaFree(ctx->mtiles[1]);
         cudaFree(ctx->mt_count);
         cudaFree(ctx->band_flag);
+        cudaFree(ctx->tile_dirty2);
         cudaFree(ctx->band_list2);
     }
     cudaFree(ctx->tile_cchg);
@@ -376,6 +425,7 @@ void ebit_destroy(ebit_ctx *ctx) {
 
 int ebit_init(ebit_ctx *ctx, const double *phi_nodes, const double *phi_faces, const double *s_exact) {
     if (!ctx || !phi_nodes) return fail(ctx, EBIT_EINVAL, "ebit_init: null argument");
+    if (int r = join_side(ctx)) return r;
     int c = ctx->cur;
     init_kernel<<<blocks_for(ctx->N, 256, ctx->sms), 256, 0, ctx->stream>>>(
         ctx->g, phi_nodes, phi_faces, s_exact, ctx->cb[c], ctx->s[c][0], ctx->s[c][1], ctx->s[c][2]);
@@ -387,6 +437,7 @@ int ebit_init(ebit_ctx *ctx, const double *phi_nodes, const double *phi_faces, c
 
 int ebit_set_state(ebit_ctx *ctx, const uint8_t *cb, const double *s) {
     if (!ctx || !cb || !s) return fail(ctx, EBIT_EINVAL, "ebit_set_state: null argument");
+    if (int r = join_side(ctx)) return r;
     int c = ctx->cur;
     CU(cudaMemcpyAsync(ctx->cb[c], cb, ctx->N, cudaMemcpyDefault, ctx->stream));
     for (int a = 0; a < 3; a++)
@@ -398,6 +449,7 @@ int ebit_set_state(ebit_ctx *ctx, const uint8_t *cb, const double *s) {
 
 int ebit_get_state(ebit_ctx *ctx, uint8_t *cb, double *s) {
     if (!ctx || !cb || !s) return fail(ctx, EBIT_EINVAL, "ebit_get_state: null argument");
+    if (int r = join_side(ctx)) return r;
     if (!ctx->scratch) CU(cudaMalloc((void **)&ctx->scratch, 3 * ctx->N * sizeof(double)));
     int c = ctx->cur;
     canonical_s_kernel<<<blocks_for(ctx->N, 256, ctx->sms), 256, 0, ctx->stream>>>(
@@ -422,6 +474,11 @@ int ebit_advect_sweep(ebit_ctx *ctx, int dir, const double *u_face, double dt) {
     // rd from the latter, and writes set wr for the next one.  After a state
     // change, and in dense mode, every tile is processed and the markers are
     // found from the colours of each tile instead.
+    // an asynchronous Front2VOF may still read the buffer this sweep writes
+    if (ctx->f2v_pending && (ctx->cur ^ 1) == ctx->f2v_buf) {
+        CU(cudaStreamWaitEvent(ctx->stream, ctx->ev_f2v, 0));
+        ctx->f2v_pending = 0;
+    }
     const int rd = ctx->mk_par, wr = rd ^ 1;
     const bool lists = !ctx->dense && ctx->mk_valid;
     const int *list = lists ? (rd ? ctx->band_list2 : ctx->band_list) : ctx->all_list;
@@ -447,7 +504,7 @@ int ebit_advect_sweep(ebit_ctx *ctx, int dir, const double *u_face, double dt) {
     a.count = count;
     a.ctr = ctx->ctr;
     a.tile_marker = ctx->tile_marker;
-    a.tile_dirty = ctx->tile_dirty;
+    a.tile_dirty = ctx->dirty_set ? ctx->tile_dirty2 : ctx->tile_dirty;
     if (!ctx->dense) {
         a.mk_out = ctx->mk_al[wr];
         a.mk_out_count = ctx->mk_count + wr;
@@ -501,20 +558,26 @@ int ebit_front2vof(ebit_ctx *ctx, double *C, int flags) {
     bool full = (flags & EBIT_FULL) || ctx->dense || C != ctx->last_C;
     // nothing was swept since the last call on this buffer: C is current
     if (!full && ctx->sweeps_since_f2v == 0) return EBIT_OK;
+    cudaStream_t st;
+    if (int r = call_stream(ctx, flags, &st)) return r;
+    // this call consumes the dirty set the sweeps since the last call marked;
+    // the next sweeps mark the other one (a batch view has one set)
+    uint8_t *dirty = ctx->dirty_set ? ctx->tile_dirty2 : ctx->tile_dirty;
+    if (ctx->tile_dirty2) ctx->dirty_set ^= 1;
     if (full) {
-        CU(cudaMemsetAsync(ctx->ncut, 0, sizeof(int), ctx->stream));
-        CU(cudaMemsetAsync(ctx->tile_dirty, 0, ctx->g.ntiles, ctx->stream));
+        CU(cudaMemsetAsync(ctx->ncut, 0, sizeof(int), st));
+        CU(cudaMemsetAsync(dirty, 0, ctx->g.ntiles, st));
         list = ctx->all_list;
         count = ctx->all_count;
     } else {
         // work_count[fp] is 0; the tile-list kernel clears the other slot for
         // the next incremental call, and the cut-cell count (its readers, the
         // previous Front2VOF and curvature, are complete)
-        ProfScope ps(ctx, EBIT_PROF_F2V);
+        ProfScope ps(ctx, EBIT_PROF_F2V, st);
         const int fp = ctx->f2v_par;
         int r = launched(ctx,
-                         launch_pdl(take_flagged_kernel, blocks_for(ctx->g.ntiles, 256, ctx->sms), 256, 0, ctx->stream,
-                                    ctx->g, ctx->tile_dirty, ctx->work_list, ctx->work_count + fp,
+                         launch_pdl(take_flagged_kernel, blocks_for(ctx->g.ntiles, 256, ctx->sms), 256, 0, st,
+                                    ctx->g, dirty, ctx->work_list, ctx->work_count + fp,
                                     ctx->work_count + (fp ^ 1), ctx->ncut),
                          "take_flagged_kernel");
         if (r) return r;
@@ -535,15 +598,21 @@ int ebit_front2vof(ebit_ctx *ctx, double *C, int flags) {
     a.bad = ctx->ctr + C_F2V_BAD;
     int r;
     {
-        ProfScope ps(ctx, EBIT_PROF_F2V);
-        r = launched(ctx, launch_pdl(f2v_band_kernel, ctx->grid_f2v, 256, 0, ctx->stream, a), "f2v_band_kernel");
+        ProfScope ps(ctx, EBIT_PROF_F2V, st);
+        r = launched(ctx, launch_pdl(f2v_band_kernel, ctx->grid_f2v, 256, 0, st, a), "f2v_band_kernel");
     }
     if (r) return r;
     {
-        ProfScope ps(ctx, EBIT_PROF_F2V);
-        r = launched(ctx, launch_pdl(f2v_list_kernel, ctx->grid_f2vl, 128, 0, ctx->stream, a), "f2v_list_kernel");
+        ProfScope ps(ctx, EBIT_PROF_F2V, st);
+        r = launched(ctx, launch_pdl(f2v_list_kernel, ctx->grid_f2vl, 128, 0, st, a), "f2v_list_kernel");
     }
     if (r) return r;
+    if (st != ctx->stream) {
+        // the sweep that overwrites state buffer c waits for this event
+        CU(cudaEventRecord(ctx->ev_f2v, st));
+        ctx->f2v_pending = 1;
+        ctx->f2v_buf = c;
+    }
     ctx->last_C = C;
     ctx->sweeps_since_f2v = 0;
     return EBIT_OK;
@@ -556,6 +625,8 @@ int ebit_curvature(ebit_ctx *ctx, const double *C, double *kappa_h, uint8_t *sta
     if (mode != EBIT_CURV_HF && !ctx->mlp) return fail(ctx, EBIT_EINVAL, "ebit_curvature: no network (ebit_set_mlp)");
     bool full = (flags & EBIT_FULL) || ctx->dense || C != ctx->last_C || kappa_h != ctx->last_kh ||
                 status != ctx->last_st;
+    cudaStream_t st;
+    if (int r = call_stream(ctx, flags, &st)) return r;
     const int nw = ctx->cur_if ^ 1;
     // list lengths rotate over three slots: this call appends to slot cs
     // (0, cleared by the previous call), reads the previous call's length in
@@ -575,9 +646,9 @@ int ebit_curvature(ebit_ctx *ctx, const double *C, double *kappa_h, uint8_t *sta
     a.zero[1] = nullptr;
     if (full) {
         // any C: scan every tile, reset non-interface cells, list the interface cells
-        ProfScope ps(ctx, EBIT_PROF_SCAN);
-        CU(cudaMemsetAsync(ctx->nscan, 0, sizeof(int), ctx->stream));
-        int r = launched(ctx, launch_pdl(hf_scan_kernel, ctx->grid_hf, 256, 0, ctx->stream, a, ctx->scan, ctx->nscan),
+        ProfScope ps(ctx, EBIT_PROF_SCAN, st);
+        CU(cudaMemsetAsync(ctx->nscan, 0, sizeof(int), st));
+        int r = launched(ctx, launch_pdl(hf_scan_kernel, ctx->grid_hf, 256, 0, st, a, ctx->scan, ctx->nscan),
                          "hf_scan_kernel");
         if (r) return r;
         a.prev = ctx->iface[ctx->cur_if];
@@ -595,10 +666,10 @@ int ebit_curvature(ebit_ctx *ctx, const double *C, double *kappa_h, uint8_t *sta
     }
     {
         // height functions on every interface cell (mode HF), or only the list
-        ProfScope ps(ctx, EBIT_PROF_HF);
+        ProfScope ps(ctx, EBIT_PROF_HF, st);
         cudaError_t e = (mode == EBIT_CURV_HF)
-                            ? launch_pdl(hf_list_kernel<true>, ctx->grid_hfl, 128, 0, ctx->stream, a)
-                            : launch_pdl(hf_list_kernel<false>, ctx->grid_hfl, 128, 0, ctx->stream, a);
+                            ? launch_pdl(hf_list_kernel<true>, ctx->grid_hfl, 128, 0, st, a)
+                            : launch_pdl(hf_list_kernel<false>, ctx->grid_hfl, 128, 0, st, a);
         int r = launched(ctx, e, "hf_list_kernel");
         if (r) return r;
     }
@@ -618,16 +689,16 @@ int ebit_curvature(ebit_ctx *ctx, const double *C, double *kappa_h, uint8_t *sta
         m.mode = mode;
         m.fb = ctx->scan;  // free again: the listing pass above has consumed it
         m.nfb = ctx->nscan;
-        if (full) CU(cudaMemsetAsync(ctx->nscan, 0, sizeof(int), ctx->stream));
+        if (full) CU(cudaMemsetAsync(ctx->nscan, 0, sizeof(int), st));
         int r;
         {
-            ProfScope pm(ctx, EBIT_PROF_MLP);
+            ProfScope pm(ctx, EBIT_PROF_MLP, st);
             m.err = ctx->mlp->err;
             cudaError_t e =
                 (ctx->mlp->path == EBIT_MLP_PATH_TCGEN05)
-                    ? launch_pdl(mlp_fwd_tc_kernel<true, true>, ctx->sms, TC_THREADS, FWD_TC_SMEM, ctx->stream, m)
+                    ? launch_pdl(mlp_fwd_tc_kernel<true, true>, ctx->sms, TC_THREADS, FWD_TC_SMEM, st, m)
                     : launch_pdl(mlp_fwd_kernel<true, true>, ctx->mlp->fwd_blocks * ctx->sms, 128, FWD_SMEM,
-                                 ctx->stream, m);
+                                 st, m);
             r = launched(ctx, e, "mlp_fwd_kernel");
         }
         if (r) return r;
@@ -641,8 +712,8 @@ int ebit_curvature(ebit_ctx *ctx, const double *C, double *kappa_h, uint8_t *sta
             f.iface = nullptr;
             f.niface = nullptr;
             f.zero[0] = f.zero[1] = nullptr;
-            ProfScope pf(ctx, EBIT_PROF_MLP);
-            r = launched(ctx, launch_pdl(hf_list_kernel<true>, ctx->grid_hfl, 128, 0, ctx->stream, f),
+            ProfScope pf(ctx, EBIT_PROF_MLP, st);
+            r = launched(ctx, launch_pdl(hf_list_kernel<true>, ctx->grid_hfl, 128, 0, st, f),
                          "hf_list_kernel");
             if (r) return r;
         }
@@ -656,6 +727,7 @@ int ebit_curvature(ebit_ctx *ctx, const double *C, double *kappa_h, uint8_t *sta
 
 int ebit_counters(ebit_ctx *ctx, ebit_counters_t *out) {
     if (!ctx || !out) return fail(ctx, EBIT_EINVAL, "ebit_counters: null argument");
+    if (int r = join_side(ctx)) return r;
     unsigned long long h[C_TOTAL];
     CU(cudaMemcpyAsync(h, ctx->ctr, sizeof(h), cudaMemcpyDeviceToHost, ctx->stream));
     CU(cudaStreamSynchronize(ctx->stream));
@@ -673,12 +745,25 @@ int ebit_counters(ebit_ctx *ctx, ebit_counters_t *out) {
 
 int ebit_reset_counters(ebit_ctx *ctx) {
     if (!ctx) return EBIT_EINVAL;
+    if (int r = join_side(ctx)) return r;
     CU(cudaMemsetAsync(ctx->ctr, 0, C_TOTAL * sizeof(unsigned long long), ctx->stream));
+    return EBIT_OK;
+}
+
+int ebit_join(ebit_ctx *ctx) {
+    if (!ctx) return EBIT_EINVAL;
+    return join_side(ctx);
+}
+
+int ebit_event_record(ebit_ctx *ctx, void *cuda_event) {
+    if (!ctx || !cuda_event) return fail(ctx, EBIT_EINVAL, "ebit_event_record: null argument");
+    CU(cudaEventRecord((cudaEvent_t)cuda_event, ctx->side_pending ? ctx->side : ctx->stream));
     return EBIT_OK;
 }
 
 int ebit_sync(ebit_ctx *ctx) {
     if (!ctx) return EBIT_EINVAL;
+    if (int r = join_side(ctx)) return r;
     unsigned long long h[C_TOTAL];
     CU(cudaMemcpyAsync(h, ctx->ctr, sizeof(h), cudaMemcpyDeviceToHost, ctx->stream));
     CU(cudaStreamSynchronize(ctx->stream));

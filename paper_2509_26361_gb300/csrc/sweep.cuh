@@ -854,8 +854,13 @@ __device__ __forceinline__ int sweep_tile(const SweepArgs &a, int tile, uint8_t 
             }
             // the warp's appends to the NL work lists and the marker list: all
             // ballots first, then lane 0 reserves every list's slots with
-            // independent atomics (one round trip to L2 for all of them)
-            {
+            // independent atomics (one round trip to L2 for all of them); a
+            // warp with nothing to append (cells away from the interface)
+            // skips it after one vote
+            bool any_push = push_al;
+#pragma unroll
+            for (int k = 0; k < NL; k++) any_push |= push[k];
+            if (__any_sync(0xffffffffu, any_push)) {
                 const unsigned full = 0xffffffffu;
                 const int lane = threadIdx.x & 31;
                 unsigned m[NL + 1];
@@ -885,10 +890,12 @@ __device__ __forceinline__ int sweep_tile(const SweepArgs &a, int tile, uint8_t 
             const unsigned v = __reduce_or_sync(0xffffffffu, mk);
             if ((threadIdx.x & 31) == 0 && v) atomicOr(s_flag, v);
         }
+        if (__any_sync(0xffffffffu, (ev[0] | ev[1] | ev[2] | ev[3] | ev[4]) != 0u)) {
 #pragma unroll
-        for (int k = 0; k < C_N; k++) {
-            unsigned v = __reduce_add_sync(0xffffffffu, ev[k]);
-            if ((threadIdx.x & 31) == 0 && v) atomicAdd(a.ctr + k, (unsigned long long)v);
+            for (int k = 0; k < C_N; k++) {
+                unsigned v = __reduce_add_sync(0xffffffffu, ev[k]);
+                if ((threadIdx.x & 31) == 0 && v) atomicAdd(a.ctr + k, (unsigned long long)v);
+            }
         }
         __syncthreads();
         int pending = -1;

@@ -26,6 +26,7 @@ EBIT_WINCONSISTENT = 1
 
 EBIT_INCREMENTAL = 0
 EBIT_FULL = 1
+EBIT_ASYNC = 2
 EBIT_CURV_HF = 0
 EBIT_CURV_MLP = 1
 EBIT_CURV_MLP_HF = 2
@@ -86,6 +87,8 @@ def load(build_if_missing: bool = True):
     lib.ebit_profile.argtypes = [P, I]
     lib.ebit_profile_read.argtypes = [P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int64)]
     lib.ebit_advect_sweep_noalloc.argtypes = [I, I, I, D, I, P, P, P, D, P, P, P]
+    lib.ebit_join.argtypes = [P]
+    lib.ebit_event_record.argtypes = [P, P]
     lib.ebit_mlp_nparams.argtypes = []
     lib.ebit_mlp_create.argtypes = [P, ctypes.POINTER(ctypes.c_void_p)]
     lib.ebit_mlp_destroy.argtypes = [P]
@@ -213,6 +216,19 @@ def ebit_reset_counters(ctx):
 
 def ebit_sync(ctx):
     return _check(ctx, load().ebit_sync(ctx))
+
+
+def ebit_join(ctx):
+    return _check(ctx, load().ebit_join(ctx))
+
+
+def ebit_event_record(ctx, event):
+    """Record a torch.cuda.Event where the context's last Front2VOF/curvature
+    output is complete (see include/ebit.h).  torch creates the CUDA event on
+    its first record, so an unused event is recorded once first."""
+    if not event.cuda_event:
+        event.record()
+    return _check(ctx, load().ebit_event_record(ctx, ctypes.c_void_p(event.cuda_event)))
 
 
 def ebit_band_tiles(ctx):
@@ -601,6 +617,12 @@ class Grid:
 
     def sync(self):
         return ebit_sync(self.ctx)
+
+    def join(self):
+        return ebit_join(self.ctx)
+
+    def record_done(self, event):
+        return ebit_event_record(self.ctx, event)
 
     def band_tiles(self):
         return ebit_band_tiles(self.ctx)

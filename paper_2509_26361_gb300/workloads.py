@@ -397,15 +397,22 @@ def fourier_spheres(n=128, seed=2, count=8, rmin=0.05, rmax=0.12, cfl=0.5, perio
     return Workload("fourier_spheres", n3, phi, faces, u, cfl, steps, period=period, shapes=sp)
 
 
-def batched_instances(seed=4, count=64, sizes=(32, 48, 64, 96, 128), cfl=0.5, rmin=0.07, rmax=0.15):
+def batched_sizes(seed=4, count=64, sizes=(32, 48, 64, 96, 128)):
+    """The seeded grid sizes of the batched instances (the first draw of
+    batched_instances' generator)."""
+    return [int(n) for n in np.random.default_rng(seed).choice(np.asarray(sizes), size=count)]
+
+
+def batched_instances(seed=4, count=64, sizes=(32, 48, 64, 96, 128), cfl=0.5, rmin=0.07, rmax=0.15, limit=None):
     """Independent periodic instances for the batched sweeps: seeded grid sizes
     from ``sizes``, each with its own seeded 12-mode Fourier field and 1-4
     non-overlapping spheres (radii U[rmin, rmax]), dt = cfl * h of the instance.
-    Returns a list of (n, phi, phi_faces, u, dt)."""
+    Returns a list of (n, phi, phi_faces, u, dt); with ``limit``, only the first
+    ``limit`` instances (the same as in the full list)."""
     rng = np.random.default_rng(seed)
     ns = rng.choice(np.asarray(sizes), size=count)
     out = []
-    for n in ns:
+    for n in ns[:limit]:
         n = int(n)
         k = int(rng.integers(1, 5))
         sp = random_spheres(rng, k, rmin, rmax, n)

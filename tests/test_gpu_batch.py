@@ -148,3 +148,38 @@ def test_per_call_velocity_matches_stored_velocity():
         assert torch.equal(ca, cb_) and torch.equal(sa, sb)
     a.close()
     b.close()
+
+
+@pytest.mark.parametrize("graph", [True, False])
+def test_batch_on_members_of_the_64_instance_config(graph):
+    """The first four instances of the batched workload itself (96^3, 128^3,
+    128^3 and 64^3, their own fields and spheres, dt = 0.5 h): three steps of
+    the batch against separate contexts, bit for bit, with the same counters."""
+    insts = W.batched_instances(limit=4)
+    assert sorted(n for n, *_ in insts) == [64, 96, 128, 128]
+    steps = 3
+    ref = []
+    for n, phi, faces, u, dt in insts:
+        g = ebit.Grid(n, n, n)
+        g.init(dev(phi), dev(faces))
+        ud = [dev(u[d]) for d in range(3)]
+        for k in range(steps):
+            g.step(k, ud, dt)
+        cb, s = g.get_state()
+        ref.append((cb.cpu(), s.cpu(), g.counters()))
+        g.close()
+    b = ebit.Batch([(n, n, n) for n, *_ in insts])
+    uf = []
+    for i, (n, phi, faces, u, dt) in enumerate(insts):
+        b.instance(i).init(dev(phi), dev(faces))
+        uf.append(tuple(dev(u[d]) for d in range(3)))
+    b.set_velocity(uf, [dt for *_, dt in insts])
+    b.run(0, steps, graph=graph)
+    b.sync()
+    for i, (cb_r, s_r, cnt_r) in enumerate(ref):
+        cb, s = b.instance(i).get_state()
+        assert torch.equal(cb.cpu(), cb_r), f"instance {i}: colours differ"
+        assert torch.equal(s.cpu(), s_r), f"instance {i}: offsets differ"
+        assert b.instance(i).counters() == cnt_r, (i, b.instance(i).counters(), cnt_r)
+        assert cnt_r["markers"] > 0
+    b.close()

@@ -355,3 +355,55 @@ def test_checkpoint_resume_is_bit_identical():
     assert present_mask(cb_a).sum() > 1000
     a.close()
     c.close()
+
+
+def test_async_front2vof_and_curvature_match_the_ordered_calls():
+    """Front2VOF and curvature on the side stream (EBIT_ASYNC), overlapping the
+    next step's sweeps, give the same fractions, curvature and statuses at
+    every step as ordered calls, read the way a host copy would read them
+    (another stream waits on ebit_event_record while the sweeps go on); the
+    state after the last step is identical; async and ordered calls mix."""
+    w = W.fourier_spheres(n=40, seed=6, count=5, rmin=0.07, rmax=0.15, steps=8)
+    ud = [to_dev(w.u[d]) for d in range(3)]
+    steps = 8
+    res = []
+    for asynch in (False, True):
+        g = ebit.Grid(*w.n3)
+        g.init(to_dev(w.phi), to_dev(w.phi_faces))
+        C = torch.zeros(g.shape, dtype=torch.float64, device="cuda")
+        kh = torch.zeros_like(C)
+        st = torch.zeros(g.shape, dtype=torch.uint8, device="cuda")
+        g.front2vof(C, ebit.EBIT_FULL)
+        g.curvature(C, kh, st, flags=ebit.EBIT_FULL)
+        snaps = []
+        copy = torch.cuda.Stream()
+        done = None
+        for n in range(steps):
+            g.step(n, ud, w.lam(n) * g.h)
+            # the previous step's copies finish before Front2VOF overwrites C
+            # (the sweeps above did not wait for them)
+            if done is not None:
+                torch.cuda.current_stream().wait_event(done)
+            # step 5 mixes in ordered calls
+            fl = ebit.EBIT_ASYNC if (asynch and n != 5) else ebit.EBIT_INCREMENTAL
+            g.front2vof(C, fl)
+            g.curvature(C, kh, st, flags=fl)
+            ev = torch.cuda.Event()
+            g.record_done(ev)
+            with torch.cuda.stream(copy):
+                copy.wait_event(ev)
+                snaps.append((C.clone(), kh.clone(), st.clone()))
+                done = torch.cuda.Event()
+                done.record(copy)
+        g.join()
+        torch.cuda.synchronize()
+        cb, s = g.get_state()
+        res.append(([tuple(t.cpu().numpy() for t in sn) for sn in snaps], cb.cpu().numpy(), s.cpu().numpy(),
+                    g.counters()))
+        g.close()
+    (sa, cba, sa_s, ca), (sb, cbb, sb_s, cbc) = res
+    for n in range(steps):
+        for x, y in zip(sa[n], sb[n]):
+            assert np.array_equal(x.view(np.uint8), y.view(np.uint8)), f"step {n}"
+    assert np.array_equal(cba, cbb) and np.array_equal(sa_s.view(np.uint64), sb_s.view(np.uint64))
+    assert ca == cbc
