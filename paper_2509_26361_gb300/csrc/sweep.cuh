@@ -264,12 +264,26 @@ __device__ double interp_u(const Grid &g, const double *__restrict__ u, const in
     int z0 = wrapc(base[2], g.n[2]), z1 = wrapc(base[2] + 1, g.n[2]);
     int r00 = (z0 * g.n[1] + y0) * g.n[0], r10 = (z0 * g.n[1] + y1) * g.n[0];
     int r01 = (z1 * g.n[1] + y0) * g.n[0], r11 = (z1 * g.n[1] + y1) * g.n[0];
-    double c00 = (1.0 - t[0]) * __ldg(u + r00 + x0) + t[0] * __ldg(u + r00 + x1);
-    double c10 = (1.0 - t[0]) * __ldg(u + r10 + x0) + t[0] * __ldg(u + r10 + x1);
-    double c01 = (1.0 - t[0]) * __ldg(u + r01 + x0) + t[0] * __ldg(u + r01 + x1);
-    double c11 = (1.0 - t[0]) * __ldg(u + r11 + x0) + t[0] * __ldg(u + r11 + x1);
-    double c0 = (1.0 - t[1]) * c00 + t[1] * c10;
-    double c1 = (1.0 - t[1]) * c01 + t[1] * c11;
+    // A marker off the sweep axis sits on a D-face plane (t[D] = 0): the lerp
+    // along D gives (1 - 0) a + 0 b = a for finite b, so its upper samples are
+    // not read (for a = -0 the sign of the zero may differ; nothing downstream
+    // depends on it).
+    const bool flatD = e != D;
+    double c00, c10, c01, c11;
+    if (D == 0 && flatD) {
+        c00 = __ldg(u + r00 + x0);
+        c10 = __ldg(u + r10 + x0);
+        c01 = __ldg(u + r01 + x0);
+        c11 = __ldg(u + r11 + x0);
+    } else {
+        c00 = (1.0 - t[0]) * __ldg(u + r00 + x0) + t[0] * __ldg(u + r00 + x1);
+        c10 = (D == 1 && flatD) ? 0.0 : (1.0 - t[0]) * __ldg(u + r10 + x0) + t[0] * __ldg(u + r10 + x1);
+        c01 = (D == 2 && flatD) ? 0.0 : (1.0 - t[0]) * __ldg(u + r01 + x0) + t[0] * __ldg(u + r01 + x1);
+        c11 = (D != 0 && flatD) ? 0.0 : (1.0 - t[0]) * __ldg(u + r11 + x0) + t[0] * __ldg(u + r11 + x1);
+    }
+    const double c0 = (D == 1 && flatD) ? c00 : (1.0 - t[1]) * c00 + t[1] * c10;
+    if (D == 2 && flatD) return c0;
+    const double c1 = (D == 1 && flatD) ? c01 : (1.0 - t[1]) * c01 + t[1] * c11;
     return (1.0 - t[2]) * c0 + t[2] * c1;
 }
 
@@ -372,27 +386,34 @@ template <int D, int NL = 4>
 __global__ void __launch_bounds__(256) advect_list_kernel(SweepArgs a, MarkerLists m) {
     pdl_wait();
     clear_sweep_counts<NL>(a);
-    // this sweep's band: every tile a listed tile's mask points to (bit
-    // near_bit(dx, dy, dz) names the neighbour in that direction), listed once
-    const int nmt = *m.mtiles_count;
-    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < 27 * nmt; t += gridDim.x * blockDim.x) {
-        const int tile = __ldg(m.mtiles + t / 27), b = t % 27;
-        if (!((__ldg(a.tile_marker + tile) >> b) & 1u)) continue;
-        const int tx = tile % a.g.td[0], ty = (tile / a.g.td[0]) % a.g.td[1], tz = tile / (a.g.td[0] * a.g.td[1]);
-        const int nx = wrapc(tx + b % 3 - 1, a.g.td[0]), ny = wrapc(ty + (b / 3) % 3 - 1, a.g.td[1]),
-                  nz = wrapc(tz + b / 9 - 1, a.g.td[2]);
-        const int nt = (nz * a.g.td[1] + ny) * a.g.td[0] + nx;
-        if (atomicExch(a.band_flag + nt, 1u) == 0u) m.band[atomicAdd(m.band_count, 1)] = nt;
-    }
+    // One index space: the markers, then this sweep's band items (tile of the
+    // marker-tile list, direction); a thread takes one item per round, so the
+    // two kinds of work run side by side rather than one after the other.
     const int n0 = *m.count[0], n1 = *m.count[1], n2 = *m.count[2];
     const int total = n0 + n1 + n2;
+    const int nmt = *m.mtiles_count;
+    const int all = total + 27 * nmt;
     const int stride = gridDim.x * blockDim.x;
-    const int iters = (total + stride - 1) / stride;
+    const int iters = (all + stride - 1) / stride;
     const int nx = a.g.n[0], nxy = a.g.n[0] * a.g.n[1];
     unsigned hits = 0, bad = 0;
     for (int it = 0; it < iters; it++) {
         const int t = list_item(it);
-        if (t >= total) continue;
+        if (t >= all) continue;
+        if (t >= total) {
+            // the band: every tile a listed tile's mask points to (bit
+            // near_bit(dx, dy, dz) names the neighbour in that direction),
+            // listed once
+            const int tb = t - total;
+            const int tile = __ldg(m.mtiles + tb / 27), b = tb % 27;
+            if (!((__ldg(a.tile_marker + tile) >> b) & 1u)) continue;
+            const int tx = tile % a.g.td[0], ty = (tile / a.g.td[0]) % a.g.td[1], tz = tile / (a.g.td[0] * a.g.td[1]);
+            const int bx = wrapc(tx + b % 3 - 1, a.g.td[0]), by = wrapc(ty + (b / 3) % 3 - 1, a.g.td[1]),
+                      bz = wrapc(tz + b / 9 - 1, a.g.td[2]);
+            const int nt = (bz * a.g.td[1] + by) * a.g.td[0] + bx;
+            if (atomicExch(a.band_flag + nt, 1u) == 0u) m.band[atomicAdd(m.band_count, 1)] = nt;
+            continue;
+        }
         // selects rather than indexing, which would copy the parameter arrays
         // to local memory
         const int k = t < n0 ? 0 : (t < n0 + n1 ? 1 : 2);
@@ -701,6 +722,7 @@ __device__ __forceinline__ int sweep_tile(const SweepArgs &a, int tile, uint8_t 
         // copy is indexed in sweep-local order (A fastest)
         constexpr int E0 = A == 0 ? RA : (T1 == 0 ? R1 : R2);
         constexpr int E1 = A == 1 ? RA : (T1 == 1 ? R1 : R2);
+        int seen = 0;  // bit 0: a staged node of colour 1, bit 1: one of colour 0
         for (int r = threadIdx.x; r < RA * R1 * R2; r += blockDim.x) {
             const int gl[3] = {r % E0, (r / E0) % E1, r / (E0 * E1)};
             const int ka = gl[A], k1 = gl[T1], k2 = gl[T2];
@@ -710,10 +732,30 @@ __device__ __forceinline__ int sweep_tile(const SweepArgs &a, int tile, uint8_t 
             q[T2] = o[T2] + k2;
             const int id = lin3(a.g, q);
             const int sr = ka + RA * (k1 + R1 * k2);
-            s_b[sr] = __ldg(a.cb + id);
+            const uint8_t b = __ldg(a.cb + id);
+            seen |= (b & 1) ? 1 : 2;
+            s_b[sr] = b;
             s_n[sr] = ld_in<F>(a.bin[A] + id);
         }
-        __syncthreads();
+        // (__syncthreads_or returns whether any thread's value is non-zero)
+        const int has1 = __syncthreads_or(seen & 1), has0 = __syncthreads_or(seen & 2);
+        if (!(has1 && has0)) {
+            // Every staged node has one colour: no marker lies on an edge whose
+            // crossing could change a node, face or edge of this tile's cells,
+            // so the sweep leaves them as they are (the band pass's uniform
+            // window, for the whole tile): canonical colour bytes, no markers,
+            // no work, and nothing for Front2VOF to redo.
+            const uint8_t byte = has1 ? 0x0F : 0x00;
+            for (int c = threadIdx.x; c < TILE_CELLS; c += blockDim.x) {
+                const int x = o[0] + (c & 7), y = o[1] + ((c >> 3) & 7), z = o[2] + (c >> 6);
+                if (x < a.g.n[0] && y < a.g.n[1] && z < a.g.n[2]) a.cbo[lin(a.g, x, y, z)] = byte;
+            }
+            if (threadIdx.x == 0) {
+                a.tile_marker[tile] = 0u;
+                if (a.band_flag) a.band_flag[tile] = 0u;
+            }
+            return -1;
+        }
         unsigned ev[C_N] = {0, 0, 0, 0, 0};
         unsigned mk = 0;  // proximity mask of the markers of this thread's cells
         for (int c = threadIdx.x; c < TILE_CELLS; c += blockDim.x) {
@@ -987,7 +1029,7 @@ __device__ __forceinline__ void fp64_item(const SweepArgs &a, int kind, int k, u
 }
 
 template <int D, int NL = 4>
-__global__ void __launch_bounds__(128) fp64_kernel(SweepArgs a) {
+__global__ void __launch_bounds__(128, 8) fp64_kernel(SweepArgs a) {
     pdl_wait();
     const int n0 = a.wcount[0], n1 = a.wcount[1], n2 = a.wcount[2], n3 = a.wcount[3];
     const int n4 = NL == 6 ? a.wcount[4] : 0, n5 = NL == 6 ? a.wcount[5] : 0;
