@@ -45,13 +45,19 @@ WORKLOADS = {"merging_drops_512": ("merging", 512), "merging_drops_256": ("mergi
 # per band cell of one split sweep and of Front2VOF (the scope table's figures)
 SWEEP_BYTES_PER_CELL = 62.75
 F2V_BYTES_PER_CELL = 36.4
-# DRAM bytes (read + write) per launch of the split-sweep kernels, from one ncu
-# capture of each; None until the current kernels have been captured.
-NCU_TRAFFIC = None
-# FP64 arithmetic rate of this GPU (thread operations per second; a probe of
-# independent add and multiply chains over every SM); the FP64-list kernel's
-# second roofline
-FP64_OPS_PER_S = 5.26e11
+# DRAM bytes (read + write) of one split sweep (list advection + band pass +
+# FP64 lists) per band cell, from one ncu capture of each kernel on the
+# converging drops at 256^3 (18.1 MB for about 4.8e5 band cells;
+# profiles/sweep_kernels_merging_drops_256.md); scaled by the band of the run.
+NCU_DRAM_BYTES_PER_BAND_CELL = 18.12e6 / 4.807e5
+# The FP64-list kernel's second roofline.  Peak: GB300's FP64 FMA rate
+# (6.2e11 thread operations per second, 2 per clock per SM; a probe of
+# independent FMA chains over every SM; the ncu counters give the same 304 per
+# clock).  Work: FP64 adds, multiplies and FMAs per marker of the sweep, from
+# the ncu capture of the kernel at 256^3 (3.49e6 per launch for 3.57e4
+# markers: 23.3 + 19.8 + 20.6 per elapsed cycle over 54 730 cycles).
+FP64_PEAK_OPS_PER_S = 6.245e11
+FP64_OPS_PER_MARKER = 3.49e6 / 3.567e4
 
 
 def peaks():
@@ -592,20 +598,31 @@ def roofline_block(res, prof):
     alg = SWEEP_BYTES_PER_CELL * band_cells
     alg_min = 2.0 * band_cells + 24.0 * markers
     achieved = alg / per_sweep_s / 1e9
-    traffic = sum(NCU_TRAFFIC.values()) if NCU_TRAFFIC else None
+    traffic = NCU_DRAM_BYTES_PER_BAND_CELL * band_cells
     stages = {"split_sweep": sum(prof[k][0] for k in ("band", "advect", "sweep", "fp64") if k in prof),
               "front2vof": prof.get("f2v", (0.0, 0))[0],
               "curvature": sum(prof.get(k, (0.0, 0))[0] for k in ("hf", "scan", "mlp"))}
+    fp64 = None
+    if "fp64" in prof and prof["fp64"][1]:
+        t_fp64 = prof["fp64"][0] * 1e-3 / prof["fp64"][1]
+        ops = FP64_OPS_PER_MARKER * markers
+        fp64 = {"kernel": "fp64_kernel (circle fits, face phases, crossing counts)", "bound": "alu",
+                "unit": "FP64 ops/s", "achieved": ops / t_fp64, "peak": FP64_PEAK_OPS_PER_S,
+                "frac": ops / t_fp64 / FP64_PEAK_OPS_PER_S, "ops_per_launch": ops, "avg_launch_us": t_fp64 * 1e6,
+                "rule": "ncu FP64 add/mul/FMA count per marker at 256^3 x markers per sweep; launch time from the "
+                        "instrumented pass (an event pair per launch)"}
     return {"bound": "hbm", "kernel": "split sweep (advect + integer pass + FP64 lists)",
             "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm, "traffic": traffic,
             "peak_source": src, "alg_bytes_per_launch": alg, "alg_bytes_rule": "62.75 B per band cell per sweep",
+            "traffic_rule": "ncu DRAM bytes per band cell of the three sweep kernels at 256^3, times this run's "
+                            "band cells per sweep",
             "band_cells_per_sweep": band_cells, "markers_per_sweep": markers,
             "min_bytes_per_sweep": alg_min, "min_frac": alg_min / per_sweep_s / 1e9 / hbm,
             "avg_sweep_us": per_sweep_s * 1e6,
             "timing": "CUDA events around the three split-sweep calls of each step in the timed region",
             "instrumented_stage_ms": {k: round(v, 4) for k, v in stages.items()},
             "instrumented_kernel_ms": {k: round(v[0], 4) for k, v in prof.items()},
-            "kernel_launches": {k: v[1] for k, v in prof.items()}}
+            "kernel_launches": {k: v[1] for k, v in prof.items()}, "fp64_pipe": fp64}
 
 
 def overlapped(res):
