@@ -454,17 +454,16 @@ class Run:
                     wall=(wall0, wall1))
 
     def instrumented(self, warmup, steps):
-        """The same steps from the same state with an event pair around every
-        kernel launch of the library: per-kernel times and the launch count.
-        The events slow the step, so none of these times enter value or
-        roofline."""
+        """The same steps from the same state, in order, with an event pair
+        around every kernel launch of the library: per-kernel times (each
+        kernel alone on the GPU) and the launch count.  The events slow the
+        step, so none of these times enter value or the HBM roofline."""
         import torch
 
-        self.start(warmup, asynch=True)
+        self.start(warmup)
         self.g.profile(True)
         for i in range(steps):
-            self.one_step(warmup + i, asynch=True)
-        self.g.join()
+            self.one_step(warmup + i)
         torch.cuda.synchronize()
         prof = self.g.profile_read()
         self.g.profile(False)
