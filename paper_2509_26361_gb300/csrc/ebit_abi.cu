@@ -986,7 +986,7 @@ static int mlp_grad_launch(ebit_mlp *mlp, const uint16_t *X, const float *t, con
     a.grad = mlp->g;
     a.loss = mlp->loss;
     const int ntile = (batch + 127) / 128;
-    mlp_train_kernel<<<std::min(ntile, mlp->sms), 128, TRAIN_SMEM, mlp->stream>>>(a);
+    mlp_train_kernel<<<std::min(ntile, mlp->sms), TRAIN_THREADS, TRAIN_SMEM, mlp->stream>>>(a);
     MCU(cudaGetLastError());
     return EBIT_OK;
 }

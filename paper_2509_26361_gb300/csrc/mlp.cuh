@@ -605,9 +605,12 @@ constexpr int TR_B1 = TR_XT + 64 * LD128 * 2;
 constexpr int TR_H1T = TR_B1 + 128 * LD128 * 2;
 constexpr int TR_DH2T = TR_H1T + 128 * LD128 * 2;
 constexpr int TR_RED = TR_DH2T + 128 * LD128 * 2;
-constexpr int TRAIN_SMEM = TR_RED + 512 * 4;
+constexpr int TRAIN_SMEM = TR_RED + 900 * 4;  // reductions 388 floats, partial row sums of y 4 x 128
+constexpr int TRAIN_THREADS = 512;            // 16 warps: 4 row blocks x 4 column blocks of 32
+static_assert(MLP_IN == 64 && MLP_H == 128, "the training kernel's warp split assumes 64 inputs, 128 hidden units");
+static_assert(TRAIN_SMEM <= 227 * 1024, "training tile exceeds the shared memory of one block");
 
-__global__ void __launch_bounds__(128) mlp_train_kernel(MlpArgs a) {
+__global__ void __launch_bounds__(TRAIN_THREADS) mlp_train_kernel(MlpArgs a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __nv_bfloat16 *sW1 = reinterpret_cast<__nv_bfloat16 *>(smem_raw + TR_W1);
     __nv_bfloat16 *sW2 = reinterpret_cast<__nv_bfloat16 *>(smem_raw + TR_W2);
@@ -618,75 +621,102 @@ __global__ void __launch_bounds__(128) mlp_train_kernel(MlpArgs a) {
     __nv_bfloat16 *sH1T = reinterpret_cast<__nv_bfloat16 *>(smem_raw + TR_H1T);
     __nv_bfloat16 *sdH2T = reinterpret_cast<__nv_bfloat16 *>(smem_raw + TR_DH2T);
     float *red = reinterpret_cast<float *>(smem_raw + TR_RED);  // dw3 | db1 | db2 | db3, loss
+    float *sy = red + 388;  // [column block][row]: partial sums of y over 32 hidden units of layer 2
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31, g = lane >> 2, t4 = lane & 3;
-    const int m0 = warp * 32;
-    load_row(sW1, LD64, tid, a.w1b, tid, MLP_IN, MLP_H);
-    for (int j = 0; j < MLP_H; j++) sW2T[j * LD128 + tid] = a.w2b[tid * MLP_H + j];
-    for (int k = tid; k < 512; k += 128) red[k] = 0.0f;
+    // warp (row block, column block) of every 128 x 128 product
+    const int m0 = (warp & 3) * 32, cb = warp >> 2, n0 = cb * 32;
+    const int row_t = tid & 127, part = tid >> 7;  // the tile row and quarter a thread stages
+    if (tid < 128) load_row(sW1, LD64, tid, a.w1b, tid, MLP_IN, MLP_H);
+    for (int j = part * 32; j < part * 32 + 32; j++) sW2T[j * LD128 + row_t] = a.w2b[row_t * MLP_H + j];
+    for (int k = tid; k < 388; k += TRAIN_THREADS) red[k] = 0.0f;
     const int B = a.batch;
     const int ntile = (B + 127) / 128;
     const float invB = 1.0f / (float)B;
     for (int tile = blockIdx.x; tile < ntile; tile += gridDim.x) {
-        const int row = tile * 128 + tid;
-        const bool live = row < B;
-        load_row(sW2, LD128, tid, a.w2b, tid, MLP_H, MLP_H);
-        __nv_bfloat16 xv[MLP_IN];
-        if (live) {
-            const long long src = a.idx ? a.idx[row] : row;
-            const uint4 *s4 = reinterpret_cast<const uint4 *>(a.X + src * MLP_IN);
-            for (int q = 0; q < MLP_IN / 8; q++) reinterpret_cast<uint4 *>(xv)[q] = s4[q];
-        } else {
-            for (int q = 0; q < MLP_IN; q++) xv[q] = __float2bfloat16_rn(0.0f);
+        // W2 (its buffer holds dH1^T by the end of a tile), this tile's rows
+        // of X and their transpose; each thread stages a quarter of one row
+        {
+            const uint4 *s4 = reinterpret_cast<const uint4 *>(a.w2b + row_t * MLP_H) + 4 * part;
+            uint4 *d4 = reinterpret_cast<uint4 *>(sW2 + row_t * LD128) + 4 * part;
+            for (int q = 0; q < 4; q++) d4[q] = s4[q];
         }
-        for (int q = 0; q < MLP_IN / 8; q++) reinterpret_cast<uint4 *>(sX + tid * LD64)[q] = reinterpret_cast<uint4 *>(xv)[q];
-        for (int i = 0; i < MLP_IN; i++) sXT[i * LD128 + tid] = xv[i];
+        {
+            const int row = tile * 128 + row_t;
+            __align__(16) __nv_bfloat16 xv[16];
+            uint4 *x4 = reinterpret_cast<uint4 *>(xv);
+            if (row < B) {
+                const long long src = a.idx ? a.idx[row] : row;
+                const uint4 *s4 = reinterpret_cast<const uint4 *>(a.X + src * MLP_IN) + 2 * part;
+                x4[0] = s4[0];
+                x4[1] = s4[1];
+            } else {
+                x4[0] = make_uint4(0u, 0u, 0u, 0u);
+                x4[1] = x4[0];
+            }
+            uint4 *d4 = reinterpret_cast<uint4 *>(sX + row_t * LD64) + 2 * part;
+            d4[0] = x4[0];
+            d4[1] = x4[1];
+#pragma unroll
+            for (int i = 0; i < 16; i++) sXT[(part * 16 + i) * LD128 + row_t] = xv[i];
+        }
         __syncthreads();
-        // ---- layer 1: H1 (rows) and H1T, ReLU masks kept in registers
-        uint32_t mask1[4] = {0, 0, 0, 0};
-        for (int c = 0; c < 4; c++) {
+        // ---- layer 1: the warp's block of H1 (rows) and H1T; ReLU mask kept
+        uint32_t mask1 = 0;
+        {
             float acc[2][4][4];
-            warp_gemm32<MLP_IN, LD64, LD64>(sX, sW1, m0, c * 32, acc);
+            warp_gemm32<MLP_IN, LD64, LD64>(sX, sW1, m0, n0, acc);
 #pragma unroll
             for (int mt = 0; mt < 2; mt++)
 #pragma unroll
                 for (int nt = 0; nt < 4; nt++)
 #pragma unroll
                     for (int e = 0; e < 4; e++) {
-                        const int r = m0 + mt * 16 + g + 8 * (e >> 1), col = c * 32 + nt * 8 + 2 * t4 + (e & 1);
+                        const int r = m0 + mt * 16 + g + 8 * (e >> 1), col = n0 + nt * 8 + 2 * t4 + (e & 1);
                         const float z = acc[mt][nt][e] + ldp(a.params, P_B1 + col);
-                        if (z > 0.0f) mask1[c] |= 1u << (mt * 16 + nt * 4 + e);
+                        if (z > 0.0f) mask1 |= 1u << (mt * 16 + nt * 4 + e);
                         const __nv_bfloat16 hb = __float2bfloat16_rn(fmaxf(z, 0.0f));
                         sB1[r * LD128 + col] = hb;
                         sH1T[col * LD128 + r] = hb;
                     }
         }
         __syncthreads();
-        // ---- layer 2, pass A: y and dy per row (replicated over the quad)
-        float yp[2][2] = {{0.0f, 0.0f}, {0.0f, 0.0f}};
-        for (int c = 0; c < 4; c++) {
-            float acc[2][4][4];
-            warp_gemm32<MLP_H, LD128, LD128>(sB1, sW2, m0, c * 32, acc);
+        // ---- layer 2, pass A: Z2 of the warp's block stays in registers for
+        // pass B; its 32 hidden units' share of y per row goes to shared memory
+        float acc2[2][4][4];
+        warp_gemm32<MLP_H, LD128, LD128>(sB1, sW2, m0, n0, acc2);
+        {
+            float yp[2][2] = {{0.0f, 0.0f}, {0.0f, 0.0f}};
 #pragma unroll
             for (int mt = 0; mt < 2; mt++)
 #pragma unroll
                 for (int nt = 0; nt < 4; nt++)
 #pragma unroll
                     for (int e = 0; e < 4; e++) {
-                        const int col = c * 32 + nt * 8 + 2 * t4 + (e & 1);
-                        yp[mt][e >> 1] += fmaxf(acc[mt][nt][e] + ldp(a.params, P_B2 + col), 0.0f) *
+                        const int col = n0 + nt * 8 + 2 * t4 + (e & 1);
+                        yp[mt][e >> 1] += fmaxf(acc2[mt][nt][e] + ldp(a.params, P_B2 + col), 0.0f) *
                                           ldp(a.params, P_W3 + col);
                     }
+#pragma unroll
+            for (int mt = 0; mt < 2; mt++)
+#pragma unroll
+                for (int hh = 0; hh < 2; hh++) {
+                    float v = yp[mt][hh];
+                    v += __shfl_xor_sync(0xffffffffu, v, 1);
+                    v += __shfl_xor_sync(0xffffffffu, v, 2);
+                    if (t4 == 0) sy[cb * 128 + m0 + mt * 16 + g + 8 * hh] = v;
+                }
         }
+        __syncthreads();
+        // y per row from the four column blocks' shares, in a fixed order;
+        // dy = dL/dy of the weighted squared error (replicated over the quad)
         float dyv[2][2];
 #pragma unroll
         for (int mt = 0; mt < 2; mt++)
 #pragma unroll
             for (int hh = 0; hh < 2; hh++) {
-                float v = yp[mt][hh];
-                v += __shfl_xor_sync(0xffffffffu, v, 1);
-                v += __shfl_xor_sync(0xffffffffu, v, 2);
-                const float yv = v + ldp(a.params, P_B3);
-                const int orow = tile * 128 + m0 + mt * 16 + g + 8 * hh;
+                const int rl = m0 + mt * 16 + g + 8 * hh;
+                const float yv = ((sy[rl] + sy[128 + rl]) + sy[256 + rl]) + sy[384 + rl] + ldp(a.params, P_B3);
+                const int orow = tile * 128 + rl;
                 float d = 0.0f;
                 if (orow < B) {
                     const float tv = a.t[a.idx ? a.idx[orow] : orow];
@@ -694,100 +724,112 @@ __global__ void __launch_bounds__(128) mlp_train_kernel(MlpArgs a) {
                     const float wgt = 1.0f / (den * den);
                     const float r = yv - tv;
                     d = 2.0f * wgt * r * invB;
-                    if (t4 == 0) {
+                    if (cb == 0 && t4 == 0) {  // once per row
                         atomicAdd(&red[385], wgt * r * r);
                         atomicAdd(&red[384], d);
                     }
                 }
                 dyv[mt][hh] = d;
             }
-        // ---- layer 2, pass B: dH2 = dy w3 (Z2 > 0) -> dH2T; dw3, db2
-        for (int c = 0; c < 4; c++) {
-            float acc[2][4][4];
-            warp_gemm32<MLP_H, LD128, LD128>(sB1, sW2, m0, c * 32, acc);
+        // ---- layer 2, pass B: dH2 = dy w3 (Z2 > 0) as rows (over H1, which
+        // pass A has finished reading) and transposed; dw3, db2
 #pragma unroll
-            for (int nt = 0; nt < 4; nt++)
+        for (int nt = 0; nt < 4; nt++)
 #pragma unroll
-                for (int q = 0; q < 2; q++) {
-                    const int col = c * 32 + nt * 8 + 2 * t4 + q;
-                    const float b2v = ldp(a.params, P_B2 + col), w3v = ldp(a.params, P_W3 + col);
-                    float sdw3 = 0.0f, sdb2 = 0.0f;
+            for (int q = 0; q < 2; q++) {
+                const int col = n0 + nt * 8 + 2 * t4 + q;
+                const float b2v = ldp(a.params, P_B2 + col), w3v = ldp(a.params, P_W3 + col);
+                float sdw3 = 0.0f, sdb2 = 0.0f;
 #pragma unroll
-                    for (int mt = 0; mt < 2; mt++)
+                for (int mt = 0; mt < 2; mt++)
 #pragma unroll
-                        for (int hh = 0; hh < 2; hh++) {
-                            const float z = acc[mt][nt][2 * hh + q] + b2v;
-                            const float dh = z > 0.0f ? dyv[mt][hh] * w3v : 0.0f;
-                            sdw3 += dyv[mt][hh] * fmaxf(z, 0.0f);
-                            sdb2 += dh;
-                            const int r = m0 + mt * 16 + g + 8 * hh;
-                            sdH2T[col * LD128 + r] = __float2bfloat16_rn(dh);
-                        }
+                    for (int hh = 0; hh < 2; hh++) {
+                        const float z = acc2[mt][nt][2 * hh + q] + b2v;
+                        const float dh = z > 0.0f ? dyv[mt][hh] * w3v : 0.0f;
+                        sdw3 += dyv[mt][hh] * fmaxf(z, 0.0f);
+                        sdb2 += dh;
+                        const int r = m0 + mt * 16 + g + 8 * hh;
+                        const __nv_bfloat16 hb = __float2bfloat16_rn(dh);
+                        sB1[r * LD128 + col] = hb;
+                        sdH2T[col * LD128 + r] = hb;
+                    }
+#pragma unroll
+                for (int o = 4; o < 32; o <<= 1) {  // over the 8 row groups of the warp
+                    sdw3 += __shfl_xor_sync(0xffffffffu, sdw3, o);
+                    sdb2 += __shfl_xor_sync(0xffffffffu, sdb2, o);
+                }
+                if (g == 0) {
                     atomicAdd(&red[col], sdw3);
                     atomicAdd(&red[256 + col], sdb2);
                 }
-        }
+            }
         __syncthreads();
-        // dH2 rows (transpose of dH2T) over B1 (H1 is no longer needed)
-        for (int j = 0; j < MLP_H; j++) sB1[tid * LD128 + j] = sdH2T[j * LD128 + tid];
-        __syncthreads();
-        // ---- dH1 = (dH2 W2) (Z1 > 0) -> dH1T over W2; db1
-        for (int c = 0; c < 4; c++) {
+        // ---- dH1 = (dH2 W2) (Z1 > 0), transposed over W2; db1
+        {
             float acc[2][4][4];
-            warp_gemm32<MLP_H, LD128, LD128>(sB1, sW2T, m0, c * 32, acc);
+            warp_gemm32<MLP_H, LD128, LD128>(sB1, sW2T, m0, n0, acc);
 #pragma unroll
             for (int nt = 0; nt < 4; nt++)
 #pragma unroll
                 for (int q = 0; q < 2; q++) {
-                    const int col = c * 32 + nt * 8 + 2 * t4 + q;
+                    const int col = n0 + nt * 8 + 2 * t4 + q;
                     float sdb1 = 0.0f;
 #pragma unroll
                     for (int mt = 0; mt < 2; mt++)
 #pragma unroll
                         for (int hh = 0; hh < 2; hh++) {
                             const int e = 2 * hh + q;
-                            const bool on = (mask1[c] >> (mt * 16 + nt * 4 + e)) & 1;
+                            const bool on = (mask1 >> (mt * 16 + nt * 4 + e)) & 1;
                             const float d1 = on ? acc[mt][nt][e] : 0.0f;
                             sdb1 += d1;
                             const int r = m0 + mt * 16 + g + 8 * hh;
                             sW2[col * LD128 + r] = __float2bfloat16_rn(d1);
                         }
-                    atomicAdd(&red[128 + col], sdb1);
+#pragma unroll
+                    for (int o = 4; o < 32; o <<= 1) sdb1 += __shfl_xor_sync(0xffffffffu, sdb1, o);
+                    if (g == 0) atomicAdd(&red[128 + col], sdb1);
                 }
         }
         __syncthreads();
-        // ---- dW2 = dH2^T H1 (A = dH2T, B = H1T) and dW1 = dH1^T X (A = dH1T, B = XT)
-        for (int c = 0; c < 4; c++) {
+        // ---- dW2 = dH2^T H1 (A = dH2T, B = H1T): the warp's 32 x 32 block
+        {
             float acc[2][4][4];
-            warp_gemm32<128, LD128, LD128>(sdH2T, sH1T, m0, c * 32, acc);
+            warp_gemm32<128, LD128, LD128>(sdH2T, sH1T, m0, n0, acc);
 #pragma unroll
             for (int mt = 0; mt < 2; mt++)
 #pragma unroll
                 for (int nt = 0; nt < 4; nt++)
 #pragma unroll
-                    for (int e = 0; e < 4; e++) {
-                        const int r = m0 + mt * 16 + g + 8 * (e >> 1), col = c * 32 + nt * 8 + 2 * t4 + (e & 1);
-                        atomicAdd(a.grad + P_W2 + r * MLP_H + col, acc[mt][nt][e]);
+                    for (int hh = 0; hh < 2; hh++) {
+                        const int r = m0 + mt * 16 + g + 8 * hh, col = n0 + nt * 8 + 2 * t4;
+                        atomicAdd(reinterpret_cast<float2 *>(a.grad + P_W2 + r * MLP_H + col),
+                                  make_float2(acc[mt][nt][2 * hh], acc[mt][nt][2 * hh + 1]));
                     }
         }
-        for (int c = 0; c < 2; c++) {
+        // ---- dW1 = dH1^T X (A = dH1T, B = XT): 8 blocks of 32 x 32, each
+        // split over the tile's two halves of 64 rows
+        {
+            const int n1 = ((warp >> 2) & 1) * 32, k1 = (warp >> 3) * 64;
             float acc[2][4][4];
-            warp_gemm32<128, LD128, LD128>(sW2, sXT, m0, c * 32, acc);
+            warp_gemm32<64, LD128, LD128>(sW2 + k1, sXT + k1, m0, n1, acc);
 #pragma unroll
             for (int mt = 0; mt < 2; mt++)
 #pragma unroll
                 for (int nt = 0; nt < 4; nt++)
 #pragma unroll
-                    for (int e = 0; e < 4; e++) {
-                        const int r = m0 + mt * 16 + g + 8 * (e >> 1), col = c * 32 + nt * 8 + 2 * t4 + (e & 1);
-                        atomicAdd(a.grad + P_W1 + r * MLP_IN + col, acc[mt][nt][e]);
+                    for (int hh = 0; hh < 2; hh++) {
+                        const int r = m0 + mt * 16 + g + 8 * hh, col = n1 + nt * 8 + 2 * t4;
+                        atomicAdd(reinterpret_cast<float2 *>(a.grad + P_W1 + r * MLP_IN + col),
+                                  make_float2(acc[mt][nt][2 * hh], acc[mt][nt][2 * hh + 1]));
                     }
         }
         __syncthreads();
     }
-    atomicAdd(a.grad + P_W3 + tid, red[tid]);
-    atomicAdd(a.grad + P_B1 + tid, red[128 + tid]);
-    atomicAdd(a.grad + P_B2 + tid, red[256 + tid]);
+    if (tid < 128) {
+        atomicAdd(a.grad + P_W3 + tid, red[tid]);
+        atomicAdd(a.grad + P_B1 + tid, red[128 + tid]);
+        atomicAdd(a.grad + P_B2 + tid, red[256 + tid]);
+    }
     if (tid == 0) {
         atomicAdd(a.grad + P_B3, red[384]);
         if (a.loss) atomicAdd(a.loss, red[385]);
