@@ -109,6 +109,31 @@ typedef struct {
     int64_t nonfinite;    /* markers whose displacement was NaN or infinite (error) */
 } ebit_counters_t;
 
+/* Device memory.  Every device allocation of the library (the state and
+ * tables of a context, a network's parameters, a batch's arrays, and the
+ * scratch that ebit_get_state and ebit_batch_autotune take) goes through
+ * cudaMalloc / cudaFree, or through the caller's pair installed here: a memory
+ * pool, a framework's caching allocator, or a test that refuses the k-th
+ * allocation.  This is host-side resource management; no passage of the
+ * paper defines it.
+ *   alloc(bytes, user)  returns a device pointer on the current device,
+ *                       aligned to 256 bytes, or NULL when it cannot allocate.
+ *   free_fn(ptr, user)  releases a pointer that alloc returned.
+ *   Both NULL restore cudaMalloc / cudaFree.
+ * A context, network or batch takes a copy of the pair in force when it is
+ * created (ebit_create, ebit_create_view, ebit_mlp_create, ebit_batch_create)
+ * and allocates and frees through that copy for its whole life, so a later
+ * call changes only objects created after it.  When an allocation fails, the
+ * creating call frees what it had allocated through free_fn and returns
+ * EBIT_ENOMEM; a later call that needs scratch returns EBIT_ENOMEM and
+ * leaves the object usable.  The pair is process-wide: do not call this
+ * concurrently with a creating call.
+ * Errors: EBIT_EINVAL when exactly one of alloc and free_fn is NULL (the
+ * previous pair stays in force). */
+typedef void *(*ebit_alloc_fn)(size_t bytes, void *user);
+typedef void (*ebit_free_fn)(void *ptr, void *user);
+int ebit_set_allocator(ebit_alloc_fn alloc, ebit_free_fn free_fn, void *user);
+
 /* Create a context for one grid: allocates the double-buffered state and the
  * tile tables on the current CUDA device.  *out receives the handle.
  * Errors: EBIT_EINVAL (null, sizes < 8, h <= 0), EBIT_ENOMEM, EBIT_ECUDA. */

@@ -8,6 +8,7 @@
 
 #include "../../include/ebit.h"
 #include "common.cuh"
+#include "devmem.h"
 
 using ebit::Grid;
 
@@ -16,6 +17,7 @@ using ebit::Grid;
 constexpr int NLISTS = 6;
 
 struct ebit_mlp {
+    ebit::DevMem mem;  // the allocator the network was created with
     cudaStream_t stream;
     int sms;
     float *p, *g, *m, *v;      // FP32 parameters, gradient, Adam moments
@@ -30,6 +32,7 @@ struct ebit_mlp {
 };
 
 struct ebit_ctx {
+    ebit::DevMem mem;  // the allocator the context was created with
     Grid g;
     int owns_state;           // 0: cb, s, scratch arrays, tile flags and counters belong to a batch
     long long N;

@@ -200,6 +200,18 @@ int sweep_launch(ebit_ctx *ctx, const SweepArgs &args, const MarkerLists *ml) {
 }  // namespace
 
 
+static DevMem g_devmem;  // the allocator new objects take (default: cudaMalloc / cudaFree)
+
+DevMem ebit::current_devmem() { return g_devmem; }
+
+int ebit_set_allocator(ebit_alloc_fn alloc, ebit_free_fn free_fn, void *user) {
+    if (!alloc != !free_fn) return EBIT_EINVAL;
+    g_devmem.alloc = alloc;
+    g_devmem.free = free_fn;
+    g_devmem.user = alloc ? user : nullptr;
+    return EBIT_OK;
+}
+
 static int create_ctx(const ebit_desc *desc, const ebit_state_arrays *st, ebit_ctx **out) {
     ebit_ctx *ctx = nullptr;
     if (!desc || !out) return EBIT_EINVAL;
@@ -260,7 +272,8 @@ static int create_ctx(const ebit_desc *desc, const ebit_state_arrays *st, ebit_c
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&ctx->sms, cudaDevAttrMultiProcessorCount, dev);
     if (ctx->sms <= 0) ctx->sms = 1;
-    auto alloc = [&](void **p, size_t bytes) -> bool { return cudaMalloc(p, bytes) == cudaSuccess; };
+    ctx->mem = current_devmem();
+    auto alloc = [&](void **p, size_t bytes) -> bool { return dev_alloc(ctx->mem, p, bytes); };
     bool ok = true;
     int nt = ctx->g.ntiles;
     if (st) {
@@ -377,48 +390,48 @@ void ebit_destroy(ebit_ctx *ctx) {
     if (ctx->own_mlp) ebit_mlp_destroy(ctx->own_mlp);
     if (ctx->owns_state) {
         for (int b = 0; b < 2; b++) {
-            cudaFree(ctx->cb[b]);
-            for (int a = 0; a < 3; a++) cudaFree(ctx->s[b][a]);
+            dev_free(ctx->mem, ctx->cb[b]);
+            for (int a = 0; a < 3; a++) dev_free(ctx->mem, ctx->s[b][a]);
         }
-        cudaFree(ctx->tile_marker);
-        cudaFree(ctx->tile_dirty);
-        cudaFree(ctx->ctr);
+        dev_free(ctx->mem, ctx->tile_marker);
+        dev_free(ctx->mem, ctx->tile_dirty);
+        dev_free(ctx->mem, ctx->ctr);
         for (int a = 0; a < 3; a++) {
-            cudaFree(ctx->adv[a]);
-            cudaFree(ctx->bin[a]);
+            dev_free(ctx->mem, ctx->adv[a]);
+            dev_free(ctx->mem, ctx->bin[a]);
         }
         for (int k = 0; k < NLISTS; k++) {
-            cudaFree(ctx->work[k]);
-            cudaFree(ctx->work2[k]);
+            dev_free(ctx->mem, ctx->work[k]);
+            dev_free(ctx->mem, ctx->work2[k]);
         }
-        cudaFree(ctx->wcount);
-        cudaFree(ctx->wcount2);
-        cudaFree(ctx->mk_al[0]);
-        cudaFree(ctx->mk_al[1]);
-        cudaFree(ctx->mk_count);
-        cudaFree(ctx->mtiles[0]);
-        cudaFree(ctx->mtiles[1]);
-        cudaFree(ctx->mt_count);
-        cudaFree(ctx->band_flag);
-        cudaFree(ctx->tile_dirty2);
-        cudaFree(ctx->band_list2);
+        dev_free(ctx->mem, ctx->wcount);
+        dev_free(ctx->mem, ctx->wcount2);
+        dev_free(ctx->mem, ctx->mk_al[0]);
+        dev_free(ctx->mem, ctx->mk_al[1]);
+        dev_free(ctx->mem, ctx->mk_count);
+        dev_free(ctx->mem, ctx->mtiles[0]);
+        dev_free(ctx->mem, ctx->mtiles[1]);
+        dev_free(ctx->mem, ctx->mt_count);
+        dev_free(ctx->mem, ctx->band_flag);
+        dev_free(ctx->mem, ctx->tile_dirty2);
+        dev_free(ctx->mem, ctx->band_list2);
     }
-    cudaFree(ctx->tile_cchg);
-    cudaFree(ctx->band_list);
-    cudaFree(ctx->band_count);
-    cudaFree(ctx->work_list);
-    cudaFree(ctx->work_count);
-    cudaFree(ctx->all_list);
-    cudaFree(ctx->all_count);
-    cudaFree(ctx->scratch);
-    cudaFree(ctx->cut);
-    cudaFree(ctx->scan);
-    cudaFree(ctx->iface[0]);
-    cudaFree(ctx->iface[1]);
-    cudaFree(ctx->ncut);
-    cudaFree(ctx->niface);
-    cudaFree(ctx->nscan);
-    cudaFree(ctx->zero);
+    dev_free(ctx->mem, ctx->tile_cchg);
+    dev_free(ctx->mem, ctx->band_list);
+    dev_free(ctx->mem, ctx->band_count);
+    dev_free(ctx->mem, ctx->work_list);
+    dev_free(ctx->mem, ctx->work_count);
+    dev_free(ctx->mem, ctx->all_list);
+    dev_free(ctx->mem, ctx->all_count);
+    dev_free(ctx->mem, ctx->scratch);
+    dev_free(ctx->mem, ctx->cut);
+    dev_free(ctx->mem, ctx->scan);
+    dev_free(ctx->mem, ctx->iface[0]);
+    dev_free(ctx->mem, ctx->iface[1]);
+    dev_free(ctx->mem, ctx->ncut);
+    dev_free(ctx->mem, ctx->niface);
+    dev_free(ctx->mem, ctx->nscan);
+    dev_free(ctx->mem, ctx->zero);
     for (cudaEvent_t e : ctx->ev) cudaEventDestroy(e);
     delete ctx;
 }
@@ -450,7 +463,10 @@ int ebit_set_state(ebit_ctx *ctx, const uint8_t *cb, const double *s) {
 int ebit_get_state(ebit_ctx *ctx, uint8_t *cb, double *s) {
     if (!ctx || !cb || !s) return fail(ctx, EBIT_EINVAL, "ebit_get_state: null argument");
     if (int r = join_side(ctx)) return r;
-    if (!ctx->scratch) CU(cudaMalloc((void **)&ctx->scratch, 3 * ctx->N * sizeof(double)));
+    if (!ctx->scratch && !dev_alloc(ctx->mem, (void **)&ctx->scratch, 3 * ctx->N * sizeof(double))) {
+        cudaGetLastError();
+        return fail(ctx, EBIT_ENOMEM, "ebit_get_state: no room for the scratch copy");
+    }
     int c = ctx->cur;
     canonical_s_kernel<<<blocks_for(ctx->N, 256, ctx->sms), 256, 0, ctx->stream>>>(
         ctx->g, ctx->cb[c], ctx->s[c][0], ctx->s[c][1], ctx->s[c][2], ctx->scratch);
@@ -856,13 +872,13 @@ int ebit_mlp_create(void *cuda_stream, ebit_mlp **out) {
     int dev = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&mlp->sms, cudaDevAttrMultiProcessorCount, dev);
-    bool ok = cudaMalloc((void **)&mlp->p, MLP_NP * 4) == cudaSuccess &&
-              cudaMalloc((void **)&mlp->g, MLP_NP * 4) == cudaSuccess &&
-              cudaMalloc((void **)&mlp->m, MLP_NP * 4) == cudaSuccess &&
-              cudaMalloc((void **)&mlp->v, MLP_NP * 4) == cudaSuccess &&
-              cudaMalloc((void **)&mlp->w1b, MLP_H * MLP_IN * 2) == cudaSuccess &&
-              cudaMalloc((void **)&mlp->w2b, MLP_H * MLP_H * 2) == cudaSuccess &&
-              cudaMalloc((void **)&mlp->loss, 4) == cudaSuccess && cudaMalloc((void **)&mlp->err, 4) == cudaSuccess;
+    mlp->mem = current_devmem();
+    const DevMem &mm = mlp->mem;
+    bool ok = dev_alloc(mm, (void **)&mlp->p, MLP_NP * 4) && dev_alloc(mm, (void **)&mlp->g, MLP_NP * 4) &&
+              dev_alloc(mm, (void **)&mlp->m, MLP_NP * 4) && dev_alloc(mm, (void **)&mlp->v, MLP_NP * 4) &&
+              dev_alloc(mm, (void **)&mlp->w1b, MLP_H * MLP_IN * 2) &&
+              dev_alloc(mm, (void **)&mlp->w2b, MLP_H * MLP_H * 2) && dev_alloc(mm, (void **)&mlp->loss, 4) &&
+              dev_alloc(mm, (void **)&mlp->err, 4);
     if (!ok) {
         cudaGetLastError();
         ebit_mlp_destroy(mlp);
@@ -907,14 +923,14 @@ int ebit_mlp_create(void *cuda_stream, ebit_mlp **out) {
 void ebit_mlp_destroy(ebit_mlp *mlp) {
     if (!mlp) return;
     cudaStreamSynchronize(mlp->stream);
-    cudaFree(mlp->p);
-    cudaFree(mlp->g);
-    cudaFree(mlp->m);
-    cudaFree(mlp->v);
-    cudaFree(mlp->w1b);
-    cudaFree(mlp->w2b);
-    cudaFree(mlp->loss);
-    cudaFree(mlp->err);
+    dev_free(mlp->mem, mlp->p);
+    dev_free(mlp->mem, mlp->g);
+    dev_free(mlp->mem, mlp->m);
+    dev_free(mlp->mem, mlp->v);
+    dev_free(mlp->mem, mlp->w1b);
+    dev_free(mlp->mem, mlp->w2b);
+    dev_free(mlp->mem, mlp->loss);
+    dev_free(mlp->mem, mlp->err);
     delete mlp;
 }
 

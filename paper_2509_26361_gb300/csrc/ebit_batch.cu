@@ -242,6 +242,7 @@ __global__ void selftest_mbarrier_kernel(int arrive, long long polls, int *ok_ou
 using namespace ebit;
 
 struct ebit_batch {
+    DevMem mem;  // the allocator the batch was created with
     int n = 0;
     cudaStream_t stream = nullptr;
     int sms = 1;
@@ -455,7 +456,8 @@ int ebit_batch_create(int n, const ebit_desc *descs, ebit_batch **out) {
     b->toff[n] = (int)tiles;
     b->cells = cells;
     b->tiles = (int)tiles;
-    auto alloc = [](void **p, size_t bytes) { return cudaMalloc(p, bytes) == cudaSuccess; };
+    b->mem = current_devmem();
+    auto alloc = [&](void **p, size_t bytes) { return dev_alloc(b->mem, p, bytes); };
     bool ok = true;
     for (int q = 0; q < 2 && ok; q++) {
         ok = ok && alloc((void **)&b->cb[q], cells);
@@ -553,27 +555,27 @@ void ebit_batch_destroy(ebit_batch *b) {
     drop_graph(b);
     for (ebit_ctx *c : b->inst) ebit_destroy(c);
     for (int q = 0; q < 2; q++) {
-        cudaFree(b->cb[q]);
-        for (int a = 0; a < 3; a++) cudaFree(b->s[q][a]);
+        dev_free(b->mem, b->cb[q]);
+        for (int a = 0; a < 3; a++) dev_free(b->mem, b->s[q][a]);
     }
     for (int a = 0; a < 3; a++) {
-        cudaFree(b->adv[a]);
-        cudaFree(b->bin[a]);
-        cudaFree(b->u[a]);
+        dev_free(b->mem, b->adv[a]);
+        dev_free(b->mem, b->bin[a]);
+        dev_free(b->mem, b->u[a]);
     }
-    for (int k = 0; k < 4; k++) cudaFree(b->work[k]);
-    cudaFree(b->wcount);
-    cudaFree(b->tile_marker);
-    cudaFree(b->tile_dirty);
-    cudaFree(b->ctr);
-    cudaFree(b->table[0]);
-    cudaFree(b->table[1]);
-    cudaFree(b->d_toff);
-    cudaFree(b->lam);
-    cudaFree(b->band);
-    cudaFree(b->nband);
-    cudaFree(b->bar);
-    cudaFree(b->err);
+    for (int k = 0; k < 4; k++) dev_free(b->mem, b->work[k]);
+    dev_free(b->mem, b->wcount);
+    dev_free(b->mem, b->tile_marker);
+    dev_free(b->mem, b->tile_dirty);
+    dev_free(b->mem, b->ctr);
+    dev_free(b->mem, b->table[0]);
+    dev_free(b->mem, b->table[1]);
+    dev_free(b->mem, b->d_toff);
+    dev_free(b->mem, b->lam);
+    dev_free(b->mem, b->band);
+    dev_free(b->mem, b->nband);
+    dev_free(b->mem, b->bar);
+    dev_free(b->mem, b->err);
     delete b;
 }
 
@@ -762,17 +764,17 @@ int ebit_batch_autotune(ebit_batch *b, int sweeps, double *ms_out) {
     uint32_t *tm_save = nullptr;
     double *s_save = nullptr;
     unsigned long long *ctr_save = nullptr;
-    bool ok = cudaMalloc((void **)&cb_save, cells) == cudaSuccess &&
-              cudaMalloc((void **)&s_save, 3 * cells * sizeof(double)) == cudaSuccess &&
-              cudaMalloc((void **)&tm_save, b->tiles * sizeof(uint32_t)) == cudaSuccess &&
-              cudaMalloc((void **)&td_save, b->tiles) == cudaSuccess &&
-              cudaMalloc((void **)&ctr_save, (size_t)b->n * C_TOTAL * 8) == cudaSuccess;
+    bool ok = dev_alloc(b->mem, (void **)&cb_save, cells) &&
+              dev_alloc(b->mem, (void **)&s_save, 3 * cells * sizeof(double)) &&
+              dev_alloc(b->mem, (void **)&tm_save, b->tiles * sizeof(uint32_t)) &&
+              dev_alloc(b->mem, (void **)&td_save, b->tiles) &&
+              dev_alloc(b->mem, (void **)&ctr_save, (size_t)b->n * C_TOTAL * 8);
     auto release = [&]() {
-        cudaFree(cb_save);
-        cudaFree(s_save);
-        cudaFree(tm_save);
-        cudaFree(td_save);
-        cudaFree(ctr_save);
+        dev_free(b->mem, cb_save);
+        dev_free(b->mem, s_save);
+        dev_free(b->mem, tm_save);
+        dev_free(b->mem, td_save);
+        dev_free(b->mem, ctr_save);
     };
     if (!ok) {
         cudaGetLastError();
@@ -855,7 +857,8 @@ const char *ebit_batch_last_error(const ebit_batch *b) { return b ? b->errmsg.c_
 int ebit_selftest_bounded_waits(void *cuda_stream, int *report) {
     cudaStream_t st = (cudaStream_t)cuda_stream;
     int *d = nullptr;
-    if (cudaMalloc((void **)&d, 16 * sizeof(int)) != cudaSuccess) {
+    const DevMem mm = current_devmem();
+    if (!dev_alloc(mm, (void **)&d, 16 * sizeof(int))) {
         cudaGetLastError();
         return EBIT_ENOMEM;
     }
@@ -881,7 +884,7 @@ int ebit_selftest_bounded_waits(void *cuda_stream, int *report) {
     }
     // the device still takes work after the waits gave up
     ok = ok && cudaMemsetAsync(d, 0, 16 * sizeof(int), st) == cudaSuccess && cudaStreamSynchronize(st) == cudaSuccess;
-    cudaFree(d);
+    dev_free(mm, d);
     if (!ok) {
         cudaGetLastError();
         return EBIT_ECUDA;

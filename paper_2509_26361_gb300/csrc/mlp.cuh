@@ -196,6 +196,22 @@ __device__ __forceinline__ uint32_t ld32s(const __nv_bfloat16 *p) {
     return *reinterpret_cast<const uint32_t *>(p);
 }
 
+// Four 8x8 bf16 matrices from shared memory (ldmatrix.x4): lanes 8i .. 8i+7
+// give the 16-byte rows of matrix i, and register i of lane l receives
+// row l / 4, columns 2 (l % 4) and 2 (l % 4) + 1 of matrix i -- the fragment
+// layout of the mma.m16n8k16 operands.  p must be 16-byte aligned.
+__device__ __forceinline__ void ldsm4(const __nv_bfloat16 *p, uint32_t r[4]) {
+#ifdef EBIT_MLP_CHECK
+    if (!__all_sync(0xffffffffu, MLP_S(p, 16, 1))) {
+        r[0] = r[1] = r[2] = r[3] = 0u;
+        return;
+    }
+#endif
+    asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+                 : "r"((uint32_t)__cvta_generic_to_shared(p)));
+}
+
 __device__ __forceinline__ void mma16816(float c[4], const uint32_t a[4], uint32_t b0, uint32_t b1) {
     asm volatile(
         "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
@@ -207,35 +223,36 @@ __device__ __forceinline__ void mma16816(float c[4], const uint32_t a[4], uint32
 // acc = A[m0 .. m0+31][0..K) * B[n0 .. n0+31][0..K)^T for the calling warp:
 // A rows are the M index, B rows the N index, both K contiguous.  Element
 // acc[mt][nt][e] is row m0 + 16 mt + g + 8 (e >> 1), column n0 + 8 nt + 2 t + (e & 1)
-// with g = lane / 4, t = lane % 4.
+// with g = lane / 4, t = lane % 4.  A and B are 16-byte aligned shared
+// memory and LDA, LDB multiples of 8 elements (ldmatrix rows).
 template <int K, int LDA, int LDB>
 __device__ __forceinline__ void warp_gemm32(const __nv_bfloat16 *A, const __nv_bfloat16 *B, int m0, int n0,
                                             float acc[2][4][4]) {
-    const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
+    const int lane = threadIdx.x & 31;
 #pragma unroll
     for (int i = 0; i < 2; i++)
 #pragma unroll
         for (int j = 0; j < 4; j++)
 #pragma unroll
             for (int e = 0; e < 4; e++) acc[i][j][e] = 0.0f;
+    // lane l addresses row l % 8 of matrix l / 8: for A the matrices are
+    // (rows +0, k +0), (rows +8, k +0), (rows +0, k +8), (rows +8, k +8); for B
+    // (n +0, k +0), (n +0, k +8), (n +8, k +0), (n +8, k +8), two n-tiles at once
+    const int li = lane & 7, lm = lane >> 3;
+    const __nv_bfloat16 *pa = A + (m0 + li + 8 * (lm & 1)) * LDA + 8 * (lm >> 1);
+    const __nv_bfloat16 *pb = B + (n0 + li + 8 * (lm >> 1)) * LDB + 8 * (lm & 1);
 #pragma unroll
     for (int k0 = 0; k0 < K; k0 += 16) {
-        uint32_t a[2][4];
+        uint32_t a[2][4], b[2][4];
 #pragma unroll
-        for (int mt = 0; mt < 2; mt++) {
-            const __nv_bfloat16 *r0 = A + (m0 + mt * 16 + g) * LDA + k0 + 2 * t;
-            a[mt][0] = ld32s(r0);
-            a[mt][1] = ld32s(r0 + 8 * LDA);
-            a[mt][2] = ld32s(r0 + 8);
-            a[mt][3] = ld32s(r0 + 8 * LDA + 8);
-        }
+        for (int mt = 0; mt < 2; mt++) ldsm4(pa + mt * 16 * LDA + k0, a[mt]);
 #pragma unroll
-        for (int nt = 0; nt < 4; nt++) {
-            const __nv_bfloat16 *rb = B + (n0 + nt * 8 + g) * LDB + k0 + 2 * t;
-            const uint32_t b0 = ld32s(rb), b1 = ld32s(rb + 8);
+        for (int np = 0; np < 2; np++) ldsm4(pb + np * 16 * LDB + k0, b[np]);
 #pragma unroll
-            for (int mt = 0; mt < 2; mt++) mma16816(acc[mt][nt], a[mt], b0, b1);
-        }
+        for (int nt = 0; nt < 4; nt++)
+#pragma unroll
+            for (int mt = 0; mt < 2; mt++)
+                mma16816(acc[mt][nt], a[mt], b[nt >> 1][2 * (nt & 1)], b[nt >> 1][2 * (nt & 1) + 1]);
     }
 }
 
@@ -360,15 +377,18 @@ __global__ void __launch_bounds__(128) mlp_fwd_kernel(MlpArgs a) {
                 for (int j = 0; j < 4; j++)
 #pragma unroll
                     for (int e = 0; e < 4; e++) acc[i][j][e] = 0.0f;
+            // B fragments of two n-tiles per ldmatrix.x4 (the layout of warp_gemm32)
+            const __nv_bfloat16 *pb = sW2 + (c * 32 + (lane & 7) + 8 * (lane >> 4)) * LD128 + 8 * ((lane >> 3) & 1);
 #pragma unroll
             for (int kk = 0; kk < 8; kk++) {
+                uint32_t b[2][4];
 #pragma unroll
-                for (int nt = 0; nt < 4; nt++) {
-                    const __nv_bfloat16 *rb = sW2 + (c * 32 + nt * 8 + g) * LD128 + kk * 16 + 2 * t4;
-                    const uint32_t b0 = ld32s(rb), b1 = ld32s(rb + 8);
+                for (int np = 0; np < 2; np++) ldsm4(pb + np * 16 * LD128 + kk * 16, b[np]);
 #pragma unroll
-                    for (int mt = 0; mt < 2; mt++) mma16816(acc[mt][nt], h1[mt][kk], b0, b1);
-                }
+                for (int nt = 0; nt < 4; nt++)
+#pragma unroll
+                    for (int mt = 0; mt < 2; mt++)
+                        mma16816(acc[mt][nt], h1[mt][kk], b[nt >> 1][2 * (nt & 1)], b[nt >> 1][2 * (nt & 1) + 1]);
             }
 #pragma unroll
             for (int mt = 0; mt < 2; mt++)
@@ -591,6 +611,27 @@ __global__ void __launch_bounds__(TC_THREADS) mlp_fwd_tc_kernel(MlpArgs a) {
     if (tid < 32 && tm_ok) tc::tmem_dealloc(tm0, 512);
 }
 
+// Adds a warp's 32 x 32 accumulator block (warp_gemm32 layout) to the FP32
+// matrix G (row stride ld floats) with one 16-byte atomic per row and four
+// columns: lanes 2q and 2q + 1 swap halves so that the even lane holds row g,
+// columns 4q .. 4q + 3 of each 8-column group and the odd lane row g + 8.
+// G + ld * row + col must be 16-byte aligned for col a multiple of 4.
+__device__ __forceinline__ void add_block4(float *G, int ld, int m0, int n0, const float acc[2][4][4]) {
+    const int lane = threadIdx.x & 31, g = lane >> 2, t4 = lane & 3;
+    const bool odd = t4 & 1;
+#pragma unroll
+    for (int mt = 0; mt < 2; mt++)
+#pragma unroll
+        for (int nt = 0; nt < 4; nt++) {
+            const float *c = acc[mt][nt];
+            const float r0 = __shfl_xor_sync(0xffffffffu, odd ? c[0] : c[2], 1);
+            const float r1 = __shfl_xor_sync(0xffffffffu, odd ? c[1] : c[3], 1);
+            const float4 v = odd ? make_float4(r0, r1, c[2], c[3]) : make_float4(c[0], c[1], r0, r1);
+            const int row = m0 + mt * 16 + g + (odd ? 8 : 0), col = n0 + nt * 8 + 2 * (t4 & 2);
+            atomicAdd(reinterpret_cast<float4 *>(G + (long long)row * ld + col), v);
+        }
+}
+
 // ------------------------------------------------------------ training
 // smem (bf16 tiles, row-major, padded):
 //   W1 [128][72] | W2 [128][136] (dH1^T after the dH1 product) | W2T [128][136] |
@@ -605,7 +646,8 @@ constexpr int TR_B1 = TR_XT + 64 * LD128 * 2;
 constexpr int TR_H1T = TR_B1 + 128 * LD128 * 2;
 constexpr int TR_DH2T = TR_H1T + 128 * LD128 * 2;
 constexpr int TR_RED = TR_DH2T + 128 * LD128 * 2;
-constexpr int TRAIN_SMEM = TR_RED + 900 * 4;  // reductions 388 floats, partial row sums of y 4 x 128
+// after the bf16 tiles: reductions (388 floats), b1 | b2 | w3 (384), the tile's targets (128)
+constexpr int TRAIN_SMEM = TR_RED + 900 * 4;
 constexpr int TRAIN_THREADS = 512;            // 16 warps: 4 row blocks x 4 column blocks of 32
 static_assert(MLP_IN == 64 && MLP_H == 128, "the training kernel's warp split assumes 64 inputs, 128 hidden units");
 static_assert(TRAIN_SMEM <= 227 * 1024, "training tile exceeds the shared memory of one block");
@@ -621,24 +663,39 @@ __global__ void __launch_bounds__(TRAIN_THREADS) mlp_train_kernel(MlpArgs a) {
     __nv_bfloat16 *sH1T = reinterpret_cast<__nv_bfloat16 *>(smem_raw + TR_H1T);
     __nv_bfloat16 *sdH2T = reinterpret_cast<__nv_bfloat16 *>(smem_raw + TR_DH2T);
     float *red = reinterpret_cast<float *>(smem_raw + TR_RED);  // dw3 | db1 | db2 | db3, loss
-    float *sy = red + 388;  // [column block][row]: partial sums of y over 32 hidden units of layer 2
+    float *prm = red + 388;  // b1 | b2 | w3, staged once
+    float *st = red + 772;   // targets of the tile's rows
+    // [column block][row]: partial sums of y over 32 hidden units of layer 2,
+    // over the X tile, which layer 1 has finished reading
+    float *sy = reinterpret_cast<float *>(sX);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31, g = lane >> 2, t4 = lane & 3;
     // warp (row block, column block) of every 128 x 128 product
     const int m0 = (warp & 3) * 32, cb = warp >> 2, n0 = cb * 32;
     const int row_t = tid & 127, part = tid >> 7;  // the tile row and quarter a thread stages
     if (tid < 128) load_row(sW1, LD64, tid, a.w1b, tid, MLP_IN, MLP_H);
-    for (int j = part * 32; j < part * 32 + 32; j++) sW2T[j * LD128 + row_t] = a.w2b[row_t * MLP_H + j];
+    {
+        // W2^T: a quarter of row row_t by 16-byte loads, written down column row_t
+        __align__(16) __nv_bfloat16 wv[32];
+        const uint4 *s4 = reinterpret_cast<const uint4 *>(a.w2b + row_t * MLP_H) + 4 * part;
+#pragma unroll
+        for (int q = 0; q < 4; q++) reinterpret_cast<uint4 *>(wv)[q] = s4[q];
+#pragma unroll
+        for (int j = 0; j < 32; j++) sW2T[(part * 32 + j) * LD128 + row_t] = wv[j];
+    }
     for (int k = tid; k < 388; k += TRAIN_THREADS) red[k] = 0.0f;
+    if (tid < 384) prm[tid] = ldp(a.params, tid < 256 ? (tid < 128 ? P_B1 + tid : P_B2 + tid - 128) : P_W3 + tid - 256);
+    const float b3 = ldp(a.params, P_B3);
     const int B = a.batch;
     const int ntile = (B + 127) / 128;
     const float invB = 1.0f / (float)B;
     for (int tile = blockIdx.x; tile < ntile; tile += gridDim.x) {
         // W2 (its buffer holds dH1^T by the end of a tile), this tile's rows
         // of X and their transpose; each thread stages a quarter of one row
-        {
-            const uint4 *s4 = reinterpret_cast<const uint4 *>(a.w2b + row_t * MLP_H) + 4 * part;
-            uint4 *d4 = reinterpret_cast<uint4 *>(sW2 + row_t * LD128) + 4 * part;
-            for (int q = 0; q < 4; q++) d4[q] = s4[q];
+#pragma unroll
+        for (int q = 0; q < 4; q++) {  // 16 threads per row of W2, 16 bytes each
+            const int c = q * TRAIN_THREADS + tid, r = c >> 4;
+            reinterpret_cast<uint4 *>(sW2 + r * LD128)[c & 15] =
+                reinterpret_cast<const uint4 *>(a.w2b + r * MLP_H)[c & 15];
         }
         {
             const int row = tile * 128 + row_t;
@@ -649,6 +706,7 @@ __global__ void __launch_bounds__(TRAIN_THREADS) mlp_train_kernel(MlpArgs a) {
                 const uint4 *s4 = reinterpret_cast<const uint4 *>(a.X + src * MLP_IN) + 2 * part;
                 x4[0] = s4[0];
                 x4[1] = s4[1];
+                if (part == 0) st[row_t] = a.t[src];
             } else {
                 x4[0] = make_uint4(0u, 0u, 0u, 0u);
                 x4[1] = x4[0];
@@ -672,7 +730,7 @@ __global__ void __launch_bounds__(TRAIN_THREADS) mlp_train_kernel(MlpArgs a) {
 #pragma unroll
                     for (int e = 0; e < 4; e++) {
                         const int r = m0 + mt * 16 + g + 8 * (e >> 1), col = n0 + nt * 8 + 2 * t4 + (e & 1);
-                        const float z = acc[mt][nt][e] + ldp(a.params, P_B1 + col);
+                        const float z = acc[mt][nt][e] + prm[col];
                         if (z > 0.0f) mask1 |= 1u << (mt * 16 + nt * 4 + e);
                         const __nv_bfloat16 hb = __float2bfloat16_rn(fmaxf(z, 0.0f));
                         sB1[r * LD128 + col] = hb;
@@ -693,8 +751,7 @@ __global__ void __launch_bounds__(TRAIN_THREADS) mlp_train_kernel(MlpArgs a) {
 #pragma unroll
                     for (int e = 0; e < 4; e++) {
                         const int col = n0 + nt * 8 + 2 * t4 + (e & 1);
-                        yp[mt][e >> 1] += fmaxf(acc2[mt][nt][e] + ldp(a.params, P_B2 + col), 0.0f) *
-                                          ldp(a.params, P_W3 + col);
+                        yp[mt][e >> 1] += fmaxf(acc2[mt][nt][e] + prm[128 + col], 0.0f) * prm[256 + col];
                     }
 #pragma unroll
             for (int mt = 0; mt < 2; mt++)
@@ -715,11 +772,11 @@ __global__ void __launch_bounds__(TRAIN_THREADS) mlp_train_kernel(MlpArgs a) {
 #pragma unroll
             for (int hh = 0; hh < 2; hh++) {
                 const int rl = m0 + mt * 16 + g + 8 * hh;
-                const float yv = ((sy[rl] + sy[128 + rl]) + sy[256 + rl]) + sy[384 + rl] + ldp(a.params, P_B3);
+                const float yv = ((sy[rl] + sy[128 + rl]) + sy[256 + rl]) + sy[384 + rl] + b3;
                 const int orow = tile * 128 + rl;
                 float d = 0.0f;
                 if (orow < B) {
-                    const float tv = a.t[a.idx ? a.idx[orow] : orow];
+                    const float tv = st[rl];
                     const float den = fmaxf(fabsf(tv), 0.05f);
                     const float wgt = 1.0f / (den * den);
                     const float r = yv - tv;
@@ -738,7 +795,7 @@ __global__ void __launch_bounds__(TRAIN_THREADS) mlp_train_kernel(MlpArgs a) {
 #pragma unroll
             for (int q = 0; q < 2; q++) {
                 const int col = n0 + nt * 8 + 2 * t4 + q;
-                const float b2v = ldp(a.params, P_B2 + col), w3v = ldp(a.params, P_W3 + col);
+                const float b2v = prm[128 + col], w3v = prm[256 + col];
                 float sdw3 = 0.0f, sdb2 = 0.0f;
 #pragma unroll
                 for (int mt = 0; mt < 2; mt++)
@@ -795,16 +852,7 @@ __global__ void __launch_bounds__(TRAIN_THREADS) mlp_train_kernel(MlpArgs a) {
         {
             float acc[2][4][4];
             warp_gemm32<128, LD128, LD128>(sdH2T, sH1T, m0, n0, acc);
-#pragma unroll
-            for (int mt = 0; mt < 2; mt++)
-#pragma unroll
-                for (int nt = 0; nt < 4; nt++)
-#pragma unroll
-                    for (int hh = 0; hh < 2; hh++) {
-                        const int r = m0 + mt * 16 + g + 8 * hh, col = n0 + nt * 8 + 2 * t4;
-                        atomicAdd(reinterpret_cast<float2 *>(a.grad + P_W2 + r * MLP_H + col),
-                                  make_float2(acc[mt][nt][2 * hh], acc[mt][nt][2 * hh + 1]));
-                    }
+            add_block4(a.grad + P_W2, MLP_H, m0, n0, acc);
         }
         // ---- dW1 = dH1^T X (A = dH1T, B = XT): 8 blocks of 32 x 32, each
         // split over the tile's two halves of 64 rows
@@ -812,16 +860,7 @@ __global__ void __launch_bounds__(TRAIN_THREADS) mlp_train_kernel(MlpArgs a) {
             const int n1 = ((warp >> 2) & 1) * 32, k1 = (warp >> 3) * 64;
             float acc[2][4][4];
             warp_gemm32<64, LD128, LD128>(sW2 + k1, sXT + k1, m0, n1, acc);
-#pragma unroll
-            for (int mt = 0; mt < 2; mt++)
-#pragma unroll
-                for (int nt = 0; nt < 4; nt++)
-#pragma unroll
-                    for (int hh = 0; hh < 2; hh++) {
-                        const int r = m0 + mt * 16 + g + 8 * hh, col = n1 + nt * 8 + 2 * t4;
-                        atomicAdd(reinterpret_cast<float2 *>(a.grad + P_W1 + r * MLP_IN + col),
-                                  make_float2(acc[mt][nt][2 * hh], acc[mt][nt][2 * hh + 1]));
-                    }
+            add_block4(a.grad + P_W1, MLP_IN, m0, n1, acc);
         }
         __syncthreads();
     }

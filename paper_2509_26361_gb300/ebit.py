@@ -54,6 +54,11 @@ class _Counters(ctypes.Structure):
 
 
 _lib = None
+_ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p)
+_FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_void_p)
+# every callback pair ever installed: an object keeps the pair it was created
+# with until it is destroyed, so none may be collected
+_allocators = []
 
 
 def library_path() -> str:
@@ -126,6 +131,7 @@ def load(build_if_missing: bool = True):
     lib.ebit_batch_autotune.argtypes = [P, I, ctypes.POINTER(ctypes.c_double)]
     lib.ebit_batch_last_error.argtypes = [P]
     lib.ebit_batch_last_error.restype = ctypes.c_char_p
+    lib.ebit_set_allocator.argtypes = [_ALLOC_FN, _FREE_FN, P]
     _lib = lib
     return lib
 
@@ -158,6 +164,24 @@ def _any(t: torch.Tensor, dtype, numel, name):
 
 
 # ----------------------------------------------------------------- C names
+def ebit_set_allocator(alloc=None, free=None):
+    """Route the library's device allocations through ``alloc(nbytes) -> int``
+    (a device pointer aligned to 256 bytes, or 0 when it cannot allocate) and
+    ``free(ptr)``; both None restores cudaMalloc / cudaFree.  Objects created
+    afterwards keep this pair for their whole life."""
+    lib = load()
+    if alloc is None and free is None:
+        return _check(None, lib.ebit_set_allocator(_ALLOC_FN(), _FREE_FN(), None))
+    if alloc is None or free is None:
+        fa = _ALLOC_FN(lambda n, u: alloc(n) or None) if alloc is not None else _ALLOC_FN()
+        ff = _FREE_FN(lambda ptr, u: free(ptr)) if free is not None else _FREE_FN()
+        return _check(None, lib.ebit_set_allocator(fa, ff, None))
+    fa = _ALLOC_FN(lambda n, u: alloc(n) or None)
+    ff = _FREE_FN(lambda ptr, u: free(ptr))
+    _allocators.append((fa, ff))
+    return _check(None, lib.ebit_set_allocator(fa, ff, None))
+
+
 def ebit_create(nx, ny, nz, h, stream=None, flags=0):
     lib = load()
     if stream is None:
