@@ -669,7 +669,8 @@ def batched_block(device, rank=0, world=1, steps=256, warmup=4):
     """The batched workload: 64 independent instances (seeded sizes from
     {32, 48, 64, 96, 128}^3, each with its own 12-mode Fourier field and 1-4
     spheres, dt = 0.5 h), 3 split sweeps per step, one cooperative launch per
-    sweep, pairs of steps replayed from a CUDA graph, launch shape autotuned.
+    sweep, pairs of steps replayed from a CUDA graph, tile shape and launch
+    shape autotuned.
     On N ranks every rank runs its own shard of the instances (balanced by
     cells, no communication on the data path); the job takes the slowest
     rank's time and counts every rank's cells.  Value: cell-steps/s over all
@@ -694,6 +695,7 @@ def batched_block(device, rank=0, world=1, steps=256, warmup=4):
     b.set_velocity(uf, [dt for *_, dt in insts])
     tune_ms = b.autotune(sweeps=6)
     shape, max_shape = b.launch_shape()
+    _, tile_dims = b.tile_shape()
     b.run(0, warmup, graph=True)
     b.sync()
     for i in range(len(insts)):
@@ -726,7 +728,8 @@ def batched_block(device, rank=0, world=1, steps=256, warmup=4):
            "sharding": "instances split over the ranks by cell count, no data-path collective",
            "value": cells * steps / (ms * 1e-3), "unit": "cell-steps/s", "ms_per_step": ms / steps,
            "launches_per_sweep": 1, "graph": b.graph_active(), "graph_note": b.graph_note(),
-           "launch_shape_ctas_per_sm": shape, "autotune_ms_per_6_sweeps": tune_ms,
+           "launch_shape_ctas_per_sm": shape, "tile_shape": "x".join(str(v) for v in tile_dims),
+           "autotune_ms_per_6_sweeps": {"x".join(str(v) for v in k): v for k, v in tune_ms.items()},
            "roofline": {"bound": "hbm", "achieved": alg / per_sweep_s / 1e9, "peak": hbm, "unit": "GB/s",
                         "frac": alg / per_sweep_s / 1e9 / hbm, "peak_source": src,
                         "alg_bytes_per_sweep": alg, "alg_bytes_rule": "62.75 B per band cell per sweep",

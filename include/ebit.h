@@ -105,7 +105,7 @@ typedef struct {
     int64_t multi;        /* edges where three markers met; the median was kept */
     int64_t inconsistent; /* colour/crossing parity disagreements (never expected) */
     int64_t cfl;          /* marker displacements of a full cell or more (error) */
-    int64_t tiles;        /* 8x8x8 tiles processed by the sweeps (band size, summed) */
+    int64_t tiles;        /* 512-cell tiles processed by the sweeps (band size, summed) */
     int64_t nonfinite;    /* markers whose displacement was NaN or infinite (error) */
 } ebit_counters_t;
 
@@ -375,12 +375,40 @@ int ebit_batch_graph_active(const ebit_batch *b);
 const char *ebit_batch_graph_note(const ebit_batch *b);
 /* Wait for the batch's stream; EBIT_ETIMEOUT if a grid barrier gave up. */
 int ebit_batch_sync(ebit_batch *b);
-/* Launch shape: blocks of 256 threads per SM (1 .. max co-resident). */
+/* Launch shape: blocks of 256 threads per SM (1 .. max co-resident for the
+ * current tile shape). */
 int ebit_batch_launch_shape(const ebit_batch *b, int *ctas_per_sm, int *max_ctas_per_sm);
 int ebit_batch_set_launch_shape(ebit_batch *b, int ctas_per_sm);
-/* Times `sweeps` sweeps at every launch shape on a copy of the current state
- * (put back afterwards), keeps the fastest; ms_out (host, may be NULL) gets
- * the time of each shape, index ctas_per_sm - 1.  Allocates a state copy. */
+/* Tile shape: the cells per tile edge along x, y, z of the band tiles that the
+ * batched sweep works on (512 cells each; every edge at least 4 cells, so the
+ * tile proximity rule of the band still reaches only adjacent tiles).  The
+ * shape changes how the work is cut and staged, never the result: tiles
+ * outside the band are unchanged by a sweep whatever their shape.
+ *   EBIT_TILE_8x8x8 (0, the initial shape and that of single contexts),
+ *   EBIT_TILE_16x8x4 (1), EBIT_TILE_32x4x4 (2: x-lines).
+ * ebit_batch_tile_shape returns the current shape and writes its edges to
+ * dims[3] (host, may be NULL).  ebit_batch_set_tile_shape re-tiles every
+ * instance (synchronises the stream; every tile is processed by the next
+ * sweep and recomputed by the next Front2VOF); EBIT_EINVAL for an unknown
+ * shape or one that does not fit an instance.  A shape fits when, along
+ * every axis with tile edge T and n cells, T floor((n - 1) / T) + T + 2 <= 2 n
+ * (a tile's staged region, which reaches T + 1 nodes past its origin, wraps
+ * at most once): edges of 4 and 8 fit every instance, 16 needs n >= 9 and
+ * 32 needs n >= 17 along that axis.  The "tiles" counter counts tiles of the
+ * shape in use. */
+enum { EBIT_TILE_8x8x8 = 0, EBIT_TILE_16x8x4 = 1, EBIT_TILE_32x4x4 = 2, EBIT_TILE_SHAPES = 3 };
+enum { EBIT_BATCH_MAX_CTAS = 8 };
+int ebit_batch_tile_shape(const ebit_batch *b, int *dims);
+int ebit_batch_set_tile_shape(ebit_batch *b, int shape);
+/* Autotuner: for every tile shape and every launch shape, starting from a
+ * copy of the current state with every tile marked, one untimed sweep forms
+ * the band, then `sweeps` sweeps are timed with CUDA events (the second of
+ * two passes; the first warms up); shapes that do not fit an instance are
+ * skipped.  Keeps the fastest pair and puts the state
+ * back (the tile tables too when the shape is unchanged).  ms_out (host, may
+ * be NULL) receives EBIT_TILE_SHAPES x EBIT_BATCH_MAX_CTAS doubles, index
+ * shape * EBIT_BATCH_MAX_CTAS + ctas_per_sm - 1, 0 where the pair was not
+ * run.  Allocates a state copy. */
 int ebit_batch_autotune(ebit_batch *b, int sweeps, double *ms_out);
 const char *ebit_batch_last_error(const ebit_batch *b);
 /* Self-test of the bounded device waits (the grid barrier of the batched

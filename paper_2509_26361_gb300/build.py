@@ -1,7 +1,8 @@
 """Build libebit.so in-tree with nvcc for sm_103a (GB300).
 
 The library is built from three CUDA translation units (the context-based ABI,
-the allocation-free sweep and the batched persistent sweep), compiled with --fmad=false so that every
+the allocation-free sweep and the batched persistent sweep), compiled in
+parallel with --fmad=false so that every
 floating-point operation of the EBIT kernels rounds separately in the written
 order.  Output: ``paper_2509_26361_gb300/_build/libebit.so``.
 """
@@ -43,23 +44,44 @@ def up_to_date() -> bool:
     return all(os.path.getmtime(s) <= t for s in sources())
 
 
+UNITS = ("ebit_abi.cu", "ebit_noalloc.cu", "ebit_batch.cu")
+
+
 def build(force: bool = False, verbose: bool = False) -> str:
+    """Compile the translation units in parallel (one nvcc each), then link."""
     if not force and up_to_date():
         return LIB
     os.makedirs(OUT_DIR, exist_ok=True)
-    tmp = LIB + f".tmp{os.getpid()}"
-    cmd = [_nvcc(), "-O3", "-std=c++17", *ARCH, "-lineinfo", "--fmad=false", "-Xcompiler", "-fPIC",
-           "-shared", "-o", tmp, os.path.join(CSRC, "ebit_abi.cu"), os.path.join(CSRC, "ebit_noalloc.cu"),
-           os.path.join(CSRC, "ebit_batch.cu"),
-           "-I", os.path.join(ROOT, "include")]
+    tag = f".tmp{os.getpid()}"
+    flags = ["-O3", "-std=c++17", *ARCH, "-lineinfo", "--fmad=false", "-Xcompiler", "-fPIC",
+             "-I", os.path.join(ROOT, "include")]
     if verbose:
-        cmd.insert(1, "-Xptxas=-v")
-    r = subprocess.run(cmd, capture_output=True, text=True)
-    if r.returncode != 0:
-        sys.stderr.write(r.stdout + r.stderr)
+        flags.insert(0, "-Xptxas=-v")
+    objs, procs = [], []
+    for u in UNITS:
+        obj = os.path.join(OUT_DIR, u.replace(".cu", tag + ".o"))
+        objs.append(obj)
+        procs.append(subprocess.Popen([_nvcc(), *flags, "-c", "-o", obj, os.path.join(CSRC, u)],
+                                      stdout=subprocess.PIPE, stderr=subprocess.PIPE, text=True))
+    failed = False
+    for pr in procs:
+        out, err = pr.communicate()
+        if pr.returncode != 0:
+            failed = True
+            sys.stderr.write(out + err)
+        elif verbose:
+            sys.stderr.write(err)
+    tmp = LIB + tag
+    if not failed:
+        r = subprocess.run([_nvcc(), *ARCH, "-shared", "-o", tmp, *objs], capture_output=True, text=True)
+        if r.returncode != 0:
+            failed = True
+            sys.stderr.write(r.stdout + r.stderr)
+    for obj in objs:
+        if os.path.exists(obj):
+            os.remove(obj)
+    if failed:
         raise RuntimeError("nvcc failed building libebit.so")
-    if verbose:
-        sys.stderr.write(r.stderr)
     os.replace(tmp, LIB)
     return LIB
 

@@ -36,8 +36,31 @@ __device__ __forceinline__ int list_item(int it) {
 }
 
 constexpr double ONE_MINUS = 0.99999999999999988898;  // 1 - 2^-53, largest offset below 1
-constexpr int TILE = 8;                               // tile edge (cells)
-constexpr int TILE_CELLS = TILE * TILE * TILE;
+constexpr int TILE = 8;                               // tile edge of a single grid (cells)
+constexpr int TILE_CELLS = TILE * TILE * TILE;          // cells of every tile shape
+
+// Tile shapes (cells per tile edge along x, y, z; 512 cells each).  A single
+// grid uses shape 0; a batch may use any (chosen by its autotuner).  Every
+// edge is at least 4 cells, more than the NEAR = 3 layers of the proximity
+// mask, so a marker can only touch its own tile and the 26 adjacent ones.
+constexpr int N_TILE_SHAPES = 3;
+__host__ __device__ constexpr int tile_log2(int sh, int a) {
+    return sh == 0 ? 3 : (sh == 1 ? (a == 0 ? 4 : (a == 1 ? 3 : 2)) : (a == 0 ? 5 : 2));
+}
+template <int SH>
+struct TileShape {
+    static constexpr int LX = tile_log2(SH, 0), LY = tile_log2(SH, 1), LZ = tile_log2(SH, 2);
+    static constexpr int TX = 1 << LX, TY = 1 << LY, TZ = 1 << LZ;
+    static_assert(TX * TY * TZ == TILE_CELLS, "512 cells per tile");
+    static_assert(TX >= 4 && TY >= 4 && TZ >= 4, "tile edges of at least 4 cells");
+    static constexpr int t(int a) { return a == 0 ? TX : (a == 1 ? TY : TZ); }
+    // cell c of a tile -> its local coordinates (x fastest)
+    __device__ static void cell(int c, int l[3]) {
+        l[0] = c & (TX - 1);
+        l[1] = (c >> LX) & (TY - 1);
+        l[2] = c >> (LX + LY);
+    }
+};
 
 // Tile proximity mask: bit near_bit(dx, dy, dz) is set when a marker owned by a
 // node of the tile lies within NEAR cells of the neighbour tile in direction
@@ -50,14 +73,15 @@ constexpr int TILE_CELLS = TILE * TILE * TILE;
 // neighbour owns a marker within three cells of it.
 constexpr int NEAR = 3;
 __host__ __device__ inline int near_bit(int dx, int dy, int dz) { return 9 * (dz + 1) + 3 * (dy + 1) + (dx + 1); }
-__host__ __device__ inline unsigned near_bits(int lx, int ly, int lz) {
+// (lx, ly, lz: the node's place in a tile of tx x ty x tz cells)
+__host__ __device__ inline unsigned near_bits(int lx, int ly, int lz, int tx = TILE, int ty = TILE, int tz = TILE) {
     unsigned m = 0;
     for (int dz = -1; dz <= 1; dz++) {
-        if ((dz < 0 && lz >= NEAR) || (dz > 0 && lz < TILE - NEAR)) continue;
+        if ((dz < 0 && lz >= NEAR) || (dz > 0 && lz < tz - NEAR)) continue;
         for (int dy = -1; dy <= 1; dy++) {
-            if ((dy < 0 && ly >= NEAR) || (dy > 0 && ly < TILE - NEAR)) continue;
+            if ((dy < 0 && ly >= NEAR) || (dy > 0 && ly < ty - NEAR)) continue;
             for (int dx = -1; dx <= 1; dx++) {
-                if ((dx < 0 && lx >= NEAR) || (dx > 0 && lx < TILE - NEAR)) continue;
+                if ((dx < 0 && lx >= NEAR) || (dx > 0 && lx < tx - NEAR)) continue;
                 m |= 1u << near_bit(dx, dy, dz);
             }
         }
@@ -74,7 +98,18 @@ struct Grid {
     int n[3];        // cells per axis
     int td[3];       // tiles per axis
     int ntiles;
+    int tl[3];       // log2 of the tile edge per axis (3, 3, 3 for 8^3 tiles)
 };
+
+// tiles per axis and in total for tile shape sh
+__host__ __device__ inline void grid_tiles(Grid &g, int sh) {
+    g.ntiles = 1;
+    for (int a = 0; a < 3; a++) {
+        g.tl[a] = tile_log2(sh, a);
+        g.td[a] = (g.n[a] + (1 << g.tl[a]) - 1) >> g.tl[a];
+        g.ntiles *= g.td[a];
+    }
+}
 
 __host__ __device__ inline int wrapc(int v, int n) {
     // v is within a few cells of [0, n)
@@ -93,9 +128,16 @@ __device__ __forceinline__ void tile_origin(const Grid &g, int t, int o[3]) {
     int r = t / g.td[0];
     int ty = r % g.td[1];
     int tz = r / g.td[1];
-    o[0] = tx * TILE;
-    o[1] = ty * TILE;
-    o[2] = tz * TILE;
+    o[0] = tx << g.tl[0];
+    o[1] = ty << g.tl[1];
+    o[2] = tz << g.tl[2];
+}
+
+// cell c (0 .. 511) of a tile of g's shape -> its local coordinates
+__device__ __forceinline__ void tile_cell(const Grid &g, int c, int l[3]) {
+    l[0] = c & ((1 << g.tl[0]) - 1);
+    l[1] = (c >> g.tl[0]) & ((1 << g.tl[1]) - 1);
+    l[2] = c >> (g.tl[0] + g.tl[1]);
 }
 
 // one atomicAdd per warp for a per-thread counter increment

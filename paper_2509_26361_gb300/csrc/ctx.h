@@ -34,6 +34,7 @@ struct ebit_mlp {
 struct ebit_ctx {
     ebit::DevMem mem;  // the allocator the context was created with
     Grid g;
+    int nt_cap;        // tiles the per-tile arrays hold (a batch instance: any tile shape)
     int owns_state;           // 0: cb, s, scratch arrays, tile flags and counters belong to a batch
     long long N;
     double h;
@@ -124,3 +125,9 @@ struct ebit_state_arrays {
 
 // A context over batch-owned state arrays (see ebit_create for the rest).
 int ebit_create_view(const ebit_desc *desc, const ebit_state_arrays *st, ebit_ctx **out);
+
+// Re-tile a batch instance with tile shape sh (its batch passes the slices of
+// its tile tables for that shape): the tile counts, the list of all tiles,
+// and every tile marked for the next sweep and Front2VOF.  EBIT_EINVAL if the
+// shape needs more tiles than the context's arrays hold.
+int ctx_retile(ebit_ctx *ctx, int sh, uint32_t *tile_marker, uint8_t *tile_dirty);

@@ -260,8 +260,7 @@ static int create_ctx(const ebit_desc *desc, const ebit_state_arrays *st, ebit_c
     ctx->g.n[0] = desc->nx;
     ctx->g.n[1] = desc->ny;
     ctx->g.n[2] = desc->nz;
-    for (int a = 0; a < 3; a++) ctx->g.td[a] = (ctx->g.n[a] + TILE - 1) / TILE;
-    ctx->g.ntiles = ctx->g.td[0] * ctx->g.td[1] * ctx->g.td[2];
+    grid_tiles(ctx->g, 0);
     ctx->N = (long long)desc->nx * desc->ny * desc->nz;
     ctx->h = desc->h;
     ctx->stream = (cudaStream_t)desc->cuda_stream;
@@ -276,6 +275,15 @@ static int create_ctx(const ebit_desc *desc, const ebit_state_arrays *st, ebit_c
     auto alloc = [&](void **p, size_t bytes) -> bool { return dev_alloc(ctx->mem, p, bytes); };
     bool ok = true;
     int nt = ctx->g.ntiles;
+    // a batch instance may be re-tiled with any tile shape (its batch's
+    // autotuner): its per-tile arrays hold the largest tile count of them
+    ctx->nt_cap = nt;
+    for (int sh = 1; st && sh < N_TILE_SHAPES; sh++) {
+        Grid t = ctx->g;
+        grid_tiles(t, sh);
+        ctx->nt_cap = std::max(ctx->nt_cap, t.ntiles);
+    }
+    const int ntc = ctx->nt_cap;
     if (st) {
         for (int b = 0; b < 2; b++) {
             ctx->cb[b] = st->cb[b];
@@ -313,9 +321,9 @@ static int create_ctx(const ebit_desc *desc, const ebit_state_arrays *st, ebit_c
          alloc((void **)&ctx->iface[1], ctx->N * sizeof(unsigned)) &&
          alloc((void **)&ctx->ncut, sizeof(int)) && alloc((void **)&ctx->niface, 3 * sizeof(int)) &&
          alloc((void **)&ctx->nscan, sizeof(int)) && alloc((void **)&ctx->zero, sizeof(int));
-    ok = ok && alloc((void **)&ctx->tile_cchg, nt) && alloc((void **)&ctx->band_list, nt * sizeof(int)) &&
-         alloc((void **)&ctx->band_count, 2 * sizeof(int)) && alloc((void **)&ctx->work_list, nt * sizeof(int)) &&
-         alloc((void **)&ctx->work_count, 2 * sizeof(int)) && alloc((void **)&ctx->all_list, nt * sizeof(int)) &&
+    ok = ok && alloc((void **)&ctx->tile_cchg, ntc) && alloc((void **)&ctx->band_list, ntc * sizeof(int)) &&
+         alloc((void **)&ctx->band_count, 2 * sizeof(int)) && alloc((void **)&ctx->work_list, ntc * sizeof(int)) &&
+         alloc((void **)&ctx->work_count, 2 * sizeof(int)) && alloc((void **)&ctx->all_list, ntc * sizeof(int)) &&
          alloc((void **)&ctx->all_count, sizeof(int));
     if (!ok) {
         cudaGetLastError();
@@ -332,11 +340,11 @@ static int create_ctx(const ebit_desc *desc, const ebit_state_arrays *st, ebit_c
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fp64_kernel<0, NLISTS>, 128, 0);
     ctx->grid_fp64 = ctx->sms * std::max(occ, 1);
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, f2v_band_kernel, 256, 0);
-    ctx->grid_f2v = std::max(1, std::min(nt, ctx->sms * std::max(occ, 1)));
+    ctx->grid_f2v = std::max(1, std::min(ntc, ctx->sms * std::max(occ, 1)));
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, f2v_list_kernel, 128, 0);
     ctx->grid_f2vl = ctx->sms * std::max(occ, 1);
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, hf_scan_kernel, 256, 0);
-    ctx->grid_hf = std::max(1, std::min(nt, ctx->sms * std::max(occ, 1)));
+    ctx->grid_hf = std::max(1, std::min(ntc, ctx->sms * std::max(occ, 1)));
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, hf_list_kernel<true>, 128, 0);
     ctx->grid_hfl = ctx->sms * std::max(occ, 1);
     cudaMemsetAsync(ctx->wcount, 0, (ctx->owns_state ? NLISTS + 1 : 4) * sizeof(int), ctx->stream);
@@ -366,6 +374,20 @@ static int create_ctx(const ebit_desc *desc, const ebit_state_arrays *st, ebit_c
     mark_all(ctx);
     *out = ctx;
     return EBIT_OK;
+}
+
+int ctx_retile(ebit_ctx *ctx, int sh, uint32_t *tile_marker, uint8_t *tile_dirty) {
+    if (!ctx || ctx->owns_state || sh < 0 || sh >= N_TILE_SHAPES || !tile_marker || !tile_dirty) return EBIT_EINVAL;
+    Grid g = ctx->g;
+    grid_tiles(g, sh);
+    if (g.ntiles > ctx->nt_cap) return fail(ctx, EBIT_EINVAL, "ctx_retile: more tiles than the context holds");
+    ctx->g = g;
+    ctx->tile_marker = tile_marker;
+    ctx->tile_dirty = tile_dirty;
+    ctx->band_last = -1;
+    iota_kernel<<<blocks_for(g.ntiles, 256, ctx->sms), 256, 0, ctx->stream>>>(ctx->all_list, g.ntiles, ctx->all_count);
+    if (int r = launch_check(ctx, "iota_kernel")) return r;
+    return mark_all(ctx);
 }
 
 int ebit_create_view(const ebit_desc *desc, const ebit_state_arrays *st, ebit_ctx **out) {

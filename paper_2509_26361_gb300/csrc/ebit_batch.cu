@@ -100,12 +100,12 @@ __device__ __forceinline__ int find_inst(const int *toff, int n, int gt) {
     return lo;
 }
 
-template <int D>
+template <int D, int SH>
 __global__ void __launch_bounds__(BATCH_THREADS, 4) batch_sweep_kernel(BatchParams p) {
     __shared__ uint16_t s_mk[3 * TILE_CELLS];
-    __shared__ uint8_t s_c[9 * 9 * 9];
-    __shared__ uint8_t s_b[RA * R1 * R2];
-    __shared__ int8_t s_bn[RA * R1 * R2];
+    __shared__ uint8_t s_c[adv_stage_max()];
+    __shared__ uint8_t s_b[stage_n(D, SH)];
+    __shared__ int8_t s_bn[stage_n(D, SH)];
     __shared__ int s_n, s_ok;
     __shared__ unsigned s_flag;
     __shared__ int s_pre[4 * BATCH_MAX + 1];
@@ -140,7 +140,7 @@ __global__ void __launch_bounds__(BATCH_THREADS, 4) batch_sweep_kernel(BatchPara
     for (int li = blockIdx.x; li < nb; li += gridDim.x) {
         const int e = __ldcg(p.band + li);
         const int i = e >> 20;
-        advect_tile<D>(p.inst[i].a, p.u[i], p.lam[i], e & 0xFFFFF, s_mk, s_c, &s_n);
+        advect_tile<D, SH>(p.inst[i].a, p.u[i], p.lam[i], e & 0xFFFFF, s_mk, s_c, &s_n);
     }
     if (!grid_barrier(p, &s_ok)) return;
 
@@ -149,7 +149,7 @@ __global__ void __launch_bounds__(BATCH_THREADS, 4) batch_sweep_kernel(BatchPara
         const int e = __ldcg(p.band + li);
         const int i = e >> 20;
         const SweepArgs &a = p.inst[i].a;
-        sweep_tile<D, true>(a, e & 0xFFFFF, s_b, s_bn, &s_flag);
+        sweep_tile<D, true, 4, SH>(a, e & 0xFFFFF, s_b, s_bn, &s_flag);
         if (threadIdx.x == 0) atomicAdd(a.ctr + C_TILES, 1ull);
     }
     if (!grid_barrier(p, &s_ok)) return;
@@ -248,7 +248,9 @@ struct ebit_batch {
     int sms = 1;
     std::vector<ebit_ctx *> inst;
     std::vector<long long> coff;   // first cell of each instance in the arena
-    std::vector<int> toff;         // first tile
+    std::vector<int> toff;         // first tile (current tile shape)
+    std::vector<int> dims;         // nx, ny, nz of each instance
+    std::vector<BatchInst> htab[2];  // host copy of the launch tables
     long long cells = 0;
     int tiles = 0;
     int parity = 0;                // buffer holding the current state
@@ -272,8 +274,10 @@ struct ebit_batch {
     int *err = nullptr;
     int have_u[3] = {0, 0, 0};
     int have_dt = 0;
-    int occ[3] = {1, 1, 1};        // co-resident blocks per SM of each direction's kernel
+    int occ[N_TILE_SHAPES][3] = {};  // co-resident blocks per SM of each shape's and direction's kernel
     int ctas_per_sm = 1;           // chosen launch shape (autotuned)
+    int shape = 0;                 // tile shape (autotuned)
+    int tiles_cap = 0;             // tiles the tile tables hold (the largest total over the shapes)
     // CUDA graph of two steps (even: x y z, odd: z y x)
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t gexec = nullptr;
@@ -296,11 +300,22 @@ int bfail(ebit_batch *b, int code, const std::string &m) {
         if (e_ != cudaSuccess) return bfail(b, EBIT_ECUDA, std::string(#call ": ") + cudaGetErrorString(e_)); \
     } while (0)
 
-const void *sweep_fn(int d) {
-    if (d == 0) return (const void *)batch_sweep_kernel<0>;
-    if (d == 1) return (const void *)batch_sweep_kernel<1>;
-    return (const void *)batch_sweep_kernel<2>;
+template <int SH>
+const void *sweep_fn_sh(int d) {
+    if (d == 0) return (const void *)batch_sweep_kernel<0, SH>;
+    if (d == 1) return (const void *)batch_sweep_kernel<1, SH>;
+    return (const void *)batch_sweep_kernel<2, SH>;
 }
+
+const void *sweep_fn(int d, int sh) {
+    static_assert(N_TILE_SHAPES == 3, "one instantiation per tile shape");
+    if (sh == 1) return sweep_fn_sh<1>(d);
+    if (sh == 2) return sweep_fn_sh<2>(d);
+    return sweep_fn_sh<0>(d);
+}
+
+// co-resident blocks per SM that every direction's kernel of shape sh allows
+int max_ctas(const ebit_batch *b, int sh) { return std::min({b->occ[sh][0], b->occ[sh][1], b->occ[sh][2]}); }
 
 BatchParams sweep_params(const ebit_batch *b, int d, int parity) {
     BatchParams p;
@@ -319,7 +334,7 @@ BatchParams sweep_params(const ebit_batch *b, int d, int parity) {
 }
 
 int sweep_grid(const ebit_batch *b, int d, int ctas_per_sm) {
-    return b->sms * std::max(1, std::min(ctas_per_sm, b->occ[d]));
+    return b->sms * std::max(1, std::min(ctas_per_sm, b->occ[b->shape][d]));
 }
 
 // cooperative launch (all blocks co-resident: the grid barrier needs it)
@@ -337,7 +352,7 @@ int launch_dir(ebit_batch *b, int d, int ctas_per_sm) {
     cfg.attrs = at;
     cfg.numAttrs = 1;
     void *args[] = {&p};
-    BCU(cudaLaunchKernelExC(&cfg, sweep_fn(d), args));
+    BCU(cudaLaunchKernelExC(&cfg, sweep_fn(d, b->shape), args));
     return EBIT_OK;
 }
 
@@ -365,7 +380,7 @@ cudaError_t build_graph(ebit_batch *b, cudaGraph_t *out) {
         BatchParams p = sweep_params(b, d, par);
         void *args[] = {&p};
         cudaKernelNodeParams kp = {};
-        kp.func = const_cast<void *>(sweep_fn(d));
+        kp.func = const_cast<void *>(sweep_fn(d, b->shape));
         kp.gridDim = dim3(sweep_grid(b, d, b->ctas_per_sm));
         kp.blockDim = dim3(BATCH_THREADS);
         kp.sharedMemBytes = 0;
@@ -406,6 +421,64 @@ void drop_graph(ebit_batch *b) {
     b->graph_ok = 0;
 }
 
+// tiles of instance i with tile shape sh
+long long inst_tiles(const ebit_batch *b, int i, int sh) {
+    long long nt = 1;
+    for (int a = 0; a < 3; a++) nt *= (b->dims[3 * i + a] + tile_edge(sh, a) - 1) / tile_edge(sh, a);
+    return nt;
+}
+
+// Does tile shape sh fit every instance?  A tile's staged region reaches from
+// one node behind its origin to T + 1 nodes past it along an axis with tile
+// edge T, and the grid wraps a coordinate by one period at most, so the last
+// tile's region must end within two periods: o_max + T + 2 <= 2 n, with
+// o_max the origin of the last tile.  (8^3 tiles fit every grid of >= 8 cells.)
+bool shape_fits(const ebit_batch *b, int sh) {
+    for (int i = 0; i < b->n; i++)
+        for (int a = 0; a < 3; a++) {
+            const int n = b->dims[3 * i + a], t = tile_edge(sh, a);
+            if (t * ((n - 1) / t) + t + 2 > 2 * n) return false;
+        }
+    return true;
+}
+
+// first tile of every instance (and the total, at index n) with tile shape sh
+void tile_offsets(const ebit_batch *b, int sh, std::vector<int> &toff) {
+    toff.assign(b->n + 1, 0);
+    for (int i = 0; i < b->n; i++) toff[i + 1] = toff[i] + (int)inst_tiles(b, i, sh);
+}
+
+// Switch the batch to tile shape sh: tile offsets, every instance context
+// re-tiled over its new slice of the tile tables (every tile marked for the
+// next sweep and Front2VOF), the launch tables rewritten, the graph dropped.
+int retile(ebit_batch *b, int sh) {
+    if (!shape_fits(b, sh)) return bfail(b, EBIT_EINVAL, "tile shape too large for an instance");
+    std::vector<int> toff;
+    tile_offsets(b, sh, toff);
+    if (toff[b->n] > b->tiles_cap) return bfail(b, EBIT_EINVAL, "retile: tile tables too small");
+    std::vector<BatchInst> *tab = b->htab;
+    for (int i = 0; i < b->n; i++) {
+        ebit_ctx *c = b->inst[i];
+        int r = ctx_retile(c, sh, b->tile_marker + toff[i], b->tile_dirty + toff[i]);
+        if (r) return bfail(b, r, "retile: " + c->err);
+        for (int q = 0; q < 2; q++) {
+            tab[q][i].a.g = c->g;
+            tab[q][i].a.tile_marker = c->tile_marker;
+            tab[q][i].a.tile_dirty = c->tile_dirty;
+        }
+    }
+    for (int q = 0; q < 2; q++)
+        BCU(cudaMemcpyAsync(b->table[q], tab[q].data(), b->n * sizeof(BatchInst), cudaMemcpyHostToDevice, b->stream));
+    BCU(cudaMemcpyAsync(b->d_toff, toff.data(), (b->n + 1) * sizeof(int), cudaMemcpyHostToDevice, b->stream));
+    BCU(cudaStreamSynchronize(b->stream));  // toff goes out of scope
+    b->toff = toff;
+    b->tiles = toff[b->n];
+    b->shape = sh;
+    b->ctas_per_sm = std::min(b->ctas_per_sm, max_ctas(b, sh));
+    drop_graph(b);
+    return EBIT_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -427,9 +500,9 @@ int ebit_batch_create(int n, const ebit_desc *descs, ebit_batch **out) {
         return EBIT_ECUDA;
     }
     b->coff.resize(n + 1);
-    b->toff.resize(n + 1);
+    b->dims.resize(3 * n);
     long long cells = 0;
-    long long tiles = 0;
+    long long tiles_cap = 0;
     for (int i = 0; i < n; i++) {
         const ebit_desc &d = descs[i];
         if (d.nx < 8 || d.ny < 8 || d.nz < 8 || !(d.h > 0.0) || d.cuda_stream != descs[0].cuda_stream ||
@@ -437,25 +510,35 @@ int ebit_batch_create(int n, const ebit_desc *descs, ebit_batch **out) {
             delete b;
             return EBIT_EINVAL;
         }
+        b->dims[3 * i] = d.nx;
+        b->dims[3 * i + 1] = d.ny;
+        b->dims[3 * i + 2] = d.nz;
         const long long nc = (long long)d.nx * d.ny * d.nz;
-        const long long nt = (long long)((d.nx + 7) / 8) * ((d.ny + 7) / 8) * ((d.nz + 7) / 8);
-        if (nt >= (1 << 20)) {
-            delete b;
-            return EBIT_EINVAL;
-        }
         b->coff[i] = cells;
-        b->toff[i] = (int)tiles;
         cells += (nc + 7) & ~7LL;  // each slice starts on a 32-bit word of the colour bytes
-        tiles += nt;
     }
-    if (cells >= (1LL << 31) || tiles >= (1LL << 31)) {
+    for (int sh = 0; sh < N_TILE_SHAPES; sh++) {
+        long long tiles = 0;
+        for (int i = 0; i < n; i++) {
+            const long long nt = inst_tiles(b, i, sh);
+            if (nt >= (1 << 20)) {  // tile ids keep 20 bits
+                delete b;
+                return EBIT_EINVAL;
+            }
+            tiles += nt;
+        }
+        tiles_cap = std::max(tiles_cap, tiles);
+    }
+    if (cells >= (1LL << 31) || tiles_cap >= (1LL << 31)) {
         delete b;
         return EBIT_EINVAL;
     }
     b->coff[n] = cells;
-    b->toff[n] = (int)tiles;
     b->cells = cells;
-    b->tiles = (int)tiles;
+    b->tiles_cap = (int)tiles_cap;
+    tile_offsets(b, 0, b->toff);
+    const long long tiles = tiles_cap;
+    b->tiles = b->toff[n];
     b->mem = current_devmem();
     auto alloc = [&](void **p, size_t bytes) { return dev_alloc(b->mem, p, bytes); };
     bool ok = true;
@@ -540,11 +623,15 @@ int ebit_batch_create(int n, const ebit_desc *descs, ebit_batch **out) {
         ebit_batch_destroy(b);
         return EBIT_ECUDA;
     }
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b->occ[0], batch_sweep_kernel<0>, BATCH_THREADS, 0);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b->occ[1], batch_sweep_kernel<1>, BATCH_THREADS, 0);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b->occ[2], batch_sweep_kernel<2>, BATCH_THREADS, 0);
-    for (int d = 0; d < 3; d++) b->occ[d] = std::max(1, b->occ[d]);
-    b->ctas_per_sm = std::min({b->occ[0], b->occ[1], b->occ[2]});
+    for (int sh = 0; sh < N_TILE_SHAPES; sh++)
+        for (int d = 0; d < 3; d++) {
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b->occ[sh][d], sweep_fn(d, sh), BATCH_THREADS, 0);
+            b->occ[sh][d] = std::max(1, b->occ[sh][d]);
+        }
+    b->htab[0] = tab[0];
+    b->htab[1] = tab[1];
+    b->shape = 0;
+    b->ctas_per_sm = max_ctas(b, 0);
     *out = b;
     return EBIT_OK;
 }
@@ -742,32 +829,50 @@ int ebit_batch_sync(ebit_batch *b) {
 int ebit_batch_launch_shape(const ebit_batch *b, int *ctas_per_sm, int *max_ctas_per_sm) {
     if (!b) return EBIT_EINVAL;
     if (ctas_per_sm) *ctas_per_sm = b->ctas_per_sm;
-    if (max_ctas_per_sm) *max_ctas_per_sm = std::min({b->occ[0], b->occ[1], b->occ[2]});
+    if (max_ctas_per_sm) *max_ctas_per_sm = max_ctas(b, b->shape);
     return EBIT_OK;
 }
 
 int ebit_batch_set_launch_shape(ebit_batch *b, int ctas_per_sm) {
-    if (!b || ctas_per_sm < 1 || ctas_per_sm > std::min({b->occ[0], b->occ[1], b->occ[2]})) return EBIT_EINVAL;
+    if (!b || ctas_per_sm < 1 || ctas_per_sm > max_ctas(b, b->shape)) return EBIT_EINVAL;
     if (ctas_per_sm != b->ctas_per_sm) drop_graph(b);
     b->ctas_per_sm = ctas_per_sm;
     return EBIT_OK;
+}
+
+int ebit_batch_tile_shape(const ebit_batch *b, int *dims) {
+    if (!b) return EBIT_EINVAL;
+    if (dims)
+        for (int a = 0; a < 3; a++) dims[a] = tile_edge(b->shape, a);
+    return b->shape;
+}
+
+int ebit_batch_set_tile_shape(ebit_batch *b, int shape) {
+    if (!b || shape < 0 || shape >= N_TILE_SHAPES) return EBIT_EINVAL;
+    if (shape == b->shape) return EBIT_OK;
+    BCU(cudaStreamSynchronize(b->stream));
+    return retile(b, shape);
 }
 
 int ebit_batch_autotune(ebit_batch *b, int sweeps, double *ms_out) {
     if (!b || sweeps < 1) return EBIT_EINVAL;
     if (!(b->have_u[0] && b->have_u[1] && b->have_u[2] && b->have_dt))
         return bfail(b, EBIT_EINVAL, "ebit_batch_autotune: no velocity set");
+    static_assert(EBIT_TILE_SHAPES == N_TILE_SHAPES, "tile shapes of the ABI");
+    if (ms_out)
+        for (int k = 0; k < EBIT_TILE_SHAPES * EBIT_BATCH_MAX_CTAS; k++) ms_out[k] = 0.0;
+    BCU(cudaStreamSynchronize(b->stream));
     // trial sweeps run on a copy of the state, which is put back afterwards
     const long long cells = b->cells;
-    const int par0 = b->parity;
+    const int par0 = b->parity, sh0 = b->shape, tiles0 = b->tiles;
     uint8_t *cb_save = nullptr, *td_save = nullptr;
     uint32_t *tm_save = nullptr;
     double *s_save = nullptr;
     unsigned long long *ctr_save = nullptr;
     bool ok = dev_alloc(b->mem, (void **)&cb_save, cells) &&
               dev_alloc(b->mem, (void **)&s_save, 3 * cells * sizeof(double)) &&
-              dev_alloc(b->mem, (void **)&tm_save, b->tiles * sizeof(uint32_t)) &&
-              dev_alloc(b->mem, (void **)&td_save, b->tiles) &&
+              dev_alloc(b->mem, (void **)&tm_save, tiles0 * sizeof(uint32_t)) &&
+              dev_alloc(b->mem, (void **)&td_save, tiles0) &&
               dev_alloc(b->mem, (void **)&ctr_save, (size_t)b->n * C_TOTAL * 8);
     auto release = [&]() {
         dev_free(b->mem, cb_save);
@@ -781,7 +886,10 @@ int ebit_batch_autotune(ebit_batch *b, int sweeps, double *ms_out) {
         release();
         return bfail(b, EBIT_ENOMEM, "ebit_batch_autotune: no room for the state copy");
     }
-    auto copy = [&](bool save) -> cudaError_t {
+    // save: the state, the counters and the tile tables (of the current shape);
+    // restore: the state into both buffers and the counters, and the tile
+    // tables when the shape is the one they were saved in
+    auto copy = [&](bool save, bool tables) -> cudaError_t {
         cudaError_t e = cudaSuccess;
         auto cp = [&](void *dst, const void *src, size_t bytes) {
             if (e == cudaSuccess) e = cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToDevice, b->stream);
@@ -789,65 +897,82 @@ int ebit_batch_autotune(ebit_batch *b, int sweeps, double *ms_out) {
         if (save) {
             cp(cb_save, b->cb[par0], cells);
             for (int a = 0; a < 3; a++) cp(s_save + a * cells, b->s[par0][a], cells * sizeof(double));
-            cp(tm_save, b->tile_marker, b->tiles * sizeof(uint32_t));
-            cp(td_save, b->tile_dirty, b->tiles);
+            cp(tm_save, b->tile_marker, tiles0 * sizeof(uint32_t));
+            cp(td_save, b->tile_dirty, tiles0);
             cp(ctr_save, b->ctr, (size_t)b->n * C_TOTAL * 8);
         } else {
             for (int q = 0; q < 2; q++) {
                 cp(b->cb[q], cb_save, cells);
                 for (int a = 0; a < 3; a++) cp(b->s[q][a], s_save + a * cells, cells * sizeof(double));
             }
-            cp(b->tile_marker, tm_save, b->tiles * sizeof(uint32_t));
-            cp(b->tile_dirty, td_save, b->tiles);
+            if (tables) {
+                cp(b->tile_marker, tm_save, tiles0 * sizeof(uint32_t));
+                cp(b->tile_dirty, td_save, tiles0);
+            }
             cp(b->ctr, ctr_save, (size_t)b->n * C_TOTAL * 8);
         }
         return e;
     };
+    auto reset_parity = [&]() {
+        b->parity = par0;
+        for (int i = 0; i < b->n; i++) b->inst[i]->cur = par0;
+    };
     cudaEvent_t e0, e1;
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
-    int best = b->ctas_per_sm;
+    int best_sh = sh0, best_c = b->ctas_per_sm;
     double best_ms = 1e300;
-    const int maxc = std::min({b->occ[0], b->occ[1], b->occ[2]});
     std::vector<int> since(b->n);
     for (int i = 0; i < b->n; i++) since[i] = b->inst[i]->sweeps_since_f2v;
     int r = EBIT_OK;
-    if (copy(true) != cudaSuccess) r = bfail(b, EBIT_ECUDA, "ebit_batch_autotune: state copy failed");
-    for (int c = 1; c <= maxc && r == EBIT_OK; c++) {
-        for (int rep = 0; rep < 2 && r == EBIT_OK; rep++) {  // first pass warms up
-            if (copy(false) != cudaSuccess) {
-                r = bfail(b, EBIT_ECUDA, "ebit_batch_autotune: state copy failed");
-                break;
-            }
-            b->parity = par0;
-            cudaEventRecord(e0, b->stream);
-            for (int k = 0; k < sweeps && r == EBIT_OK; k++) r = sweep_once(b, k % 3, c);
-            cudaEventRecord(e1, b->stream);
-            if (ebit_batch_sync(b) != EBIT_OK) r = EBIT_ETIMEOUT;
-            float ms = 0.f;
-            cudaEventElapsedTime(&ms, e0, e1);
-            if (rep == 1 && r == EBIT_OK) {
-                if (ms_out) ms_out[c - 1] = ms;
-                if (ms < best_ms) {
-                    best_ms = ms;
-                    best = c;
+    if (copy(true, true) != cudaSuccess) r = bfail(b, EBIT_ECUDA, "ebit_batch_autotune: state copy failed");
+    for (int sh = 0; sh < N_TILE_SHAPES && r == EBIT_OK; sh++) {
+        if (!shape_fits(b, sh)) continue;
+        const int maxc = std::min(max_ctas(b, sh), (int)EBIT_BATCH_MAX_CTAS);
+        for (int c = 1; c <= maxc && r == EBIT_OK; c++) {
+            for (int rep = 0; rep < 2 && r == EBIT_OK; rep++) {  // first pass warms up
+                // from the saved state with every tile marked (the re-tiling),
+                // one untimed sweep to form the band, then the timed sweeps
+                r = retile(b, sh);
+                if (r == EBIT_OK && copy(false, false) != cudaSuccess)
+                    r = bfail(b, EBIT_ECUDA, "ebit_batch_autotune: state copy failed");
+                if (r != EBIT_OK) break;
+                reset_parity();
+                r = sweep_once(b, 0, c);
+                cudaEventRecord(e0, b->stream);
+                for (int k = 1; k <= sweeps && r == EBIT_OK; k++) r = sweep_once(b, k % 3, c);
+                cudaEventRecord(e1, b->stream);
+                if (ebit_batch_sync(b) != EBIT_OK) r = EBIT_ETIMEOUT;
+                float ms = 0.f;
+                cudaEventElapsedTime(&ms, e0, e1);
+                if (rep == 1 && r == EBIT_OK) {
+                    if (ms_out) ms_out[sh * EBIT_BATCH_MAX_CTAS + c - 1] = ms;
+                    if (ms < best_ms) {
+                        best_ms = ms;
+                        best_sh = sh;
+                        best_c = c;
+                    }
                 }
             }
         }
     }
-    if (r == EBIT_OK && copy(false) != cudaSuccess) r = bfail(b, EBIT_ECUDA, "ebit_batch_autotune: restore failed");
+    // back to the saved state, in the chosen shape; the saved tile tables
+    // return with the shape they belong to, any other shape starts with every
+    // tile marked (the same results: tiles outside the band are unchanged)
+    const int sh_end = r == EBIT_OK ? best_sh : sh0;
+    int r2 = retile(b, sh_end);
+    if (r2 == EBIT_OK && copy(false, sh_end == sh0) != cudaSuccess)
+        r2 = bfail(b, EBIT_ECUDA, "ebit_batch_autotune: restore failed");
     cudaStreamSynchronize(b->stream);
-    b->parity = par0;
-    for (int i = 0; i < b->n; i++) {
-        b->inst[i]->cur = par0;
-        b->inst[i]->sweeps_since_f2v = since[i];
-    }
+    reset_parity();
+    for (int i = 0; i < b->n; i++) b->inst[i]->sweeps_since_f2v = since[i];
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     release();
+    if (r == EBIT_OK) r = r2;
     if (r == EBIT_OK) {
-        if (best != b->ctas_per_sm) drop_graph(b);
-        b->ctas_per_sm = best;
+        drop_graph(b);
+        b->ctas_per_sm = best_c;
     }
     return r;
 }

@@ -116,8 +116,7 @@ extern "C" int ebit_advect_sweep_noalloc(int nx, int ny, int nz, double h, int d
     g.n[0] = nx;
     g.n[1] = ny;
     g.n[2] = nz;
-    for (int a = 0; a < 3; a++) g.td[a] = (g.n[a] + TILE - 1) / TILE;
-    g.ntiles = g.td[0] * g.td[1] * g.td[2];
+    grid_tiles(g, 0);
     if (g.ntiles > NA_MAX_TILES) return EBIT_EINVAL;  // cannot happen within 64^3 cells; kept as a guard
 
     int *list = (int *)(base + OFF_LIST);

@@ -182,7 +182,9 @@ __global__ void __launch_bounds__(256) f2v_band_kernel(F2VArgs a) {
         int o[3];
         tile_origin(a.g, tile, o);
         for (int c = threadIdx.x; c < TILE_CELLS; c += blockDim.x) {
-            int x = o[0] + (c & 7), y = o[1] + ((c >> 3) & 7), z = o[2] + (c >> 6);
+            int l[3];
+            tile_cell(a.g, c, l);
+            int x = o[0] + l[0], y = o[1] + l[1], z = o[2] + l[2];
             bool cutc = false;
             int id0 = 0;
             if (x < a.g.n[0] && y < a.g.n[1] && z < a.g.n[2]) {

@@ -305,25 +305,30 @@ __device__ __forceinline__ int warp_append(int *counter, bool flag) {
 // clamped; a displacement that is not finite (NaN or infinite velocity) is
 // counted apart and the marker stays where it is.  Called by all threads of the block; s_mk/s_c/s_n are its shared
 // staging; u is u_D on the D-faces and lam = dt / h.
-template <int D>
+// Tile shape SH (TileShape<SH>); s_c holds (TX + 1) (TY + 1) (TZ + 1) colours.
+template <int D, int SH = 0>
 __device__ __forceinline__ void advect_tile(const SweepArgs &a, const double *__restrict__ u, double lam, int tile,
                                             uint16_t *s_mk, uint8_t *s_c, int *s_n) {
+    using S = TileShape<SH>;
+    constexpr int CX = S::TX + 1, CY = S::TY + 1, CZ = S::TZ + 1;
     int o[3];
     tile_origin(a.g, tile, o);
     if (threadIdx.x == 0) *s_n = 0;
-    for (int r = threadIdx.x; r < 729; r += blockDim.x) {
-        int rx = r % 9, ry = (r / 9) % 9, rz = r / 81;
+    for (int r = threadIdx.x; r < CX * CY * CZ; r += blockDim.x) {
+        int rx = r % CX, ry = (r / CX) % CY, rz = r / (CX * CY);
         s_c[r] = __ldg(a.cb + lin(a.g, o[0] + rx, o[1] + ry, o[2] + rz)) & 1;
     }
     __syncthreads();
     for (int c = threadIdx.x; c < TILE_CELLS; c += blockDim.x) {
-        int q[3] = {o[0] + (c & 7), o[1] + ((c >> 3) & 7), o[2] + (c >> 6)};
+        int l[3];
+        S::cell(c, l);
+        int q[3] = {o[0] + l[0], o[1] + l[1], o[2] + l[2]};
         bool valid = q[0] < a.g.n[0] && q[1] < a.g.n[1] && q[2] < a.g.n[2];
         int mask = 0;
         if (valid) {
-            const int r = (c & 7) + 9 * ((c >> 3) & 7) + 81 * (c >> 6);
+            const int r = l[0] + CX * (l[1] + CY * l[2]);
             const int c0 = s_c[r];
-            mask = (s_c[r + 1] != c0) | ((s_c[r + 9] != c0) << 1) | ((s_c[r + 81] != c0) << 2);
+            mask = (s_c[r + 1] != c0) | ((s_c[r + CX] != c0) << 1) | ((s_c[r + CX * CY] != c0) << 2);
         }
         for (int e = 0; e < 3; e++) {
             int slot = warp_append(s_n, (mask >> e) & 1);
@@ -335,7 +340,9 @@ __device__ __forceinline__ void advect_tile(const SweepArgs &a, const double *__
     unsigned hits = 0, bad = 0;
     for (int k = threadIdx.x; k < n; k += blockDim.x) {
         int it = s_mk[k], c = it & 511, e = it >> 9;
-        int q[3] = {o[0] + (c & 7), o[1] + ((c >> 3) & 7), o[2] + (c >> 6)};
+        int l[3];
+        S::cell(c, l);
+        int q[3] = {o[0] + l[0], o[1] + l[1], o[2] + l[2]};
         const int id = lin3(a.g, q);
         double sv = __ldg(a.s[e] + id);
         double cf = interp_u<D>(a.g, u, q, e, sv) * lam;
@@ -700,9 +707,36 @@ __device__ __forceinline__ bool saddle4(int c00, int c10, int c01, int c11) {
 }
 
 // ------------------------------------------------------- band pass (integer)
-// staged colour region of a tile, in sweep-local axes: A in [-1, 9], T1 and T2
-// in [0, 8] relative to the tile origin
-constexpr int RA = 11, R1 = 9, R2 = 9;
+// staged colour region of a tile, in sweep-local axes: A in [-1, TA + 1], T1
+// in [0, T1], T2 in [0, T2] relative to the tile origin (TA, T1, T2: the
+// tile's edges along the sweep axis and the two others)
+__host__ __device__ constexpr int tile_edge(int sh, int a) { return 1 << tile_log2(sh, a); }
+__host__ __device__ constexpr int stage_n(int d, int sh) {
+    return (tile_edge(sh, d) + 3) * (tile_edge(sh, (d + 1) % 3) + 1) * (tile_edge(sh, (d + 2) % 3) + 1);
+}
+template <int D, int SH>
+struct Stage {
+    static constexpr int RA = tile_edge(SH, D) + 3, R1 = tile_edge(SH, (D + 1) % 3) + 1,
+                         R2 = tile_edge(SH, (D + 2) % 3) + 1;
+};
+// the largest staged region over directions and shapes, and the largest
+// colour block of advect_tile
+__host__ __device__ constexpr int stage_max() {
+    int m = 0;
+    for (int sh = 0; sh < N_TILE_SHAPES; sh++)
+        for (int d = 0; d < 3; d++) m = stage_n(d, sh) > m ? stage_n(d, sh) : m;
+    return m;
+}
+__host__ __device__ constexpr int adv_stage_max() {
+    int m = 0;
+    for (int sh = 0; sh < N_TILE_SHAPES; sh++) {
+        const int v = (tile_edge(sh, 0) + 1) * (tile_edge(sh, 1) + 1) * (tile_edge(sh, 2) + 1);
+        m = v > m ? v : m;
+    }
+    return m;
+}
+constexpr int RA = 11, R1 = 9, R2 = 9;  // 8^3 tiles (every direction)
+static_assert(stage_n(0, 0) == RA * R1 * R2, "8^3 staging");
 
 // One band tile, all threads of the block; s_b/s_n/s_flag are its shared
 // staging (colour bytes and the A-axis bins of the same window; a bin is read
@@ -710,9 +744,11 @@ constexpr int RA = 11, R1 = 9, R2 = 9;
 // NL = 6: an unaligned edge without a marker whose window shows a colour change
 // goes to work list 4 or 5 (the crossing count of the annihilation counter is
 // taken by the FP64-list kernel, with full warps); NL = 4: counted here.
-template <int D, bool F, int NL = 4>
+template <int D, bool F, int NL = 4, int SH = 0>
 __device__ __forceinline__ int sweep_tile(const SweepArgs &a, int tile, uint8_t *s_b, int8_t *s_n, unsigned *s_flag) {
     constexpr int A = D, T1 = (D + 1) % 3, T2 = (D + 2) % 3;
+    using S = TileShape<SH>;
+    constexpr int RA = Stage<D, SH>::RA, R1 = Stage<D, SH>::R1, R2 = Stage<D, SH>::R2;
     {
         int o[3];
         tile_origin(a.g, tile, o);
@@ -747,7 +783,9 @@ __device__ __forceinline__ int sweep_tile(const SweepArgs &a, int tile, uint8_t 
             // no work, and nothing for Front2VOF to redo.
             const uint8_t byte = has1 ? 0x0F : 0x00;
             for (int c = threadIdx.x; c < TILE_CELLS; c += blockDim.x) {
-                const int x = o[0] + (c & 7), y = o[1] + ((c >> 3) & 7), z = o[2] + (c >> 6);
+                int l[3];
+                S::cell(c, l);
+                const int x = o[0] + l[0], y = o[1] + l[1], z = o[2] + l[2];
                 if (x < a.g.n[0] && y < a.g.n[1] && z < a.g.n[2]) a.cbo[lin(a.g, x, y, z)] = byte;
             }
             if (threadIdx.x == 0) {
@@ -759,7 +797,9 @@ __device__ __forceinline__ int sweep_tile(const SweepArgs &a, int tile, uint8_t 
         unsigned ev[C_N] = {0, 0, 0, 0, 0};
         unsigned mk = 0;  // proximity mask of the markers of this thread's cells
         for (int c = threadIdx.x; c < TILE_CELLS; c += blockDim.x) {
-            int x = o[0] + (c & 7), y = o[1] + ((c >> 3) & 7), z = o[2] + (c >> 6);
+            int l[3];
+            S::cell(c, l);
+            int x = o[0] + l[0], y = o[1] + l[1], z = o[2] + l[2];
             bool valid = x < a.g.n[0] && y < a.g.n[1] && z < a.g.n[2];
             bool push[6] = {false, false, false, false, false, false};
             bool push_al = false;
@@ -767,7 +807,6 @@ __device__ __forceinline__ int sweep_tile(const SweepArgs &a, int tile, uint8_t 
             if (valid) {
                 SweepCell<D, F> cell(a, x, y, z);
                 myid = lin(a.g, x, y, z);
-                const int l[3] = {c & 7, (c >> 3) & 7, c >> 6};
                 // staged index of node (da, d1, d2) relative to the cell
                 const int r0 = (l[A] + 1) + RA * (l[T1] + R1 * l[T2]);
                 auto sidx = [&](int da, int d1, int d2) { return r0 + da + RA * (d1 + R1 * d2); };
@@ -891,7 +930,7 @@ __device__ __forceinline__ int sweep_tile(const SweepArgs &a, int tile, uint8_t 
                     int fa = saddle4(n0, nc[0][1][0], nc[0][0][1], nc[0][1][1]) ? ((myb >> (1 + A)) & 1) : n0;
                     byte |= fa << (1 + A);
                     a.cbo[myid] = (uint8_t)byte;
-                    if (in_marker || out_marker) mk |= near_bits(l[0], l[1], l[2]);
+                    if (in_marker || out_marker) mk |= near_bits(l[0], l[1], l[2], S::TX, S::TY, S::TZ);
                 }
             }
             // the warp's appends to the NL work lists and the marker list: all

@@ -34,6 +34,9 @@ EBIT_DESC_DENSE = 1
 
 ST_NONE, ST_HF_X, ST_HF_Y, ST_HF_Z, ST_NO_HF, ST_MLP = 0, 1, 2, 3, 4, 5
 EBIT_MLP_PATH_MMA, EBIT_MLP_PATH_TCGEN05 = 0, 1
+# tile shapes of a batch (cells per tile edge along x, y, z), in ABI order
+TILE_SHAPES = ((8, 8, 8), (16, 8, 4), (32, 4, 4))
+EBIT_BATCH_MAX_CTAS = 8
 
 COUNTER_NAMES = ("markers", "annihilate", "multi", "inconsistent", "cfl")
 
@@ -129,6 +132,8 @@ def load(build_if_missing: bool = True):
     lib.ebit_batch_launch_shape.argtypes = [P, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]
     lib.ebit_batch_set_launch_shape.argtypes = [P, I]
     lib.ebit_batch_autotune.argtypes = [P, I, ctypes.POINTER(ctypes.c_double)]
+    lib.ebit_batch_tile_shape.argtypes = [P, ctypes.POINTER(ctypes.c_int)]
+    lib.ebit_batch_set_tile_shape.argtypes = [P, I]
     lib.ebit_batch_last_error.argtypes = [P]
     lib.ebit_batch_last_error.restype = ctypes.c_char_p
     lib.ebit_set_allocator.argtypes = [_ALLOC_FN, _FREE_FN, P]
@@ -548,11 +553,26 @@ class Batch:
     def set_launch_shape(self, ctas_per_sm):
         return _bcheck(self.b, load().ebit_batch_set_launch_shape(self.b, int(ctas_per_sm)))
 
+    def tile_shape(self):
+        """(shape id, (tx, ty, tz)) of the band tiles in use."""
+        dims = (ctypes.c_int * 3)()
+        sh = _bcheck(self.b, load().ebit_batch_tile_shape(self.b, dims))
+        return sh, tuple(int(v) for v in dims)
+
+    def set_tile_shape(self, shape):
+        """Re-tile every instance with tile shape ``shape`` (an index of TILE_SHAPES)."""
+        return _bcheck(self.b, load().ebit_batch_set_tile_shape(self.b, int(shape)))
+
     def autotune(self, sweeps=6):
-        _, m = self.launch_shape()
-        ms = (ctypes.c_double * m)()
+        """Time every tile shape and launch shape on a copy of the state, keep
+        the fastest pair; returns {(tx, ty, tz): [ms for 1, 2, ... blocks/SM]}."""
+        ms = (ctypes.c_double * (len(TILE_SHAPES) * EBIT_BATCH_MAX_CTAS))()
         _bcheck(self.b, load().ebit_batch_autotune(self.b, int(sweeps), ms))
-        return [float(v) for v in ms]
+        out = {}
+        for sh, dims in enumerate(TILE_SHAPES):
+            row = [float(v) for v in ms[sh * EBIT_BATCH_MAX_CTAS:(sh + 1) * EBIT_BATCH_MAX_CTAS]]
+            out[dims] = [v for v in row if v > 0.0]
+        return out
 
     def close(self):
         if self.b is not None:

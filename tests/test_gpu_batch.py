@@ -100,14 +100,23 @@ def test_batch_instance_matches_oracle():
     b.close()
 
 
+def _same_events(got, ref):
+    """Event counters equal; the tile count depends on the tile shape."""
+    return {k: v for k, v in got.items() if k != "tiles"} == {k: v for k, v in ref.items() if k != "tiles"}
+
+
 def test_autotune_keeps_the_state_and_the_result():
-    insts = instances(5, [24, 32, 16])
+    insts = instances(5, [24, 32, 20])
     ref = reference_states(insts, 4)
     b = make_batch(insts)
     before = [b.instance(i).get_state() for i in range(len(insts))]
     ms = b.autotune(sweeps=3)
+    assert set(ms) == set(ebit.TILE_SHAPES)
+    assert all(len(v) >= 1 and all(t > 0 for t in v) for v in ms.values())
+    sh, dims = b.tile_shape()
     c, m = b.launch_shape()
-    assert 1 <= c <= m and len(ms) == m and all(v > 0 for v in ms)
+    assert dims == ebit.TILE_SHAPES[sh] and 1 <= c <= m
+    assert ms[dims][c - 1] == min(t for v in ms.values() for t in v)
     for i in range(len(insts)):
         cb, s = b.instance(i).get_state()
         assert torch.equal(cb, before[i][0]) and torch.equal(s, before[i][1])
@@ -116,7 +125,72 @@ def test_autotune_keeps_the_state_and_the_result():
     for i, (cb_r, s_r, _, cnt_r) in enumerate(ref):
         cb, s = b.instance(i).get_state()
         assert torch.equal(cb.cpu(), cb_r) and torch.equal(s.cpu(), s_r)
-        assert b.instance(i).counters() == cnt_r
+        assert _same_events(b.instance(i).counters(), cnt_r)
+        if sh == 0:
+            assert b.instance(i).counters() == cnt_r
+    b.close()
+
+
+@pytest.mark.parametrize("shape", [1, 2])
+def test_every_tile_shape_equals_separate_contexts(shape):
+    """16x8x4 and 32x4x4 band tiles (ragged instances: 24, 20 and 40 are not
+    multiples of 16 or 32) give the 8^3 result: colours, offsets, fractions
+    and event counters."""
+    insts = instances(4, [20, 24, 32, 40, 24])
+    steps = 5
+    ref = reference_states(insts, steps)
+    b = make_batch(insts)
+    b.set_tile_shape(shape)
+    assert b.tile_shape() == (shape, ebit.TILE_SHAPES[shape])
+    b.run(0, steps, graph=True)
+    b.sync()
+    for i, (cb_r, s_r, C_r, cnt_r) in enumerate(ref):
+        g = b.instance(i)
+        cb, s = g.get_state()
+        assert torch.equal(cb.cpu(), cb_r), f"instance {i}: colours differ"
+        assert torch.equal(s.cpu(), s_r), f"instance {i}: offsets differ"
+        C = torch.zeros(g.shape, dtype=torch.float64, device="cuda")
+        g.front2vof(C)
+        assert torch.equal(C.cpu(), C_r), f"instance {i}: volume fractions differ"
+        assert _same_events(g.counters(), cnt_r), (i, g.counters(), cnt_r)
+    b.close()
+
+
+def test_tile_shape_changes_between_steps():
+    """Re-tiling between steps (every tile marked, then the band re-formed)
+    continues the same run."""
+    insts = instances(12, [24, 40, 32])
+    ref = reference_states(insts, 6)
+    b = make_batch(insts)
+    for k, shape in enumerate((0, 2, 1)):
+        b.set_tile_shape(shape)
+        b.run(2 * k, 2, graph=(k != 1))
+    b.sync()
+    for i, (cb_r, s_r, C_r, cnt_r) in enumerate(ref):
+        g = b.instance(i)
+        cb, s = g.get_state()
+        assert torch.equal(cb.cpu(), cb_r) and torch.equal(s.cpu(), s_r)
+        C = torch.zeros(g.shape, dtype=torch.float64, device="cuda")
+        g.front2vof(C)
+        assert torch.equal(C.cpu(), C_r)
+        assert _same_events(g.counters(), cnt_r)
+    with pytest.raises(ebit.EbitError):
+        b.set_tile_shape(len(ebit.TILE_SHAPES))
+    b.close()
+
+
+def test_tile_shape_that_does_not_fit_is_refused():
+    """A 16-cell instance is too small for 32-cell tile edges (the staged
+    region would wrap twice): refused on the host, and the autotuner skips
+    that shape."""
+    insts = instances(13, [16, 24])
+    b = make_batch(insts)
+    with pytest.raises(ebit.EbitError) as e:
+        b.set_tile_shape(2)
+    assert e.value.code == ebit.EBIT_EINVAL
+    assert b.tile_shape()[0] == 0
+    ms = b.autotune(sweeps=2)
+    assert ms[(32, 4, 4)] == [] and ms[(8, 8, 8)] and ms[(16, 8, 4)]
     b.close()
 
 
@@ -150,8 +224,8 @@ def test_per_call_velocity_matches_stored_velocity():
     b.close()
 
 
-@pytest.mark.parametrize("graph", [True, False])
-def test_batch_on_members_of_the_64_instance_config(graph):
+@pytest.mark.parametrize("graph,shape", [(True, 0), (False, 0), (True, 2)])
+def test_batch_on_members_of_the_64_instance_config(graph, shape):
     """The first four instances of the batched workload itself (96^3, 128^3,
     128^3 and 64^3, their own fields and spheres, dt = 0.5 h): three steps of
     the batch against separate contexts, bit for bit, with the same counters."""
@@ -174,12 +248,14 @@ def test_batch_on_members_of_the_64_instance_config(graph):
         b.instance(i).init(dev(phi), dev(faces))
         uf.append(tuple(dev(u[d]) for d in range(3)))
     b.set_velocity(uf, [dt for *_, dt in insts])
+    b.set_tile_shape(shape)
     b.run(0, steps, graph=graph)
     b.sync()
     for i, (cb_r, s_r, cnt_r) in enumerate(ref):
         cb, s = b.instance(i).get_state()
         assert torch.equal(cb.cpu(), cb_r), f"instance {i}: colours differ"
         assert torch.equal(s.cpu(), s_r), f"instance {i}: offsets differ"
-        assert b.instance(i).counters() == cnt_r, (i, b.instance(i).counters(), cnt_r)
+        got = b.instance(i).counters()
+        assert (got == cnt_r) if shape == 0 else _same_events(got, cnt_r), (i, got, cnt_r)
         assert cnt_r["markers"] > 0
     b.close()
