@@ -427,6 +427,14 @@ const char *ebit_batch_last_error(const ebit_batch *b);
  * cannot be allocated or a launch or copy fails. */
 int ebit_selftest_bounded_waits(void *cuda_stream, int *report);
 
+/* Self-test of the integer double -> float conversion that the learned
+ * curvature's gather uses for the C values (no paper passage: GB300's FP64
+ * pipe is narrow, so the gather converts from the bit patterns).  out[i] =
+ * in[i] rounded to float, nearest-even, exactly as the IEEE conversion for
+ * every non-NaN input; a NaN gives a quiet NaN.  in, out: n device values
+ * (caller-owned), on cuda_stream.  EBIT_EINVAL for null arrays or n < 0. */
+int ebit_selftest_f64_to_f32(const double *in, float *out, int n, void *cuda_stream);
+
 /* One split advection sweep that allocates no device memory.
  * The paper has no counterpart: this entry point exists for callers that
  * cannot allocate device memory -- a flow solver that reserves all of its

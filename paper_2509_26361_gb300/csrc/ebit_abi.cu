@@ -975,6 +975,16 @@ int ebit_mlp_get_params(ebit_mlp *mlp, float *params) {
     return EBIT_OK;
 }
 
+int ebit_selftest_f64_to_f32(const double *in, float *out, int n, void *cuda_stream) {
+    if (!in || !out || n < 0) return EBIT_EINVAL;
+    if (n == 0) return EBIT_OK;
+    int dev = 0, sms = 1;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    f64_to_f32_kernel<<<std::min((n + 255) / 256, 4 * std::max(sms, 1)), 256, 0, (cudaStream_t)cuda_stream>>>(in, out, n);
+    return cudaGetLastError() == cudaSuccess ? EBIT_OK : EBIT_ECUDA;
+}
+
 int ebit_mlp_gather(ebit_mlp *mlp, const double *C, int nx, int ny, int nz, const int *cells, int m, uint16_t *X,
                     uint8_t *frag) {
     if (!mlp || !C || !cells || !X || m < 0 || nx < 8 || ny < 8 || nz < 8 || !aligned16(X)) return EBIT_EINVAL;

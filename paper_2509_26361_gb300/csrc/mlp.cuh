@@ -57,80 +57,184 @@ __device__ __forceinline__ bool fragmented27(unsigned pos) {
     return r != pos;
 }
 
+// IEEE-754 binary64 -> binary32, round to nearest, ties to even, from the bit
+// patterns alone (integer instructions: GB300's FP64 pipe, which a float
+// conversion would use, is narrow).  Finite values, zeros and infinities
+// convert exactly as the IEEE operation does; a NaN becomes the quiet NaN of
+// its sign.  Written from the two formats: 11/8 exponent bits with biases
+// 1023/127, 52/23 fraction bits, float subnormals below 2^-126.
+//
+// Rare classes (zero, float subnormal range, overflow, infinity, NaN).
+__device__ __noinline__ unsigned f64_bits_to_f32_rare(unsigned long long u) {
+    const unsigned sign = (unsigned)(u >> 63) << 31;
+    const int e = (int)((u >> 52) & 0x7FF);
+    const unsigned long long frac = u & ((1ull << 52) - 1);
+    if (e == 0x7FF) return sign | (frac ? 0x7FC00000u : 0x7F800000u);
+    if (e == 0) return sign;  // zero, or a double subnormal (below half the smallest float)
+    if (e - 1023 + 127 >= 255) return sign | 0x7F800000u;
+    // float subnormal: value = M 2^(e - 1075) = f 2^-149, f = M >> (926 - e)
+    const unsigned long long M = frac | (1ull << 52);
+    const int sh = 926 - e;  // >= 30
+    unsigned f = 0;
+    if (sh < 64) {
+        f = (unsigned)(M >> sh);
+        const unsigned long long rem = M & ((1ull << sh) - 1), half = 1ull << (sh - 1);
+        if (rem > half || (rem == half && (f & 1u))) f++;
+    }
+    return sign | f;  // f = 2^23 reads as the smallest normal
+}
+
+__device__ __forceinline__ float f64_bits_to_f32(long long bits) {
+    const unsigned long long u = (unsigned long long)bits;
+    const unsigned long long x = u & 0x7FFFFFFFFFFFFFFFull;
+    const unsigned e = (unsigned)(x >> 52);
+    if (e - 897u < 254u) {
+        // float exponent 1 .. 254: round the exponent and fraction field at its
+        // 29th bit (ties to the even kept bit); a carry out of the fraction
+        // raises the exponent, to infinity from the largest binade
+        const unsigned long long t = x + 0x0FFFFFFFull + ((x >> 29) & 1ull);
+        return __uint_as_float((unsigned)(t >> 29) - (896u << 23) | ((unsigned)(u >> 63) << 31));
+    }
+    return __uint_as_float(f64_bits_to_f32_rare(u));
+}
+
+// binary64 bits > +0 (a positive number, +infinity included; not a NaN)
+__device__ __forceinline__ bool f64_bits_positive(long long bits) {
+    return bits > 0 && bits <= 0x7FF0000000000000LL;
+}
+
+template <int A>
+__device__ __forceinline__ int blk(int i0, int i1, int i2) {
+    // block index with coordinate i0 on axis A and i1, i2 on the next two
+    int d[3];
+    d[A] = i0;
+    d[(A + 1) % 3] = i1;
+    d[(A + 2) % 3] = i2;
+    return 9 * d[2] + 3 * d[1] + d[0];
+}
+
+// reflect the 3x3x3 block along axis A when `on`
+template <int A>
+__device__ __forceinline__ void reflect27(float (&f)[27], bool on) {
+#pragma unroll
+    for (int i1 = 0; i1 < 3; i1++)
+#pragma unroll
+        for (int i2 = 0; i2 < 3; i2++) {
+            const int p = blk<A>(0, i1, i2), q = blk<A>(2, i1, i2);
+            const float lo = f[p], hi = f[q];
+            f[p] = on ? hi : lo;
+            f[q] = on ? lo : hi;
+        }
+}
+
+// transpose axes I < J of the block when `on`
+template <int I, int J>
+__device__ __forceinline__ void transpose27(float (&f)[27], bool on) {
+    constexpr int K = 3 - I - J;
+#pragma unroll
+    for (int a = 0; a < 3; a++)
+#pragma unroll
+        for (int b = a + 1; b < 3; b++)
+#pragma unroll
+            for (int c = 0; c < 3; c++) {
+                int d[3], e[3];
+                d[I] = a;
+                d[J] = b;
+                d[K] = c;
+                e[I] = b;
+                e[J] = a;
+                e[K] = c;
+                const int p = 9 * d[2] + 3 * d[1] + d[0], q = 9 * e[2] + 3 * e[1] + e[0];
+                const float u = f[p], v = f[q];
+                f[p] = on ? v : u;
+                f[q] = on ? u : v;
+            }
+}
+
 // 3x3x3 block around cell (x, y, z); reflect the axes with n < 0; order the
 // axes by increasing |n| (stable); write the 27 values in z-major order of the
 // canonical axes, split into bf16 head and tail.  The normal is taken in float
 // and its decisions (signs, order) kept when every sign and comparison clears
 // twice the bound above, so they equal those of the double-precision normal;
-// otherwise the double-precision normal decides.  sf: this thread's column of
-// 27 floats (stride `stride`) in shared memory.  Returns the fragment flag.
+// otherwise the double-precision normal decides.  The symmetry is applied in
+// registers: the reflections, then the axis transpositions of the three-step
+// sorting network that orders |n| (output axis j takes input axis o_j; each
+// exchange of two entries of o exchanges those two output axes).  Returns the
+// fragment flag.
 __device__ __forceinline__ bool canon_encode(const double *__restrict__ C, const Grid &g, int x, int y, int z,
-                                             __nv_bfloat16 out[MLP_IN], float *sf, int stride) {
+                                             __nv_bfloat16 out[MLP_IN]) {
+    const long long *Cb = reinterpret_cast<const long long *>(C);
+    int xo[3], yo[3], zo[3];
+#pragma unroll
+    for (int i = 0; i < 3; i++) {
+        xo[i] = wrapc(x + i - 1, g.n[0]);
+        yo[i] = wrapc(y + i - 1, g.n[1]) * g.n[0];
+        zo[i] = wrapc(z + i - 1, g.n[2]) * (g.n[0] * g.n[1]);
+    }
     float f[27];
     unsigned pos = 0;
 #pragma unroll
     for (int b = 0; b < 27; b++) {
-        const double c = __ldg(C + lin(g, x + b % 3 - 1, y + (b / 3) % 3 - 1, z + b / 9 - 1));
-        if (c > 0.0) pos |= 1u << b;
-        f[b] = (float)c;
-        sf[b * stride] = f[b];
+        const long long bits = __ldg(Cb + zo[b / 9] + yo[(b / 3) % 3] + xo[b % 3]);
+        if (f64_bits_positive(bits)) pos |= 1u << b;
+        f[b] = f64_bits_to_f32(bits);
     }
     float nf[3];
     youngs<float>(f, nf);
     const float a0 = fabsf(nf[0]), a1 = fabsf(nf[1]), a2 = fabsf(nf[2]);
-    int sg[3];
-    float m[3];
-    double md[3];
     const bool sure = a0 > CANON_EPS && a1 > CANON_EPS && a2 > CANON_EPS && fabsf(a0 - a1) > 2.0f * CANON_EPS &&
                       fabsf(a0 - a2) > 2.0f * CANON_EPS && fabsf(a1 - a2) > 2.0f * CANON_EPS;
-    int o0 = 0, o1 = 1, o2 = 2, t;
+    bool neg0, neg1, neg2, s1, s2, s3;
     if (sure) {
-#pragma unroll
-        for (int d = 0; d < 3; d++) sg[d] = nf[d] < 0.0f ? -1 : 1;
-        m[0] = a0;
-        m[1] = a1;
-        m[2] = a2;
-        if (m[o1] < m[o0]) { t = o0; o0 = o1; o1 = t; }
-        if (m[o2] < m[o1]) {
-            t = o1; o1 = o2; o2 = t;
-            if (m[o1] < m[o0]) { t = o0; o0 = o1; o1 = t; }
-        }
+        neg0 = nf[0] < 0.0f;
+        neg1 = nf[1] < 0.0f;
+        neg2 = nf[2] < 0.0f;
+        float p0 = a0, p1 = a1, p2 = a2, t;
+        s1 = p1 < p0;
+        if (s1) { t = p0; p0 = p1; p1 = t; }
+        s2 = p2 < p1;
+        if (s2) { t = p1; p1 = p2; p2 = t; }
+        s3 = s2 && p1 < p0;
     } else {
         double v[27];
 #pragma unroll
-        for (int b = 0; b < 27; b++) v[b] = __ldg(C + lin(g, x + b % 3 - 1, y + (b / 3) % 3 - 1, z + b / 9 - 1));
+        for (int b = 0; b < 27; b++) v[b] = __ldg(C + zo[b / 9] + yo[(b / 3) % 3] + xo[b % 3]);
         double n[3];
         youngs<double>(v, n);
-#pragma unroll
-        for (int d = 0; d < 3; d++) {
-            sg[d] = n[d] < 0.0 ? -1 : 1;
-            md[d] = fabs(n[d]);
-        }
-        if (md[o1] < md[o0]) { t = o0; o0 = o1; o1 = t; }
-        if (md[o2] < md[o1]) {
-            t = o1; o1 = o2; o2 = t;
-            if (md[o1] < md[o0]) { t = o0; o0 = o1; o1 = t; }
-        }
+        neg0 = n[0] < 0.0;
+        neg1 = n[1] < 0.0;
+        neg2 = n[2] < 0.0;
+        double p0 = fabs(n[0]), p1 = fabs(n[1]), p2 = fabs(n[2]), t;
+        s1 = p1 < p0;
+        if (s1) { t = p0; p0 = p1; p1 = t; }
+        s2 = p2 < p1;
+        if (s2) { t = p1; p1 = p2; p2 = t; }
+        s3 = s2 && p1 < p0;
     }
-    int k = 0;
-    for (int u2 = -1; u2 <= 1; u2++)
-        for (int u1 = -1; u1 <= 1; u1++)
-            for (int u0 = -1; u0 <= 1; u0++) {
-                int d[3];
-                d[o0] = sg[o0] * u0;
-                d[o1] = sg[o1] * u1;
-                d[o2] = sg[o2] * u2;
-                const float fv = sf[((d[2] + 1) * 9 + (d[1] + 1) * 3 + (d[0] + 1)) * stride];
-                const __nv_bfloat16 hi = __float2bfloat16_rn(fv);
-                out[k] = hi;
-                out[32 + k] = __float2bfloat16_rn(fv - __bfloat162float(hi));
-                k++;
-            }
+    reflect27<0>(f, neg0);
+    reflect27<1>(f, neg1);
+    reflect27<2>(f, neg2);
+    transpose27<0, 1>(f, s1);
+    transpose27<1, 2>(f, s2);
+    transpose27<0, 1>(f, s3);
+#pragma unroll
+    for (int k = 0; k < 27; k++) {
+        const __nv_bfloat16 hi = __float2bfloat16_rn(f[k]);
+        out[k] = hi;
+        out[32 + k] = __float2bfloat16_rn(f[k] - __bfloat162float(hi));
+    }
+#pragma unroll
     for (int q = 27; q < 32; q++) {
         out[q] = __float2bfloat16_rn(0.0f);
         out[32 + q] = __float2bfloat16_rn(0.0f);
     }
     return fragmented27(pos);
+}
+
+// the bit-pattern conversion over an array (self-test of f64_bits_to_f32)
+__global__ void f64_to_f32_kernel(const double *__restrict__ in, float *__restrict__ out, int n) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+        out[i] = f64_bits_to_f32(__double_as_longlong(in[i]));
 }
 
 constexpr int GATHER_THREADS = 128;
@@ -139,12 +243,11 @@ __global__ void __launch_bounds__(GATHER_THREADS) mlp_gather_kernel(const double
                                                                     const int *__restrict__ cells, int m,
                                                                     __nv_bfloat16 *__restrict__ X,
                                                                     uint8_t *__restrict__ frag) {
-    __shared__ float s_f[27 * GATHER_THREADS];
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < m; i += gridDim.x * blockDim.x) {
         const int id = cells[i];
         const int x = id % g.n[0], y = (id / g.n[0]) % g.n[1], z = id / (g.n[0] * g.n[1]);
         __nv_bfloat16 v[MLP_IN];
-        const bool fr = canon_encode(C, g, x, y, z, v, s_f + threadIdx.x, GATHER_THREADS);
+        const bool fr = canon_encode(C, g, x, y, z, v);
         if (frag) frag[i] = fr ? 1 : 0;
         uint4 *dst = reinterpret_cast<uint4 *>(X + (long long)i * MLP_IN);
         const uint4 *src = reinterpret_cast<const uint4 *>(v);
@@ -300,10 +403,18 @@ struct MlpArgs {
 };
 
 // ------------------------------------------------------------ forward
-// smem: X [128][72] | W1 [128][72] | W2 [128][136] | fragment flags [128].  The
-// layer-1 activations stay in registers: the accumulator fragments of two
-// adjacent 8-column tiles are exactly the A fragment of one 16-wide k step.
-constexpr int FWD_SMEM = (2 * 128 * LD64 + 128 * LD128) * 2 + 128;
+// smem: X [128][72] | W1 [128][72] | W2 [128][136] | fragment flags [128] |
+// b1 | b2 | w3 | b3 (FP32, 388 floats).  The layer-1 activations stay in
+// registers: the accumulator fragments of two adjacent 8-column tiles are
+// exactly the A fragment of one 16-wide k step.
+constexpr int FWD_SMEM = (2 * 128 * LD64 + 128 * LD128) * 2 + 128 + 388 * 4;
+
+// b1 | b2 | w3 | b3 into shared memory (388 floats; read as broadcasts in the
+// epilogues instead of one global load per parameter per thread)
+__device__ __forceinline__ void stage_params(float *prm, const float *__restrict__ p) {
+    for (int k = threadIdx.x; k < 385; k += blockDim.x)
+        prm[k] = ldp(p, k < 256 ? (k < 128 ? P_B1 + k : P_B2 + k - 128) : (k < 384 ? P_W3 + k - 256 : P_B3));
+}
 
 __device__ __forceinline__ uint32_t pack_bf16x2(float lo, float hi) {
     __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
@@ -311,16 +422,18 @@ __device__ __forceinline__ uint32_t pack_bf16x2(float lo, float hi) {
 }
 
 template <bool GATHER, bool CURV>
-__global__ void __launch_bounds__(128) mlp_fwd_kernel(MlpArgs a) {
+__global__ void __launch_bounds__(128, 3) mlp_fwd_kernel(MlpArgs a) {
     pdl_wait();
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __nv_bfloat16 *sX = reinterpret_cast<__nv_bfloat16 *>(smem_raw);
     __nv_bfloat16 *sW1 = sX + 128 * LD64;
     __nv_bfloat16 *sW2 = sW1 + 128 * LD64;
     uint8_t *sFrag = reinterpret_cast<uint8_t *>(sW2 + 128 * LD128);
+    float *prm = reinterpret_cast<float *>(sFrag + 128);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31, g = lane >> 2, t4 = lane & 3;
     load_row(sW1, LD64, tid, a.w1b, tid, MLP_IN, MLP_H);
     load_row(sW2, LD128, tid, a.w2b, tid, MLP_H, MLP_H);
+    stage_params(prm, a.params);
     const int m = a.ncells ? *a.ncells : a.m;
     const int ntile = (m + 127) / 128;
     const int m0 = warp * 32;
@@ -333,8 +446,7 @@ __global__ void __launch_bounds__(128) mlp_fwd_kernel(MlpArgs a) {
             if (live) {
                 const int cell = a.cells[row];
                 const int x = cell % a.g.n[0], y = (cell / a.g.n[0]) % a.g.n[1], z = cell / (a.g.n[0] * a.g.n[1]);
-                // the block values are staged in this thread's own input row
-                sFrag[tid] = canon_encode(a.C, a.g, x, y, z, v, reinterpret_cast<float *>(sX + tid * LD64), 1) ? 1 : 0;
+                sFrag[tid] = canon_encode(a.C, a.g, x, y, z, v) ? 1 : 0;
             } else {
                 for (int q = 0; q < MLP_IN; q++) v[q] = __float2bfloat16_rn(0.0f);
             }
@@ -359,7 +471,7 @@ __global__ void __launch_bounds__(128) mlp_fwd_kernel(MlpArgs a) {
 #pragma unroll
                 for (int nt = 0; nt < 4; nt++) {
                     const int col = c * 32 + nt * 8 + 2 * t4;
-                    const float b0 = ldp(a.params, P_B1 + col), b1 = ldp(a.params, P_B1 + col + 1);
+                    const float b0 = prm[col], b1 = prm[col + 1];
                     const int kk = 2 * c + (nt >> 1), half = nt & 1;
                     h1[mt][kk][2 * half] = pack_bf16x2(fmaxf(acc[mt][nt][0] + b0, 0.0f), fmaxf(acc[mt][nt][1] + b1, 0.0f));
                     h1[mt][kk][2 * half + 1] =
@@ -397,8 +509,7 @@ __global__ void __launch_bounds__(128) mlp_fwd_kernel(MlpArgs a) {
 #pragma unroll
                     for (int e = 0; e < 4; e++) {
                         const int col = c * 32 + nt * 8 + 2 * t4 + (e & 1);
-                        yp[mt][e >> 1] += fmaxf(acc[mt][nt][e] + ldp(a.params, P_B2 + col), 0.0f) *
-                                          ldp(a.params, P_W3 + col);
+                        yp[mt][e >> 1] += fmaxf(acc[mt][nt][e] + prm[128 + col], 0.0f) * prm[256 + col];
                     }
         }
 #pragma unroll
@@ -408,7 +519,7 @@ __global__ void __launch_bounds__(128) mlp_fwd_kernel(MlpArgs a) {
                 float v = yp[mt][hh];
                 v += __shfl_xor_sync(0xffffffffu, v, 1);
                 v += __shfl_xor_sync(0xffffffffu, v, 2);
-                yp[mt][hh] = v + ldp(a.params, P_B3);
+                yp[mt][hh] = v + prm[384];
             }
         if (t4 == 0) {
 #pragma unroll
@@ -457,7 +568,8 @@ constexpr int TCF_MBAR = TCF_G0 + TC_GROUPS * TCF_GSTRIDE;          // 8 B per g
 constexpr int TCF_TB = TCF_MBAR + 8 * TC_GROUPS;
 constexpr int TCF_FRAG = TCF_TB + 16;                                // 128 B per group
 constexpr int TCF_BAD = TCF_FRAG + 128 * TC_GROUPS;                  // int per group
-constexpr int FWD_TC_SMEM = TCF_BAD + 4 * TC_GROUPS + 1024;
+constexpr int TCF_PRM = (TCF_BAD + 4 * TC_GROUPS + 15) & ~15;        // b1 | b2 | w3 | b3
+constexpr int FWD_TC_SMEM = TCF_PRM + 388 * 4 + 1024;
 constexpr int TC_THREADS = 128 * TC_GROUPS;
 constexpr long long MLP_WAIT = 1LL << 20;  // mbarrier polls before a wait gives up
 
@@ -484,6 +596,7 @@ __global__ void __launch_bounds__(TC_THREADS) mlp_fwd_tc_kernel(MlpArgs a) {
     uint32_t *tbase = reinterpret_cast<uint32_t *>(base + TCF_TB);
     uint8_t *sFrag = base + TCF_FRAG + 128 * grp;
     volatile int *sBad = reinterpret_cast<volatile int *>(base + TCF_BAD) + grp;
+    float *prm = reinterpret_cast<float *>(base + TCF_PRM);
     const uint32_t mb = tc::smem_u32(mbar);
     if (t == 0) {
         tc::mbar_init(mb, 1);
@@ -495,6 +608,7 @@ __global__ void __launch_bounds__(TC_THREADS) mlp_fwd_tc_kernel(MlpArgs a) {
         load_row_kmaj(sW1, a.w1b, tid, tid, MLP_IN);
         load_row_kmaj(sW2, a.w2b, tid, tid, MLP_H);
     }
+    stage_params(prm, a.params);
     tc::fence_proxy_async();
     tc::fence_before_sync();
     __syncthreads();
@@ -521,7 +635,7 @@ __global__ void __launch_bounds__(TC_THREADS) mlp_fwd_tc_kernel(MlpArgs a) {
                 cell = a.cells[row];
                 const int x = cell % a.g.n[0], y = (cell / a.g.n[0]) % a.g.n[1], z = cell / (a.g.n[0] * a.g.n[1]);
                 // the block values are staged in the group's H1 tile (free until layer 1)
-                sFrag[t] = canon_encode(a.C, a.g, x, y, z, v, reinterpret_cast<float *>(sH1 + t * 112), 1) ? 1 : 0;
+                sFrag[t] = canon_encode(a.C, a.g, x, y, z, v) ? 1 : 0;
             } else if (!GATHER && live) {
                 const uint4 *s4 = reinterpret_cast<const uint4 *>(a.X + (long long)row * MLP_IN);
                 for (int q = 0; q < MLP_IN / 8; q++) reinterpret_cast<uint4 *>(v)[q] = s4[q];
@@ -553,8 +667,15 @@ __global__ void __launch_bounds__(TC_THREADS) mlp_fwd_tc_kernel(MlpArgs a) {
         for (int c = 0; c < 4; c++) {
             float v[32];
             tc::tmem_ld32(lane_base + c * 32, v);
+            const float4 *b4 = reinterpret_cast<const float4 *>(prm + c * 32);
 #pragma unroll
-            for (int j = 0; j < 32; j++) v[j] = fmaxf(v[j] + ldp(a.params, P_B1 + c * 32 + j), 0.0f);
+            for (int q = 0; q < 8; q++) {
+                const float4 bq = b4[q];
+                v[4 * q] = fmaxf(v[4 * q] + bq.x, 0.0f);
+                v[4 * q + 1] = fmaxf(v[4 * q + 1] + bq.y, 0.0f);
+                v[4 * q + 2] = fmaxf(v[4 * q + 2] + bq.z, 0.0f);
+                v[4 * q + 3] = fmaxf(v[4 * q + 3] + bq.w, 0.0f);
+            }
 #pragma unroll
             for (int q = 0; q < 4; q++)
                 *reinterpret_cast<uint4 *>(sH1 + tc::kmaj_off(t, c * 32 + q * 8, MLP_H)) = tc::pack8_bf16(v + q * 8);
@@ -582,11 +703,18 @@ __global__ void __launch_bounds__(TC_THREADS) mlp_fwd_tc_kernel(MlpArgs a) {
         for (int c = 0; c < 4; c++) {
             float v[32];
             tc::tmem_ld32(lane_base + c * 32, v);
+            const float4 *b4 = reinterpret_cast<const float4 *>(prm + 128 + c * 32);
+            const float4 *w4 = reinterpret_cast<const float4 *>(prm + 256 + c * 32);
 #pragma unroll
-            for (int j = 0; j < 32; j++)
-                yv += fmaxf(v[j] + ldp(a.params, P_B2 + c * 32 + j), 0.0f) * ldp(a.params, P_W3 + c * 32 + j);
+            for (int q = 0; q < 8; q++) {
+                const float4 bq = b4[q], wq4 = w4[q];
+                yv += fmaxf(v[4 * q] + bq.x, 0.0f) * wq4.x;
+                yv += fmaxf(v[4 * q + 1] + bq.y, 0.0f) * wq4.y;
+                yv += fmaxf(v[4 * q + 2] + bq.z, 0.0f) * wq4.z;
+                yv += fmaxf(v[4 * q + 3] + bq.w, 0.0f) * wq4.w;
+            }
         }
-        yv += ldp(a.params, P_B3);
+        yv += prm[384];
         if (live) {
             if (CURV) {
                 if (a.mode == 2 && (fabsf(yv) > 1.0f || sFrag[t])) {

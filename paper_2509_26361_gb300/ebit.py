@@ -117,6 +117,7 @@ def load(build_if_missing: bool = True):
     lib.ebit_batch_create.argtypes = [I, ctypes.POINTER(_Desc), ctypes.POINTER(ctypes.c_void_p)]
     lib.ebit_batch_destroy.argtypes = [P]
     lib.ebit_selftest_bounded_waits.argtypes = [P, P]
+    lib.ebit_selftest_f64_to_f32.argtypes = [P, P, I, P]
     lib.ebit_batch_destroy.restype = None
     lib.ebit_batch_size.argtypes = [P]
     lib.ebit_batch_instance.argtypes = [P, I]
@@ -185,6 +186,15 @@ def ebit_set_allocator(alloc=None, free=None):
     ff = _FREE_FN(lambda ptr, u: free(ptr))
     _allocators.append((fa, ff))
     return _check(None, lib.ebit_set_allocator(fa, ff, None))
+
+
+def ebit_selftest_f64_to_f32(x):
+    """The gather's bit-pattern double -> float rounding over a float64 CUDA tensor."""
+    xp = _dev(x, torch.float64, name="x")
+    out = torch.empty(x.shape, dtype=torch.float32, device=x.device)
+    _check(None, load().ebit_selftest_f64_to_f32(xp, _dev(out, torch.float32, name="out"), int(x.numel()),
+                                                  ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)))
+    return out
 
 
 def ebit_create(nx, ny, nz, h, stream=None, flags=0):
