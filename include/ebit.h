@@ -427,6 +427,46 @@ const char *ebit_batch_last_error(const ebit_batch *b);
  * cannot be allocated or a launch or copy fails. */
 int ebit_selftest_bounded_waits(void *cuda_stream, int *report);
 
+/* AMR refinement rule and narrow-band brick store (Sec. 2.5).  With one marker
+ * per edge, two refinement levels must never share the interface, so every
+ * cell within the 3x3x3 block of cells around an interfacial cell is refined
+ * to the finest level.  A cell is interfacial when its eight corner colours
+ * differ (an edge carries a marker exactly when its end colours differ).
+ *
+ * ebit_refine_mask: mask [N] (device, caller-owned, may be NULL) receives 1
+ *   for every cell that the rule refines and 0 elsewhere (cell idx = its lowest
+ *   corner's node idx); count (host, may be NULL) the number of such cells,
+ *   which makes the call synchronise.  Reads the current state (after any
+ *   EBIT_ASYNC work is joined).
+ *
+ * ebit_pack_bricks: the narrow-band store of the current state.  The bricks are
+ *   the 8x8x8 tiles that hold a refined cell, in ascending tile id (tile id =
+ *   (tz * tiles_y + ty) * tiles_x + tx, tiles_a = ceil(n_a / 8)).  Any other
+ *   tile holds no interfacial cell: one node colour, no marker, face colours
+ *   equal to it.  Outputs, device arrays owned by the caller:
+ *     tiles [capacity]              brick k's tile id;
+ *     cb    [capacity][512]         brick k's colour bytes, cell c = x + 8 (y + 8 z)
+ *                                   in the tile (0 for cells past the grid);
+ *     s     [capacity][3][512]      its offsets per edge family, 0 on an edge
+ *                                   without a marker;
+ *     bg    [tiles]                 bit 0: every tile's origin-node colour
+ *                                   (the colour of each tile that is not a brick).
+ *   *nbricks (host) receives the brick count.  capacity = 0 (arrays may be
+ *   NULL) only counts.  Synchronises.  EBIT_EINVAL when capacity is below the
+ *   count (the outputs are then unspecified) or the grid uses tiles other than
+ *   8^3 (a batch instance re-tiled by its autotuner).
+ *
+ * ebit_unpack_bricks: replaces the state with the one a store describes: the
+ *   bricks' cells from cb and s, every other tile filled with its bg colour
+ *   (colour byte 0x0F or 0x00, offsets 0); each tile at most once.  Like
+ *   ebit_set_state, the next sweep and Front2VOF treat every tile.  EBIT_EINVAL
+ *   for a tile id out of range (checked on the device; synchronises) or on a
+ *   batch instance.  Arrays as for ebit_pack_bricks, borrowed for the call. */
+int ebit_refine_mask(ebit_ctx *ctx, uint8_t *mask, int64_t *count);
+int ebit_pack_bricks(ebit_ctx *ctx, int capacity, int *tiles, uint8_t *cb, double *s, uint8_t *bg, int *nbricks);
+int ebit_unpack_bricks(ebit_ctx *ctx, int nbricks, const int *tiles, const uint8_t *cb, const double *s,
+                       const uint8_t *bg);
+
 /* Self-test of the integer double -> float conversion that the learned
  * curvature's gather uses for the C values (no paper passage: GB300's FP64
  * pipe is narrow, so the gather converts from the bit patterns).  out[i] =

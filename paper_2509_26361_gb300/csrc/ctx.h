@@ -64,6 +64,9 @@ struct ebit_ctx {
     int *all_list, *all_count;
     unsigned long long *ctr;  // C_N event counters + Front2VOF inconsistencies
     double *scratch;          // 3N doubles, allocated on first ebit_get_state
+    int *amr_flag;            // per tile: holds a refined cell (ebit_refine_mask / ebit_pack_bricks), lazily
+    int *amr_slot;            // per tile: its brick in a store being unpacked, or -1, lazily
+    unsigned long long *amr_ctr;  // refined cells | brick count, ids out of range (two ints)
     double *adv[3];           // advected marker coordinates of the current sweep (scratch)
     int8_t *bin[3];           // floor(2 adv) (scratch)
     unsigned *work[NLISTS];   // work lists of a sweep (scratch; a batch view has the first 4)

@@ -23,6 +23,7 @@
 #include "mlp.cuh"
 #include "state.cuh"
 #include "sweep.cuh"
+#include "amr.cuh"
 
 using namespace ebit;
 
@@ -267,6 +268,8 @@ static int create_ctx(const ebit_desc *desc, const ebit_state_arrays *st, ebit_c
     ctx->dense = (desc->flags & EBIT_DESC_DENSE) ? 1 : 0;
     ctx->cur = 0;
     ctx->scratch = nullptr;
+    ctx->amr_flag = ctx->amr_slot = nullptr;
+    ctx->amr_ctr = nullptr;
     int dev = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&ctx->sms, cudaDevAttrMultiProcessorCount, dev);
@@ -446,6 +449,9 @@ void ebit_destroy(ebit_ctx *ctx) {
     dev_free(ctx->mem, ctx->all_list);
     dev_free(ctx->mem, ctx->all_count);
     dev_free(ctx->mem, ctx->scratch);
+    dev_free(ctx->mem, ctx->amr_flag);
+    dev_free(ctx->mem, ctx->amr_slot);
+    dev_free(ctx->mem, ctx->amr_ctr);
     dev_free(ctx->mem, ctx->cut);
     dev_free(ctx->mem, ctx->scan);
     dev_free(ctx->mem, ctx->iface[0]);
@@ -479,6 +485,102 @@ int ebit_set_state(ebit_ctx *ctx, const uint8_t *cb, const double *s) {
         CU(cudaMemcpyAsync(ctx->s[c][a], s + a * ctx->N, ctx->N * sizeof(double), cudaMemcpyDefault, ctx->stream));
     int r = copy_other(ctx);
     if (r) return r;
+    return mark_all(ctx);
+}
+
+// the refinement scratch (per-tile flags and slots, two counters), on first use
+static int amr_scratch(ebit_ctx *ctx) {
+    if (ctx->amr_flag) return EBIT_OK;
+    const size_t nt = (size_t)ctx->nt_cap;
+    if (!dev_alloc(ctx->mem, (void **)&ctx->amr_flag, nt * sizeof(int)) ||
+        !dev_alloc(ctx->mem, (void **)&ctx->amr_slot, nt * sizeof(int)) ||
+        !dev_alloc(ctx->mem, (void **)&ctx->amr_ctr, 2 * sizeof(unsigned long long))) {
+        cudaGetLastError();
+        dev_free(ctx->mem, ctx->amr_flag);
+        dev_free(ctx->mem, ctx->amr_slot);
+        dev_free(ctx->mem, ctx->amr_ctr);
+        ctx->amr_flag = ctx->amr_slot = nullptr;
+        ctx->amr_ctr = nullptr;
+        return fail(ctx, EBIT_ENOMEM, "refinement scratch: allocation failed");
+    }
+    return EBIT_OK;
+}
+
+// refine_kernel over the current state: per-tile flags, background colours
+// (bg may be ctx scratch when the caller gives none), refined-cell count
+static int refine_pass(ebit_ctx *ctx, uint8_t *mask, uint8_t *bg) {
+    if (int r = amr_scratch(ctx)) return r;
+    CU(cudaMemsetAsync(ctx->amr_ctr, 0, 2 * sizeof(unsigned long long), ctx->stream));
+    refine_kernel<<<std::min(ctx->g.ntiles, 4 * ctx->sms), 256, 0, ctx->stream>>>(
+        ctx->g, ctx->cb[ctx->cur], mask, ctx->amr_flag, bg ? bg : reinterpret_cast<uint8_t *>(ctx->amr_slot),
+        ctx->amr_ctr);
+    return launch_check(ctx, "refine_kernel");
+}
+
+int ebit_refine_mask(ebit_ctx *ctx, uint8_t *mask, int64_t *count) {
+    if (!ctx) return EBIT_EINVAL;
+    if (ctx->g.tl[0] != 3 || ctx->g.tl[1] != 3 || ctx->g.tl[2] != 3)
+        return fail(ctx, EBIT_EINVAL, "ebit_refine_mask: 8^3 tiles only");
+    if (int r = join_side(ctx)) return r;
+    if (int r = refine_pass(ctx, mask, nullptr)) return r;
+    if (count) {
+        unsigned long long n = 0;
+        CU(cudaMemcpyAsync(&n, ctx->amr_ctr, sizeof(n), cudaMemcpyDeviceToHost, ctx->stream));
+        CU(cudaStreamSynchronize(ctx->stream));
+        *count = (int64_t)n;
+    }
+    return EBIT_OK;
+}
+
+int ebit_pack_bricks(ebit_ctx *ctx, int capacity, int *tiles, uint8_t *cb, double *s, uint8_t *bg, int *nbricks) {
+    if (!ctx || !nbricks || capacity < 0) return fail(ctx, EBIT_EINVAL, "ebit_pack_bricks: bad argument");
+    if (capacity > 0 && (!tiles || !cb || !s || !bg)) return fail(ctx, EBIT_EINVAL, "ebit_pack_bricks: null array");
+    if (ctx->g.tl[0] != 3 || ctx->g.tl[1] != 3 || ctx->g.tl[2] != 3)
+        return fail(ctx, EBIT_EINVAL, "ebit_pack_bricks: 8^3 tiles only");
+    if (int r = join_side(ctx)) return r;
+    if (int r = refine_pass(ctx, nullptr, capacity > 0 ? bg : nullptr)) return r;
+    int *nb_dev = reinterpret_cast<int *>(ctx->amr_ctr + 1);
+    compact_tiles_kernel<<<1, 1024, 0, ctx->stream>>>(ctx->amr_flag, ctx->g.ntiles, tiles, capacity, nb_dev);
+    if (int r = launch_check(ctx, "compact_tiles_kernel")) return r;
+    int n = 0;
+    CU(cudaMemcpyAsync(&n, nb_dev, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+    CU(cudaStreamSynchronize(ctx->stream));
+    *nbricks = n;
+    if (capacity == 0) return EBIT_OK;
+    if (n > capacity) return fail(ctx, EBIT_EINVAL, "ebit_pack_bricks: capacity below the brick count");
+    if (n > 0) {
+        const int c = ctx->cur;
+        pack_kernel<<<std::min(n, 8 * ctx->sms), 256, 0, ctx->stream>>>(ctx->g, ctx->cb[c], ctx->s[c][0], ctx->s[c][1],
+                                                                        ctx->s[c][2], tiles, n, cb, s);
+        if (int r = launch_check(ctx, "pack_kernel")) return r;
+    }
+    return EBIT_OK;
+}
+
+int ebit_unpack_bricks(ebit_ctx *ctx, int nbricks, const int *tiles, const uint8_t *cb, const double *s,
+                       const uint8_t *bg) {
+    if (!ctx || nbricks < 0 || !bg || (nbricks > 0 && (!tiles || !cb || !s)))
+        return fail(ctx, EBIT_EINVAL, "ebit_unpack_bricks: bad argument");
+    if (!ctx->owns_state) return fail(ctx, EBIT_EINVAL, "ebit_unpack_bricks: a batch instance's state is the batch's");
+    if (int r = join_side(ctx)) return r;
+    if (int r = amr_scratch(ctx)) return r;
+    int *bad_dev = reinterpret_cast<int *>(ctx->amr_ctr + 1) + 1;
+    CU(cudaMemsetAsync(ctx->amr_slot, 0xFF, (size_t)ctx->g.ntiles * sizeof(int), ctx->stream));
+    CU(cudaMemsetAsync(bad_dev, 0, sizeof(int), ctx->stream));
+    if (nbricks > 0) {
+        brick_slots_kernel<<<blocks_for(nbricks, 256, ctx->sms), 256, 0, ctx->stream>>>(tiles, nbricks, ctx->g.ntiles,
+                                                                                        ctx->amr_slot, bad_dev);
+        if (int r = launch_check(ctx, "brick_slots_kernel")) return r;
+    }
+    int bad = 0;
+    CU(cudaMemcpyAsync(&bad, bad_dev, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+    CU(cudaStreamSynchronize(ctx->stream));
+    if (bad) return fail(ctx, EBIT_EINVAL, "ebit_unpack_bricks: tile id out of range");
+    const int c = ctx->cur;
+    unpack_kernel<<<std::min(ctx->g.ntiles, 8 * ctx->sms), 256, 0, ctx->stream>>>(
+        ctx->g, ctx->amr_slot, cb, s, bg, ctx->cb[c], ctx->s[c][0], ctx->s[c][1], ctx->s[c][2]);
+    if (int r = launch_check(ctx, "unpack_kernel")) return r;
+    if (int r = copy_other(ctx)) return r;
     return mark_all(ctx);
 }
 

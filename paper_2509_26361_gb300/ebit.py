@@ -118,6 +118,9 @@ def load(build_if_missing: bool = True):
     lib.ebit_batch_destroy.argtypes = [P]
     lib.ebit_selftest_bounded_waits.argtypes = [P, P]
     lib.ebit_selftest_f64_to_f32.argtypes = [P, P, I, P]
+    lib.ebit_refine_mask.argtypes = [P, P, ctypes.POINTER(ctypes.c_int64)]
+    lib.ebit_pack_bricks.argtypes = [P, I, P, P, P, P, ctypes.POINTER(ctypes.c_int)]
+    lib.ebit_unpack_bricks.argtypes = [P, I, P, P, P, P]
     lib.ebit_batch_destroy.restype = None
     lib.ebit_batch_size.argtypes = [P]
     lib.ebit_batch_instance.argtypes = [P, I]
@@ -687,6 +690,49 @@ class Grid:
     def load_mlp(self, params):
         """Parameters (float32, host or device) into a network the context owns."""
         return ebit_mlp_load(self.ctx, params)
+
+    @property
+    def tiles(self):
+        """Number of 8^3 tiles (bricks) of the grid."""
+        t = 1
+        for v in self.n3:
+            t *= (v + 7) // 8
+        return t
+
+    def refine_mask(self):
+        """(mask uint8 tensor of the grid's shape, count): the cells that the
+        AMR rule of Sec. 2.5 refines (3x3x3 around every interfacial cell)."""
+        mask = torch.empty(self.shape, dtype=torch.uint8, device=self.device)
+        n = ctypes.c_int64()
+        _check(self.ctx, load().ebit_refine_mask(self.ctx, _dev(mask, torch.uint8, self.N, "mask"), ctypes.byref(n)))
+        return mask, int(n.value)
+
+    def pack_bricks(self):
+        """The narrow-band brick store of the state: dict of device tensors
+        tiles [n] int32, cb [n, 512] uint8, s [n, 3, 512] float64, bg [tiles] uint8."""
+        lib = load()
+        n = ctypes.c_int()
+        _check(self.ctx, lib.ebit_pack_bricks(self.ctx, 0, None, None, None, None, ctypes.byref(n)))
+        cap = max(int(n.value), 1)
+        t = torch.empty(cap, dtype=torch.int32, device=self.device)
+        cb = torch.empty((cap, 512), dtype=torch.uint8, device=self.device)
+        s = torch.empty((cap, 3, 512), dtype=torch.float64, device=self.device)
+        bg = torch.empty(self.tiles, dtype=torch.uint8, device=self.device)
+        _check(self.ctx, lib.ebit_pack_bricks(self.ctx, cap, _dev(t, torch.int32), _dev(cb, torch.uint8),
+                                              _dev(s, torch.float64), _dev(bg, torch.uint8), ctypes.byref(n)))
+        k = int(n.value)
+        return {"tiles": t[:k], "cb": cb[:k], "s": s[:k], "bg": bg}
+
+    def unpack_bricks(self, store):
+        """Replace the state with the one a brick store describes."""
+        t, cb, s, bg = store["tiles"], store["cb"], store["s"], store["bg"]
+        k = int(t.numel())
+        if bg.numel() != self.tiles:
+            raise ValueError(f"bg must have {self.tiles} entries")
+        return _check(self.ctx, load().ebit_unpack_bricks(
+            self.ctx, k, _dev(t.contiguous(), torch.int32) if k else None,
+            _dev(cb.contiguous(), torch.uint8) if k else None, _dev(s.contiguous(), torch.float64) if k else None,
+            _dev(bg.contiguous(), torch.uint8)))
 
     def profile(self, enable=True):
         return ebit_profile(self.ctx, enable)
