@@ -553,6 +553,32 @@ class Run:
         return dict(learned.precision_error(self.mlp, X), note="kappa*h of the tensor-core pass against the same "
                     "network evaluated in FP64 without bf16 rounding, on the interface cells after the timed steps")
 
+    def brick_store(self):
+        """The AMR refinement rule (Sec. 2.5) and the narrow-band brick store
+        on the state after the timed steps: refined cells, bricks, stored bytes
+        against the dense state, and the time of each call (CUDA events)."""
+        import torch
+
+        E = lambda: torch.cuda.Event(enable_timing=True)
+        self.g.join()
+        e = [E() for _ in range(4)]
+        e[0].record()
+        _, nref = self.g.refine_mask()
+        e[1].record()
+        e[2].record()
+        st = self.g.pack_bricks()
+        e[3].record()
+        torch.cuda.synchronize()
+        nb = int(st["tiles"].numel())
+        stored = nb * 512 * 25 + self.g.tiles + nb * 4
+        dense = self.cells * 25
+        del st
+        return {"refined_cells": int(nref), "refined_frac": nref / self.cells, "bricks": nb, "tiles": self.g.tiles,
+                "stored_bytes": stored, "dense_bytes": dense, "ratio": stored / dense,
+                "refine_mask_ms": e[0].elapsed_time(e[1]), "pack_ms_incl_count": e[2].elapsed_time(e[3]),
+                "note": "bricks: the 8^3 tiles holding a cell the 3x3x3 rule refines; 25 B per cell stored "
+                        "(colour byte + three FP64 offsets), one byte per other tile"}
+
     def shape_error(self):
         """E_shape (Eq. 10) and E_mass (Eq. 9) over one period of a reversing
         field: the run from t = 0 for the workload's period, the fractions
@@ -790,6 +816,7 @@ def main():
         time.sleep(0.3)
     res = run.timed(args.warmup, args.steps, world)
     precision = run.precision() if rank == 0 else None
+    bricks = run.brick_store() if rank == 0 else None
     total_ms = max_over_ranks(res["total_ms"], world, dev)
     res_sync = run.timed_sync(args.warmup, args.steps, world)
     clk = clocks.summary(*res["wall"]) if rank == 0 else None
@@ -820,7 +847,7 @@ def main():
                              timing="CUDA events around the three split-sweep calls of each step of the ordered "
                                     "pass (the sweeps alone on the GPU, L2 flushed before every step)"),
             "e2e": e2e, "gpu_launches": launches,
-            "clocks": clk, "counters": res["cnt"], "learned_bf16_vs_fp64": precision}
+            "clocks": clk, "counters": res["cnt"], "learned_bf16_vs_fp64": precision, "brick_store": bricks}
     hbm, _ = peaks()
     cells = run.cells
     line["dense_equivalent"] = {
