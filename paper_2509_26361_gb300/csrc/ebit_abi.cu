@@ -907,7 +907,7 @@ int ebit_sync(ebit_ctx *ctx) {
     unsigned long long h[C_TOTAL];
     CU(cudaMemcpyAsync(h, ctx->ctr, sizeof(h), cudaMemcpyDeviceToHost, ctx->stream));
     CU(cudaStreamSynchronize(ctx->stream));
-    // a non-finite velocity is named before the CFL verdict it would also trip
+    // a non-finite velocity is reported before the CFL error it would also trip
     if (h[C_NONFINITE]) return fail(ctx, EBIT_ENONFINITE, "a marker's displacement was not finite (NaN or infinite velocity)");
     if (h[C_CFL]) return fail(ctx, EBIT_ECFL, "a marker moved a full cell or more in one sweep");
     return EBIT_OK;
