@@ -579,6 +579,38 @@ class Run:
                 "note": "bricks: the 8^3 tiles holding a cell the 3x3x3 rule refines; 25 B per cell stored "
                         "(colour byte + three FP64 offsets), one byte per other tile"}
 
+    def coupling(self, reps=5):
+        """The one-fluid coupling terms (Eq. 6 and the surface-tension force) on
+        the fractions and curvatures after the timed steps: CUDA events around
+        each call of a dense pass over the grid; HBM roofline by its
+        algorithmic bytes (C read, rho, mu and three force components
+        written: 48 B per cell, plus the status byte and kappa_h, 9 B, per
+        cell with a valid curvature).  The arrays (5.4 GB at 512^3) exceed L2."""
+        import torch
+
+        self.g.join()
+        out = (torch.empty(self.g.shape, dtype=torch.float64, device=self.dev),
+               torch.empty(self.g.shape, dtype=torch.float64, device=self.dev),
+               torch.empty((3,) + self.g.shape, dtype=torch.float64, device=self.dev))
+        args = dict(sigma=0.072, rho1=998.0, rho2=1.2, mu1=1.0e-3, mu2=1.8e-5)
+        E = lambda: torch.cuda.Event(enable_timing=True)
+        evs = [(E(), E()) for _ in range(reps)]
+        for a, b in evs:
+            a.record()
+            self.g.one_fluid(self.C, self.kh, self.st, out=out, **args)
+            b.record()
+        torch.cuda.synchronize()
+        ms = [a.elapsed_time(b) for a, b in evs[1:]]
+        valid = int(torch.isin(self.st, torch.tensor([1, 2, 3, 5], dtype=torch.uint8, device=self.dev)).sum())
+        alg = 48.0 * self.cells + 9.0 * valid
+        t = float(np.mean(ms)) * 1e-3
+        hbm, src = peaks()
+        del out
+        return {"kernel": "coupling_kernel", "ms": float(np.mean(ms)), "cells": self.cells, "valid_curvature_cells": valid,
+                "roofline": {"bound": "hbm", "achieved": alg / t / 1e9, "peak": hbm, "unit": "GB/s",
+                             "frac": alg / t / 1e9 / hbm, "peak_source": src, "alg_bytes_per_launch": alg,
+                             "alg_bytes_rule": "48 B per cell + 9 B per cell with a valid curvature"}}
+
     def shape_error(self):
         """E_shape (Eq. 10) and E_mass (Eq. 9) over one period of a reversing
         field: the run from t = 0 for the workload's period, the fractions
@@ -817,6 +849,7 @@ def main():
     res = run.timed(args.warmup, args.steps, world)
     precision = run.precision() if rank == 0 else None
     bricks = run.brick_store() if rank == 0 else None
+    coupling = run.coupling() if rank == 0 else None
     total_ms = max_over_ranks(res["total_ms"], world, dev)
     res_sync = run.timed_sync(args.warmup, args.steps, world)
     clk = clocks.summary(*res["wall"]) if rank == 0 else None
@@ -847,7 +880,8 @@ def main():
                              timing="CUDA events around the three split-sweep calls of each step of the ordered "
                                     "pass (the sweeps alone on the GPU, L2 flushed before every step)"),
             "e2e": e2e, "gpu_launches": launches,
-            "clocks": clk, "counters": res["cnt"], "learned_bf16_vs_fp64": precision, "brick_store": bricks}
+            "clocks": clk, "counters": res["cnt"], "learned_bf16_vs_fp64": precision, "brick_store": bricks,
+            "one_fluid_coupling": coupling}
     hbm, _ = peaks()
     cells = run.cells
     line["dense_equivalent"] = {

@@ -253,7 +253,8 @@ enum {
     EBIT_PROF_ADVECT = 5, /* marker advection (velocity interpolation) kernels */
     EBIT_PROF_FP64 = 6,   /* sweep work lists: circle fits and face-centre colours */
     EBIT_PROF_SCAN = 7,   /* full interface-cell scan of ebit_curvature (EBIT_FULL or foreign C) */
-    EBIT_PROF_KINDS = 8
+    EBIT_PROF_COUPLING = 8, /* one-fluid properties and surface-tension force (ebit_one_fluid) */
+    EBIT_PROF_KINDS = 9
 };
 /* enable != 0 switches timing on and zeroes the sums; 0 switches it off. */
 int ebit_profile(ebit_ctx *ctx, int enable);
@@ -426,6 +427,28 @@ const char *ebit_batch_last_error(const ebit_batch *b);
  * EBIT_ETIMEOUT otherwise, EBIT_ENOMEM / EBIT_ECUDA if its 64-byte buffer
  * cannot be allocated or a launch or copy fails. */
 int ebit_selftest_bounded_waits(void *cuda_stream, int *report);
+
+/* One-fluid coupling terms (Sec. 2.5): what a Navier-Stokes solver in the
+ * one-fluid formulation takes from the interface.
+ *   rho [N], mu [N] (device, may be NULL): Eq. 6 with the Heaviside function of
+ *     the reference phase taken as C: rho = C rho1 + (1 - C) rho2, and mu
+ *     likewise, per cell.
+ *   force [3N] (device, family-major, may be NULL): the surface-tension term
+ *     sigma kappa n delta_S as a well-balanced continuum surface force on the
+ *     MAC faces.  force[a][idx], on the a-face of cell idx (between cells
+ *     idx - e_a and idx, where u_a lives), is sigma kappa_f (C[idx] -
+ *     C[idx - e_a]) / h, with kappa = kappa_h / h on cells whose status is
+ *     EBIT_ST_HF_X/Y/Z or EBIT_ST_MLP, and kappa_f the mean of the face's two
+ *     cells' values, the one valid value, or 0.  A uniform kappa_f makes the
+ *     force the exact discrete gradient of sigma kappa_f C: a pressure of that
+ *     form balances it.
+ *   C [N] (device) the fractions; kappa_h [N], status [N] (device) the output
+ *     of ebit_curvature, needed for force only.
+ * Runs on the context's stream after any EBIT_ASYNC work.  EBIT_EINVAL for a
+ * null C (or null curvature arrays with force), EBIT_ENONFINITE for a
+ * non-finite coefficient. */
+int ebit_one_fluid(ebit_ctx *ctx, const double *C, const double *kappa_h, const uint8_t *status, double sigma,
+                   double rho1, double rho2, double mu1, double mu2, double *rho, double *mu, double *force);
 
 /* AMR refinement rule and narrow-band brick store (Sec. 2.5).  With one marker
  * per edge, two refinement levels must never share the interface, so every

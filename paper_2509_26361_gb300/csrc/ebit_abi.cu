@@ -24,6 +24,7 @@
 #include "state.cuh"
 #include "sweep.cuh"
 #include "amr.cuh"
+#include "coupling.cuh"
 
 using namespace ebit;
 
@@ -582,6 +583,33 @@ int ebit_unpack_bricks(ebit_ctx *ctx, int nbricks, const int *tiles, const uint8
     if (int r = launch_check(ctx, "unpack_kernel")) return r;
     if (int r = copy_other(ctx)) return r;
     return mark_all(ctx);
+}
+
+int ebit_one_fluid(ebit_ctx *ctx, const double *C, const double *kappa_h, const uint8_t *status, double sigma,
+                   double rho1, double rho2, double mu1, double mu2, double *rho, double *mu, double *force) {
+    if (!ctx || !C || (force && (!kappa_h || !status))) return fail(ctx, EBIT_EINVAL, "ebit_one_fluid: null argument");
+    if (!std::isfinite(sigma) || !std::isfinite(rho1) || !std::isfinite(rho2) || !std::isfinite(mu1) ||
+        !std::isfinite(mu2))
+        return fail(ctx, EBIT_ENONFINITE, "ebit_one_fluid: non-finite coefficient");
+    if (int r = join_side(ctx)) return r;
+    CouplingArgs a;
+    a.g = ctx->g;
+    a.C = C;
+    a.kh = kappa_h;
+    a.st = status;
+    a.sigma = sigma;
+    a.rho1 = rho1;
+    a.rho2 = rho2;
+    a.mu1 = mu1;
+    a.mu2 = mu2;
+    a.h = ctx->h;
+    a.rho = rho;
+    a.mu = mu;
+    for (int d = 0; d < 3; d++) a.f[d] = force ? force + d * ctx->N : nullptr;
+    if (!rho && !mu && !force) return EBIT_OK;
+    ProfScope ps(ctx, EBIT_PROF_COUPLING, ctx->stream);
+    coupling_kernel<<<std::min(ctx->g.n[1] * ctx->g.n[2], 8 * ctx->sms), 256, 0, ctx->stream>>>(a);
+    return launch_check(ctx, "coupling_kernel");
 }
 
 int ebit_get_state(ebit_ctx *ctx, uint8_t *cb, double *s) {

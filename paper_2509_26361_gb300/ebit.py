@@ -119,6 +119,7 @@ def load(build_if_missing: bool = True):
     lib.ebit_selftest_bounded_waits.argtypes = [P, P]
     lib.ebit_selftest_f64_to_f32.argtypes = [P, P, I, P]
     lib.ebit_refine_mask.argtypes = [P, P, ctypes.POINTER(ctypes.c_int64)]
+    lib.ebit_one_fluid.argtypes = [P, P, P, P, D, D, D, D, D, P, P, P]
     lib.ebit_pack_bricks.argtypes = [P, I, P, P, P, P, ctypes.POINTER(ctypes.c_int)]
     lib.ebit_unpack_bricks.argtypes = [P, I, P, P, P, P]
     lib.ebit_batch_destroy.restype = None
@@ -277,7 +278,7 @@ def ebit_band_tiles(ctx):
     return int(load().ebit_band_tiles(ctx))
 
 
-PROF_KINDS = ("sweep", "band", "f2v", "hf", "mlp", "advect", "fp64", "scan")
+PROF_KINDS = ("sweep", "band", "f2v", "hf", "mlp", "advect", "fp64", "scan", "coupling")
 
 
 def ebit_profile(ctx, enable):
@@ -285,8 +286,8 @@ def ebit_profile(ctx, enable):
 
 
 def ebit_profile_read(ctx):
-    ms = (ctypes.c_double * 8)()
-    n = (ctypes.c_int64 * 8)()
+    ms = (ctypes.c_double * len(PROF_KINDS))()
+    n = (ctypes.c_int64 * len(PROF_KINDS))()
     _check(ctx, load().ebit_profile_read(ctx, ms, n))
     return {k: (float(ms[i]), int(n[i])) for i, k in enumerate(PROF_KINDS) if n[i]}
 
@@ -698,6 +699,24 @@ class Grid:
         for v in self.n3:
             t *= (v + 7) // 8
         return t
+
+    def one_fluid(self, C, kh=None, st=None, sigma=0.0, rho1=1.0, rho2=1.0, mu1=1.0, mu2=1.0, force=True, out=None):
+        """Eq. 6 properties (rho, mu per cell) and, with force, the face-centred
+        well-balanced surface-tension force [3, nz, ny, nx] from C and the
+        curvature output (kh, st); out = (rho, mu, f) reuses buffers."""
+        if out is not None:
+            rho, mu, f = out
+        else:
+            rho = torch.empty(self.shape, dtype=torch.float64, device=self.device)
+            mu = torch.empty_like(rho)
+            f = torch.empty((3,) + self.shape, dtype=torch.float64, device=self.device) if force else None
+        _check(self.ctx, load().ebit_one_fluid(
+            self.ctx, _dev(C, torch.float64, self.N, "C"),
+            _dev(kh, torch.float64, self.N, "kh") if force else None,
+            _dev(st, torch.uint8, self.N, "st") if force else None,
+            float(sigma), float(rho1), float(rho2), float(mu1), float(mu2),
+            _dev(rho, torch.float64), _dev(mu, torch.float64), _dev(f, torch.float64) if force else None))
+        return rho, mu, f
 
     def refine_mask(self):
         """(mask uint8 tensor of the grid's shape, count): the cells that the

@@ -41,3 +41,15 @@ def test_binding_fails_loudly_without_gpu():
 
     with pytest.raises(Exception):
         ebit.Grid(16, 16, 16)
+
+
+def test_profile_kinds_match_the_header():
+    """The binding's list of profiling kinds sizes the arrays that
+    ebit_profile_read fills: it must have EBIT_PROF_KINDS entries."""
+    import os
+
+    from paper_2509_26361_gb300 import ebit
+
+    src = open(os.path.join(ROOT, "include", "ebit.h")).read()
+    m = re.search(r"EBIT_PROF_KINDS\s*=\s*(\d+)", src)
+    assert m and int(m.group(1)) == len(ebit.PROF_KINDS)
