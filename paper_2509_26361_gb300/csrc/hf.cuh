@@ -66,7 +66,7 @@ __device__ __forceinline__ bool hf_axis(const CAccess<WRAP> &c, int d, bool belo
     e2[t2] = 1;
     double eta[3][3];
     bool ok = true;
-#pragma unroll
+#pragma unroll 1
     for (int b2 = -1; b2 <= 1; b2++)
 #pragma unroll
         for (int b1 = -1; b1 <= 1; b1++) {
@@ -216,8 +216,11 @@ __device__ __noinline__ int hf_cell(const HFArgs &a, int x, int y, int z, double
 // complete; one thread per entry, full warps for the FP64 work.  Without
 // COMPUTE the interface cells are only listed (the learned curvature writes
 // them next).
+// 4 blocks of 128 per SM: with the outer column loop kept rolled the kernel
+// fits 127 registers without spilling, where the fully unrolled one took 226
+// (2 blocks per SM) to keep all 81 column loads in flight
 template <bool COMPUTE>
-__global__ void __launch_bounds__(128) hf_list_kernel(HFArgs a) {
+__global__ void __launch_bounds__(128, 4) hf_list_kernel(HFArgs a) {
     pdl_wait();
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         if (a.zero[0]) *a.zero[0] = 0;
