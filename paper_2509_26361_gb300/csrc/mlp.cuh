@@ -559,11 +559,15 @@ __global__ void __launch_bounds__(128, 3) mlp_fwd_kernel(MlpArgs a) {
 // shared tiles (8x8 core matrices of 128 bytes, see tc.cuh) into the group's
 // TMEM columns, which both layers reuse; thread t of the group owns row t (TMEM
 // lane t), read back with tcgen05.ld by its warp.  Groups synchronise on their
-// own named barrier.
-// smem (1024-aligned): W1 16 KB | W2 32 KB | per group: X 16 KB, H1 32 KB (also
-// the gather's staging) | mbarriers | TMEM base | fragment flags | wait flags
-constexpr int TC_GROUPS = 3;
-constexpr int TCF_W1 = 0, TCF_W2 = 16384, TCF_G0 = 49152, TCF_GSTRIDE = 49152;
+// own named barrier.  Four groups use all 512 TMEM columns and the block's
+// 65 536 registers (128 per thread): the X tile is dead once layer 1's MMAs
+// have completed, so the group's H1 tile overlays it (32 KB per group instead
+// of 48), which fits four groups' tiles in shared memory.
+// smem (1024-aligned): W1 16 KB | W2 32 KB | per group: X 16 KB, then H1 32 KB
+// in the same place | mbarriers | TMEM base | fragment flags | wait flags |
+// b1 | b2 | w3 | b3
+constexpr int TC_GROUPS = 4;
+constexpr int TCF_W1 = 0, TCF_W2 = 16384, TCF_G0 = 49152, TCF_GSTRIDE = 32768;
 constexpr int TCF_MBAR = TCF_G0 + TC_GROUPS * TCF_GSTRIDE;          // 8 B per group
 constexpr int TCF_TB = TCF_MBAR + 8 * TC_GROUPS;
 constexpr int TCF_FRAG = TCF_TB + 16;                                // 128 B per group
@@ -591,7 +595,9 @@ __global__ void __launch_bounds__(TC_THREADS) mlp_fwd_tc_kernel(MlpArgs a) {
     unsigned char *base = (unsigned char *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     const int tid = threadIdx.x, grp = tid >> 7, t = tid & 127, wq = (tid >> 5) & 3;
     unsigned char *sW1 = base + TCF_W1, *sW2 = base + TCF_W2;
-    unsigned char *sX = base + TCF_G0 + grp * TCF_GSTRIDE, *sH1 = sX + 16384;
+    // H1 is written by layer 1's epilogue after its MMAs completed (X read) and
+    // read by layer 2's MMAs, which complete before the next tile's gather
+    unsigned char *sX = base + TCF_G0 + grp * TCF_GSTRIDE, *sH1 = sX;
     uint64_t *mbar = reinterpret_cast<uint64_t *>(base + TCF_MBAR) + grp;
     uint32_t *tbase = reinterpret_cast<uint32_t *>(base + TCF_TB);
     uint8_t *sFrag = base + TCF_FRAG + 128 * grp;
@@ -634,7 +640,6 @@ __global__ void __launch_bounds__(TC_THREADS) mlp_fwd_tc_kernel(MlpArgs a) {
             if (GATHER && live) {
                 cell = a.cells[row];
                 const int x = cell % a.g.n[0], y = (cell / a.g.n[0]) % a.g.n[1], z = cell / (a.g.n[0] * a.g.n[1]);
-                // the block values are staged in the group's H1 tile (free until layer 1)
                 sFrag[t] = canon_encode(a.C, a.g, x, y, z, v) ? 1 : 0;
             } else if (!GATHER && live) {
                 const uint4 *s4 = reinterpret_cast<const uint4 *>(a.X + (long long)row * MLP_IN);
