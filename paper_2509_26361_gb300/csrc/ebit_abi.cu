@@ -1029,7 +1029,7 @@ int ebit_mlp_create(void *cuda_stream, ebit_mlp **out) {
     bool ok = dev_alloc(mm, (void **)&mlp->p, MLP_NP * 4) && dev_alloc(mm, (void **)&mlp->g, MLP_NP * 4) &&
               dev_alloc(mm, (void **)&mlp->m, MLP_NP * 4) && dev_alloc(mm, (void **)&mlp->v, MLP_NP * 4) &&
               dev_alloc(mm, (void **)&mlp->w1b, MLP_H * MLP_IN * 2) &&
-              dev_alloc(mm, (void **)&mlp->w2b, MLP_H * MLP_H * 2) && dev_alloc(mm, (void **)&mlp->loss, 4) &&
+              dev_alloc(mm, (void **)&mlp->w2b, MLP_H * MLP_H * 2) && dev_alloc(mm, (void **)&mlp->loss, 8) &&
               dev_alloc(mm, (void **)&mlp->err, 4);
     if (!ok) {
         cudaGetLastError();
@@ -1060,6 +1060,7 @@ int ebit_mlp_create(void *cuda_stream, ebit_mlp **out) {
     mlp->fwd_tc_blocks = 1;
     mlp->path = EBIT_MLP_PATH_TCGEN05;
     cudaMemsetAsync(mlp->err, 0, sizeof(int), mlp->stream);
+    cudaMemsetAsync(mlp->loss, 0, 8, mlp->stream);  // a training step starts from a cleared loss
     cudaMemsetAsync(mlp->p, 0, MLP_NP * 4, mlp->stream);
     cudaMemsetAsync(mlp->g, 0, MLP_NP * 4, mlp->stream);
     cudaMemsetAsync(mlp->m, 0, MLP_NP * 4, mlp->stream);
@@ -1151,8 +1152,9 @@ int ebit_mlp_forward(ebit_mlp *mlp, const uint16_t *X, int m, float *y) {
     return EBIT_OK;
 }
 
+// mlp->loss[0] is 0 on entry: cleared at creation, by the Adam kernel of each
+// training step and at the end of ebit_mlp_gradient
 static int mlp_grad_launch(ebit_mlp *mlp, const uint16_t *X, const float *t, const int *idx, int batch) {
-    MCU(cudaMemsetAsync(mlp->loss, 0, 4, mlp->stream));
     MlpArgs a{};
     a.X = reinterpret_cast<const __nv_bfloat16 *>(X);
     a.t = t;
@@ -1176,6 +1178,7 @@ int ebit_mlp_gradient(ebit_mlp *mlp, const uint16_t *X, const float *t, int batc
     if (r) return r;
     MCU(cudaMemcpyAsync(grad_out, mlp->g, MLP_NP * 4, cudaMemcpyDefault, mlp->stream));
     MCU(cudaMemsetAsync(mlp->g, 0, MLP_NP * 4, mlp->stream));
+    MCU(cudaMemsetAsync(mlp->loss, 0, 4, mlp->stream));
     return EBIT_OK;
 }
 
@@ -1186,10 +1189,20 @@ int ebit_mlp_train_step(ebit_mlp *mlp, const uint16_t *X, const float *t, const 
     if (r) return r;
     mlp->step++;
     const float bc1 = 1.0f - powf(0.9f, (float)mlp->step), bc2 = 1.0f - powf(0.999f, (float)mlp->step);
+    // a device loss_out is written by the Adam kernel itself; a host one is
+    // copied from the second loss slot after it
+    bool dev_out = false;
+    if (loss_out) {
+        cudaPointerAttributes pa;
+        if (cudaPointerGetAttributes(&pa, loss_out) == cudaSuccess)
+            dev_out = pa.type == cudaMemoryTypeDevice || pa.type == cudaMemoryTypeManaged;
+        cudaGetLastError();
+    }
+    float *dst = loss_out ? (dev_out ? loss_out : mlp->loss + 1) : nullptr;
     mlp_adam_kernel<<<(MLP_NP + 255) / 256, 256, 0, mlp->stream>>>(mlp->p, mlp->g, mlp->m, mlp->v, mlp->w1b, mlp->w2b,
-                                                                  lr, bc1, bc2);
+                                                                  lr, bc1, bc2, mlp->loss, dst);
     MCU(cudaGetLastError());
-    if (loss_out) MCU(cudaMemcpyAsync(loss_out, mlp->loss, 4, cudaMemcpyDefault, mlp->stream));
+    if (loss_out && !dev_out) MCU(cudaMemcpyAsync(loss_out, mlp->loss + 1, 4, cudaMemcpyDefault, mlp->stream));
     return EBIT_OK;
 }
 

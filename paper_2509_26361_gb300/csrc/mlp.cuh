@@ -1008,11 +1008,17 @@ __global__ void __launch_bounds__(TRAIN_THREADS) mlp_train_kernel(MlpArgs a) {
     }
 }
 
-// Adam on the FP32 master parameters, bf16 copies of W1 and W2, gradient reset
+// Adam on the FP32 master parameters, bf16 copies of W1 and W2, gradient reset;
+// the batch loss handed to loss_dst (may be null) and cleared for the next
+// step, which saves the step a memset and a copy on the stream
 __global__ void mlp_adam_kernel(float *__restrict__ p, float *__restrict__ g, float *__restrict__ m,
                                 float *__restrict__ v, __nv_bfloat16 *__restrict__ w1b, __nv_bfloat16 *__restrict__ w2b,
-                                float lr, float bc1, float bc2) {
+                                float lr, float bc1, float bc2, float *__restrict__ loss, float *__restrict__ loss_dst) {
     const float b1 = 0.9f, b2 = 0.999f, eps = 1e-8f;
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        if (loss_dst) *loss_dst = *loss;
+        *loss = 0.0f;
+    }
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < MLP_NP; i += gridDim.x * blockDim.x) {
         const float gi = g[i];
         const float mi = b1 * m[i] + (1.0f - b1) * gi;

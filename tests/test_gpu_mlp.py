@@ -244,3 +244,48 @@ def test_tensor_paths_agree_on_the_curvature_field():
     assert np.max(np.abs(out[0][0] - out[1][0])) <= 1e-5
     g.close()
     m.close()
+
+
+def test_training_step_is_the_gradient_then_adam_and_reports_each_batch_loss():
+    """One training step equals the library's gradient followed by Adam written
+    out on the host (FP32, the kernel's order of operations), and each step
+    reports the loss of its own batch at the parameters it started from: the
+    device-pointer and host-pointer paths, two steps in a row (the loss is
+    cleared between steps)."""
+    rng = np.random.default_rng(21)
+    p0 = (omlp.init_params(6) + rng.normal(scale=0.02, size=omlp.N_PARAMS)).astype(np.float32)
+    B, lr = 640, 1e-3
+    X = _random_inputs(B, rng)
+    t = rng.uniform(0.05, 0.8, size=B).astype(np.float32)
+    Xd, td = dev(X).to(torch.bfloat16), dev(t)
+    m = ebit.Mlp(p0.astype(np.float64))
+    g = m.gradient(Xd, td).cpu().numpy().astype(np.float32)
+    loss = torch.zeros(1, dtype=torch.float32, device="cuda")
+    m.train_step(Xd, td, lr, loss)
+    m.sync()
+    p1 = m.get_params().cpu().numpy().astype(np.float32)
+    # Adam step 1 in float32 (m0 = v0 = 0)
+    b1, b2, eps = np.float32(0.9), np.float32(0.999), np.float32(1e-8)
+    mh = np.float32(1.0 - b1) * g
+    vh = np.float32(1.0 - b2) * g * g
+    bc1, bc2 = np.float32(1.0) - b1, np.float32(1.0) - b2
+    ph = p0 - np.float32(lr) * (mh / bc1) / (np.sqrt(vh / bc2) + eps)
+    # where the gradient is not tiny the step does not depend on the order of
+    # the FP32 gradient sums of the two launches; elsewhere it is at most lr
+    big = np.abs(g) > 1e-3 * np.abs(g).max()
+    assert big.sum() > 0.3 * big.size
+    assert np.max(np.abs(p1 - ph)[big]) <= 1e-6, np.max(np.abs(p1 - ph)[big])
+    assert np.max(np.abs(p1 - p0)) <= 1.001 * lr
+    Xh = bf16_bits_to_f64(Xd)
+    l0, _ = omlp.loss_and_grad(p0.astype(np.float64), Xh, t.astype(np.float64), emulate=True)
+    assert abs(loss.item() / B - l0) <= 2e-2 * l0, (loss.item() / B, l0)
+    # second step, loss into host memory through the C ABI
+    cf = ctypes.c_float(-1.0)
+    P = lambda x: ctypes.c_void_p(x.data_ptr())
+    rc = ebit.load().ebit_mlp_train_step(m.h, P(Xd), P(td), None, B, ctypes.c_float(lr),
+                                          ctypes.c_void_p(ctypes.addressof(cf)))
+    assert rc == 0
+    m.sync()
+    l1, _ = omlp.loss_and_grad(p1.astype(np.float64), Xh, t.astype(np.float64), emulate=True)
+    assert abs(cf.value / B - l1) <= 2e-2 * l1, (cf.value / B, l1, l0)
+    m.close()
